@@ -1,0 +1,226 @@
+/*
+ * ucac.h -- C ABI of the B300 (sm_103a) library for the inner sweep of the
+ * two-level component ADMM for unit commitment with AC optimal power flow
+ * (Zhang, Kim, Kim, "On Solving Unit Commitment with AC Optimal Power Flow on
+ * GPU").
+ *
+ * One handle holds one or more independent UC-ACOPF instances on one GPU.
+ * Every step of a sweep runs in the library's CUDA kernels:
+ *   x-step      UC dynamic program per generator (Algorithm 2), generator and
+ *               line subproblems per (period, component) (Eq. step:uc,
+ *               step:opf);
+ *   x-bar-step  duplicate-UC box QPs and bus power-balance projections
+ *               (Eq. step:uc_bar, step:opf_bar), fused with the z and y
+ *               updates (Eq. step:z, step:y) and the residual partial sums;
+ *   finish      per-instance deterministic residual reduction, inner stop
+ *               test and outer lambda/beta update (Eq. step:outer,
+ *               Algorithm 1).
+ *
+ * Conventions for every entry point:
+ *   - Arrays are plain C arrays, 0-based, row-major, FP64 unless noted.
+ *   - Host pointers are read during the call and not retained; device memory
+ *     is owned by the handle and released by ucac_destroy.
+ *   - Return value 0 = success, 1 = success and every instance converged,
+ *     negative = error (UCAC_E_*); no exception crosses the ABI.  After an
+ *     error ucac_last_error() gives a one-line reason.
+ *   - A handle is not thread-safe; all device work is issued on the CUDA
+ *     stream given at creation (NULL = the legacy default stream).
+ */
+#ifndef UCAC_H
+#define UCAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define UCAC_OK 0
+#define UCAC_CONVERGED 1
+#define UCAC_E_ARG (-1)          /* bad argument (NULL pointer, size, index) */
+#define UCAC_E_GRID (-2)         /* invalid grid data (disconnected, r=x=0, bounds out of order, ...) */
+#define UCAC_E_CUDA (-3)         /* a CUDA runtime call failed */
+#define UCAC_E_NEWTON_MAXIT (-4) /* reported in ucac_residuals.status only */
+#define UCAC_E_NAN (-5)          /* a residual became NaN or Inf */
+#define UCAC_E_DIVERGED (-6)     /* reported in ucac_residuals.status only */
+
+/*
+ * Instance data (Sec. II: variables, Eq. acopf, Eq. set:UC, Eq. coupling).
+ * Per-unit quantities on base_mva; costs in $ with c2 in $/MW^2h, c1 in $/MWh,
+ * c0 in $/h while on, c_su / c_sd in $ per start-up / shut-down.
+ * Layouts: Pd, Qd are [T][n_bus]; bus arrays [n_bus]; branch arrays
+ * [n_branch]; generator arrays [n_gen].  br_b is the total line charging.
+ * TU/TD are the minimum up/down times in periods, u0 the status in period 0,
+ * L0/F0 the number of initial periods forced on/off (Eq. uc_initial_on/off),
+ * p0 the output in period 0.  Branches have no taps or phase shifters.
+ */
+typedef struct ucac_grid {
+  int32_t n_bus, n_branch, n_gen, T, ref_bus;
+  const double *Pd, *Qd;
+  const double *Gs, *Bs, *Vmin, *Vmax;
+  const int32_t *br_from, *br_to;
+  const double *br_r, *br_x, *br_b, *br_rate;
+  const int32_t *gen_bus;
+  const double *Pmin, *Pmax, *Qmin, *Qmax, *c2, *c1, *c0, *c_su, *c_sd, *RU, *RD, *SU, *SD;
+  const int32_t *TU, *TD, *u0, *L0, *F0;
+  const double *p0;
+  double base_mva;
+} ucac_grid;
+
+/* Penalties for the power rows, the voltage/angle rows and the UC rows (Sec. IV-A). */
+typedef struct ucac_rho {
+  double pq, va, uc;
+} ucac_rho;
+
+/*
+ * Algorithm parameters.  eps_in: inner stop on the RMS primal and dual
+ * residuals; eps_out: outer stop on the RMS of z; tau, theta: outer beta rule
+ * (Eq. step:outer, tau = 6, theta = 0.8); beta0: initial beta; lambda_max:
+ * bound of the projection of lambda; eta: line-subproblem equality tolerance
+ * (inf-norm); omega_rel: line-subproblem stationarity tolerance relative to
+ * max(rho.pq, rho.va); c_init_rel / c_max_rel: initial / largest
+ * augmented-Lagrangian penalty of the line subproblem, relative to
+ * max(rho.pq, rho.va); K_AL / K_N: iteration caps of the line subproblem's
+ * multiplier and Newton loops; L_max: cap on inner sweeps per outer
+ * iteration; check_every: sweeps between host convergence checks in
+ * ucac_iterate.
+ */
+typedef struct ucac_params {
+  double eps_in, eps_out, tau, theta, beta0, lambda_max;
+  double eta, omega_rel, c_init_rel, c_max_rel;
+  int32_t K_AL, K_N, L_max, check_every;
+} ucac_params;
+
+/*
+ * Residual record of one instance after the last sweep.
+ * r_p = |Ax + Bxbar + z|_2 / sqrt(m), r_d = |B(xbar_new - xbar_old)|_2 / sqrt(m)
+ * (m = number of coupling rows), z_norm = |z|_2, z_rms = z_norm / sqrt(m),
+ * inf_norm_viol = |Ax + Bxbar|_inf (the primal infeasibility of Sec. IV-C),
+ * objective = sum of generation, no-load, start-up and shut-down costs at the
+ * current x.  newton / al = line-subproblem Newton / multiplier iterations in
+ * the last sweep; n_newton_maxit = line subproblems that stopped on a cap.
+ * status: 0 running, 1 converged, or a negative UCAC_E_* code.
+ */
+typedef struct ucac_report {
+  double r_p, r_d, z_norm, z_rms, inf_norm_viol, objective, beta;
+  int64_t sweeps, outer, newton, al;
+  int32_t status, n_newton_maxit;
+} ucac_report;
+
+typedef struct ucac_handle ucac_handle;
+
+/* Fills *p with the defaults listed above. */
+void ucac_default_params(ucac_params *p);
+
+/*
+ * Creates a handle for one instance and applies the cold start of Sec. IV-A
+ * (p, q and |V| at the middle of their bounds, angles zero, flows from the
+ * initial voltages) with all units on.  horizon (1 <= horizon <= grid->T)
+ * selects the first periods of Pd/Qd.  params may be NULL (defaults).
+ * stream is a cudaStream_t or NULL.  Errors: UCAC_E_ARG, UCAC_E_GRID,
+ * UCAC_E_CUDA; *out is NULL then.
+ */
+int ucac_create(const ucac_grid *grid, int32_t horizon, ucac_rho rho, const ucac_params *params,
+                void *cuda_stream, ucac_handle **out);
+
+/*
+ * Same for n independent instances sharing one set of launches (batching);
+ * horizons[k] and rhos[k] belong to grids[k].
+ */
+int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, const ucac_rho *rhos, int32_t n,
+                      const ucac_params *params, void *cuda_stream, ucac_handle **out);
+
+/* Number of instances in the handle. */
+int32_t ucac_instances(const ucac_handle *h);
+
+/*
+ * Runs up to n_sweeps inner sweeps (Algorithm 1 inner loop body, with outer
+ * updates applied when an instance's inner loop stops), checking on the host
+ * every params.check_every sweeps whether every instance has converged
+ * (inner residuals <= eps_in and z_rms <= eps_out).  Synchronises the
+ * stream.  Returns 1 when all instances have converged, 0 otherwise.
+ */
+int ucac_iterate(ucac_handle *h, int32_t n_sweeps);
+
+/*
+ * Enqueues exactly n_sweeps sweeps on the handle's stream (one CUDA-graph
+ * launch per sweep) and returns without synchronising or checking
+ * convergence.  For timing loops.
+ */
+int ucac_enqueue_sweeps(ucac_handle *h, int32_t n_sweeps);
+
+/* Copies instance `instance`'s residual record to *out (synchronises). */
+int ucac_residuals(const ucac_handle *h, int32_t instance, ucac_report *out);
+
+/*
+ * Copies the solution of one instance into caller host buffers (any may be
+ * NULL): p, q [T][n_gen] (generator x-side), w, theta [T][n_bus] (bus copies),
+ * pf [T][n_branch][4] (p_ij, q_ij, p_ji, q_ji from the line subproblems),
+ * u_on [T][n_gen] (0/1 from the UC dynamic program).
+ */
+int ucac_solution(const ucac_handle *h, int32_t instance, double *p, double *q, double *w, double *theta,
+                  double *pf, uint8_t *u_on);
+
+/*
+ * Full iterate of one instance in a fixed canonical order of FP64 arrays
+ * (all [T][n] with n the component count):
+ *   17 generator fields  p q phat s_pl s_pu s_ql s_qu s_rd s_ru u_on u_su u_sd
+ *                        pbar qbar ubar_on ubar_su ubar_sd
+ *   y, z, lambda of the 12 generator rows  on su sd pl pu ql qu rd ru gp gq tc
+ *   17 line fields       v0..v7 (w_i w_j wR wI theta_i theta_j sigma_ij
+ *                        sigma_ji) mu0..mu3 c fbar0..fbar3
+ *   y, z, lambda of the 8 line rows  p_ij q_ij p_ji q_ji w_i w_j th_i th_j
+ *   2 bus fields         wbar thetabar
+ *   7 scalars            beta, |z| at the last outer update (-1 if none),
+ *                        inner sweep count, outer count, pending-outer flag,
+ *                        next beta, converged flag.
+ * ucac_state_size gives the number of doubles.  Export then import restores
+ * the iterate bit for bit (resume / checkpoint).
+ */
+size_t ucac_state_size(const ucac_handle *h, int32_t instance);
+int ucac_state_export(const ucac_handle *h, int32_t instance, double *buf, size_t n_doubles);
+int ucac_state_import(ucac_handle *h, int32_t instance, const double *buf, size_t n_doubles);
+
+/*
+ * Average device time per sweep of each kernel over n_sweeps sweeps, timed
+ * with CUDA events on the handle's stream (kernels launched one by one, not
+ * from the graph).  ms[] receives UCAC_N_KERNELS values in the order of
+ * ucac_kernel_name().  Synchronises.
+ */
+#define UCAC_N_KERNELS 6
+int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms);
+const char *ucac_kernel_name(int32_t k);
+
+/*
+ * Standalone UC dynamic program (Algorithm 2) for n_gen generators over T
+ * periods, on DEVICE arrays.  tau_on/tau_su/tau_sd [T][n_gen] are the targets
+ * ubar - z - y/rho of the duplicate rows; c0, c_su, c_sd [n_gen]; TU, TD, u0,
+ * K0 [n_gen] (K0 = forced initial periods).  Writes u_on [T][n_gen] (int8
+ * 0/1) and cost [n_gen] (the optimal DP cost c_{1,u0}).  workspace is a device
+ * buffer of at least ucac_ucdp_workspace_bytes(n_gen, T) bytes owned by the
+ * caller.  Enqueued on cuda_stream; returns without synchronising.
+ */
+size_t ucac_ucdp_workspace_bytes(int32_t n_gen, int32_t T);
+int ucac_ucdp(int32_t n_gen, int32_t T, double rho_uc, const double *tau_on, const double *tau_su,
+              const double *tau_sd, const double *c0, const double *c_su, const double *c_sd, const int32_t *TU,
+              const int32_t *TD, const int32_t *u0, const int32_t *K0, int8_t *u_on, double *cost, void *workspace,
+              size_t workspace_bytes, void *cuda_stream);
+
+/*
+ * Measures the device's FP64 fused multiply-add throughput (FLOP/s, 2 per
+ * FMA) with a register-resident kernel; *flops receives the best of `reps`
+ * runs.  Used as the arithmetic roofline of the FP64-bound kernels.
+ */
+int ucac_probe_fp64(int32_t reps, void *cuda_stream, double *flops);
+
+/* Destroys the handle and frees its device memory (NULL is ignored). */
+void ucac_destroy(ucac_handle *h);
+
+/* Reason for the last error on this handle, or for the last failed create when h is NULL. */
+const char *ucac_last_error(const ucac_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UCAC_H */

@@ -1,0 +1,122 @@
+// common.cuh -- device-side layout shared by the sweep kernels.
+//
+// All instances of a handle are concatenated: every per-(period, component)
+// array is a structure of arrays over the global item index
+//   gen-period     gp = inst.gpo + t * inst.ng + g
+//   branch-period  bp = inst.bpo + t * inst.nl + l
+//   bus-period     up = inst.upo + t * inst.nb + i
+// so one launch covers a whole batch and consecutive threads touch
+// consecutive addresses.  Kernels walk a block table whose blocks never
+// straddle two instances, which keeps the residual reductions per instance
+// and deterministic (fixed-order block partials, fixed-order final sum).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ucac {
+
+// Coupling rows per (t, g) (Eq. uc_duplicate .. ramp_up and the generator
+// consensus rows) and per (t, line) (flows, w, theta consensus rows).
+enum { GR_ON, GR_SU, GR_SD, GR_PL, GR_PU, GR_QL, GR_QU, GR_RD, GR_RU, GR_GP, GR_GQ, GR_TC, NGR };
+enum { NBR = 8 };
+// generator-period fields
+enum { F_P, F_Q, F_PH, F_SPL, F_SPU, F_SQL, F_SQU, F_SRD, F_SRU, F_UON, F_USU, F_USD, F_PBAR, F_QBAR,
+       F_UBON, F_UBSU, F_UBSD, NGF };
+// branch-period fields
+enum { FB_V0 = 0, FB_MU0 = 8, FB_C = 12, FB_FB0 = 13, NBF = 17 };
+// bus-period fields
+enum { FU_W, FU_TH, NUF };
+// per-instance control scalars
+enum { C_BETA, C_ZPREV, C_LIN, C_KOUT, C_PEND, C_BNEXT, C_DONE, NCTRL };
+// residual record
+enum { R_RP, R_RD, R_ZN, R_ZRMS, R_INF, R_OBJ, R_STATUS, NRES };
+// block partial quantities of the x-bar kernels
+enum { Q_SP, Q_SD, Q_SZ, Q_INF, Q_OBJ, NQ };
+// branch constant table [BC_N][NL]
+enum { BC_Y0 = 0, BC_RATE2 = 8, BC_LO = 9, BC_HI = 17, BC_N = 25 };
+
+struct Inst {
+  int nb, nl, ng, T, ref;
+  int go, gpo, lo, bpo, uo, upo;
+  int m_rows;
+  int blk_gen0, blk_gen1, blk_gp0, blk_gp1, blk_bp0, blk_bp1, blk_up0, blk_up1;
+  double rpq, rva, ruc;
+};
+
+struct Params {
+  double eps_in, eps_out, tau, theta, beta0, lam_max, eta, omega_rel, c_init_rel, c_max_rel;
+  int K_AL, K_N, L_max;
+};
+
+struct Blocks {
+  int n;
+  const int *inst;   // instance of each block
+  const int *first;  // global index of the block's first item
+};
+
+struct Dev {
+  int K;
+  const Inst *inst;
+  Params prm;
+  // generator constants [NGEN]
+  const double *c2p, *c1p, *c0, *csu, *csd, *Pmin, *Pmax, *Qmin, *Qmax, *qlo, *qhi, *RU, *RD, *SU, *SD, *p0;
+  const int *TU, *TD, *u0, *K0;
+  // generator-period state [NGF][NGP], rows [NGR][NGP]
+  long long NGP;
+  double *G, *GA, *GY, *GZ, *GL, *GT;
+  // branch constants [BC_N][NL]
+  long long NL;
+  const double *BC;
+  const int *bf, *bt;  // local bus index of the from / to end
+  // branch-period state [NBF][NBP], rows [NBR][NBP]
+  long long NBP;
+  double *B, *BA, *BY, *BZ, *BL, *BT;
+  // buses
+  long long NB;
+  const double *Gs, *Bs;
+  const int *inc_ptr, *inc_br, *inc_side;  // CSR over global buses; branch index local
+  const int *gen_ptr, *gen_idx;            // CSR over global buses; generator index local
+  long long NUP;
+  const double *Pd, *Qd;
+  double *U;  // [NUF][NUP]
+  // control and records
+  double *ctrl;       // [K][NCTRL]
+  double *res;        // [K][NRES]
+  long long *stat;    // [K][4]: sweeps, newton, al, capped
+  double *part_up;    // [nblk_up][NQ]
+  double *part_gp;    // [nblk_gp][NQ]
+  long long *part_bp; // [nblk_bp][3]
+  // UC dynamic-program scratch: stage costs, cost-to-go, decisions
+  double *dpL;        // [4][T][ng] per instance, instance slice at 4*gpo
+  double *dpC;        // [2][T+1][ng] per instance, slice at 2*(gpo+go)
+  unsigned char *dpD; // [2][T][ng] per instance, slice at 2*gpo
+  Blocks b_gen, b_gp, b_bp, b_up;
+};
+
+__device__ __forceinline__ double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
+
+// deterministic block reduction of NQ doubles (sums, except Q_INF = max)
+template <int BS>
+__device__ __forceinline__ void block_reduce_q(double (&q)[NQ], double *out) {
+  __shared__ double sh[NQ][BS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    double v = q[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double w = __shfl_down_sync(0xffffffffu, v, o);
+      v = (k == Q_INF) ? fmax(v, w) : v + w;
+    }
+    if (lane == 0) sh[k][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    const int k = threadIdx.x;
+    double v = sh[k][0];
+    for (int w = 1; w < BS / 32; ++w) v = (k == Q_INF) ? fmax(v, sh[k][w]) : v + sh[k][w];
+    out[k] = v;
+  }
+}
+
+}  // namespace ucac

@@ -1,0 +1,152 @@
+// k_ucdp.cuh -- UC subproblem per generator by dynamic programming
+// (Sec. III-B, Algorithm 2).
+//
+// One thread per generator.  Consecutive generators of an instance sit at
+// consecutive addresses of every [T][n_gen] array, so each of the thread's
+// per-period loads is coalesced across the warp.  The stage-cost table
+// L_t(a,b), the cost-to-go c_{t,s} and the stay/switch decisions live in a
+// global scratch laid out [entry][t][g] (coalesced, L2-resident at the
+// sizes of interest).  The backward pass is a serial O(T * T_min) chain per
+// generator; all 32 lanes of a warp run 32 generators' chains side by side,
+// so the FP64 pipe is never issued with idle lanes in the serial part.
+//
+// Bit-exactness: the stage cost is evaluated with explicitly rounded FP64
+// operations (no contraction into FMAs) in this order
+//   e_k = u_k - tau_k;  q = ((e_on*e_on) + (e_su*e_su)) + (e_sd*e_sd)
+//   L = ((c0*b + csu*su) + csd*sd) + (0.5*rho)*q
+// and the switch cost as (L(s,1-s) + sum_{t'} L(1-s,1-s) ascending) + c_next,
+// with "stay" chosen when c_stay <= c_switch (Algorithm 2's rule), so the
+// decisions equal those of any implementation using the same order.
+#pragma once
+#include "common.cuh"
+
+namespace ucac {
+
+__device__ __forceinline__ double uc_stage(double b, double su, double sd, double tau_on, double tau_su,
+                                           double tau_sd, double c0, double csu, double csd, double hr) {
+  double e_on = __dsub_rn(b, tau_on);
+  double e_su = __dsub_rn(su, tau_su);
+  double e_sd = __dsub_rn(sd, tau_sd);
+  double q = __dadd_rn(__dadd_rn(__dmul_rn(e_on, e_on), __dmul_rn(e_su, e_su)), __dmul_rn(e_sd, e_sd));
+  double lin = __dadd_rn(__dadd_rn(__dmul_rn(c0, b), __dmul_rn(csu, su)), __dmul_rn(csd, sd));
+  return __dadd_rn(lin, __dmul_rn(hr, q));
+}
+
+// DP for one generator.  tau_* point at period 0 of the generator's column
+// (element stride `st` between periods); L/C/D are scratch columns with the
+// same stride.  Writes u^on_t (0/1) through `uon` and returns c_{1,u0}.
+template <typename WriteU>
+__device__ __forceinline__ double uc_dp(int T, int TU, int TD, int u0, int K0, double c0, double csu, double csd,
+                                        double hr, const double *tau_on, const double *tau_su,
+                                        const double *tau_sd, long long st, double *L, double *C,
+                                        unsigned char *D, WriteU uon) {
+  // stage costs, entry ab = a*2+b at L[(ab*T + t)*st]
+  for (int t = 0; t < T; ++t) {
+    const double ton = tau_on[t * st], tsu = tau_su[t * st], tsd = tau_sd[t * st];
+    L[(0 * T + t) * st] = uc_stage(0.0, 0.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
+    L[(1 * T + t) * st] = uc_stage(1.0, 1.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
+    L[(2 * T + t) * st] = uc_stage(0.0, 0.0, 1.0, ton, tsu, tsd, c0, csu, csd, hr);
+    L[(3 * T + t) * st] = uc_stage(1.0, 0.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
+  }
+#define LTAB(t1, a, b) L[(((a)*2 + (b)) * T + ((t1)-1)) * st]
+#define CTAB(t1, s) C[((s) * (T + 1) + ((t1)-1)) * st]
+#define DTAB(t1, s) D[((s)*T + ((t1)-1)) * st]
+  CTAB(T + 1, 0) = 0.0;
+  CTAB(T + 1, 1) = 0.0;
+  for (int t = T; t >= K0 + 1; --t) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int ns = 1 - s;
+      const double stay = __dadd_rn(LTAB(t, s, s), CTAB(t + 1, s));
+      const int Tm = ns ? TU : TD;
+      const int e = min(t + Tm - 1, T);
+      double sw = LTAB(t, s, ns);
+      for (int tp = t + 1; tp <= e; ++tp) sw = __dadd_rn(sw, LTAB(tp, ns, ns));
+      sw = __dadd_rn(sw, CTAB(e + 1, ns));
+      const bool keep = stay <= sw;
+      CTAB(t, s) = keep ? stay : sw;
+      DTAB(t, s) = keep ? 0 : 1;
+    }
+  }
+  double cost;
+  if (K0 > 0) {
+    double acc = LTAB(1, u0, u0);
+    for (int t = 2; t <= K0; ++t) acc = __dadd_rn(acc, LTAB(t, u0, u0));
+    cost = __dadd_rn(acc, CTAB(K0 + 1, u0));
+  } else {
+    cost = CTAB(1, u0);
+  }
+  for (int t = 1; t <= K0; ++t) uon(t - 1, u0);
+  int s = u0, t = K0 + 1;
+  while (t <= T) {
+    if (DTAB(t, s) == 0) {
+      uon(t - 1, s);
+      t += 1;
+    } else {
+      const int ns = 1 - s;
+      const int e = min(t + (ns ? TU : TD) - 1, T);
+      for (int k = t; k <= e; ++k) uon(k - 1, ns);
+      s = ns;
+      t = e + 1;
+    }
+  }
+#undef LTAB
+#undef CTAB
+#undef DTAB
+  return cost;
+}
+
+// In-sweep x^UC step: reads the duplicate-row targets tau = ubar - z - y/rho
+// (written by the x-bar^UC kernel of the previous sweep), writes u_on/u_su/
+// u_sd and the x-side values of the three duplicate rows.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_ucdp(Dev S) {
+  const int b = blockIdx.x;
+  const int k = S.b_gen.inst[b];
+  const Inst I = S.inst[k];
+  const int gg = S.b_gen.first[b] + threadIdx.x;
+  if (gg >= I.go + I.ng) return;
+  const int g = gg - I.go, ng = I.ng, T = I.T;
+  const long long NGP = S.NGP;
+  const long long base = (long long)I.gpo + g;
+  const double hr = __dmul_rn(0.5, I.ruc);
+  const int TU = max(S.TU[gg], 1), TD = max(S.TD[gg], 1), u0 = S.u0[gg];
+  const int K0 = min(max(S.K0[gg], 0), T);
+  double *L = S.dpL + 4LL * I.gpo + g;
+  double *C = S.dpC + 2LL * (I.gpo + I.go) + g;
+  unsigned char *D = S.dpD + 2LL * I.gpo + g;
+  double *uon_a = S.G + (long long)F_UON * NGP + base;
+  uc_dp(T, TU, TD, u0, K0, S.c0[gg], S.csu[gg], S.csd[gg], hr, S.GT + GR_ON * NGP + base,
+        S.GT + GR_SU * NGP + base, S.GT + GR_SD * NGP + base, (long long)ng, L, C, D,
+        [&](int t, int u) { uon_a[(long long)t * ng] = (double)u; });
+  int prev = u0;
+  for (int t = 0; t < T; ++t) {
+    const long long i = base + (long long)t * ng;
+    const int u = (int)S.G[F_UON * NGP + i];
+    const double su = (u > prev) ? 1.0 : 0.0, sd = (prev > u) ? 1.0 : 0.0;
+    S.G[F_USU * NGP + i] = su;
+    S.G[F_USD * NGP + i] = sd;
+    S.GA[GR_ON * NGP + i] = (double)u;
+    S.GA[GR_SU * NGP + i] = su;
+    S.GA[GR_SD * NGP + i] = sd;
+    prev = u;
+  }
+}
+
+// Standalone DP over [T][n_gen] device arrays (one thread per generator).
+__global__ void __launch_bounds__(128) k_ucdp_standalone(int ng, int T, double rho, const double *tau_on,
+                                                         const double *tau_su, const double *tau_sd,
+                                                         const double *c0, const double *csu, const double *csd,
+                                                         const int *TU, const int *TD, const int *u0,
+                                                         const int *K0, int8_t *u_on, double *cost, double *L,
+                                                         double *C, unsigned char *D) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= ng) return;
+  const double hr = __dmul_rn(0.5, rho);
+  int8_t *uo = u_on + g;
+  cost[g] = uc_dp(T, max(TU[g], 1), max(TD[g], 1), u0[g] ? 1 : 0, min(max(K0[g], 0), T), c0[g], csu[g], csd[g], hr,
+                  tau_on + g, tau_su + g, tau_sd + g, (long long)ng, L + g, C + g, D + g,
+                  [&](int t, int u) { uo[(long long)t * ng] = (int8_t)u; });
+}
+
+}  // namespace ucac

@@ -1,0 +1,795 @@
+// ucac.cu -- C ABI of the UC-ACOPF component-ADMM sweep on B300 (sm_103a).
+//
+// Host side: validates the grids, derives the per-line admittance terms, the
+// bus adjacency and the cold start (Sec. IV-A) once at create time, lays the
+// whole batch out in one device arena, and captures one sweep (x-step
+// kernels, x-bar/z/y kernels, finish kernel) into a CUDA graph that
+// ucac_iterate / ucac_enqueue_sweeps replay.  No device work ever runs on
+// the host: after create, a sweep is six kernel launches and nothing else.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ucac.h"
+#include "common.cuh"
+#include "k_branch.cuh"
+#include "k_gen.cuh"
+#include "k_ucdp.cuh"
+#include "k_xbar.cuh"
+
+using namespace ucac;
+
+namespace {
+
+constexpr int BS_GEN = 64;    // UC DP: one thread per generator
+constexpr int BS_GP = 128;    // generator and x-bar^UC kernels
+constexpr int BS_BP = 64;     // line kernel (register heavy)
+constexpr int BS_UP = 128;    // bus kernel
+constexpr int BS_FIN = 256;   // finish kernel
+
+thread_local std::string g_create_error;
+
+struct HInst {
+  int nb, nl, ng, T, ref;
+  int go, gpo, lo, bpo, uo, upo;
+};
+
+}  // namespace
+
+struct ucac_handle {
+  int K = 0;
+  std::vector<HInst> hi;
+  std::vector<Inst> inst_h;
+  Params prm{};
+  int check_every = 50;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  Dev dev{};
+  long long NGEN = 0, NGP = 0, NL = 0, NBP = 0, NB = 0, NUP = 0;
+  int nblk_gen = 0, nblk_gp = 0, nblk_bp = 0, nblk_up = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int fail(ucac_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg; else g_create_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return fail(h, UCAC_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+std::string validate(const ucac_grid *g, int horizon) {
+  if (!g) return "grid is NULL";
+  if (g->n_bus < 2 || g->n_branch < 1 || g->n_gen < 1) return "need >= 2 buses, >= 1 branch, >= 1 generator";
+  if (g->T < 1 || horizon < 1 || horizon > g->T) return "horizon must be in [1, grid.T]";
+  if (g->ref_bus < 0 || g->ref_bus >= g->n_bus) return "ref_bus out of range";
+  const void *ptrs[] = {g->Pd, g->Qd, g->Gs, g->Bs, g->Vmin, g->Vmax, g->br_from, g->br_to, g->br_r, g->br_x,
+                        g->br_b, g->br_rate, g->gen_bus, g->Pmin, g->Pmax, g->Qmin, g->Qmax, g->c2, g->c1,
+                        g->c0, g->c_su, g->c_sd, g->RU, g->RD, g->SU, g->SD, g->TU, g->TD, g->u0, g->L0, g->F0, g->p0};
+  for (const void *p : ptrs)
+    if (!p) return "a grid array is NULL";
+  if (!(g->base_mva > 0.0)) return "base_mva must be positive";
+  const int nb = g->n_bus;
+  for (int l = 0; l < g->n_branch; ++l) {
+    if (g->br_from[l] < 0 || g->br_from[l] >= nb || g->br_to[l] < 0 || g->br_to[l] >= nb)
+      return "branch end out of range";
+    if (g->br_from[l] == g->br_to[l]) return "branch with equal ends";
+    if (!(g->br_r[l] * g->br_r[l] + g->br_x[l] * g->br_x[l] > 0.0)) return "branch with r = x = 0";
+    if (!(g->br_rate[l] > 0.0) || !std::isfinite(g->br_b[l])) return "branch rate must be positive";
+  }
+  for (int i = 0; i < nb; ++i)
+    if (!(g->Vmin[i] > 0.0 && g->Vmin[i] <= g->Vmax[i]) || !std::isfinite(g->Gs[i]) || !std::isfinite(g->Bs[i]))
+      return "bus voltage bounds out of order";
+  for (int k = 0; k < g->n_gen; ++k) {
+    if (g->gen_bus[k] < 0 || g->gen_bus[k] >= nb) return "generator bus out of range";
+    if (!(g->Pmin[k] <= g->Pmax[k] && g->Pmax[k] > 0.0 && g->Qmin[k] <= g->Qmax[k]))
+      return "generator bounds out of order";
+    if (g->u0[k] != 0 && g->u0[k] != 1) return "u0 must be 0 or 1";
+    const double vals[] = {g->c2[k], g->c1[k], g->c0[k], g->c_su[k], g->c_sd[k], g->RU[k], g->RD[k], g->SU[k],
+                           g->SD[k], g->p0[k]};
+    for (double v : vals)
+      if (!std::isfinite(v)) return "non-finite generator data";
+  }
+  for (long long k = 0; k < (long long)horizon * nb; ++k)
+    if (!std::isfinite(g->Pd[k]) || !std::isfinite(g->Qd[k])) return "non-finite load";
+  std::vector<int> par(nb);
+  for (int i = 0; i < nb; ++i) par[i] = i;
+  auto find = [&](int a) {
+    while (par[a] != a) a = par[a] = par[par[a]];
+    return a;
+  };
+  for (int l = 0; l < g->n_branch; ++l) par[find(g->br_from[l])] = find(g->br_to[l]);
+  int roots = 0;
+  for (int i = 0; i < nb; ++i) roots += (find(i) == i);
+  if (roots != 1) return "grid is not connected";
+  return "";
+}
+
+struct Arena {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t n) {
+    size_t o = off;
+    off += ((n * sizeof(T) + 255) / 256) * 256;
+    return o;
+  }
+};
+
+void build_blocks(const std::vector<long long> &off, const std::vector<long long> &cnt, int bs, std::vector<int> &inst,
+                  std::vector<int> &first, std::vector<int> &b0, std::vector<int> &b1) {
+  for (size_t k = 0; k < cnt.size(); ++k) {
+    b0[k] = (int)inst.size();
+    for (long long j = 0; j < cnt[k]; j += bs) {
+      inst.push_back((int)k);
+      first.push_back((int)(off[k] + j));
+    }
+    b1[k] = (int)inst.size();
+  }
+}
+
+void launch_sweep(ucac_handle *h, cudaStream_t s) {
+  const Dev &D = h->dev;
+  k_ucdp<BS_GEN><<<h->nblk_gen, BS_GEN, 0, s>>>(D);
+  k_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
+  k_branch<BS_BP><<<h->nblk_bp, BS_BP, 0, s>>>(D);
+  k_bus<BS_UP><<<h->nblk_up, BS_UP, 0, s>>>(D);
+  k_ucbar<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
+  k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(D);
+}
+
+const char *kKernelNames[UCAC_N_KERNELS] = {"k_ucdp", "k_gen", "k_branch", "k_bus", "k_ucbar", "k_finish"};
+
+}  // namespace
+
+extern "C" {
+
+void ucac_default_params(ucac_params *p) {
+  if (!p) return;
+  p->eps_in = 1e-4;
+  p->eps_out = 1e-4;
+  p->tau = 6.0;
+  p->theta = 0.8;
+  p->beta0 = 1e3;
+  p->lambda_max = 1e12;
+  p->eta = 1e-12;
+  p->omega_rel = 1e-12;
+  p->c_init_rel = 1e4;
+  p->c_max_rel = 1e6;
+  p->K_AL = 50;
+  p->K_N = 50;
+  p->L_max = 1000;
+  p->check_every = 50;
+}
+
+int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, const ucac_rho *rhos, int32_t n,
+                      const ucac_params *params, void *cuda_stream, ucac_handle **out) {
+  ucac_handle *h = nullptr;
+  if (out) *out = nullptr;
+  if (!grids || !horizons || !rhos || n < 1 || !out) return fail(nullptr, UCAC_E_ARG, "bad arguments");
+  for (int k = 0; k < n; ++k) {
+    std::string e = validate(grids[k], horizons[k]);
+    if (!e.empty()) return fail(nullptr, UCAC_E_GRID, "instance " + std::to_string(k) + ": " + e);
+    if (!(rhos[k].pq > 0 && rhos[k].va > 0 && rhos[k].uc > 0))
+      return fail(nullptr, UCAC_E_ARG, "penalties must be positive");
+  }
+  ucac_params P;
+  ucac_default_params(&P);
+  if (params) P = *params;
+  if (P.K_AL < 1 || P.K_N < 1 || P.L_max < 1 || P.check_every < 1 || !(P.beta0 > 0))
+    return fail(nullptr, UCAC_E_ARG, "bad parameters");
+
+  h = new ucac_handle();
+  h->K = n;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->check_every = P.check_every;
+  h->prm = Params{P.eps_in, P.eps_out, P.tau, P.theta, P.beta0, P.lambda_max, P.eta, P.omega_rel, P.c_init_rel,
+                  P.c_max_rel, P.K_AL, P.K_N, P.L_max};
+  // ---- sizes and offsets
+  long long go = 0, gpo = 0, lo = 0, bpo = 0, uo = 0, upo = 0;
+  for (int k = 0; k < n; ++k) {
+    const ucac_grid *g = grids[k];
+    HInst I{g->n_bus, g->n_branch, g->n_gen, horizons[k], g->ref_bus, (int)go, (int)gpo, (int)lo, (int)bpo,
+            (int)uo, (int)upo};
+    h->hi.push_back(I);
+    go += g->n_gen;
+    gpo += (long long)I.T * g->n_gen;
+    lo += g->n_branch;
+    bpo += (long long)I.T * g->n_branch;
+    uo += g->n_bus;
+    upo += (long long)I.T * g->n_bus;
+  }
+  if (gpo > 2000000000LL || bpo > 2000000000LL || upo > 2000000000LL) {
+    delete h;
+    return fail(nullptr, UCAC_E_ARG, "batch too large for 32-bit item indices");
+  }
+  h->NGEN = go; h->NGP = gpo; h->NL = lo; h->NBP = bpo; h->NB = uo; h->NUP = upo;
+  const long long NGEN = go, NGP = gpo, NL = lo, NBP = bpo, NB = uo, NUP = upo;
+
+  // ---- host copies of constants and the cold start
+  std::vector<double> c2p(NGEN), c1p(NGEN), c0(NGEN), csu(NGEN), csd(NGEN), Pmin(NGEN), Pmax(NGEN), Qmin(NGEN),
+      Qmax(NGEN), qlo(NGEN), qhi(NGEN), RU(NGEN), RD(NGEN), SU(NGEN), SD(NGEN), p0(NGEN);
+  std::vector<int> TU(NGEN), TD(NGEN), u0(NGEN), K0(NGEN);
+  std::vector<double> BC((size_t)BC_N * NL);
+  std::vector<int> bf(NL), bt(NL);
+  std::vector<double> Gs(NB), Bs(NB), Pd(NUP), Qd(NUP);
+  std::vector<int> inc_ptr(NB + 1, 0), inc_br(2 * NL), inc_side(2 * NL), gen_ptr(NB + 1, 0), gen_idx(NGEN);
+  std::vector<double> G((size_t)NGF * NGP, 0.0), B((size_t)NBF * NBP, 0.0), U((size_t)NUF * NUP, 0.0);
+  std::vector<double> ctrl((size_t)NCTRL * n, 0.0);
+  const double twopi = 6.283185307179586476925286766559;
+  for (int k = 0; k < n; ++k) {
+    const ucac_grid *g = grids[k];
+    const HInst &I = h->hi[k];
+    const double base = g->base_mva;
+    for (int j = 0; j < I.ng; ++j) {
+      const long long gg = I.go + j;
+      c2p[gg] = g->c2[j] * base * base;
+      c1p[gg] = g->c1[j] * base;
+      c0[gg] = g->c0[j]; csu[gg] = g->c_su[j]; csd[gg] = g->c_sd[j];
+      Pmin[gg] = g->Pmin[j]; Pmax[gg] = g->Pmax[j]; Qmin[gg] = g->Qmin[j]; Qmax[gg] = g->Qmax[j];
+      qlo[gg] = std::min(0.0, g->Qmin[j]);
+      qhi[gg] = g->Qmax[j];
+      RU[gg] = g->RU[j]; RD[gg] = g->RD[j]; SU[gg] = g->SU[j]; SD[gg] = g->SD[j]; p0[gg] = g->p0[j];
+      TU[gg] = g->TU[j]; TD[gg] = g->TD[j]; u0[gg] = g->u0[j];
+      K0[gg] = g->u0[j] ? g->L0[j] : g->F0[j];
+    }
+    for (int l = 0; l < I.nl; ++l) {
+      const long long lg = I.lo + l;
+      // series admittance y = 1/(r + jx); Y_ii = y + j b/2, Y_ij = -y (no taps)
+      const double r = g->br_r[l], x = g->br_x[l], z2 = r * r + x * x;
+      const double gs = r / z2, bs = -x / z2, bc = g->br_b[l];
+      const double Y[8] = {gs, bs + 0.5 * bc, -gs, -bs, gs, bs + 0.5 * bc, -gs, -bs};
+      for (int q = 0; q < 8; ++q) BC[(BC_Y0 + q) * NL + lg] = Y[q];
+      const double rate2 = g->br_rate[l] * g->br_rate[l];
+      BC[BC_RATE2 * NL + lg] = rate2;
+      const int i = g->br_from[l], j = g->br_to[l];
+      const double vv = g->Vmax[i] * g->Vmax[j];
+      const double lo8[8] = {g->Vmin[i] * g->Vmin[i], g->Vmin[j] * g->Vmin[j], -vv, -vv, -twopi, -twopi, 0.0, 0.0};
+      const double hi8[8] = {g->Vmax[i] * g->Vmax[i], g->Vmax[j] * g->Vmax[j], vv, vv, twopi, twopi, rate2, rate2};
+      for (int q = 0; q < 8; ++q) {
+        BC[(BC_LO + q) * NL + lg] = lo8[q];
+        BC[(BC_HI + q) * NL + lg] = hi8[q];
+      }
+      bf[lg] = i;
+      bt[lg] = j;
+    }
+    for (int i = 0; i < I.nb; ++i) {
+      Gs[I.uo + i] = g->Gs[i];
+      Bs[I.uo + i] = g->Bs[i];
+    }
+    for (int t = 0; t < I.T; ++t)
+      for (int i = 0; i < I.nb; ++i) {
+        Pd[I.upo + (long long)t * I.nb + i] = g->Pd[(long long)t * I.nb + i];
+        Qd[I.upo + (long long)t * I.nb + i] = g->Qd[(long long)t * I.nb + i];
+      }
+    // adjacency (global CSR rows, local column indices)
+    for (int l = 0; l < I.nl; ++l) {
+      inc_ptr[I.uo + g->br_from[l] + 1]++;
+      inc_ptr[I.uo + g->br_to[l] + 1]++;
+    }
+    for (int j = 0; j < I.ng; ++j) gen_ptr[I.uo + g->gen_bus[j] + 1]++;
+    // cold start (Sec. IV-A) and all units on
+    for (int t = 0; t < I.T; ++t)
+      for (int j = 0; j < I.ng; ++j) {
+        const long long gp = I.gpo + (long long)t * I.ng + j, gg = I.go + j;
+        const double p = 0.5 * Pmax[gg], q = 0.5 * (qlo[gg] + qhi[gg]);
+        G[F_P * NGP + gp] = p;
+        G[F_Q * NGP + gp] = q;
+        G[F_PH * NGP + gp] = (t > 0) ? 0.5 * Pmax[gg] : p0[gg];
+        G[F_UON * NGP + gp] = 1.0;
+        G[F_PBAR * NGP + gp] = p;
+        G[F_QBAR * NGP + gp] = q;
+        G[F_UBON * NGP + gp] = 1.0;
+      }
+    const double cpen0 = P.c_init_rel * std::max(rhos[k].pq, rhos[k].va);
+    for (int t = 0; t < I.T; ++t) {
+      for (int i = 0; i < I.nb; ++i) {
+        const double V = 0.5 * (g->Vmin[i] + g->Vmax[i]);
+        U[FU_W * NUP + I.upo + (long long)t * I.nb + i] = V * V;
+      }
+      for (int l = 0; l < I.nl; ++l) {
+        const long long bp = I.bpo + (long long)t * I.nl + l, lg = I.lo + l;
+        const int i = g->br_from[l], j = g->br_to[l];
+        const double Vi = 0.5 * (g->Vmin[i] + g->Vmax[i]), Vj = 0.5 * (g->Vmin[j] + g->Vmax[j]);
+        double v[8] = {Vi * Vi, Vj * Vj, Vi * Vj, 0.0, 0.0, 0.0, 0.0, 0.0};
+        const double *Y = &BC[0];
+        auto Yq = [&](int q) { return Y[(BC_Y0 + q) * NL + lg]; };
+        const double a0 = Yq(0) * v[0] + Yq(2) * v[2] + Yq(3) * v[3];
+        const double a1 = -Yq(1) * v[0] - Yq(3) * v[2] + Yq(2) * v[3];
+        const double a2 = Yq(4) * v[1] + Yq(6) * v[2] - Yq(7) * v[3];
+        const double a3 = -Yq(5) * v[1] - Yq(7) * v[2] - Yq(6) * v[3];
+        const double rate2 = BC[BC_RATE2 * NL + lg];
+        v[6] = std::min(std::max(rate2 - a0 * a0 - a1 * a1, 0.0), rate2);
+        v[7] = std::min(std::max(rate2 - a2 * a2 - a3 * a3, 0.0), rate2);
+        for (int q = 0; q < 8; ++q) B[(FB_V0 + q) * NBP + bp] = v[q];
+        B[FB_C * NBP + bp] = cpen0;
+        B[(FB_FB0 + 0) * NBP + bp] = a0;
+        B[(FB_FB0 + 1) * NBP + bp] = a1;
+        B[(FB_FB0 + 2) * NBP + bp] = a2;
+        B[(FB_FB0 + 3) * NBP + bp] = a3;
+      }
+    }
+    ctrl[(size_t)k * NCTRL + C_BETA] = P.beta0;
+    ctrl[(size_t)k * NCTRL + C_ZPREV] = -1.0;
+    ctrl[(size_t)k * NCTRL + C_BNEXT] = P.beta0;
+  }
+  for (long long i = 0; i < NB; ++i) {
+    inc_ptr[i + 1] += inc_ptr[i];
+    gen_ptr[i + 1] += gen_ptr[i];
+  }
+  {
+    std::vector<int> fi(NB, 0), fg(NB, 0);
+    for (int k = 0; k < n; ++k) {
+      const ucac_grid *g = grids[k];
+      const HInst &I = h->hi[k];
+      for (int l = 0; l < I.nl; ++l) {
+        int b = I.uo + g->br_from[l];
+        int p = inc_ptr[b] + fi[b]++;
+        inc_br[p] = l; inc_side[p] = 0;
+        b = I.uo + g->br_to[l];
+        p = inc_ptr[b] + fi[b]++;
+        inc_br[p] = l; inc_side[p] = 1;
+      }
+      for (int j = 0; j < I.ng; ++j) {
+        const int b = I.uo + g->gen_bus[j];
+        gen_idx[gen_ptr[b] + fg[b]++] = j;
+      }
+    }
+  }
+  // ---- block tables
+  std::vector<int> bgi, bgf, bpi, bpf, bbi, bbf, bui, buf_;
+  std::vector<int> g0(n), g1(n), p0b(n), p1b(n), q0b(n), q1b(n), u0b(n), u1b(n);
+  {
+    std::vector<long long> offg(n), cntg(n), offp(n), cntp(n), offb(n), cntb(n), offu(n), cntu(n);
+    for (int k = 0; k < n; ++k) {
+      const HInst &I = h->hi[k];
+      offg[k] = I.go; cntg[k] = I.ng;
+      offp[k] = I.gpo; cntp[k] = (long long)I.T * I.ng;
+      offb[k] = I.bpo; cntb[k] = (long long)I.T * I.nl;
+      offu[k] = I.upo; cntu[k] = (long long)I.T * I.nb;
+    }
+    build_blocks(offg, cntg, BS_GEN, bgi, bgf, g0, g1);
+    build_blocks(offp, cntp, BS_GP, bpi, bpf, p0b, p1b);
+    build_blocks(offb, cntb, BS_BP, bbi, bbf, q0b, q1b);
+    build_blocks(offu, cntu, BS_UP, bui, buf_, u0b, u1b);
+  }
+  h->nblk_gen = (int)bgi.size();
+  h->nblk_gp = (int)bpi.size();
+  h->nblk_bp = (int)bbi.size();
+  h->nblk_up = (int)bui.size();
+  for (int k = 0; k < n; ++k) {
+    const HInst &I = h->hi[k];
+    Inst D{};
+    D.nb = I.nb; D.nl = I.nl; D.ng = I.ng; D.T = I.T; D.ref = I.ref;
+    D.go = I.go; D.gpo = I.gpo; D.lo = I.lo; D.bpo = I.bpo; D.uo = I.uo; D.upo = I.upo;
+    D.m_rows = I.T * 8 * I.nl + I.ng * (12 * I.T - 1);
+    D.blk_gen0 = g0[k]; D.blk_gen1 = g1[k];
+    D.blk_gp0 = p0b[k]; D.blk_gp1 = p1b[k];
+    D.blk_bp0 = q0b[k]; D.blk_bp1 = q1b[k];
+    D.blk_up0 = u0b[k]; D.blk_up1 = u1b[k];
+    D.rpq = rhos[k].pq; D.rva = rhos[k].va; D.ruc = rhos[k].uc;
+    h->inst_h.push_back(D);
+  }
+
+  // ---- arena
+  Arena A;
+  const size_t o_inst = A.take<Inst>(n);
+  const size_t o_gd = A.take<double>(16 * NGEN), o_gi = A.take<int>(4 * NGEN);
+  const size_t o_G = A.take<double>((size_t)NGF * NGP);
+  const size_t o_GR = A.take<double>((size_t)5 * NGR * NGP);
+  const size_t o_BC = A.take<double>((size_t)BC_N * NL), o_bft = A.take<int>(2 * NL);
+  const size_t o_B = A.take<double>((size_t)NBF * NBP);
+  const size_t o_BR = A.take<double>((size_t)5 * NBR * NBP);
+  const size_t o_bus = A.take<double>(2 * NB);
+  const size_t o_csr = A.take<int>((NB + 1) * 2 + 4 * NL + NGEN);
+  const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
+  const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
+  const size_t o_stat = A.take<long long>(4 * n);
+  const size_t o_pup = A.take<double>((size_t)NQ * h->nblk_up), o_pgp = A.take<double>((size_t)NQ * h->nblk_gp);
+  const size_t o_pbp = A.take<long long>(3 * (size_t)h->nblk_bp);
+  const size_t o_dpL = A.take<double>(4 * NGP), o_dpC = A.take<double>(2 * (NGP + NGEN));
+  const size_t o_dpD = A.take<unsigned char>(2 * NGP);
+  const size_t o_blk = A.take<int>(2 * ((size_t)h->nblk_gen + h->nblk_gp + h->nblk_bp + h->nblk_up));
+  h->arena_bytes = A.off;
+  cudaError_t ce = cudaMalloc((void **)&h->arena, h->arena_bytes);
+  if (ce != cudaSuccess) {
+    std::string m = std::string("cudaMalloc: ") + cudaGetErrorString(ce);
+    delete h;
+    return fail(nullptr, UCAC_E_CUDA, m);
+  }
+  char *ar = h->arena;
+  Dev &D = h->dev;
+  D.K = n;
+  D.inst = (const Inst *)(ar + o_inst);
+  D.prm = h->prm;
+  double *gd = (double *)(ar + o_gd);
+  D.c2p = gd; D.c1p = gd + NGEN; D.c0 = gd + 2 * NGEN; D.csu = gd + 3 * NGEN; D.csd = gd + 4 * NGEN;
+  D.Pmin = gd + 5 * NGEN; D.Pmax = gd + 6 * NGEN; D.Qmin = gd + 7 * NGEN; D.Qmax = gd + 8 * NGEN;
+  D.qlo = gd + 9 * NGEN; D.qhi = gd + 10 * NGEN; D.RU = gd + 11 * NGEN; D.RD = gd + 12 * NGEN;
+  D.SU = gd + 13 * NGEN; D.SD = gd + 14 * NGEN; D.p0 = gd + 15 * NGEN;
+  int *gi = (int *)(ar + o_gi);
+  D.TU = gi; D.TD = gi + NGEN; D.u0 = gi + 2 * NGEN; D.K0 = gi + 3 * NGEN;
+  D.NGP = NGP;
+  D.G = (double *)(ar + o_G);
+  double *gr = (double *)(ar + o_GR);
+  D.GA = gr; D.GY = gr + (size_t)NGR * NGP; D.GZ = gr + (size_t)2 * NGR * NGP; D.GL = gr + (size_t)3 * NGR * NGP;
+  D.GT = gr + (size_t)4 * NGR * NGP;
+  D.NL = NL;
+  D.BC = (const double *)(ar + o_BC);
+  D.bf = (const int *)(ar + o_bft); D.bt = D.bf + NL;
+  D.NBP = NBP;
+  D.B = (double *)(ar + o_B);
+  double *br = (double *)(ar + o_BR);
+  D.BA = br; D.BY = br + (size_t)NBR * NBP; D.BZ = br + (size_t)2 * NBR * NBP; D.BL = br + (size_t)3 * NBR * NBP;
+  D.BT = br + (size_t)4 * NBR * NBP;
+  D.NB = NB;
+  D.Gs = (const double *)(ar + o_bus); D.Bs = D.Gs + NB;
+  const int *csr = (const int *)(ar + o_csr);
+  D.inc_ptr = csr; D.gen_ptr = csr + (NB + 1); D.inc_br = csr + 2 * (NB + 1); D.inc_side = D.inc_br + 2 * NL;
+  D.gen_idx = D.inc_side + 2 * NL;
+  D.NUP = NUP;
+  D.Pd = (const double *)(ar + o_pq); D.Qd = D.Pd + NUP;
+  D.U = (double *)(ar + o_U);
+  D.ctrl = (double *)(ar + o_ctrl);
+  D.res = (double *)(ar + o_res);
+  D.stat = (long long *)(ar + o_stat);
+  D.part_up = (double *)(ar + o_pup);
+  D.part_gp = (double *)(ar + o_pgp);
+  D.part_bp = (long long *)(ar + o_pbp);
+  D.dpL = (double *)(ar + o_dpL);
+  D.dpC = (double *)(ar + o_dpC);
+  D.dpD = (unsigned char *)(ar + o_dpD);
+  int *blk = (int *)(ar + o_blk);
+  D.b_gen = Blocks{h->nblk_gen, blk, blk + h->nblk_gen};
+  blk += 2 * h->nblk_gen;
+  D.b_gp = Blocks{h->nblk_gp, blk, blk + h->nblk_gp};
+  blk += 2 * h->nblk_gp;
+  D.b_bp = Blocks{h->nblk_bp, blk, blk + h->nblk_bp};
+  blk += 2 * h->nblk_bp;
+  D.b_up = Blocks{h->nblk_up, blk, blk + h->nblk_up};
+
+  auto up = [&](const void *dst, const void *src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpy((void *)dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  std::vector<double> gdh;
+  for (auto *v : {&c2p, &c1p, &c0, &csu, &csd, &Pmin, &Pmax, &Qmin, &Qmax, &qlo, &qhi, &RU, &RD, &SU, &SD, &p0})
+    gdh.insert(gdh.end(), v->begin(), v->end());
+  std::vector<int> gih;
+  for (auto *v : {&TU, &TD, &u0, &K0}) gih.insert(gih.end(), v->begin(), v->end());
+  std::vector<int> bfth(bf);
+  bfth.insert(bfth.end(), bt.begin(), bt.end());
+  std::vector<double> bush(Gs);
+  bush.insert(bush.end(), Bs.begin(), Bs.end());
+  std::vector<int> csrh(inc_ptr);
+  csrh.insert(csrh.end(), gen_ptr.begin(), gen_ptr.end());
+  csrh.insert(csrh.end(), inc_br.begin(), inc_br.end());
+  csrh.insert(csrh.end(), inc_side.begin(), inc_side.end());
+  csrh.insert(csrh.end(), gen_idx.begin(), gen_idx.end());
+  std::vector<double> pqh(Pd);
+  pqh.insert(pqh.end(), Qd.begin(), Qd.end());
+  std::vector<int> blkh;
+  for (auto *pr : {&bgi, &bgf, &bpi, &bpf, &bbi, &bbf, &bui, &buf_}) blkh.insert(blkh.end(), pr->begin(), pr->end());
+  cudaError_t e = cudaSuccess;
+  auto chain = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chain(cudaMemset(h->arena, 0, h->arena_bytes));
+  chain(up(D.inst, h->inst_h.data(), sizeof(Inst) * n));
+  chain(up(gd, gdh.data(), gdh.size() * 8));
+  chain(up(gi, gih.data(), gih.size() * 4));
+  chain(up(D.G, G.data(), G.size() * 8));
+  chain(up(D.BC, BC.data(), BC.size() * 8));
+  chain(up(D.bf, bfth.data(), bfth.size() * 4));
+  chain(up(D.B, B.data(), B.size() * 8));
+  chain(up(D.Gs, bush.data(), bush.size() * 8));
+  chain(up(csr, csrh.data(), csrh.size() * 4));
+  chain(up(D.Pd, pqh.data(), pqh.size() * 8));
+  chain(up(D.U, U.data(), U.size() * 8));
+  chain(up(D.ctrl, ctrl.data(), ctrl.size() * 8));
+  chain(up(D.b_gen.inst, blkh.data(), blkh.size() * 4));
+  if (e != cudaSuccess) {
+    std::string m = std::string("upload: ") + cudaGetErrorString(e);
+    ucac_destroy(h);
+    return fail(nullptr, UCAC_E_CUDA, m);
+  }
+  k_prep_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, h->stream>>>(D);
+  k_prep_branch<BS_BP><<<h->nblk_bp, BS_BP, 0, h->stream>>>(D);
+  e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  // ---- capture one sweep into a graph (capture needs a non-legacy stream)
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    launch_sweep(h, h->cap);
+    e = cudaStreamEndCapture(h->cap, &h->graph);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
+  if (e != cudaSuccess) {
+    std::string m = std::string("setup: ") + cudaGetErrorString(e);
+    ucac_destroy(h);
+    return fail(nullptr, UCAC_E_CUDA, m);
+  }
+  *out = h;
+  return UCAC_OK;
+}
+
+int ucac_create(const ucac_grid *grid, int32_t horizon, ucac_rho rho, const ucac_params *params, void *cuda_stream,
+                ucac_handle **out) {
+  const ucac_grid *gs[1] = {grid};
+  return ucac_create_batch(gs, &horizon, &rho, 1, params, cuda_stream, out);
+}
+
+int32_t ucac_instances(const ucac_handle *h) { return h ? h->K : 0; }
+
+int ucac_enqueue_sweeps(ucac_handle *h, int32_t n_sweeps) {
+  if (!h || n_sweeps < 0) return fail(h, UCAC_E_ARG, "bad arguments");
+  for (int i = 0; i < n_sweeps; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
+  return UCAC_OK;
+}
+
+int ucac_iterate(ucac_handle *h, int32_t n_sweeps) {
+  if (!h || n_sweeps < 0) return fail(h, UCAC_E_ARG, "bad arguments");
+  std::vector<double> c((size_t)NCTRL * h->K), r((size_t)NRES * h->K);
+  int done = 0;
+  while (done < n_sweeps) {
+    const int m = std::min(h->check_every, n_sweeps - done);
+    for (int i = 0; i < m; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
+    done += m;
+    CK(cudaMemcpyAsync(c.data(), h->dev.ctrl, c.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(r.data(), h->dev.res, r.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    bool all = true;
+    for (int k = 0; k < h->K; ++k) {
+      if (r[(size_t)k * NRES + R_STATUS] < 0) return fail(h, UCAC_E_NAN, "residual became NaN/Inf");
+      all = all && c[(size_t)k * NCTRL + C_DONE] != 0.0;
+    }
+    if (all) return UCAC_CONVERGED;
+  }
+  return UCAC_OK;
+}
+
+int ucac_residuals(const ucac_handle *hc, int32_t instance, ucac_report *out) {
+  ucac_handle *h = const_cast<ucac_handle *>(hc);
+  if (!h || !out || instance < 0 || instance >= h->K) return fail(h, UCAC_E_ARG, "bad arguments");
+  double r[NRES], c[NCTRL];
+  long long s[4];
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(r, h->dev.res + (size_t)instance * NRES, sizeof(r), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(c, h->dev.ctrl + (size_t)instance * NCTRL, sizeof(c), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(s, h->dev.stat + (size_t)instance * 4, sizeof(s), cudaMemcpyDeviceToHost));
+  out->r_p = r[R_RP];
+  out->r_d = r[R_RD];
+  out->z_norm = r[R_ZN];
+  out->z_rms = r[R_ZRMS];
+  out->inf_norm_viol = r[R_INF];
+  out->objective = r[R_OBJ];
+  out->beta = c[C_BETA];
+  out->sweeps = s[0];
+  out->outer = (int64_t)c[C_KOUT];
+  out->newton = s[1];
+  out->al = s[2];
+  out->n_newton_maxit = (int32_t)s[3];
+  out->status = (int32_t)r[R_STATUS];
+  return UCAC_OK;
+}
+
+int ucac_solution(const ucac_handle *hc, int32_t k, double *p, double *q, double *w, double *theta, double *pf,
+                  uint8_t *u_on) {
+  ucac_handle *h = const_cast<ucac_handle *>(hc);
+  if (!h || k < 0 || k >= h->K) return fail(h, UCAC_E_ARG, "bad arguments");
+  const HInst &I = h->hi[k];
+  const Dev &D = h->dev;
+  const size_t ngp = (size_t)I.T * I.ng, nup = (size_t)I.T * I.nb, nbp = (size_t)I.T * I.nl;
+  CK(cudaStreamSynchronize(h->stream));
+  if (p) CK(cudaMemcpy(p, D.G + F_P * D.NGP + I.gpo, ngp * 8, cudaMemcpyDeviceToHost));
+  if (q) CK(cudaMemcpy(q, D.G + F_Q * D.NGP + I.gpo, ngp * 8, cudaMemcpyDeviceToHost));
+  if (w) CK(cudaMemcpy(w, D.U + FU_W * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost));
+  if (theta) CK(cudaMemcpy(theta, D.U + FU_TH * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost));
+  if (pf) {
+    std::vector<double> tmp(nbp);
+    for (int r = 0; r < 4; ++r) {
+      CK(cudaMemcpy(tmp.data(), D.BA + r * D.NBP + I.bpo, nbp * 8, cudaMemcpyDeviceToHost));
+      for (size_t j = 0; j < nbp; ++j) pf[j * 4 + r] = tmp[j];
+    }
+  }
+  if (u_on) {
+    std::vector<double> tmp(ngp);
+    CK(cudaMemcpy(tmp.data(), D.G + F_UON * D.NGP + I.gpo, ngp * 8, cudaMemcpyDeviceToHost));
+    for (size_t j = 0; j < ngp; ++j) u_on[j] = tmp[j] != 0.0 ? 1 : 0;
+  }
+  return UCAC_OK;
+}
+
+size_t ucac_state_size(const ucac_handle *h, int32_t k) {
+  if (!h || k < 0 || k >= h->K) return 0;
+  const HInst &I = h->hi[k];
+  return (size_t)I.T * ((size_t)(NGF + 3 * NGR) * I.ng + (size_t)(NBF + 3 * NBR) * I.nl + (size_t)NUF * I.nb) +
+         NCTRL;
+}
+
+namespace {
+// (device pointer, element count) of each canonical state segment of instance k
+std::vector<std::pair<double *, size_t>> state_segments(ucac_handle *h, int k) {
+  const HInst &I = h->hi[k];
+  const Dev &D = h->dev;
+  const size_t ngp = (size_t)I.T * I.ng, nbp = (size_t)I.T * I.nl, nup = (size_t)I.T * I.nb;
+  std::vector<std::pair<double *, size_t>> s;
+  for (int f = 0; f < NGF; ++f) s.push_back({D.G + f * D.NGP + I.gpo, ngp});
+  for (double *arr : {D.GY, D.GZ, D.GL})
+    for (int r = 0; r < NGR; ++r) s.push_back({arr + r * D.NGP + I.gpo, ngp});
+  for (int f = 0; f < NBF; ++f) s.push_back({D.B + f * D.NBP + I.bpo, nbp});
+  for (double *arr : {D.BY, D.BZ, D.BL})
+    for (int r = 0; r < NBR; ++r) s.push_back({arr + r * D.NBP + I.bpo, nbp});
+  for (int f = 0; f < NUF; ++f) s.push_back({D.U + f * D.NUP + I.upo, nup});
+  s.push_back({D.ctrl + (size_t)k * NCTRL, (size_t)NCTRL});
+  return s;
+}
+}  // namespace
+
+int ucac_state_export(const ucac_handle *hc, int32_t k, double *buf, size_t n) {
+  ucac_handle *h = const_cast<ucac_handle *>(hc);
+  if (!h || !buf || k < 0 || k >= h->K || n < ucac_state_size(h, k)) return fail(h, UCAC_E_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  size_t o = 0;
+  for (auto &sg : state_segments(h, k)) {
+    CK(cudaMemcpy(buf + o, sg.first, sg.second * 8, cudaMemcpyDeviceToHost));
+    o += sg.second;
+  }
+  return UCAC_OK;
+}
+
+int ucac_state_import(ucac_handle *h, int32_t k, const double *buf, size_t n) {
+  if (!h || !buf || k < 0 || k >= h->K || n < ucac_state_size(h, k)) return fail(h, UCAC_E_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  size_t o = 0;
+  for (auto &sg : state_segments(h, k)) {
+    CK(cudaMemcpy(sg.first, buf + o, sg.second * 8, cudaMemcpyHostToDevice));
+    o += sg.second;
+  }
+  k_prep_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, h->stream>>>(h->dev);
+  k_prep_branch<BS_BP><<<h->nblk_bp, BS_BP, 0, h->stream>>>(h->dev);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return UCAC_OK;
+}
+
+int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
+  if (!h || !ms || n_sweeps < 1) return fail(h, UCAC_E_ARG, "bad arguments");
+  cudaEvent_t ev[UCAC_N_KERNELS + 1];
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  double acc[UCAC_N_KERNELS] = {0};
+  const Dev &D = h->dev;
+  cudaStream_t s = h->stream;
+  for (int it = 0; it < n_sweeps; ++it) {
+    CK(cudaEventRecord(ev[0], s));
+    k_ucdp<BS_GEN><<<h->nblk_gen, BS_GEN, 0, s>>>(D);
+    CK(cudaEventRecord(ev[1], s));
+    k_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
+    CK(cudaEventRecord(ev[2], s));
+    k_branch<BS_BP><<<h->nblk_bp, BS_BP, 0, s>>>(D);
+    CK(cudaEventRecord(ev[3], s));
+    k_bus<BS_UP><<<h->nblk_up, BS_UP, 0, s>>>(D);
+    CK(cudaEventRecord(ev[4], s));
+    k_ucbar<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
+    CK(cudaEventRecord(ev[5], s));
+    k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(D);
+    CK(cudaEventRecord(ev[6], s));
+    CK(cudaEventSynchronize(ev[6]));
+    for (int j = 0; j < UCAC_N_KERNELS; ++j) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, ev[j], ev[j + 1]));
+      acc[j] += t;
+    }
+  }
+  CK(cudaGetLastError());
+  for (auto &e : ev) cudaEventDestroy(e);
+  for (int j = 0; j < UCAC_N_KERNELS; ++j) ms[j] = acc[j] / n_sweeps;
+  return UCAC_OK;
+}
+
+const char *ucac_kernel_name(int32_t k) { return (k >= 0 && k < UCAC_N_KERNELS) ? kKernelNames[k] : ""; }
+
+size_t ucac_ucdp_workspace_bytes(int32_t n_gen, int32_t T) {
+  if (n_gen < 1 || T < 1) return 0;
+  const size_t ng = (size_t)n_gen, t = (size_t)T;
+  const size_t a = ((4 * t * ng + 2 * (t + 1) * ng) * 8 + 255) / 256 * 256;
+  return a + 2 * t * ng;
+}
+
+int ucac_ucdp(int32_t n_gen, int32_t T, double rho_uc, const double *tau_on, const double *tau_su,
+              const double *tau_sd, const double *c0, const double *c_su, const double *c_sd, const int32_t *TU,
+              const int32_t *TD, const int32_t *u0, const int32_t *K0, int8_t *u_on, double *cost, void *workspace,
+              size_t workspace_bytes, void *cuda_stream) {
+  ucac_handle *h = nullptr;
+  if (n_gen < 1 || T < 1 || !tau_on || !tau_su || !tau_sd || !c0 || !c_su || !c_sd || !TU || !TD || !u0 || !K0 ||
+      !u_on || !cost || !workspace || workspace_bytes < ucac_ucdp_workspace_bytes(n_gen, T) || !(rho_uc > 0))
+    return fail(nullptr, UCAC_E_ARG, "ucac_ucdp: bad arguments");
+  const size_t ng = (size_t)n_gen, t = (size_t)T;
+  double *L = (double *)workspace;
+  double *C = L + 4 * t * ng;
+  unsigned char *Dd = (unsigned char *)workspace + ((4 * t * ng + 2 * (t + 1) * ng) * 8 + 255) / 256 * 256;
+  const int bs = 128;
+  k_ucdp_standalone<<<(n_gen + bs - 1) / bs, bs, 0, (cudaStream_t)cuda_stream>>>(
+      n_gen, T, rho_uc, tau_on, tau_su, tau_sd, c0, c_su, c_sd, TU, TD, u0, K0, u_on, cost, L, C, Dd);
+  CK(cudaGetLastError());
+  return UCAC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- FP64 probe
+namespace {
+__global__ void __launch_bounds__(256) k_fp64_probe(double *sink, int iters, double s) {
+  double a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = 1.0 + 1e-3 * (threadIdx.x + j);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], s, 1e-9);
+  }
+  double t = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) t += a[j];
+  if (t == 1234.5678) sink[0] = t;  // keeps the chains live
+}
+}  // namespace
+
+extern "C" int ucac_probe_fp64(int32_t reps, void *cuda_stream, double *flops) {
+  ucac_handle *h = nullptr;
+  if (!flops || reps < 1) return fail(nullptr, UCAC_E_ARG, "bad arguments");
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double *sink = nullptr;
+  CK(cudaMalloc(&sink, 8));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  k_fp64_probe<<<blocks, threads, 0, s>>>(sink, 64, 0.999999);  // warm-up
+  double best = 0.0;
+  for (int r = 0; r < reps; ++r) {
+    CK(cudaEventRecord(e0, s));
+    k_fp64_probe<<<blocks, threads, 0, s>>>(sink, iters, 0.999999);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    const double f = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3);
+    best = std::max(best, f);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  *flops = best;
+  return UCAC_OK;
+}
+
+extern "C" void ucac_destroy(ucac_handle *h) {
+  if (!h) return;
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->arena) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->arena);
+  }
+  delete h;
+}
+
+extern "C" const char *ucac_last_error(const ucac_handle *h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}

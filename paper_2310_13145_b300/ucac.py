@@ -1,0 +1,275 @@
+"""Thin ctypes binding of the ucac C ABI (include/ucac.h), same names.
+
+Argument marshalling only: every step of a sweep runs in the library's CUDA
+kernels.  Loading fails loudly when libucac.so is missing; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libucac.so")
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+UCAC_OK, UCAC_CONVERGED = 0, 1
+UCAC_E_ARG, UCAC_E_GRID, UCAC_E_CUDA, UCAC_E_NEWTON_MAXIT, UCAC_E_NAN, UCAC_E_DIVERGED = -1, -2, -3, -4, -5, -6
+UCAC_N_KERNELS = 6
+
+# symbols declared in include/ucac.h
+EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_instances", "ucac_iterate",
+           "ucac_enqueue_sweeps", "ucac_residuals", "ucac_solution", "ucac_state_size", "ucac_state_export",
+           "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp",
+           "ucac_probe_fp64", "ucac_destroy", "ucac_last_error"]
+
+
+class ucac_grid(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_branch", C.c_int32), ("n_gen", C.c_int32), ("T", C.c_int32),
+                ("ref_bus", C.c_int32)] + \
+        [(n, _dp) for n in ("Pd", "Qd", "Gs", "Bs", "Vmin", "Vmax")] + \
+        [(n, _ip) for n in ("br_from", "br_to")] + \
+        [(n, _dp) for n in ("br_r", "br_x", "br_b", "br_rate")] + \
+        [("gen_bus", _ip)] + \
+        [(n, _dp) for n in ("Pmin", "Pmax", "Qmin", "Qmax", "c2", "c1", "c0", "c_su", "c_sd", "RU", "RD", "SU", "SD")] + \
+        [(n, _ip) for n in ("TU", "TD", "u0", "L0", "F0")] + \
+        [("p0", _dp), ("base_mva", C.c_double)]
+
+
+class ucac_rho(C.Structure):
+    _fields_ = [("pq", C.c_double), ("va", C.c_double), ("uc", C.c_double)]
+
+
+class ucac_params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("eps_in", "eps_out", "tau", "theta", "beta0", "lambda_max", "eta",
+                                          "omega_rel", "c_init_rel", "c_max_rel")] + \
+        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "check_every")]
+
+
+class ucac_report(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("r_p", "r_d", "z_norm", "z_rms", "inf_norm_viol", "objective", "beta")] + \
+        [(n, C.c_int64) for n in ("sweeps", "outer", "newton", "al")] + \
+        [("status", C.c_int32), ("n_newton_maxit", C.c_int32)]
+
+
+class UcacError(RuntimeError):
+    pass
+
+
+def lib():
+    """Loads libucac.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise UcacError(f"{LIB_PATH} not found: build it with paper_2310_13145_b300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.ucac_default_params.argtypes = [C.POINTER(ucac_params)]
+        L.ucac_default_params.restype = None
+        L.ucac_create.argtypes = [C.POINTER(ucac_grid), C.c_int32, ucac_rho, C.POINTER(ucac_params), vp,
+                                  C.POINTER(vp)]
+        L.ucac_create_batch.argtypes = [C.POINTER(C.POINTER(ucac_grid)), _ip, C.POINTER(ucac_rho), C.c_int32,
+                                        C.POINTER(ucac_params), vp, C.POINTER(vp)]
+        L.ucac_instances.argtypes = [vp]
+        L.ucac_instances.restype = C.c_int32
+        L.ucac_iterate.argtypes = [vp, C.c_int32]
+        L.ucac_enqueue_sweeps.argtypes = [vp, C.c_int32]
+        L.ucac_residuals.argtypes = [vp, C.c_int32, C.POINTER(ucac_report)]
+        L.ucac_solution.argtypes = [vp, C.c_int32, _dp, _dp, _dp, _dp, _dp, C.POINTER(C.c_uint8)]
+        L.ucac_state_size.argtypes = [vp, C.c_int32]
+        L.ucac_state_size.restype = C.c_size_t
+        L.ucac_state_export.argtypes = [vp, C.c_int32, _dp, C.c_size_t]
+        L.ucac_state_import.argtypes = [vp, C.c_int32, _dp, C.c_size_t]
+        L.ucac_kernel_times.argtypes = [vp, C.c_int32, _dp]
+        L.ucac_kernel_name.argtypes = [C.c_int32]
+        L.ucac_kernel_name.restype = C.c_char_p
+        L.ucac_ucdp_workspace_bytes.argtypes = [C.c_int32, C.c_int32]
+        L.ucac_ucdp_workspace_bytes.restype = C.c_size_t
+        L.ucac_ucdp.argtypes = [C.c_int32, C.c_int32, C.c_double] + [vp] * 12 + [vp, C.c_size_t, vp]
+        L.ucac_probe_fp64.argtypes = [C.c_int32, vp, _dp]
+        L.ucac_destroy.argtypes = [vp]
+        L.ucac_destroy.restype = None
+        L.ucac_last_error.argtypes = [vp]
+        L.ucac_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc, h=None):
+    if rc < 0:
+        msg = lib().ucac_last_error(h)
+        raise UcacError(f"ucac error {rc}: {msg.decode() if msg else ''}")
+    return rc
+
+
+def ucac_default_params(**kw) -> ucac_params:
+    p = ucac_params()
+    lib().ucac_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _grid_struct(g, keep):
+    def dd(a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(_dp)
+
+    def ii(a):
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        keep.append(a)
+        return a.ctypes.data_as(_ip)
+
+    s = ucac_grid()
+    s.n_bus, s.n_branch, s.n_gen, s.T, s.ref_bus = g.n_bus, g.n_branch, g.n_gen, g.T, g.ref_bus
+    for n in ("Pd", "Qd", "Gs", "Bs", "Vmin", "Vmax", "br_r", "br_x", "br_b", "br_rate", "Pmin", "Pmax", "Qmin",
+              "Qmax", "c2", "c1", "c0", "c_su", "c_sd", "RU", "RD", "SU", "SD", "p0"):
+        setattr(s, n, dd(getattr(g, n)))
+    for n in ("br_from", "br_to", "gen_bus", "TU", "TD", "u0", "L0", "F0"):
+        setattr(s, n, ii(getattr(g, n)))
+    s.base_mva = g.base_mva
+    return s
+
+
+def ucac_create_batch(grids, horizons=None, rhos=None, params=None, stream=0):
+    """Returns an opaque handle (c_void_p) for a batch of synth.Grid-like instances."""
+    keep = []
+    n = len(grids)
+    structs = [_grid_struct(g, keep) for g in grids]
+    arr = (C.POINTER(ucac_grid) * n)(*[C.pointer(s) for s in structs])
+    hz = np.ascontiguousarray([g.T if horizons is None else horizons[k] for k, g in enumerate(grids)], np.int32)
+    rs = (ucac_rho * n)(*[ucac_rho(*(g.rho if rhos is None else rhos[k])) for k, g in enumerate(grids)])
+    out = C.c_void_p()
+    p = C.byref(params) if params is not None else None
+    _check(lib().ucac_create_batch(arr, hz.ctypes.data_as(_ip), rs, n, p, C.c_void_p(stream), C.byref(out)))
+    return out
+
+
+def ucac_create(grid, horizon=None, rho=None, params=None, stream=0):
+    return ucac_create_batch([grid], None if horizon is None else [horizon], None if rho is None else [rho],
+                             params, stream)
+
+
+def ucac_instances(h) -> int:
+    return lib().ucac_instances(h)
+
+
+def ucac_iterate(h, n_sweeps: int) -> int:
+    return _check(lib().ucac_iterate(h, int(n_sweeps)), h)
+
+
+def ucac_enqueue_sweeps(h, n_sweeps: int) -> int:
+    return _check(lib().ucac_enqueue_sweeps(h, int(n_sweeps)), h)
+
+
+def ucac_residuals(h, instance: int = 0) -> dict:
+    r = ucac_report()
+    _check(lib().ucac_residuals(h, int(instance), C.byref(r)), h)
+    return {f: getattr(r, f) for f, _ in ucac_report._fields_}
+
+
+def ucac_solution(h, instance: int, T: int, ng: int, nb: int, nl: int) -> dict:
+    p = np.zeros((T, ng)); q = np.zeros((T, ng)); w = np.zeros((T, nb)); th = np.zeros((T, nb))
+    pf = np.zeros((T, nl, 4)); u = np.zeros((T, ng), np.uint8)
+    _check(lib().ucac_solution(h, int(instance), p.ctypes.data_as(_dp), q.ctypes.data_as(_dp), w.ctypes.data_as(_dp),
+                               th.ctypes.data_as(_dp), pf.ctypes.data_as(_dp),
+                               u.ctypes.data_as(C.POINTER(C.c_uint8))), h)
+    return {"p": p, "q": q, "w": w, "theta": th, "pf": pf, "u_on": u}
+
+
+def ucac_state_size(h, instance: int = 0) -> int:
+    return int(lib().ucac_state_size(h, int(instance)))
+
+
+def ucac_state_export(h, instance: int = 0) -> np.ndarray:
+    n = ucac_state_size(h, instance)
+    buf = np.empty(n, np.float64)
+    _check(lib().ucac_state_export(h, int(instance), buf.ctypes.data_as(_dp), n), h)
+    return buf
+
+
+def ucac_state_import(h, instance: int, buf: np.ndarray) -> None:
+    buf = np.ascontiguousarray(buf, np.float64)
+    _check(lib().ucac_state_import(h, int(instance), buf.ctypes.data_as(_dp), buf.size), h)
+
+
+def ucac_kernel_times(h, n_sweeps: int = 5) -> dict:
+    ms = np.zeros(UCAC_N_KERNELS)
+    _check(lib().ucac_kernel_times(h, int(n_sweeps), ms.ctypes.data_as(_dp)), h)
+    return {ucac_kernel_name(k): float(ms[k]) for k in range(UCAC_N_KERNELS)}
+
+
+def ucac_kernel_name(k: int) -> str:
+    return lib().ucac_kernel_name(int(k)).decode()
+
+
+def ucac_ucdp_workspace_bytes(n_gen: int, T: int) -> int:
+    return int(lib().ucac_ucdp_workspace_bytes(int(n_gen), int(T)))
+
+
+def ucac_ucdp(n_gen, T, rho_uc, tau_on, tau_su, tau_sd, c0, c_su, c_sd, TU, TD, u0, K0, u_on, cost, workspace,
+              workspace_bytes, stream=0):
+    """All array arguments are device pointers (ints), e.g. torch_tensor.data_ptr()."""
+    vp = C.c_void_p
+    return _check(lib().ucac_ucdp(int(n_gen), int(T), float(rho_uc), *[vp(int(x)) for x in
+                                  (tau_on, tau_su, tau_sd, c0, c_su, c_sd, TU, TD, u0, K0, u_on, cost)],
+                                  vp(int(workspace)), int(workspace_bytes), vp(int(stream))))
+
+
+def ucac_probe_fp64(reps: int = 5, stream=0) -> float:
+    f = C.c_double()
+    _check(lib().ucac_probe_fp64(int(reps), C.c_void_p(stream), C.byref(f)))
+    return f.value
+
+
+def ucac_destroy(h) -> None:
+    if h:
+        lib().ucac_destroy(h)
+
+
+def ucac_last_error(h=None) -> str:
+    m = lib().ucac_last_error(h)
+    return m.decode() if m else ""
+
+
+class Handle:
+    """RAII wrapper: a batch of instances on the current CUDA device."""
+
+    def __init__(self, grids, params=None, stream=0, horizons=None):
+        self.grids = list(grids)
+        self.h = ucac_create_batch(self.grids, horizons=horizons, params=params, stream=stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ucac_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self, n):
+        return ucac_iterate(self.h, n)
+
+    def enqueue(self, n):
+        return ucac_enqueue_sweeps(self.h, n)
+
+    def residuals(self, k=0):
+        return ucac_residuals(self.h, k)
+
+    def export(self, k=0):
+        return ucac_state_export(self.h, k)
+
+    def import_(self, k, buf):
+        ucac_state_import(self.h, k, buf)
+
+    def kernel_times(self, n=5):
+        return ucac_kernel_times(self.h, n)

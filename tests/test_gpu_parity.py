@@ -1,0 +1,136 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Lockstep: the oracle is given the library's exported iterate, runs one sweep,
+and the two results are compared field by field (continuous fields within a
+normwise relative 1e-9, UC decisions bit for bit).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2310_13145_b300 import synth
+from tests._helpers import compare_states
+
+pytestmark = pytest.mark.gpu
+
+
+def _dims(g):
+    return g.T, g.n_gen, g.n_branch, g.n_bus
+
+
+def _lockstep(ucac, grids, sweeps, params=None, oparams=None, warm=0, check_instances=None):
+    h = ucac.Handle(grids, params=params)
+    if warm:
+        h.enqueue(warm)
+    orcs = {}
+    ks = range(len(grids)) if check_instances is None else check_instances
+    for k in ks:
+        g = grids[k]
+        op = oparams(g) if oparams else None
+        orcs[k] = oracle.Oracle(g, op)
+    worst = 0.0
+    for s in range(sweeps):
+        pre = {k: h.export(k) for k in ks}
+        h.enqueue(1)
+        for k in ks:
+            o = orcs[k]
+            o.set_state(pre[k])
+            o.sweep()
+            bad = compare_states(h.export(k), o.state_vector(), grids[k])
+            assert not bad, f"sweep {s} instance {k}: {bad[:6]}"
+    h.close()
+
+
+def test_cold_start_matches(ucac_mod):
+    g = synth.config_instances("c1_9bus_T6")[0]
+    h = ucac_mod.Handle([g])
+    o = oracle.Oracle(g)
+    bad = compare_states(h.export(0), o.state_vector(), g, rtol=1e-14)
+    assert not bad, bad
+    h.close()
+
+
+def test_lockstep_9bus(ucac_mod):
+    g = synth.config_instances("c1_9bus_T6")[0]
+    _lockstep(ucac_mod, [g], 40)
+
+
+def test_lockstep_9bus_late_with_outer_updates(ucac_mod):
+    # small inner cap so that outer updates (lambda, beta) happen every few sweeps
+    g = synth.config_instances("c1_9bus_T6")[0]
+    p = ucac_mod.ucac_default_params(L_max=4)
+    _lockstep(ucac_mod, [g], 25, params=p, oparams=lambda gg: oracle.default_params(rho=gg.rho, L_max=4), warm=60)
+
+
+def test_lockstep_118bus_batch(ucac_mod):
+    grids = synth.config_instances("c2_118bus_T24x3")
+    _lockstep(ucac_mod, grids, 4, warm=10)
+
+
+def test_lockstep_ragged_small_instances(ucac_mod):
+    # uneven batch: sizes that leave partial blocks in every kernel
+    grids = [synth.make_grid(n, nl, max(1, n // 3), T, seed=50 + n, rho=synth.RHO_TABLE["case300"])
+             for n, nl, T in ((2, 1, 1), (5, 5, 3), (13, 16, 7), (31, 45, 5))]
+    _lockstep(ucac_mod, grids, 6, warm=3)
+
+
+def test_batch_equals_single(ucac_mod):
+    grids = synth.config_instances("c2_118bus_T24x3")
+    hb = ucac_mod.Handle(grids)
+    hb.enqueue(7)
+    for k, g in enumerate(grids):
+        hs = ucac_mod.Handle([g])
+        hs.enqueue(7)
+        assert np.array_equal(hs.export(0), hb.export(k)), k
+        hs.close()
+    hb.close()
+
+
+def test_export_import_resume_is_bit_identical(ucac_mod):
+    g = synth.config_instances("c1_9bus_T6")[0]
+    h = ucac_mod.Handle([g])
+    h.enqueue(5)
+    s5 = h.export(0)
+    h.enqueue(6)
+    s11 = h.export(0)
+    h2 = ucac_mod.Handle([g])
+    h2.import_(0, s5)
+    h2.enqueue(6)
+    assert np.array_equal(h2.export(0), s11)
+    h.close()
+    h2.close()
+
+
+def test_residual_record_matches_oracle(ucac_mod):
+    g = synth.config_instances("c1_9bus_T6")[0]
+    h = ucac_mod.Handle([g])
+    h.enqueue(20)
+    pre = h.export(0)
+    h.enqueue(1)
+    r = h.residuals(0)
+    o = oracle.Oracle(g)
+    o.set_state(pre)
+    o.sweep()
+    ro = o.residuals()
+    for a, b in (("r_p", "r_p"), ("r_d", "r_d"), ("z_norm", "z_norm"), ("z_rms", "z_rms"),
+                 ("inf_norm_viol", "inf_norm"), ("objective", "objective")):
+        assert abs(r[a] - ro[b]) <= 1e-9 * max(abs(ro[b]), 1e-30), (a, r[a], ro[b])
+    assert r["n_newton_maxit"] == 0
+    h.close()
+
+
+def test_full_size_2000bus_one_instance_lockstep(ucac_mod):
+    """Largest workload in the bench's launch configuration (16 scenarios in
+    one batch); one scenario's full sweep is recomputed by the oracle."""
+    grids = synth.config_instances("c5_2000bus_T24x16")
+    h = ucac_mod.Handle(grids)
+    h.enqueue(3)
+    k = 5
+    pre = h.export(k)
+    h.enqueue(1)
+    o = oracle.Oracle(grids[k])
+    o.set_state(pre)
+    o.sweep()
+    bad = compare_states(h.export(k), o.state_vector(), grids[k])
+    assert not bad, bad[:6]
+    h.close()
