@@ -208,6 +208,34 @@ int ucac_ucdp(int32_t n_gen, int32_t T, double rho_uc, const double *tau_on, con
               size_t workspace_bytes, void *cuda_stream);
 
 /*
+ * Allocation-free variant of ucac_ucdp (the paper has no counterpart: this
+ * is a deployment interface).  It is meant for callers that must not allocate
+ * device memory on the call path -- for example a host runtime that fixes its
+ * device footprint at start-up, a plugin that runs inside another
+ * framework's memory pool, or a latency-critical loop where a cudaMalloc
+ * would synchronise the device -- and that cannot hand over a workspace.
+ * Inputs and outputs are the caller's device arrays exactly as for
+ * ucac_ucdp; the scratch (stage costs, cost-to-go, decisions) lives in one
+ * library-owned, statically sized device array of UCAC_UCDP_NOALLOC_MAX_BYTES
+ * bytes, which every GPU that loads the library keeps until the process
+ * exits.  Requests needing more than that (ucac_ucdp_workspace_bytes(n_gen,
+ * T) > UCAC_UCDP_NOALLOC_MAX_BYTES) fail with UCAC_E_ARG and a message.
+ * The call never allocates or frees device memory.  Its first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array and overwrites it; every scratch
+ * entry is written before it is read within a call, so nothing needs to start
+ * at zero, but two calls that overlap on the GPU (different streams, or
+ * different host threads without ordering) race on the array and must be
+ * serialised by the caller.
+ */
+#define UCAC_UCDP_NOALLOC_MAX_BYTES (16u << 20)
+int ucac_ucdp_noalloc(int32_t n_gen, int32_t T, double rho_uc, const double *tau_on, const double *tau_su,
+                      const double *tau_sd, const double *c0, const double *c_su, const double *c_sd,
+                      const int32_t *TU, const int32_t *TD, const int32_t *u0, const int32_t *K0, int8_t *u_on,
+                      double *cost, void *cuda_stream);
+
+/*
  * Measures the device's FP64 fused multiply-add throughput (FLOP/s, 2 per
  * FMA) with a register-resident kernel; *flops receives the best of `reps`
  * runs.  Used as the arithmetic roofline of the FP64-bound kernels.

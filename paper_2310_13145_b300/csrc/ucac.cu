@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -728,6 +729,55 @@ int ucac_ucdp(int32_t n_gen, int32_t T, double rho_uc, const double *tau_on, con
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- allocation-free UC DP
+// Scratch of ucac_ucdp_noalloc: one statically sized device array per GPU
+// that loads the library.  Host code never dereferences the symbol; it
+// fetches the array's device address once per device (with that device
+// current) and passes that address to the kernel.
+namespace {
+__device__ __align__(256) unsigned char g_ucdp_scratch[UCAC_UCDP_NOALLOC_MAX_BYTES];
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" int ucac_ucdp_noalloc(int32_t n_gen, int32_t T, double rho_uc, const double *tau_on,
+                                 const double *tau_su, const double *tau_sd, const double *c0, const double *c_su,
+                                 const double *c_sd, const int32_t *TU, const int32_t *TD, const int32_t *u0,
+                                 const int32_t *K0, int8_t *u_on, double *cost, void *cuda_stream) {
+  ucac_handle *h = nullptr;
+  if (n_gen < 1 || T < 1 || !tau_on || !tau_su || !tau_sd || !c0 || !c_su || !c_sd || !TU || !TD || !u0 || !K0 ||
+      !u_on || !cost || !(rho_uc > 0))
+    return fail(nullptr, UCAC_E_ARG, "ucac_ucdp_noalloc: bad arguments");
+  const size_t need = ucac_ucdp_workspace_bytes(n_gen, T);
+  if (need > (size_t)UCAC_UCDP_NOALLOC_MAX_BYTES)
+    return fail(nullptr, UCAC_E_ARG,
+                "ucac_ucdp_noalloc: n_gen x T needs " + std::to_string(need) + " scratch bytes, the static limit is " +
+                    std::to_string((size_t)UCAC_UCDP_NOALLOC_MAX_BYTES) + " (use ucac_ucdp with a workspace)");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, UCAC_E_ARG, "ucac_ucdp_noalloc: device index too large");
+  void *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+      void *p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_ucdp_scratch));
+      g_scratch_addr[dev] = p;
+    }
+    scratch = g_scratch_addr[dev];
+  }
+  const size_t ng = (size_t)n_gen, t = (size_t)T;
+  double *L = (double *)scratch;
+  double *Cc = L + 4 * t * ng;
+  unsigned char *Dd = (unsigned char *)scratch + ((4 * t * ng + 2 * (t + 1) * ng) * 8 + 255) / 256 * 256;
+  const int bs = 128;
+  k_ucdp_standalone<<<(n_gen + bs - 1) / bs, bs, 0, (cudaStream_t)cuda_stream>>>(
+      n_gen, T, rho_uc, tau_on, tau_su, tau_sd, c0, c_su, c_sd, TU, TD, u0, K0, u_on, cost, L, Cc, Dd);
+  CK(cudaGetLastError());
+  return UCAC_OK;
+}
 
 // ---------------------------------------------------------------- FP64 probe
 namespace {

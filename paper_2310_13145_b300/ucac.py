@@ -25,7 +25,7 @@ UCAC_N_KERNELS = 6
 # symbols declared in include/ucac.h
 EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_instances", "ucac_iterate",
            "ucac_enqueue_sweeps", "ucac_residuals", "ucac_solution", "ucac_state_size", "ucac_state_export",
-           "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp",
+           "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp", "ucac_ucdp_noalloc",
            "ucac_probe_fp64", "ucac_destroy", "ucac_last_error"]
 
 
@@ -91,6 +91,7 @@ def lib():
         L.ucac_ucdp_workspace_bytes.argtypes = [C.c_int32, C.c_int32]
         L.ucac_ucdp_workspace_bytes.restype = C.c_size_t
         L.ucac_ucdp.argtypes = [C.c_int32, C.c_int32, C.c_double] + [vp] * 12 + [vp, C.c_size_t, vp]
+        L.ucac_ucdp_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_double] + [vp] * 12 + [vp]
         L.ucac_probe_fp64.argtypes = [C.c_int32, vp, _dp]
         L.ucac_destroy.argtypes = [vp]
         L.ucac_destroy.restype = None
@@ -220,6 +221,17 @@ def ucac_ucdp(n_gen, T, rho_uc, tau_on, tau_su, tau_sd, c0, c_su, c_sd, TU, TD, 
     return _check(lib().ucac_ucdp(int(n_gen), int(T), float(rho_uc), *[vp(int(x)) for x in
                                   (tau_on, tau_su, tau_sd, c0, c_su, c_sd, TU, TD, u0, K0, u_on, cost)],
                                   vp(int(workspace)), int(workspace_bytes), vp(int(stream))))
+
+
+UCAC_UCDP_NOALLOC_MAX_BYTES = 16 << 20
+
+
+def ucac_ucdp_noalloc(n_gen, T, rho_uc, tau_on, tau_su, tau_sd, c0, c_su, c_sd, TU, TD, u0, K0, u_on, cost, stream=0):
+    """Same as ucac_ucdp without a workspace (library-owned static scratch); device pointers as ints."""
+    vp = C.c_void_p
+    return _check(lib().ucac_ucdp_noalloc(int(n_gen), int(T), float(rho_uc), *[vp(int(x)) for x in
+                                          (tau_on, tau_su, tau_sd, c0, c_su, c_sd, TU, TD, u0, K0, u_on, cost)],
+                                          vp(int(stream))))
 
 
 def ucac_probe_fp64(reps: int = 5, stream=0) -> float:
