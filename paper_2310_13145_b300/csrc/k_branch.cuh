@@ -220,7 +220,7 @@ __device__ __forceinline__ bool chol8(double (&A)[8][8], double (&b)[8]) {
   return true;
 }
 
-// Inner solve (same steps as the oracle's): returns Newton iterations used;
+// Inner solve (the damped projected Newton method described above): returns Newton iterations used;
 // conv = true when the stationarity test or the final-step test ended it.
 __device__ __forceinline__ int br_inner(const BrK &K, const BrP &P, double (&v)[8], int K_N, double omega,
                                         double &Delta, bool &conv) {
