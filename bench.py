@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ucac", choices=["ucac", "reference"])
     ap.add_argument("--workload", default="c5_2000bus_T24x16", choices=sorted(synth.CONFIGS))
+    ap.add_argument("--instances", type=int, default=None, help="use only the first N instances (profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -188,7 +189,7 @@ def reference_arm(a, grids):
 def main():
     a = parse()
     rank, world, local = dist_info()
-    grids = synth.config_instances(a.workload)
+    grids = synth.config_instances(a.workload, a.instances)
     if a.impl == "reference":
         reference_arm(a, grids)
         return
