@@ -76,6 +76,7 @@ struct Dev {
   const double *Gs, *Bs;
   const int *inc_ptr, *inc_br, *inc_side;  // CSR over global buses; branch index local
   const int *gen_ptr, *gen_idx;            // CSR over global buses; generator index local
+  const int *bus_order;                    // [NB] per instance: local buses sorted by (degree, generators)
   long long NUP;
   const double *Pd, *Qd;
   double *U;  // [NUF][NUP]
@@ -85,7 +86,8 @@ struct Dev {
   long long *stat;    // [K][4]: sweeps, newton, al, capped
   double *part_up;    // [nblk_up][NQ]
   double *part_gp;    // [nblk_gp][NQ]
-  long long *part_bp; // [nblk_bp][3]
+  long long *bstat;   // [K][3]: Newton iterations, AL rounds, capped solves (line kernel, per sweep)
+  unsigned long long *bp_counter;  // work counter of the persistent line kernel
   // UC dynamic-program scratch: stage costs, cost-to-go, decisions
   double *dpL;        // [4][T][ng] per instance, instance slice at 4*gpo
   double *dpC;        // [2][T+1][ng] per instance, slice at 2*(gpo+go)

@@ -16,11 +16,17 @@
 // the step (see br_inner).  The multipliers mu and the penalty c persist per
 // (t, line) across sweeps, as does v (the warm start).
 //
-// B300 mapping: one thread per branch-period; the 8x8 Hessian, its Cholesky
-// factor and all vectors are indexed only by compile-time constants (fully
-// unrolled loops, the active set applied by masking rather than by
-// compacting indices), so they stay in registers.  The kernel is bound by the
-// FP64 pipe, not memory: its loads/stores are a few hundred bytes per solve.
+// B300 mapping: a persistent kernel.  Every lane owns one line solve at a
+// time; each pass of the main loop performs one Newton iteration for every
+// lane (so the warp executes the same instructions whatever the phase of
+// each solve), and a lane whose solve has finished fetches the next
+// branch-period from a global counter (warp-aggregated atomic).  Lanes thus
+// never wait for the slowest solve of their warp, which is what idles half of
+// a statically mapped warp: iteration counts differ from solve to solve.  The
+// 8x8 Hessian, its Cholesky factor and all vectors are indexed only by
+// compile-time constants (fully unrolled loops, the active set applied by
+// masking), so they stay in registers.  The kernel is bound by the FP64 pipe,
+// not memory: its loads/stores are a few hundred bytes per solve.
 #pragma once
 #include "common.cuh"
 
@@ -220,238 +226,268 @@ __device__ __forceinline__ bool chol8(double (&A)[8][8], double (&b)[8]) {
   return true;
 }
 
-// Inner solve (the damped projected Newton method described above): returns Newton iterations used;
-// conv = true when the stationarity test or the final-step test ended it.
-__device__ __forceinline__ int br_inner(const BrK &K, const BrP &P, double (&v)[8], int K_N, double omega,
-                                        double &Delta, bool &conv) {
-  double g[8], H[8][8];
-  double f = br_phi(K, P, v);
-  br_derivs(K, P, v, g, H);
-  int it = 0;
-  conv = false;
-  for (; it < K_N; ++it) {
-    double pg = 0.0, hmax = 0.0, vmax = 0.0, eps = 0.0;
+// One iteration of the inner solve (projected Newton with an epsilon-active
+// set and a trust radius):
+//   1. stationarity |P(v - g) - v|_inf <= omega -> converged;
+//   2. active set: within eps of a bound with the gradient pointing out
+//      (eps = min(1e-6, diagonally scaled projected-gradient size)); active
+//      coordinates move onto their bound;
+//   3. Newton step on the free set by Cholesky of H_FF (+ lambda I, lambda =
+//      1e-10 max diag H growing x10, only when H_FF is not positive definite);
+//   4. an undamped step <= 1e-9 (1 + |v|_inf), or one predicting a decrease
+//      <= 1e-12 (1 + |phi|), is taken as the final step -> converged;
+//   5. otherwise the step is cut to the radius Delta, projected, and accepted
+//      when actual >= 1e-4 x predicted decrease (Delta x2 after a very good
+//      radius-limited step, Delta = |s|/4 after a rejection).
+enum { NI_CONT = 0, NI_CONV = 1, NI_STOP = 2 };
+
+__device__ __forceinline__ int newton_iter(const BrK &K, const BrP &P, double (&v)[8], double &f,
+                                           const double (&g)[8], const double (&H)[8][8], double &Delta,
+                                           double omega, bool &accepted, int &counted) {
+  accepted = false;
+  counted = 0;
+  double pg = 0.0, hmax = 0.0, vmax = 0.0, eps = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    pg = fmax(pg, fabs(clampd(v[i] - g[i], K.lo[i], K.hi[i]) - v[i]));
+    hmax = fmax(hmax, H[i][i]);
+    vmax = fmax(vmax, fabs(v[i]));
+    const double di = (H[i][i] > 0.0) ? g[i] / H[i][i] : g[i];
+    eps = fmax(eps, fabs(clampd(v[i] - di, K.lo[i], K.hi[i]) - v[i]));
+  }
+  if (pg <= omega) return NI_CONV;
+  eps = fmin(eps, 1e-6);
+  bool act[8];
+  double d[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    act[i] = false;
+    d[i] = 0.0;
+    if (v[i] <= K.lo[i] + eps && g[i] > 0.0) {
+      act[i] = true;
+      d[i] = K.lo[i] - v[i];
+    } else if (v[i] >= K.hi[i] - eps && g[i] < 0.0) {
+      act[i] = true;
+      d[i] = K.hi[i] - v[i];
+    }
+  }
+  double lm = 0.0, x[8];
+  bool ok = false;
+  for (int tries = 0; tries < 40; ++tries) {
+    double A[8][8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      pg = fmax(pg, fabs(clampd(v[i] - g[i], K.lo[i], K.hi[i]) - v[i]));
-      hmax = fmax(hmax, H[i][i]);
-      vmax = fmax(vmax, fabs(v[i]));
-      const double di = (H[i][i] > 0.0) ? g[i] / H[i][i] : g[i];
-      eps = fmax(eps, fabs(clampd(v[i] - di, K.lo[i], K.hi[i]) - v[i]));
+      double r = -g[i];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (act[j]) r -= H[i][j] * d[j];
+        A[i][j] = (act[i] || act[j]) ? ((i == j) ? 1.0 : 0.0) : H[i][j];
+      }
+      if (!act[i]) A[i][i] += lm;
+      x[i] = act[i] ? d[i] : r;
     }
-    if (pg <= omega) {
-      conv = true;
+    if (chol8(A, x)) {
+      ok = true;
       break;
     }
-    eps = fmin(eps, 1e-6);
-    bool act[8];
-    double d[8];
+    lm = (lm == 0.0) ? 1e-10 * hmax : 10.0 * lm;
+  }
+  if (!ok) return NI_STOP;
+  double dn = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    d[i] = x[i];
+    dn = fmax(dn, fabs(d[i]));
+  }
+  counted = 1;
+  if (lm == 0.0) {
+    double gd = 0.0, dHd = 0.0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      act[i] = false;
-      d[i] = 0.0;
-      if (v[i] <= K.lo[i] + eps && g[i] > 0.0) {
-        act[i] = true;
-        d[i] = K.lo[i] - v[i];
-      } else if (v[i] >= K.hi[i] - eps && g[i] < 0.0) {
-        act[i] = true;
-        d[i] = K.hi[i] - v[i];
-      }
-    }
-    double lm = 0.0, x[8];
-    bool ok = false;
-    for (int tries = 0; tries < 40; ++tries) {
-      double A[8][8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        double r = -g[i];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          if (act[j]) r -= H[i][j] * d[j];
-          A[i][j] = (act[i] || act[j]) ? ((i == j) ? 1.0 : 0.0) : H[i][j];
-        }
-        if (!act[i]) A[i][i] += lm;
-        x[i] = act[i] ? d[i] : r;
-      }
-      if (chol8(A, x)) {
-        ok = true;
-        break;
-      }
-      lm = (lm == 0.0) ? 1e-10 * hmax : 10.0 * lm;
-    }
-    if (!ok) break;
-    double dn = 0.0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      d[i] = x[i];
-      dn = fmax(dn, fabs(d[i]));
-    }
-    double predN = 0.0;
-    if (lm == 0.0) {
-      double gd = 0.0, dHd = 0.0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        gd += g[i] * d[i];
-        double t = 0.0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) t += H[i][j] * d[j];
-        dHd += d[i] * t;
-      }
-      predN = -(gd + 0.5 * dHd);
-      if (dn <= 1e-9 * (1.0 + vmax) || predN <= 1e-12 * (1.0 + fabs(f))) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = clampd(v[i] + d[i], K.lo[i], K.hi[i]);
-        conv = true;
-        ++it;
-        break;
-      }
-    }
-    const double scale = (dn > Delta) ? Delta / dn : 1.0;
-    double vt[8], s[8], smax = 0.0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      vt[i] = clampd(v[i] + scale * d[i], K.lo[i], K.hi[i]);
-      s[i] = vt[i] - v[i];
-      smax = fmax(smax, fabs(s[i]));
-    }
-    double gs = 0.0, sHs = 0.0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      gs += g[i] * s[i];
+      gd += g[i] * d[i];
       double t = 0.0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) t += H[i][j] * s[j];
-      sHs += s[i] * t;
+      for (int j = 0; j < 8; ++j) t += H[i][j] * d[j];
+      dHd += d[i] * t;
     }
-    const double pred = -(gs + 0.5 * sHs);
-    const double ft = br_phi(K, P, vt);
-    const double ared = f - ft;
-    if (pred > 0.0 && ared >= 1e-4 * pred) {
+    const double predN = -(gd + 0.5 * dHd);
+    if (dn <= 1e-9 * (1.0 + vmax) || predN <= 1e-12 * (1.0 + fabs(f))) {
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = vt[i];
-      f = ft;
-      br_derivs(K, P, v, g, H);
-      if (ared >= 0.75 * pred && scale < 1.0) Delta = 2.0 * Delta;
-    } else {
-      Delta = 0.25 * smax;
-      if (Delta <= 1e-15 * (1.0 + vmax)) break;
+      for (int i = 0; i < 8; ++i) v[i] = clampd(v[i] + d[i], K.lo[i], K.hi[i]);
+      return NI_CONV;
     }
   }
-  return it;
-}
-
-struct BrResult {
-  int newton, al, status;
-};
-
-__device__ __forceinline__ BrResult branch_solve(const BrK &K, BrP &P, double (&v)[8], double eta, double omega,
-                                                 double c_max, int K_AL, int K_N) {
+  const double scale = (dn > Delta) ? Delta / dn : 1.0;
+  double vt[8], s[8], smax = 0.0;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = clampd(v[i], K.lo[i], K.hi[i]);
-  double hprev = INFINITY, Delta = 1.0;
-  BrResult R{0, 0, 1};
-  for (int al = 0; al < K_AL;) {
-    bool conv = false;
-    Delta = fmax(Delta, 1e-3);
-    R.newton += br_inner(K, P, v, K_N, omega, Delta, conv);
-    double a[4], h[4];
-    br_flows(K, v, a);
-    br_cons(K, v, a, h);
-    double hn = 0.0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      P.mu[k] += P.c * h[k];
-      hn = fmax(hn, fabs(h[k]));
-    }
-    ++al;
-    R.al = al;
-    if (hn <= eta && conv) {
-      R.status = 0;
-      break;
-    }
-    if (hn > 0.25 * hprev) P.c = fmin(10.0 * P.c, c_max);
-    hprev = hn;
+  for (int i = 0; i < 8; ++i) {
+    vt[i] = clampd(v[i] + scale * d[i], K.lo[i], K.hi[i]);
+    s[i] = vt[i] - v[i];
+    smax = fmax(smax, fabs(s[i]));
   }
-  return R;
+  double gs = 0.0, sHs = 0.0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    gs += g[i] * s[i];
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += H[i][j] * s[j];
+    sHs += s[i] * t;
+  }
+  const double pred = -(gs + 0.5 * sHs);
+  const double ft = br_phi(K, P, vt);
+  const double ared = f - ft;
+  if (pred > 0.0 && ared >= 1e-4 * pred) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = vt[i];
+    f = ft;
+    accepted = true;
+    if (ared >= 0.75 * pred && scale < 1.0) Delta = 2.0 * Delta;
+    return NI_CONT;
+  }
+  Delta = 0.25 * smax;
+  if (Delta <= 1e-15 * (1.0 + vmax)) {
+    counted = 0;
+    return NI_STOP;
+  }
+  return NI_CONT;
 }
 
+__device__ __forceinline__ int find_instance(const Dev &S, long long bp) {
+  int lo = 0, hi = S.K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((long long)S.inst[mid].bpo <= bp) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Persistent line kernel.  Per solve (augmented-Lagrangian loop around the
+// inner Newton iterations, reading R6):
+//   inner solve until converged / stopped / K_N iterations; then mu += c h;
+//   finished when |h|_inf <= eta after a converged inner solve (or after K_AL
+//   rounds, status "capped"); otherwise c x10 (<= c_max) if |h| fell by less
+//   than 4x, Delta >= 1e-3, and a new inner solve starts.
 template <int BS>
 __global__ void __launch_bounds__(BS) k_branch(Dev S) {
-  const int b = blockIdx.x;
-  const int k = S.b_bp.inst[b];
-  const Inst I = S.inst[k];
-  const long long bp = (long long)S.b_bp.first[b] + threadIdx.x;
-  const bool valid = bp < (long long)I.bpo + (long long)I.T * I.nl;
-  long long nwt = 0, nal = 0, ncap = 0;
-  if (valid) {
-    const int loc = (int)(bp - I.bpo);
-    const int t = loc / I.nl, l = loc - t * I.nl;
-    const long long lg = (long long)I.lo + l, NL = S.NL, NBP = S.NBP;
-    BrK K;
-    K.Gii = S.BC[(BC_Y0 + 0) * NL + lg];
-    K.Bii = S.BC[(BC_Y0 + 1) * NL + lg];
-    K.Gij = S.BC[(BC_Y0 + 2) * NL + lg];
-    K.Bij = S.BC[(BC_Y0 + 3) * NL + lg];
-    K.Gjj = S.BC[(BC_Y0 + 4) * NL + lg];
-    K.Bjj = S.BC[(BC_Y0 + 5) * NL + lg];
-    K.Gji = S.BC[(BC_Y0 + 6) * NL + lg];
-    K.Bji = S.BC[(BC_Y0 + 7) * NL + lg];
-    K.rate2 = S.BC[BC_RATE2 * NL + lg];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long long NBP = S.NBP, NL = S.NL;
+  const double eta = S.prm.eta;
+  const int K_N = S.prm.K_N, K_AL = S.prm.K_AL;
+  bool active = true;
+  long long bp = -1;
+  int k = 0, itn = 0, al = 0, newton = 0;
+  bool need_f = false, need_gH = false;
+  double f = 0.0, Delta = 1.0, hprev = INFINITY, omega = 0.0, cmax = 0.0;
+  double v[8], g[8], H[8][8];
+  BrK K;
+  BrP P;
+  while (true) {
+    // ---- refill: lanes without a solve take the next branch-periods
+    const bool want = active && bp < 0;
+    const unsigned m = __ballot_sync(FULL, want);
+    if (m) {
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(S.bp_counter, (unsigned long long)__popc(m));
+      base = __shfl_sync(FULL, base, leader);
+      if (want) {
+        const long long item = (long long)base + __popc(m & ((1u << lane) - 1u));
+        if (item >= NBP) {
+          active = false;
+        } else {
+          bp = item;
+          k = find_instance(S, bp);
+          const Inst &I = S.inst[k];
+          const int loc = (int)(bp - I.bpo);
+          const int t = loc / I.nl, l = loc - t * I.nl;
+          const long long lg = (long long)I.lo + l;
+          K.Gii = S.BC[(BC_Y0 + 0) * NL + lg];
+          K.Bii = S.BC[(BC_Y0 + 1) * NL + lg];
+          K.Gij = S.BC[(BC_Y0 + 2) * NL + lg];
+          K.Bij = S.BC[(BC_Y0 + 3) * NL + lg];
+          K.Gjj = S.BC[(BC_Y0 + 4) * NL + lg];
+          K.Bjj = S.BC[(BC_Y0 + 5) * NL + lg];
+          K.Gji = S.BC[(BC_Y0 + 6) * NL + lg];
+          K.Bji = S.BC[(BC_Y0 + 7) * NL + lg];
+          K.rate2 = S.BC[BC_RATE2 * NL + lg];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      K.lo[i] = S.BC[(BC_LO + i) * NL + lg];
-      K.hi[i] = S.BC[(BC_HI + i) * NL + lg];
+          for (int i = 0; i < 8; ++i) {
+            K.lo[i] = S.BC[(BC_LO + i) * NL + lg];
+            K.hi[i] = S.BC[(BC_HI + i) * NL + lg];
+          }
+#pragma unroll
+          for (int r = 0; r < 8; ++r) P.tg[r] = S.BT[r * NBP + bp];
+          P.rpq = I.rpq;
+          P.rva = I.rva;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) P.mu[q] = S.B[(FB_MU0 + q) * NBP + bp];
+          P.c = S.B[FB_C * NBP + bp];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = clampd(S.B[(FB_V0 + i) * NBP + bp], K.lo[i], K.hi[i]);
+          const double rmax = fmax(I.rpq, I.rva);
+          omega = S.prm.omega_rel * rmax;
+          cmax = S.prm.c_max_rel * rmax;
+          hprev = INFINITY;
+          Delta = 1.0;
+          itn = al = newton = 0;
+          need_f = need_gH = true;
+        }
+      }
     }
-    BrP P;
+    if (__ballot_sync(FULL, active) == 0) break;
+    if (active) {
+      // ---- one Newton iteration
+      if (need_f) f = br_phi(K, P, v);
+      if (need_gH) br_derivs(K, P, v, g, H);
+      need_f = need_gH = false;
+      bool accepted;
+      int counted;
+      const int out = newton_iter(K, P, v, f, g, H, Delta, omega, accepted, counted);
+      newton += counted;
+      need_gH = accepted;
+      ++itn;
+      if (out != NI_CONT || itn >= K_N) {
+        // ---- end of an inner solve: multiplier update
+        const bool conv = (out == NI_CONV);
+        double a[4], h[4];
+        br_flows(K, v, a);
+        br_cons(K, v, a, h);
+        double hn = 0.0;
 #pragma unroll
-    for (int r = 0; r < 8; ++r) P.tg[r] = S.BT[r * NBP + bp];
-    P.rpq = I.rpq;
-    P.rva = I.rva;
+        for (int q = 0; q < 4; ++q) {
+          P.mu[q] += P.c * h[q];
+          hn = fmax(hn, fabs(h[q]));
+        }
+        ++al;
+        const bool done = (hn <= eta && conv);
+        if (done || al >= K_AL) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) P.mu[q] = S.B[(FB_MU0 + q) * NBP + bp];
-    P.c = S.B[FB_C * NBP + bp];
-    double v[8];
+          for (int i = 0; i < 8; ++i) S.B[(FB_V0 + i) * NBP + bp] = v[i];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = S.B[(FB_V0 + i) * NBP + bp];
-    const double rmax = fmax(I.rpq, I.rva);
-    const BrResult R = branch_solve(K, P, v, S.prm.eta, S.prm.omega_rel * rmax, S.prm.c_max_rel * rmax,
-                                    S.prm.K_AL, S.prm.K_N);
+          for (int q = 0; q < 4; ++q) S.B[(FB_MU0 + q) * NBP + bp] = P.mu[q];
+          S.B[FB_C * NBP + bp] = P.c;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) S.B[(FB_V0 + i) * NBP + bp] = v[i];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) S.B[(FB_MU0 + q) * NBP + bp] = P.mu[q];
-    S.B[FB_C * NBP + bp] = P.c;
-    double a[4];
-    br_flows(K, v, a);
-#pragma unroll
-    for (int r = 0; r < 4; ++r) S.BA[r * NBP + bp] = a[r];
-    S.BA[4 * NBP + bp] = v[0];
-    S.BA[5 * NBP + bp] = v[1];
-    S.BA[6 * NBP + bp] = v[4];
-    S.BA[7 * NBP + bp] = v[5];
-    nwt = R.newton;
-    nal = R.al;
-    ncap = (R.status != 0);
-  }
-  // block sums of the iteration counters (fixed order)
-  __shared__ long long sh[3][BS / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    nwt += __shfl_down_sync(0xffffffffu, nwt, o);
-    nal += __shfl_down_sync(0xffffffffu, nal, o);
-    ncap += __shfl_down_sync(0xffffffffu, ncap, o);
-  }
-  if (lane == 0) {
-    sh[0][wid] = nwt;
-    sh[1][wid] = nal;
-    sh[2][wid] = ncap;
-  }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    long long s = 0;
-    for (int w = 0; w < BS / 32; ++w) s += sh[threadIdx.x][w];
-    S.part_bp[(long long)b * 3 + threadIdx.x] = s;
+          for (int r = 0; r < 4; ++r) S.BA[r * NBP + bp] = a[r];
+          S.BA[4 * NBP + bp] = v[0];
+          S.BA[5 * NBP + bp] = v[1];
+          S.BA[6 * NBP + bp] = v[4];
+          S.BA[7 * NBP + bp] = v[5];
+          long long *st = S.bstat + (long long)k * 3;
+          atomicAdd((unsigned long long *)&st[0], (unsigned long long)newton);
+          atomicAdd((unsigned long long *)&st[1], (unsigned long long)al);
+          if (!done) atomicAdd((unsigned long long *)&st[2], 1ull);
+          bp = -1;
+        } else {
+          if (hn > 0.25 * hprev) P.c = fmin(10.0 * P.c, cmax);
+          hprev = hn;
+          Delta = fmax(Delta, 1e-3);
+          itn = 0;
+          need_f = need_gH = true;
+        }
+      }
+    }
   }
 }
 

@@ -37,20 +37,37 @@ __device__ __forceinline__ RowCtx row_ctx(const Dev &S, int k) {
   return R;
 }
 
-// x-step target of a row from its x-bar value b: (b - z) - y/rho, each
-// operation rounded separately (the UC dynamic program's inputs depend on it
-// bit for bit).
-__device__ __forceinline__ double row_target(double b, double z, double y, double rho) {
+// Per-family constants of the row update: rho, 1/rho and 1/(beta + rho), so
+// that the per-row work has no FP64 division (a division costs the FP64 pipe
+// about as much as ten multiply-adds, and the pipe is the bottleneck).
+struct Fam {
+  double rho, irho, ibr;
+};
+
+__device__ __forceinline__ Fam fam(double rho, const RowCtx &R) { return Fam{rho, 1.0 / rho, 1.0 / (R.beta + rho)}; }
+
+// x-step target of a UC duplicate row from its x-bar value b: (b - z) - y/rho
+// with each operation rounded separately and a true division -- the UC
+// dynamic program's inputs depend on it bit for bit.
+__device__ __forceinline__ double row_target_exact(double b, double z, double y, double rho) {
   return __dsub_rn(__dsub_rn(b, z), __ddiv_rn(y, rho));
 }
 
-// x-bar-step target of a row from its x value a: (a + z) + y/rho
-__device__ __forceinline__ double row_mtarget(double a, double z, double y, double rho) {
-  return (a + z) + y / rho;
+// x-step target of every other row: (b - z) - y * (1/rho), also separately
+// rounded so that the sweep kernels and the target preparation after an
+// import produce the same bits.
+__device__ __forceinline__ double row_target_fast(double b, double z, double y, double irho) {
+  return __dsub_rn(__dsub_rn(b, z), __dmul_rn(y, irho));
 }
 
+// x-bar-step target of a row from its x value a: (a + z) + y/rho
+__device__ __forceinline__ double row_mtarget(double a, double z, double y, const Fam &F) {
+  return (a + z) + y * F.irho;
+}
+
+template <bool EXACT>
 __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, double *L, double *Tg, long long idx,
-                                           double b_new, double b_old, double rho, const RowCtx &R,
+                                           double b_new, double b_old, const Fam &F, const RowCtx &R,
                                            double (&q)[NQ]) {
   const double a = A[idx], y = Y[idx], z = Z[idx];
   double lam = L[idx];
@@ -59,11 +76,11 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
     L[idx] = lam;
   }
   const double c = a - b_new;
-  const double zn = -(lam + y + rho * c) / (R.beta + rho);
-  const double yn = y + rho * (c + zn);
+  const double zn = -(lam + y + F.rho * c) * F.ibr;
+  const double yn = y + F.rho * (c + zn);
   Z[idx] = zn;
   Y[idx] = yn;
-  Tg[idx] = row_target(b_new, zn, yn, rho);
+  Tg[idx] = EXACT ? row_target_exact(b_new, zn, yn, F.rho) : row_target_fast(b_new, zn, yn, F.irho);
   q[Q_SP] += (c + zn) * (c + zn);
   q[Q_SD] += (b_new - b_old) * (b_new - b_old);
   q[Q_SZ] += zn * zn;
@@ -71,55 +88,61 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
 }
 
 // ------------------------------------------------------------ bus (R8) ----
+// Buses are visited in a per-instance order sorted by (degree, generators):
+// neighbouring lanes then loop over equally many incident rows, which keeps
+// the warp converged (the order changes no result).
 template <int BS>
 __global__ void __launch_bounds__(BS) k_bus(Dev S) {
   const int b = blockIdx.x;
   const int k = S.b_up.inst[b];
   const Inst I = S.inst[k];
-  const long long up = (long long)S.b_up.first[b] + threadIdx.x;
+  const long long upl = (long long)S.b_up.first[b] + threadIdx.x;
   double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (up < (long long)I.upo + (long long)I.T * I.nb) {
-    const int loc = (int)(up - I.upo);
-    const int t = loc / I.nb, i = loc - t * I.nb, ig = I.uo + i;
+  if (upl < (long long)I.upo + (long long)I.T * I.nb) {
+    const int loc = (int)(upl - I.upo);
+    const int t = loc / I.nb, i = S.bus_order[I.uo + (loc - t * I.nb)], ig = I.uo + i;
+    const long long up = (long long)I.upo + (long long)t * I.nb + i;
     const long long NGP = S.NGP, NBP = S.NBP, NUP = S.NUP;
     const RowCtx R = row_ctx(S, k);
-    const double rpq = I.rpq, rva = I.rva, irpq = 1.0 / rpq;
+    const Fam Fpq = fam(I.rpq, R), Fva = fam(I.rva, R);
+    const double irpq = Fpq.irho;
     const bool last = (t == I.T - 1);
     const int g0 = S.gen_ptr[ig], g1 = S.gen_ptr[ig + 1], e0 = S.inc_ptr[ig], e1 = S.inc_ptr[ig + 1];
     // pass 1: targets m_v, weights W_v and the 2x2 multiplier system
     double M00 = 0.0, M01 = 0.0, M11 = 0.0, r0 = 0.0, r1 = 0.0, mw = 0.0, mth = 0.0;
     for (int e = g0; e < g1; ++e) {
       const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
-      double num = rpq * row_mtarget(S.GA[GR_GP * NGP + gp], S.GZ[GR_GP * NGP + gp], S.GY[GR_GP * NGP + gp], rpq);
-      double W = rpq;
+      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GZ[GR_GP * NGP + gp], S.GY[GR_GP * NGP + gp], Fpq);
+      double iW = irpq;
       if (!last) {
         const long long gn = gp + I.ng;
-        num += rpq * row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], rpq);
-        W += rpq;
+        m = 0.5 * (m + row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], Fpq));
+        iW = 0.5 * irpq;
       }
-      M00 += 1.0 / W;
-      r0 += num / W;
+      M00 += iW;
+      r0 += m;
       M11 += irpq;
-      r1 += row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], rpq);
+      r1 += row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq);
     }
     for (int e = e0; e < e1; ++e) {
       const long long bp = (long long)I.bpo + (long long)t * I.nl + S.inc_br[e];
       const int sd = S.inc_side[e];
       const int rp = sd ? 2 : 0, rw = sd ? 5 : 4;
       M00 += irpq;
-      r0 -= row_mtarget(S.BA[rp * NBP + bp], S.BZ[rp * NBP + bp], S.BY[rp * NBP + bp], rpq);
+      r0 -= row_mtarget(S.BA[rp * NBP + bp], S.BZ[rp * NBP + bp], S.BY[rp * NBP + bp], Fpq);
       M11 += irpq;
-      r1 -= row_mtarget(S.BA[(rp + 1) * NBP + bp], S.BZ[(rp + 1) * NBP + bp], S.BY[(rp + 1) * NBP + bp], rpq);
-      mw += row_mtarget(S.BA[rw * NBP + bp], S.BZ[rw * NBP + bp], S.BY[rw * NBP + bp], rva);
-      mth += row_mtarget(S.BA[(rw + 2) * NBP + bp], S.BZ[(rw + 2) * NBP + bp], S.BY[(rw + 2) * NBP + bp], rva);
+      r1 -= row_mtarget(S.BA[(rp + 1) * NBP + bp], S.BZ[(rp + 1) * NBP + bp], S.BY[(rp + 1) * NBP + bp], Fpq);
+      mw += row_mtarget(S.BA[rw * NBP + bp], S.BZ[rw * NBP + bp], S.BY[rw * NBP + bp], Fva);
+      mth += row_mtarget(S.BA[(rw + 2) * NBP + bp], S.BZ[(rw + 2) * NBP + bp], S.BY[(rw + 2) * NBP + bp], Fva);
     }
     const int deg = e1 - e0;
-    mw /= deg;
-    mth /= deg;
-    const double Ww = rva * deg, aPw = -S.Gs[ig], aQw = S.Bs[ig];
-    M00 += aPw * aPw / Ww;
-    M01 += aPw * aQw / Ww;
-    M11 += aQw * aQw / Ww;
+    const double ideg = 1.0 / deg;
+    mw *= ideg;
+    mth *= ideg;
+    const double iWw = Fva.irho * ideg, aPw = -S.Gs[ig], aQw = S.Bs[ig];
+    M00 += aPw * aPw * iWw;
+    M01 += aPw * aQw * iWw;
+    M11 += aQw * aQw * iWw;
     r0 += aPw * mw - S.Pd[up];
     r1 += aQw * mw - S.Qd[up];
     double nuP, nuQ;
@@ -127,36 +150,36 @@ __global__ void __launch_bounds__(BS) k_bus(Dev S) {
       nuP = (M00 > 0.0) ? r0 / M00 : 0.0;
       nuQ = (M11 > 0.0) ? r1 / M11 : 0.0;
     } else {
-      const double det = M00 * M11 - M01 * M01;
-      nuP = (M11 * r0 - M01 * r1) / det;
-      nuQ = (M00 * r1 - M01 * r0) / det;
+      const double idet = 1.0 / (M00 * M11 - M01 * M01);
+      nuP = (M11 * r0 - M01 * r1) * idet;
+      nuQ = (M00 * r1 - M01 * r0) * idet;
     }
     // pass 2: new x-bar values, then the rows they own
     for (int e = g0; e < g1; ++e) {
       const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
       const long long gn = gp + I.ng;
-      double num = rpq * row_mtarget(S.GA[GR_GP * NGP + gp], S.GZ[GR_GP * NGP + gp], S.GY[GR_GP * NGP + gp], rpq);
-      double W = rpq;
+      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GZ[GR_GP * NGP + gp], S.GY[GR_GP * NGP + gp], Fpq);
+      double iW = irpq;
       if (!last) {
-        num += rpq * row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], rpq);
-        W += rpq;
+        m = 0.5 * (m + row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], Fpq));
+        iW = 0.5 * irpq;
       }
-      const double pnew = num / W - nuP / W;
-      const double qnew = row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], rpq) -
-                          nuQ * irpq;
+      const double pnew = m - nuP * iW;
+      const double qnew =
+          row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq) - nuQ * irpq;
       const double pold = S.G[F_PBAR * NGP + gp], qold = S.G[F_QBAR * NGP + gp];
       S.G[F_PBAR * NGP + gp] = pnew;
       S.G[F_QBAR * NGP + gp] = qnew;
-      row_update(S.GA + GR_GP * NGP, S.GY + GR_GP * NGP, S.GZ + GR_GP * NGP, S.GL + GR_GP * NGP,
-                 S.GT + GR_GP * NGP, gp, pnew, pold, rpq, R, q);
+      row_update<false>(S.GA + GR_GP * NGP, S.GY + GR_GP * NGP, S.GZ + GR_GP * NGP, S.GL + GR_GP * NGP,
+                        S.GT + GR_GP * NGP, gp, pnew, pold, Fpq, R, q);
       if (!last)
-        row_update(S.GA + GR_TC * NGP, S.GY + GR_TC * NGP, S.GZ + GR_TC * NGP, S.GL + GR_TC * NGP,
-                   S.GT + GR_TC * NGP, gn, pnew, pold, rpq, R, q);
-      row_update(S.GA + GR_GQ * NGP, S.GY + GR_GQ * NGP, S.GZ + GR_GQ * NGP, S.GL + GR_GQ * NGP,
-                 S.GT + GR_GQ * NGP, gp, qnew, qold, rpq, R, q);
+        row_update<false>(S.GA + GR_TC * NGP, S.GY + GR_TC * NGP, S.GZ + GR_TC * NGP, S.GL + GR_TC * NGP,
+                          S.GT + GR_TC * NGP, gn, pnew, pold, Fpq, R, q);
+      row_update<false>(S.GA + GR_GQ * NGP, S.GY + GR_GQ * NGP, S.GZ + GR_GQ * NGP, S.GL + GR_GQ * NGP,
+                        S.GT + GR_GQ * NGP, gp, qnew, qold, Fpq, R, q);
     }
     const double wold = S.U[FU_W * NUP + up], thold = S.U[FU_TH * NUP + up];
-    const double wnew = mw - (nuP * aPw + nuQ * aQw) / Ww;
+    const double wnew = mw - (nuP * aPw + nuQ * aQw) * iWw;
     const double thnew = (i == I.ref) ? 0.0 : mth;
     S.U[FU_W * NUP + up] = wnew;
     S.U[FU_TH * NUP + up] = thnew;
@@ -167,29 +190,92 @@ __global__ void __launch_bounds__(BS) k_bus(Dev S) {
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int r = rp + u;
-        const double m = row_mtarget(S.BA[r * NBP + bp], S.BZ[r * NBP + bp], S.BY[r * NBP + bp], rpq);
+        const double m = row_mtarget(S.BA[r * NBP + bp], S.BZ[r * NBP + bp], S.BY[r * NBP + bp], Fpq);
         const double vnew = m + (u == 0 ? nuP : nuQ) * irpq;
         const double vold = S.B[(FB_FB0 + r) * NBP + bp];
         S.B[(FB_FB0 + r) * NBP + bp] = vnew;
-        row_update(S.BA + r * NBP, S.BY + r * NBP, S.BZ + r * NBP, S.BL + r * NBP, S.BT + r * NBP, bp, vnew,
-                   vold, rpq, R, q);
+        row_update<false>(S.BA + r * NBP, S.BY + r * NBP, S.BZ + r * NBP, S.BL + r * NBP, S.BT + r * NBP, bp, vnew,
+                          vold, Fpq, R, q);
       }
-      row_update(S.BA + rw * NBP, S.BY + rw * NBP, S.BZ + rw * NBP, S.BL + rw * NBP, S.BT + rw * NBP, bp, wnew,
-                 wold, rva, R, q);
-      row_update(S.BA + (rw + 2) * NBP, S.BY + (rw + 2) * NBP, S.BZ + (rw + 2) * NBP, S.BL + (rw + 2) * NBP,
-                 S.BT + (rw + 2) * NBP, bp, thnew, thold, rva, R, q);
+      row_update<false>(S.BA + rw * NBP, S.BY + rw * NBP, S.BZ + rw * NBP, S.BL + rw * NBP, S.BT + rw * NBP, bp,
+                        wnew, wold, Fva, R, q);
+      row_update<false>(S.BA + (rw + 2) * NBP, S.BY + (rw + 2) * NBP, S.BZ + (rw + 2) * NBP, S.BL + (rw + 2) * NBP,
+                        S.BT + (rw + 2) * NBP, bp, thnew, thold, Fva, R, q);
     }
   }
   block_reduce_q<BS>(q, S.part_up + (long long)b * NQ);
 }
 
 // ------------------------------------------------------ x-bar^UC (R7) -----
-// min 1/2 x^T H x - g^T x over [0,1]^n (n = 2 or 3) by enumerating the 3^n
-// faces: on each face the free coordinates solve the reduced system (masked
-// 3x3 Cholesky); candidates inside the box whose fixed coordinates satisfy
-// the KKT sign conditions are kept, least objective wins (fallback: least
+// min 1/2 x^T H x - g^T x over [0,1]^n (n = 2 or 3): a face fixes each
+// coordinate free, at 0 or at 1; on a face the free coordinates solve the
+// reduced system (masked 3x3 Cholesky).  A face's point is the answer when it
+// lies in the box and the fixed coordinates satisfy the KKT sign conditions
+// (the minimiser is unique: H is positive definite).  The face of the previous
+// iterate is tried first -- near convergence it is almost always the answer,
+// so one face is solved instead of 27; otherwise every face is enumerated and
+// the KKT-consistent candidate of least objective is kept (fallback: least
 // objective among in-box candidates).
-__device__ __forceinline__ void boxqp3(int n, const double (&H)[3][3], const double (&gv)[3], double (&x)[3]) {
+struct FaceRes {
+  double x[3], f;
+  bool inbox, kkt;
+};
+
+__device__ __forceinline__ FaceRes solve_face(int n, const int (&st)[3], const double (&H)[3][3],
+                                              const double (&gv)[3], double tolx, double tolg) {
+  FaceRes R;
+  double A[3][3], rhs[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const bool fi = (st[i] == 0);
+    double r = gv[i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const bool fj = (st[j] == 0);
+      const double xj = (st[j] == 2) ? 1.0 : 0.0;
+      if (!fj) r -= H[i][j] * xj;
+      A[i][j] = (fi && fj) ? H[i][j] : ((i == j) ? 1.0 : 0.0);
+    }
+    rhs[i] = fi ? r : ((st[i] == 2) ? 1.0 : 0.0);
+  }
+  const double L00 = sqrt(A[0][0]), i00 = 1.0 / L00;
+  const double L10 = A[1][0] * i00, L20 = A[2][0] * i00;
+  const double L11 = sqrt(A[1][1] - L10 * L10), i11 = 1.0 / L11;
+  const double L21 = (A[2][1] - L20 * L10) * i11;
+  const double L22 = sqrt(A[2][2] - L20 * L20 - L21 * L21), i22 = 1.0 / L22;
+  const double y0 = rhs[0] * i00;
+  const double y1 = (rhs[1] - L10 * y0) * i11;
+  const double y2 = (rhs[2] - L20 * y0 - L21 * y1) * i22;
+  R.x[2] = y2 * i22;
+  R.x[1] = (y1 - L21 * R.x[2]) * i11;
+  R.x[0] = (y0 - L10 * R.x[1] - L20 * R.x[2]) * i00;
+  R.inbox = true;
+  R.kkt = true;
+  R.f = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i >= n) continue;
+    if (st[i] != 0) R.x[i] = (st[i] == 2) ? 1.0 : 0.0;
+    if (!(R.x[i] >= -tolx && R.x[i] <= 1.0 + tolx)) R.inbox = false;
+  }
+  if (n == 2) R.x[2] = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (i >= n) continue;
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      if (j < n) t += H[i][j] * R.x[j];
+    const double gr = t - gv[i];
+    R.f += 0.5 * R.x[i] * t - gv[i] * R.x[i];
+    if (st[i] == 1 && gr < -tolg) R.kkt = false;
+    if (st[i] == 2 && gr > tolg) R.kkt = false;
+  }
+  return R;
+}
+
+__device__ __forceinline__ void boxqp3(int n, const double (&H)[3][3], const double (&gv)[3], const double (&x0)[3],
+                                       double (&x)[3]) {
   double scale = 0.0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -199,83 +285,34 @@ __device__ __forceinline__ void boxqp3(int n, const double (&H)[3][3], const dou
       if (i < n && j < n) scale = fmax(scale, fabs(H[i][j]));
   }
   const double tolx = 1e-12, tolg = 1e-12 * scale;
+  {
+    int st[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) st[i] = (i >= n) ? 1 : (x0[i] <= 0.0 ? 1 : (x0[i] >= 1.0 ? 2 : 0));
+    const FaceRes R = solve_face(n, st, H, gv, tolx, tolg);
+    if (R.inbox && R.kkt) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) x[i] = clampd(R.x[i], 0.0, 1.0);
+      return;
+    }
+  }
   double best = INFINITY, bestf = INFINITY;
   double xb[3] = {0.0, 0.0, 0.0}, xf[3] = {0.0, 0.0, 0.0};
   bool have = false, havef = false;
   for (int face = 0; face < 27; ++face) {
-    int st[3] = {face % 3, (face / 3) % 3, face / 9};  // 0 free, 1 at 0, 2 at 1
+    int st[3] = {face % 3, (face / 3) % 3, face / 9};
     if (n == 2 && st[2] != 0) continue;
     if (n == 2) st[2] = 1;  // absent coordinate pinned at 0
-    double A[3][3], rhs[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const bool fi = (st[i] == 0);
-      double r = gv[i];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const bool fj = (st[j] == 0);
-        const double xj = (st[j] == 2) ? 1.0 : 0.0;
-        if (!fj) r -= H[i][j] * xj;
-        A[i][j] = (fi && fj) ? H[i][j] : ((i == j) ? 1.0 : 0.0);
-      }
-      rhs[i] = fi ? r : ((st[i] == 2) ? 1.0 : 0.0);
-    }
-    // 3x3 Cholesky
-    bool ok = true;
-    double L00 = 0, L10 = 0, L11 = 0, L20 = 0, L21 = 0, L22 = 0;
-    {
-      double s = A[0][0];
-      if (!(s > 0.0)) ok = false;
-      L00 = sqrt(fmax(s, 0.0));
-      L10 = A[1][0] / L00;
-      L20 = A[2][0] / L00;
-      s = A[1][1] - L10 * L10;
-      if (!(s > 0.0)) ok = false;
-      L11 = sqrt(fmax(s, 0.0));
-      L21 = (A[2][1] - L20 * L10) / L11;
-      s = A[2][2] - L20 * L20 - L21 * L21;
-      if (!(s > 0.0)) ok = false;
-      L22 = sqrt(fmax(s, 0.0));
-    }
-    if (!ok) continue;
-    double y0 = rhs[0] / L00;
-    double y1 = (rhs[1] - L10 * y0) / L11;
-    double y2 = (rhs[2] - L20 * y0 - L21 * y1) / L22;
-    double xc[3];
-    xc[2] = y2 / L22;
-    xc[1] = (y1 - L21 * xc[2]) / L11;
-    xc[0] = (y0 - L10 * xc[1] - L20 * xc[2]) / L00;
-    bool inbox = true;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      if (i >= n) continue;
-      if (st[i] != 0) xc[i] = (st[i] == 2) ? 1.0 : 0.0;
-      if (xc[i] < -tolx || xc[i] > 1.0 + tolx) inbox = false;
-    }
-    if (n == 2) xc[2] = 0.0;
-    if (!inbox) continue;
-    double fval = 0.0, gr[3];
-    bool kkt = true;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      if (i >= n) continue;
-      double t = 0.0;
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        if (j < n) t += H[i][j] * xc[j];
-      gr[i] = t - gv[i];
-      fval += 0.5 * xc[i] * t - gv[i] * xc[i];
-      if (st[i] == 1 && gr[i] < -tolg) kkt = false;
-      if (st[i] == 2 && gr[i] > tolg) kkt = false;
-    }
-    if (fval < bestf) {
-      bestf = fval;
-      xf[0] = xc[0]; xf[1] = xc[1]; xf[2] = xc[2];
+    const FaceRes R = solve_face(n, st, H, gv, tolx, tolg);
+    if (!R.inbox) continue;
+    if (R.f < bestf) {
+      bestf = R.f;
+      xf[0] = R.x[0]; xf[1] = R.x[1]; xf[2] = R.x[2];
       havef = true;
     }
-    if (kkt && fval < best) {
-      best = fval;
-      xb[0] = xc[0]; xb[1] = xc[1]; xb[2] = xc[2];
+    if (R.kkt && R.f < best) {
+      best = R.f;
+      xb[0] = R.x[0]; xb[1] = R.x[1]; xb[2] = R.x[2];
       have = true;
     }
   }
@@ -297,10 +334,11 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
     const bool has_next = tau < I.T - 1;
     const long long gn = gp + I.ng;
     const RowCtx R = row_ctx(S, k);
+    const Fam Fpq = fam(I.rpq, R), Fuc = fam(I.ruc, R);
     const double rpq = I.rpq, ruc = I.ruc;
     const double Pmin = S.Pmin[gg], Pmax = S.Pmax[gg], Qmin = S.Qmin[gg], Qmax = S.Qmax[gg];
     const double RU = S.RU[gg], RD = S.RD[gg], SU = S.SU[gg], SD = S.SD[gg];
-#define MT(r, idx, rho) row_mtarget(S.GA[(r)*NGP + (idx)], S.GZ[(r)*NGP + (idx)], S.GY[(r)*NGP + (idx)], rho)
+#define MT(r, idx, F) row_mtarget(S.GA[(r)*NGP + (idx)], S.GZ[(r)*NGP + (idx)], S.GY[(r)*NGP + (idx)], F)
     double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gv[3] = {0, 0, 0};
     auto addrow = [&](double w, double m, double e0, double e1, double e2) {
       const double e[3] = {e0, e1, e2};
@@ -311,52 +349,54 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
         for (int c = 0; c < 3; ++c) H[a][c] += w * e[a] * e[c];
       }
     };
-    addrow(ruc, MT(GR_ON, gp, ruc), 1.0, 0.0, 0.0);
-    addrow(ruc, MT(GR_SD, gp, ruc), 0.0, 1.0, 0.0);
-    addrow(rpq, MT(GR_PL, gp, rpq), Pmin, 0.0, 0.0);
-    addrow(rpq, MT(GR_PU, gp, rpq), Pmax, 0.0, 0.0);
-    addrow(rpq, MT(GR_QL, gp, rpq), Qmin, 0.0, 0.0);
-    addrow(rpq, MT(GR_QU, gp, rpq), Qmax, 0.0, 0.0);
-    addrow(rpq, MT(GR_RD, gp, rpq), -RD, -SD, 0.0);
+    addrow(ruc, MT(GR_ON, gp, Fuc), 1.0, 0.0, 0.0);
+    addrow(ruc, MT(GR_SD, gp, Fuc), 0.0, 1.0, 0.0);
+    addrow(rpq, MT(GR_PL, gp, Fpq), Pmin, 0.0, 0.0);
+    addrow(rpq, MT(GR_PU, gp, Fpq), Pmax, 0.0, 0.0);
+    addrow(rpq, MT(GR_QL, gp, Fpq), Qmin, 0.0, 0.0);
+    addrow(rpq, MT(GR_QU, gp, Fpq), Qmax, 0.0, 0.0);
+    addrow(rpq, MT(GR_RD, gp, Fpq), -RD, -SD, 0.0);
     if (has_next) {
-      addrow(ruc, MT(GR_SU, gn, ruc), 0.0, 0.0, 1.0);
-      addrow(rpq, MT(GR_RU, gn, rpq), RU, 0.0, SU);
+      addrow(ruc, MT(GR_SU, gn, Fuc), 0.0, 0.0, 1.0);
+      addrow(rpq, MT(GR_RU, gn, Fpq), RU, 0.0, SU);
     }
+    const double on_old = S.G[F_UBON * NGP + gp], sd_old = S.G[F_UBSD * NGP + gp];
+    const double su1_old = has_next ? S.G[F_UBSU * NGP + gn] : 0.0;
+    const double su0_old = (tau == 0) ? S.G[F_UBSU * NGP + gp] : 0.0;
+    const double x0[3] = {on_old, sd_old, su1_old};
     double x[3];
-    boxqp3(has_next ? 3 : 2, H, gv, x);
+    boxqp3(has_next ? 3 : 2, H, gv, x0, x);
     // lone block: ubar_su at t = 0 (ubar_on before period 1 is the data u0)
     double su0 = 0.0;
     const double u0 = (double)S.u0[gg];
     if (tau == 0) {
       const double Hs = ruc + rpq * SU * SU;
-      const double gs = ruc * MT(GR_SU, gp, ruc) + rpq * SU * (MT(GR_RU, gp, rpq) - RU * u0);
+      const double gs = ruc * MT(GR_SU, gp, Fuc) + rpq * SU * (MT(GR_RU, gp, Fpq) - RU * u0);
       su0 = clampd(gs / Hs, 0.0, 1.0);
     }
 #undef MT
-    const double on_old = S.G[F_UBON * NGP + gp], sd_old = S.G[F_UBSD * NGP + gp];
-    const double su1_old = has_next ? S.G[F_UBSU * NGP + gn] : 0.0;
-    const double su0_old = (tau == 0) ? S.G[F_UBSU * NGP + gp] : 0.0;
     const double on = x[0], sdv = x[1], su1 = x[2];
     S.G[F_UBON * NGP + gp] = on;
     S.G[F_UBSD * NGP + gp] = sdv;
     if (has_next) S.G[F_UBSU * NGP + gn] = su1;
     if (tau == 0) S.G[F_UBSU * NGP + gp] = su0;
-#define RU_(r, idx, bn, bo, rho) \
-  row_update(S.GA + (r)*NGP, S.GY + (r)*NGP, S.GZ + (r)*NGP, S.GL + (r)*NGP, S.GT + (r)*NGP, idx, bn, bo, rho, R, q)
-    RU_(GR_ON, gp, on, on_old, ruc);
-    RU_(GR_SD, gp, sdv, sd_old, ruc);
-    RU_(GR_PL, gp, Pmin * on, Pmin * on_old, rpq);
-    RU_(GR_PU, gp, Pmax * on, Pmax * on_old, rpq);
-    RU_(GR_QL, gp, Qmin * on, Qmin * on_old, rpq);
-    RU_(GR_QU, gp, Qmax * on, Qmax * on_old, rpq);
-    RU_(GR_RD, gp, (-RD * on) - SD * sdv, (-RD * on_old) - SD * sd_old, rpq);
+#define RU_(E, r, idx, bn, bo, F)                                                                            \
+  row_update<E>(S.GA + (r)*NGP, S.GY + (r)*NGP, S.GZ + (r)*NGP, S.GL + (r)*NGP, S.GT + (r)*NGP, idx, bn, bo, \
+                F, R, q)
+    RU_(true, GR_ON, gp, on, on_old, Fuc);
+    RU_(true, GR_SD, gp, sdv, sd_old, Fuc);
+    RU_(false, GR_PL, gp, Pmin * on, Pmin * on_old, Fpq);
+    RU_(false, GR_PU, gp, Pmax * on, Pmax * on_old, Fpq);
+    RU_(false, GR_QL, gp, Qmin * on, Qmin * on_old, Fpq);
+    RU_(false, GR_QU, gp, Qmax * on, Qmax * on_old, Fpq);
+    RU_(false, GR_RD, gp, (-RD * on) - SD * sdv, (-RD * on_old) - SD * sd_old, Fpq);
     if (has_next) {
-      RU_(GR_SU, gn, su1, su1_old, ruc);
-      RU_(GR_RU, gn, RU * on + SU * su1, RU * on_old + SU * su1_old, rpq);
+      RU_(true, GR_SU, gn, su1, su1_old, Fuc);
+      RU_(false, GR_RU, gn, RU * on + SU * su1, RU * on_old + SU * su1_old, Fpq);
     }
     if (tau == 0) {
-      RU_(GR_SU, gp, su0, su0_old, ruc);
-      RU_(GR_RU, gp, RU * u0 + SU * su0, RU * u0 + SU * su0_old, rpq);
+      RU_(true, GR_SU, gp, su0, su0_old, Fuc);
+      RU_(false, GR_RU, gp, RU * u0 + SU * su0, RU * u0 + SU * su0_old, Fpq);
     }
 #undef RU_
     const double p = S.G[F_P * NGP + gp];
@@ -391,23 +431,12 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
       q[j] = (j == Q_INF) ? fmax(q[j], v) : q[j] + v;
     }
   }
-  long long st3[3] = {0, 0, 0};
-  for (int bb = I.blk_bp0 + threadIdx.x; bb < I.blk_bp1; bb += BS)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) st3[j] += S.part_bp[(long long)bb * 3 + j];
   __shared__ double out[NQ];
   block_reduce_q<BS>(q, out);
-  __shared__ long long sst[3][BS];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) sst[j][threadIdx.x] = st3[j];
   __syncthreads();
   if (threadIdx.x == 0) {
-    long long nw = 0, na = 0, nc = 0;
-    for (int j = 0; j < BS; ++j) {
-      nw += sst[0][j];
-      na += sst[1][j];
-      nc += sst[2][j];
-    }
+    const long long nw = S.bstat[(long long)k * 3], na = S.bstat[(long long)k * 3 + 1];
+    const long long nc = S.bstat[(long long)k * 3 + 2];
     const Params &P = S.prm;
     double *c = S.ctrl + (long long)k * NCTRL;
     double *r = S.res + (long long)k * NRES;
@@ -477,10 +506,11 @@ __global__ void __launch_bounds__(BS) k_prep_gen(Dev S) {
   bv[GR_GP] = S.G[F_PBAR * NGP + gp];
   bv[GR_GQ] = S.G[F_QBAR * NGP + gp];
   bv[GR_TC] = (t > 0) ? S.G[F_PBAR * NGP + gp - I.ng] : 0.0;
+  const double irpq = 1.0 / I.rpq;
 #pragma unroll
   for (int r = 0; r < NGR; ++r) {
-    const double rho = (r <= GR_SD) ? I.ruc : I.rpq;
-    S.GT[r * NGP + gp] = row_target(bv[r], S.GZ[r * NGP + gp], S.GY[r * NGP + gp], rho);
+    S.GT[r * NGP + gp] = (r <= GR_SD) ? row_target_exact(bv[r], S.GZ[r * NGP + gp], S.GY[r * NGP + gp], I.ruc)
+                                      : row_target_fast(bv[r], S.GZ[r * NGP + gp], S.GY[r * NGP + gp], irpq);
   }
 }
 
@@ -503,11 +533,10 @@ __global__ void __launch_bounds__(BS) k_prep_branch(Dev S) {
   bv[5] = S.U[FU_W * NUP + ut];
   bv[6] = S.U[FU_TH * NUP + uf];
   bv[7] = S.U[FU_TH * NUP + ut];
+  const double irpq = 1.0 / I.rpq, irva = 1.0 / I.rva;
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    const double rho = (r < 4) ? I.rpq : I.rva;
-    S.BT[r * NBP + bp] = row_target(bv[r], S.BZ[r * NBP + bp], S.BY[r * NBP + bp], rho);
-  }
+  for (int r = 0; r < 8; ++r)
+    S.BT[r * NBP + bp] = row_target_fast(bv[r], S.BZ[r * NBP + bp], S.BY[r * NBP + bp], (r < 4) ? irpq : irva);
 }
 
 }  // namespace ucac

@@ -55,6 +55,7 @@ struct ucac_handle {
   Dev dev{};
   long long NGEN = 0, NGP = 0, NL = 0, NBP = 0, NB = 0, NUP = 0;
   int nblk_gen = 0, nblk_gp = 0, nblk_bp = 0, nblk_up = 0;
+  int grid_branch = 0;  // persistent line kernel: resident blocks on the whole GPU
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::string err;
@@ -142,11 +143,17 @@ void build_blocks(const std::vector<long long> &off, const std::vector<long long
   }
 }
 
+void reset_branch_work(ucac_handle *h, cudaStream_t s) {
+  cudaMemsetAsync(h->dev.bp_counter, 0, sizeof(unsigned long long), s);
+  cudaMemsetAsync(h->dev.bstat, 0, sizeof(long long) * 3 * h->K, s);
+}
+
 void launch_sweep(ucac_handle *h, cudaStream_t s) {
   const Dev &D = h->dev;
   k_ucdp<BS_GEN><<<h->nblk_gen, BS_GEN, 0, s>>>(D);
   k_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
-  k_branch<BS_BP><<<h->nblk_bp, BS_BP, 0, s>>>(D);
+  reset_branch_work(h, s);
+  k_branch<BS_BP><<<h->grid_branch, BS_BP, 0, s>>>(D);
   k_bus<BS_UP><<<h->nblk_up, BS_UP, 0, s>>>(D);
   k_ucbar<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
   k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(D);
@@ -395,12 +402,12 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_B = A.take<double>((size_t)NBF * NBP);
   const size_t o_BR = A.take<double>((size_t)5 * NBR * NBP);
   const size_t o_bus = A.take<double>(2 * NB);
-  const size_t o_csr = A.take<int>((NB + 1) * 2 + 4 * NL + NGEN);
+  const size_t o_csr = A.take<int>((NB + 1) * 2 + 4 * NL + NGEN + NB);
   const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
   const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
   const size_t o_stat = A.take<long long>(4 * n);
   const size_t o_pup = A.take<double>((size_t)NQ * h->nblk_up), o_pgp = A.take<double>((size_t)NQ * h->nblk_gp);
-  const size_t o_pbp = A.take<long long>(3 * (size_t)h->nblk_bp);
+  const size_t o_pbp = A.take<long long>(3 * (size_t)n + 8);
   const size_t o_dpL = A.take<double>(4 * NGP), o_dpC = A.take<double>(2 * (NGP + NGEN));
   const size_t o_dpD = A.take<unsigned char>(2 * NGP);
   const size_t o_blk = A.take<int>(2 * ((size_t)h->nblk_gen + h->nblk_gp + h->nblk_bp + h->nblk_up));
@@ -441,6 +448,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const int *csr = (const int *)(ar + o_csr);
   D.inc_ptr = csr; D.gen_ptr = csr + (NB + 1); D.inc_br = csr + 2 * (NB + 1); D.inc_side = D.inc_br + 2 * NL;
   D.gen_idx = D.inc_side + 2 * NL;
+  D.bus_order = D.gen_idx + NGEN;
   D.NUP = NUP;
   D.Pd = (const double *)(ar + o_pq); D.Qd = D.Pd + NUP;
   D.U = (double *)(ar + o_U);
@@ -449,7 +457,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.stat = (long long *)(ar + o_stat);
   D.part_up = (double *)(ar + o_pup);
   D.part_gp = (double *)(ar + o_pgp);
-  D.part_bp = (long long *)(ar + o_pbp);
+  D.bstat = (long long *)(ar + o_pbp);
+  D.bp_counter = (unsigned long long *)(D.bstat + 3 * (size_t)n);
   D.dpL = (double *)(ar + o_dpL);
   D.dpC = (double *)(ar + o_dpC);
   D.dpD = (unsigned char *)(ar + o_dpD);
@@ -480,6 +489,22 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   csrh.insert(csrh.end(), inc_br.begin(), inc_br.end());
   csrh.insert(csrh.end(), inc_side.begin(), inc_side.end());
   csrh.insert(csrh.end(), gen_idx.begin(), gen_idx.end());
+  {
+    // per instance: local bus indices sorted by (degree, generator count), stable
+    std::vector<int> order(NB);
+    for (int k = 0; k < n; ++k) {
+      const HInst &I = h->hi[k];
+      std::vector<int> o(I.nb);
+      for (int i = 0; i < I.nb; ++i) o[i] = i;
+      auto key = [&](int i) {
+        const int b = I.uo + i;
+        return std::make_pair(inc_ptr[b + 1] - inc_ptr[b], gen_ptr[b + 1] - gen_ptr[b]);
+      };
+      std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return key(a) < key(b); });
+      for (int i = 0; i < I.nb; ++i) order[I.uo + i] = o[i];
+    }
+    csrh.insert(csrh.end(), order.begin(), order.end());
+  }
   std::vector<double> pqh(Pd);
   pqh.insert(pqh.end(), Qd.begin(), Qd.end());
   std::vector<int> blkh;
@@ -505,9 +530,17 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     ucac_destroy(h);
     return fail(nullptr, UCAC_E_CUDA, m);
   }
+  {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_branch<BS_BP>, BS_BP, 0);
+    const long long need = (NBP + BS_BP - 1) / BS_BP;
+    h->grid_branch = (int)std::max(1LL, std::min<long long>((long long)sms * std::max(per_sm, 1), need));
+  }
   k_prep_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, h->stream>>>(D);
   k_prep_branch<BS_BP><<<h->nblk_bp, BS_BP, 0, h->stream>>>(D);
-  e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   // ---- capture one sweep into a graph (capture needs a non-legacy stream)
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
@@ -678,8 +711,9 @@ int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
     k_ucdp<BS_GEN><<<h->nblk_gen, BS_GEN, 0, s>>>(D);
     CK(cudaEventRecord(ev[1], s));
     k_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
+    reset_branch_work(h, s);
     CK(cudaEventRecord(ev[2], s));
-    k_branch<BS_BP><<<h->nblk_bp, BS_BP, 0, s>>>(D);
+    k_branch<BS_BP><<<h->grid_branch, BS_BP, 0, s>>>(D);
     CK(cudaEventRecord(ev[3], s));
     k_bus<BS_UP><<<h->nblk_up, BS_UP, 0, s>>>(D);
     CK(cudaEventRecord(ev[4], s));
