@@ -37,15 +37,20 @@ from paper_2310_13145_b300 import synth  # noqa: E402
 METRIC = "ADMM sweeps/s (one sweep = all instances of the workload)"
 UNIT = "sweeps/s"
 
-# Algorithmic FP64 operation counts of the line kernel (k_branch), counted from
-# its source: one damped-Newton iteration (projected-gradient and active-set
+# Algorithmic FP64 operation counts of the line kernel, counted from its
+# source (divisions, square roots, sincos/atan2 count as one operation each).
+# Polar form (default): objective+gradient+Hessian at the current point 315
+# (four flows with first and second derivatives 272, voltage/angle rows 20,
+# line limits 20, products 3), one Newton iteration 258 (projected-gradient
+# and active-set scan 42, masked 3x3 Cholesky and solves 49, Newton decrement
+# 30, trial step 15, model decrease 27, objective at the trial point 90, ratio
+# test 5); one multiplier round 100 (objective at the point, two inequality
+# multiplier updates).
+# W-form: one damped-Newton iteration 1229 (projected-gradient and active-set
 # scan 64, masked Cholesky build 64 + factor 168 + 2 triangular solves 112,
 # Newton-decrement and model terms 288, trial step 24, objective at the trial
-# point 85, gradient and Hessian at the accepted point 280) and one
-# augmented-Lagrangian round (flows, constraints, multiplier update 60).
-# Divisions, square roots and atan2 count as one operation each.
-FLOP_PER_NEWTON = 1229
-FLOP_PER_AL = 60
+# point 85, gradient and Hessian at the accepted point 280); one AL round 60.
+FLOPS = {"polar": (315 + 258, 100), "w": (1229, 60)}
 FP64_NOMINAL_TFLOPS = 1.25
 
 
@@ -57,6 +62,7 @@ def parse():
     ap.add_argument("--impl", default="ucac", choices=["ucac", "reference"])
     ap.add_argument("--workload", default="c5_2000bus_T24x16", choices=sorted(synth.CONFIGS))
     ap.add_argument("--instances", type=int, default=None, help="use only the first N instances (profiling)")
+    ap.add_argument("--line-form", default="polar", choices=["polar", "w"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -206,7 +212,9 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     stream = torch.cuda.Stream()
-    h = ucac.Handle(grids, stream=stream.cuda_stream)
+    params = ucac.ucac_default_params()
+    params.line_form = ucac.UCAC_LINE_POLAR if a.line_form == "polar" else ucac.UCAC_LINE_W
+    h = ucac.Handle(grids, params=params, stream=stream.cuda_stream)
     with torch.cuda.stream(stream):
         h.enqueue(a.warmup)
         stream.synchronize()
@@ -235,9 +243,10 @@ def main():
     fp64 = ucac.ucac_probe_fp64(5, stream.cuda_stream)
     torch.cuda.synchronize()
     t_br = kt["k_branch"] * 1e-3
-    flops = newton * FLOP_PER_NEWTON + al * FLOP_PER_AL
+    f_newton, f_al = FLOPS[a.line_form]
+    flops = newton * f_newton + al * f_al
     achieved = flops / t_br / 1e12
-    roofline = {"bound": "alu", "kernel": "k_branch", "achieved": achieved, "peak": fp64 / 1e12, "unit": "TFLOP/s",
+    roofline = {"bound": "alu", "kernel": "k_branch (line subproblems, %s form)" % a.line_form, "achieved": achieved, "peak": fp64 / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / (fp64 / 1e12), "traffic": None,
                 "peak_source": "measured FP64 FMA probe on this GPU (nominal %.2f)" % FP64_NOMINAL_TFLOPS,
                 "newton_per_sweep": newton, "al_per_sweep": al, "kernel_ms": kt}
@@ -245,7 +254,7 @@ def main():
     # read back the solution and the residual record
     e2e = None
     if not a.no_e2e:
-        e2e = e2e_run(ucac, grids, a.steps, stream)
+        e2e = e2e_run(ucac, grids, a.steps, stream, params)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         v, sample = oracle_sweep_rate(grids, budget_s=15.0)
@@ -256,7 +265,8 @@ def main():
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (seeded grids shaped like the paper's workloads)",
-                "config": {"workload": a.workload, "instances": len(grids), "parallelism": "replicas" if world > 1 else "single",
+                "config": {"workload": a.workload, "instances": len(grids), "line_form": a.line_form,
+                           "parallelism": "replicas" if world > 1 else "single",
                            "l2": "state larger than L2 (no flush needed)", "r_p_inst0": r["r_p"]},
                 "gpu_launches": 6 * a.steps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks}
@@ -265,7 +275,7 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def e2e_run(ucac, grids, steps, stream):
+def e2e_run(ucac, grids, steps, stream, params):
     import torch
     # pinned host copies of every grid array
     pinned = []
@@ -280,7 +290,7 @@ def e2e_run(ucac, grids, steps, stream):
     d2h = sum(g.T * (3 * g.n_gen + 2 * g.n_bus + 4 * g.n_branch) * 8 for g in grids)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = ucac.Handle(pinned, stream=stream.cuda_stream)
+    h = ucac.Handle(pinned, params=params, stream=stream.cuda_stream)
     ucac.ucac_iterate(h.h, steps)
     for k, g in enumerate(grids):
         ucac.ucac_solution(h.h, k, g.T, g.n_gen, g.n_bus, g.n_branch)

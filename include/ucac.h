@@ -84,12 +84,18 @@ typedef struct ucac_rho {
  * max(rho.pq, rho.va); K_AL / K_N: iteration caps of the line subproblem's
  * multiplier and Newton loops; L_max: cap on inner sweeps per outer
  * iteration; check_every: sweeps between host convergence checks in
- * ucac_iterate.
+ * ucac_iterate; line_form: coordinates of the line subproblem solver,
+ * UCAC_LINE_POLAR (default: (V_i, V_j, theta_i - theta_j), where the product
+ * and angle equations hold identically) or UCAC_LINE_W (the W-form variables
+ * with an augmented Lagrangian on all four equalities).  Both solve the same
+ * subproblem.
  */
+#define UCAC_LINE_W 0
+#define UCAC_LINE_POLAR 1
 typedef struct ucac_params {
   double eps_in, eps_out, tau, theta, beta0, lambda_max;
   double eta, omega_rel, c_init_rel, c_max_rel;
-  int32_t K_AL, K_N, L_max, check_every;
+  int32_t K_AL, K_N, L_max, check_every, line_form, reserved;
 } ucac_params;
 
 /*

@@ -20,6 +20,7 @@
 #include "common.cuh"
 #include "k_branch.cuh"
 #include "k_gen.cuh"
+#include "k_line_polar.cuh"
 #include "k_ucdp.cuh"
 #include "k_xbar.cuh"
 
@@ -148,12 +149,19 @@ void reset_branch_work(ucac_handle *h, cudaStream_t s) {
   cudaMemsetAsync(h->dev.bstat, 0, sizeof(long long) * 3 * h->K, s);
 }
 
+void launch_line(ucac_handle *h, cudaStream_t s) {
+  reset_branch_work(h, s);
+  if (h->prm.line_form == UCAC_LINE_POLAR)
+    k_line_polar<BS_BP><<<h->grid_branch, BS_BP, 0, s>>>(h->dev);
+  else
+    k_branch<BS_BP><<<h->grid_branch, BS_BP, 0, s>>>(h->dev);
+}
+
 void launch_sweep(ucac_handle *h, cudaStream_t s) {
   const Dev &D = h->dev;
   k_ucdp<BS_GEN><<<h->nblk_gen, BS_GEN, 0, s>>>(D);
   k_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
-  reset_branch_work(h, s);
-  k_branch<BS_BP><<<h->grid_branch, BS_BP, 0, s>>>(D);
+  launch_line(h, s);
   k_bus<BS_UP><<<h->nblk_up, BS_UP, 0, s>>>(D);
   k_ucbar<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
   k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(D);
@@ -181,6 +189,8 @@ void ucac_default_params(ucac_params *p) {
   p->K_N = 50;
   p->L_max = 1000;
   p->check_every = 50;
+  p->line_form = UCAC_LINE_POLAR;
+  p->reserved = 0;
 }
 
 int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, const ucac_rho *rhos, int32_t n,
@@ -197,7 +207,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   ucac_params P;
   ucac_default_params(&P);
   if (params) P = *params;
-  if (P.K_AL < 1 || P.K_N < 1 || P.L_max < 1 || P.check_every < 1 || !(P.beta0 > 0))
+  if (P.K_AL < 1 || P.K_N < 1 || P.L_max < 1 || P.check_every < 1 || !(P.beta0 > 0) ||
+      (P.line_form != UCAC_LINE_W && P.line_form != UCAC_LINE_POLAR))
     return fail(nullptr, UCAC_E_ARG, "bad parameters");
 
   h = new ucac_handle();
@@ -205,7 +216,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   h->stream = (cudaStream_t)cuda_stream;
   h->check_every = P.check_every;
   h->prm = Params{P.eps_in, P.eps_out, P.tau, P.theta, P.beta0, P.lambda_max, P.eta, P.omega_rel, P.c_init_rel,
-                  P.c_max_rel, P.K_AL, P.K_N, P.L_max};
+                  P.c_max_rel, P.K_AL, P.K_N, P.L_max, P.line_form};
   // ---- sizes and offsets
   long long go = 0, gpo = 0, lo = 0, bpo = 0, uo = 0, upo = 0;
   for (int k = 0; k < n; ++k) {
@@ -534,7 +545,10 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     int dev = 0, sms = 0, per_sm = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_branch<BS_BP>, BS_BP, 0);
+    if (e == cudaSuccess)
+      e = (h->prm.line_form == UCAC_LINE_POLAR)
+              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_polar<BS_BP>, BS_BP, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_branch<BS_BP>, BS_BP, 0);
     const long long need = (NBP + BS_BP - 1) / BS_BP;
     h->grid_branch = (int)std::max(1LL, std::min<long long>((long long)sms * std::max(per_sm, 1), need));
   }
@@ -711,9 +725,8 @@ int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
     k_ucdp<BS_GEN><<<h->nblk_gen, BS_GEN, 0, s>>>(D);
     CK(cudaEventRecord(ev[1], s));
     k_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
-    reset_branch_work(h, s);
     CK(cudaEventRecord(ev[2], s));
-    k_branch<BS_BP><<<h->grid_branch, BS_BP, 0, s>>>(D);
+    launch_line(h, s);
     CK(cudaEventRecord(ev[3], s));
     k_bus<BS_UP><<<h->nblk_up, BS_UP, 0, s>>>(D);
     CK(cudaEventRecord(ev[4], s));

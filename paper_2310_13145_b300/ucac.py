@@ -21,6 +21,7 @@ _ip = C.POINTER(C.c_int32)
 UCAC_OK, UCAC_CONVERGED = 0, 1
 UCAC_E_ARG, UCAC_E_GRID, UCAC_E_CUDA, UCAC_E_NEWTON_MAXIT, UCAC_E_NAN, UCAC_E_DIVERGED = -1, -2, -3, -4, -5, -6
 UCAC_N_KERNELS = 6
+UCAC_LINE_W, UCAC_LINE_POLAR = 0, 1
 
 # symbols declared in include/ucac.h
 EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_instances", "ucac_iterate",
@@ -48,7 +49,7 @@ class ucac_rho(C.Structure):
 class ucac_params(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("eps_in", "eps_out", "tau", "theta", "beta0", "lambda_max", "eta",
                                           "omega_rel", "c_init_rel", "c_max_rel")] + \
-        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "check_every")]
+        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "check_every", "line_form", "reserved")]
 
 
 class ucac_report(C.Structure):
