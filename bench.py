@@ -57,12 +57,14 @@ FP64_NOMINAL_TFLOPS = 1.25
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ucac", choices=["ucac", "reference"])
     ap.add_argument("--workload", default="c5_2000bus_T24x16", choices=sorted(synth.CONFIGS))
     ap.add_argument("--instances", type=int, default=None, help="use only the first N instances (profiling)")
     ap.add_argument("--line-form", default="polar", choices=["polar", "w"])
+    ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-1e-4 run")
+    ap.add_argument("--ttc-max-sweeps", type=int, default=6000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -70,6 +72,23 @@ def parse():
 
 def dist_info():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def reduce_max(x: float, world: int, device="cpu") -> float:
+    """Maximum of x over all ranks (the whole job ends when the slowest rank does)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(steps: int, world: int, max_ms: float) -> float:
+    """Sweeps per second of the whole job: every rank runs `steps` sweeps of its
+    own replica of the workload (weak scaling)."""
+    return steps * world / (max_ms * 1e-3)
 
 
 # ------------------------------------------------------------------ clocks
@@ -229,12 +248,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = a.steps * world / (ms * 1e-3)
+    ms = reduce_max(e0.elapsed_time(e1), world, device="cuda")
+    value = whole_job_value(a.steps, world, ms)
     # per-kernel device times (events on the handle's stream) and iteration counts
     r = h.residuals(0)
     kt = h.kernel_times(3)
@@ -255,6 +270,9 @@ def main():
     e2e = None
     if not a.no_e2e:
         e2e = e2e_run(ucac, grids, a.steps, stream, params)
+    ttc = None
+    if not a.no_ttc:
+        ttc = time_to_tolerance(ucac, grids, stream, params, a.ttc_max_sweeps)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         v, sample = oracle_sweep_rate(grids, budget_s=15.0)
@@ -269,10 +287,36 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "state larger than L2 (no flush needed)", "r_p_inst0": r["r_p"]},
                 "gpu_launches": 6 * a.steps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "time_to_1e-4": ttc,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def time_to_tolerance(ucac, grids, stream, params, max_sweeps):
+    """Cold start to convergence of every instance (r_p, r_d <= 1e-4 RMS and
+    z_rms <= 1e-4, the inner and outer stops of Algorithm 1) through the public
+    API: create from host arrays, ucac_iterate with host checks every 50
+    sweeps (the checks are inside the timed region)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = ucac.Handle(grids, params=params, stream=stream.cuda_stream)
+    t1 = time.perf_counter()
+    done, rc = 0, 0
+    while done < max_sweeps and rc != 1:
+        rc = h.iterate(params.check_every)
+        done += params.check_every
+    t2 = time.perf_counter()
+    rs = [h.residuals(k) for k in range(len(grids))]
+    h.close()
+    return {"converged": rc == 1, "seconds": t2 - t0, "create_s": t1 - t0, "iterate_s": t2 - t1,
+            "sweeps": done, "check_every": params.check_every,
+            "objective_mean": statistics.mean(r["objective"] for r in rs),
+            "r_p_max": max(r["r_p"] for r in rs), "r_d_max": max(r["r_d"] for r in rs),
+            "z_rms_max": max(r["z_rms"] for r in rs), "inf_norm_max": max(r["inf_norm_viol"] for r in rs),
+            "outer_max": max(r["outer"] for r in rs), "variant": "plain (no learned warm start)"}
 
 
 def e2e_run(ucac, grids, steps, stream, params):

@@ -25,11 +25,18 @@ __all__ = ["Grid", "make_grid", "config_instances", "CONFIGS", "RHO_TABLE"]
 
 # Random networks drawn here are far weaker than MATPOWER's (per-bus loads
 # U(0.5,1.5) p.u. against 1-3 p.u. line ratings and reactances up to 0.3 p.u.);
-# at the configured load level most draws are AC-infeasible (line limits and
-# the 0.9/1.1 voltage bounds bind and the ADMM stalls).  Every load is
-# therefore multiplied by this network-loading factor on top of the paper's
-# 0.7 discount.
+# at the configured load level most draws are AC-infeasible (voltage lower
+# bounds and generator reactive limits bind at the far end of long radial
+# paths, and the ADMM stalls with |Ax + Bxbar|_inf ~ 0.1).  Every load is
+# therefore multiplied by a network-loading factor on top of the paper's 0.7
+# discount: 0.4 up to 300 buses, decreasing as (300/n)^(1/4) beyond (0.25 at
+# 2000 buses), since path lengths grow with the size of the random grid.
 NETWORK_LOADING = 0.4
+
+
+def network_loading(n_bus: int) -> float:
+    return NETWORK_LOADING * min(1.0, (300.0 / n_bus) ** 0.25)
+
 
 # Penalties per workload, taken from the paper's Table 1 rows (case9 for the
 # 9-bus grid, case118 for the 118-bus grid, case300 for the large ones).
@@ -140,7 +147,8 @@ def _load_shape(T: int) -> np.ndarray:
 
 def make_grid(n_bus: int, n_branch: int, n_gen: int, T: int, seed: int = 0,
               load_seed: int | None = None, load_scale: float = 1.0,
-              rho=(5e3, 1e4, 1e4), name: str = "") -> Grid:
+              rho=(5e3, 1e4, 1e4), name: str = "", loading: float | None = None,
+              q_ratio: float = 0.5) -> Grid:
     """Draw one instance.
 
     `seed` fixes the network, generator fleet and base loads; `load_seed`, when
@@ -158,7 +166,8 @@ def make_grid(n_bus: int, n_branch: int, n_gen: int, T: int, seed: int = 0,
     rl = _rng(seed, 3)
     base = rl.uniform(0.5, 1.5, n_bus)
     shape = _load_shape(T)
-    Pd = 0.7 * NETWORK_LOADING * load_scale * shape[:, None] * base[None, :]
+    loading = network_loading(n_bus) if loading is None else loading
+    Pd = 0.7 * loading * load_scale * shape[:, None] * base[None, :]
     if load_seed is not None:
         rs = _rng(seed, 1000 + int(load_seed))
         Pd = Pd * (1.0 + 0.05 * rs.standard_normal((T, n_bus)))
@@ -180,7 +189,7 @@ def make_grid(n_bus: int, n_branch: int, n_gen: int, T: int, seed: int = 0,
         Pd=np.ascontiguousarray(Pd), Qd=np.ascontiguousarray(Qd),
         Gs=np.zeros(n_bus), Bs=np.zeros(n_bus), Vmin=0.9 * ones, Vmax=1.1 * ones,
         br_from=frm, br_to=to, br_r=r, br_x=x, br_b=np.zeros(n_branch), br_rate=rate,
-        gen_bus=gen_bus, Pmin=0.2 * Pmax, Pmax=Pmax, Qmin=-0.3 * Pmax, Qmax=0.5 * Pmax,
+        gen_bus=gen_bus, Pmin=0.2 * Pmax, Pmax=Pmax, Qmin=-0.3 * Pmax, Qmax=q_ratio * Pmax,
         c2=c2, c1=c1, c0=c0, c_su=c_su, c_sd=np.zeros(n_gen),
         RU=0.5 * Pmax, RD=0.5 * Pmax, SU=0.5 * Pmax, SD=0.5 * Pmax,
         TU=np.full(n_gen, 2, np.int32), TD=np.full(n_gen, 2, np.int32),
