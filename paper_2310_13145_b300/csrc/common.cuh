@@ -33,7 +33,8 @@ enum { R_RP, R_RD, R_ZN, R_ZRMS, R_INF, R_OBJ, R_STATUS, NRES };
 // block partial quantities of the x-bar kernels
 enum { Q_SP, Q_SD, Q_SZ, Q_INF, Q_OBJ, NQ };
 // branch constant table [BC_N][NL]
-enum { BC_Y0 = 0, BC_RATE2 = 8, BC_LO = 9, BC_HI = 17, BC_N = 25 };
+// (BC_VB: Vmin_i, Vmax_i, Vmin_j, Vmax_j for the polar line solver)
+enum { BC_Y0 = 0, BC_RATE2 = 8, BC_LO = 9, BC_HI = 17, BC_VB = 25, BC_N = 29 };
 
 struct Inst {
   int nb, nl, ng, T, ref;

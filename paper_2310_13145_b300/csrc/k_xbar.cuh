@@ -20,7 +20,18 @@
 #pragma once
 #include "common.cuh"
 
+// resident blocks per SM requested for the bus kernel (register cap), and the
+// unroll factor of its gather loop (memory-level parallelism)
+#ifndef UCAC_BUS_MINB
+#define UCAC_BUS_MINB 6
+#endif
+#ifndef UCAC_BUS_UNROLL
+#define UCAC_BUS_UNROLL 4
+#endif
+
 namespace ucac {
+
+constexpr int kBusUnroll = UCAC_BUS_UNROLL;
 
 struct RowCtx {
   double beta, beta_cur, lam_max;
@@ -92,7 +103,7 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
 // neighbouring lanes then loop over equally many incident rows, which keeps
 // the warp converged (the order changes no result).
 template <int BS>
-__global__ void __launch_bounds__(BS) k_bus(Dev S) {
+__global__ void __launch_bounds__(BS, UCAC_BUS_MINB) k_bus(Dev S) {
   const int b = blockIdx.x;
   const int k = S.b_up.inst[b];
   const Inst I = S.inst[k];
@@ -124,6 +135,7 @@ __global__ void __launch_bounds__(BS) k_bus(Dev S) {
       M11 += irpq;
       r1 += row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq);
     }
+#pragma unroll kBusUnroll
     for (int e = e0; e < e1; ++e) {
       const long long bp = (long long)I.bpo + (long long)t * I.nl + S.inc_br[e];
       const int sd = S.inc_side[e];

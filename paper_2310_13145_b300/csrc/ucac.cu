@@ -282,6 +282,10 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
         BC[(BC_LO + q) * NL + lg] = lo8[q];
         BC[(BC_HI + q) * NL + lg] = hi8[q];
       }
+      BC[(BC_VB + 0) * NL + lg] = g->Vmin[i];
+      BC[(BC_VB + 1) * NL + lg] = g->Vmax[i];
+      BC[(BC_VB + 2) * NL + lg] = g->Vmin[j];
+      BC[(BC_VB + 3) * NL + lg] = g->Vmax[j];
       bf[lg] = i;
       bt[lg] = j;
     }
