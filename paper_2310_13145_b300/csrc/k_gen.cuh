@@ -14,7 +14,9 @@
 // at t_rd, t_ru).  The global minimiser lies in some closed cell and is the
 // box-constrained minimiser of that cell's quadratic, so the candidate whose
 // point lies in its own cell (least violation, to absorb rounding) is the
-// answer.  Pure FP64 register arithmetic, one thread per gen-period.
+// answer.  The piece of the previous iterate is tried first (near convergence
+// it is the answer, so one piece is solved instead of nine).  Pure FP64
+// register arithmetic, one thread per gen-period.
 #pragma once
 #include "common.cuh"
 
@@ -45,7 +47,8 @@ struct GenOut {
 };
 
 __device__ __forceinline__ GenOut gen_solve(double c2p, double c1p, double rho, double pmax, double qlo,
-                                            double qhi, double p0, bool has_prev, const double (&tg)[9]) {
+                                            double qhi, double p0, bool has_prev, const double (&tg)[9],
+                                            double p_prev, double ph_prev) {
   const double t_pl = tg[0], t_pu = tg[1], t_ql = tg[2], t_qu = tg[3], t_rd = tg[4], t_ru = tg[5];
   const double t_gp = tg[6], t_gq = tg[7], t_tc = tg[8];
   GenOut o;
@@ -76,60 +79,67 @@ __device__ __forceinline__ GenOut gen_solve(double c2p, double c1p, double rho, 
     }
     o.q = q;
   }
-  // ---- (p, phat)
-  double p = 0.0, ph = p0, best = INFINITY;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    int apl, apu;
-    double plo, phi;
+  // ---- (p, phat): candidate of piece (i, j) and its distance from its cell
+  auto piece = [&](int i, int j, double &pc, double &phc) -> double {
+    int apl, apu, ard, aru;
+    double plo, phi, dlo, dhi;
     regime(i, t_pl, t_pu, apl, apu, plo, phi);
-    // d/dp of the p-terms: alpha p - beta
+    regime(j, t_rd, t_ru, ard, aru, dlo, dhi);
+    // d/dp of the p-terms: alpha p - beta; d/dd of the ramp terms: gamma d - delta
     const double alpha = 2.0 * c2p + rho * (1.0 + apl + apu);
     const double beta = -c1p + rho * (t_gp + (apl ? t_pl : 0.0) + (apu ? t_pu : 0.0));
+    const double gamma = rho * (ard + aru);
+    const double delta = rho * ((ard ? t_rd : 0.0) + (aru ? t_ru : 0.0));
+    if (!has_prev) {
+      phc = p0;
+      pc = clampd((beta + delta + gamma * p0) / (alpha + gamma), 0.0, pmax);
+    } else {
+      // minimise 1/2 x^T H x - r^T x over [0,pmax]^2, x = (p, phat)
+      const double h11 = alpha + gamma, h12 = -gamma, h22 = rho + gamma;
+      const double r1 = beta + delta, r2 = rho * t_tc - delta;
+      const double idet = 1.0 / (h11 * h22 - h12 * h12);
+      pc = (h22 * r1 - h12 * r2) * idet;
+      phc = (h11 * r2 - h12 * r1) * idet;
+      if (!(pc >= 0.0 && pc <= pmax && phc >= 0.0 && phc <= pmax)) {
+        // minimum on the boundary: best of the four clamped edge minimisers
+        const double ih11 = 1.0 / h11, ih22 = 1.0 / h22;
+        double bq = INFINITY, bp = 0.0, bph = 0.0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      int ard, aru;
-      double dlo, dhi;
-      regime(j, t_rd, t_ru, ard, aru, dlo, dhi);
-      // d/dd of the ramp terms: gamma d - delta
-      const double gamma = rho * (ard + aru);
-      const double delta = rho * ((ard ? t_rd : 0.0) + (aru ? t_ru : 0.0));
-      double pc, phc;
-      if (!has_prev) {
-        phc = p0;
-        pc = clampd((beta + delta + gamma * p0) / (alpha + gamma), 0.0, pmax);
-      } else {
-        // minimise 1/2 x^T H x - r^T x over [0,pmax]^2, x = (p, phat)
-        const double h11 = alpha + gamma, h12 = -gamma, h22 = rho + gamma;
-        const double r1 = beta + delta, r2 = rho * t_tc - delta;
-        const double det = h11 * h22 - h12 * h12;
-        pc = (h22 * r1 - h12 * r2) / det;
-        phc = (h11 * r2 - h12 * r1) / det;
-        if (!(pc >= 0.0 && pc <= pmax && phc >= 0.0 && phc <= pmax)) {
-          // minimum on the boundary: best of the four clamped edge minimisers
-          double bq = INFINITY, bp = 0.0, bph = 0.0;
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            double xp, xh;
-            if (e < 2) {
-              xp = (e == 0) ? 0.0 : pmax;
-              xh = clampd((r2 - h12 * xp) / h22, 0.0, pmax);
-            } else {
-              xh = (e == 2) ? 0.0 : pmax;
-              xp = clampd((r1 - h12 * xh) / h11, 0.0, pmax);
-            }
-            const double qv = 0.5 * (h11 * xp * xp + 2.0 * h12 * xp * xh + h22 * xh * xh) - r1 * xp - r2 * xh;
-            if (qv < bq) {
-              bq = qv;
-              bp = xp;
-              bph = xh;
-            }
+        for (int e = 0; e < 4; ++e) {
+          double xp, xh;
+          if (e < 2) {
+            xp = (e == 0) ? 0.0 : pmax;
+            xh = clampd((r2 - h12 * xp) * ih22, 0.0, pmax);
+          } else {
+            xh = (e == 2) ? 0.0 : pmax;
+            xp = clampd((r1 - h12 * xh) * ih11, 0.0, pmax);
           }
-          pc = bp;
-          phc = bph;
+          const double qv = 0.5 * (h11 * xp * xp + 2.0 * h12 * xp * xh + h22 * xh * xh) - r1 * xp - r2 * xh;
+          if (qv < bq) {
+            bq = qv;
+            bp = xp;
+            bph = xh;
+          }
         }
+        pc = bp;
+        phc = bph;
       }
-      const double viol = dist_interval(pc, plo, phi) + dist_interval(pc - phc, dlo, dhi);
+    }
+    return dist_interval(pc, plo, phi) + dist_interval(pc - phc, dlo, dhi);
+  };
+  auto regime_of = [](double v, double bl, double bh) { return v < fmin(bl, bh) ? 0 : (v > fmax(bl, bh) ? 2 : 1); };
+  double p = 0.0, ph = p0;
+  // the previous iterate's piece first: near convergence it is the answer
+  const double tol = 1e-13 * (1.0 + fmax(fmax(fabs(t_pl), fabs(t_pu)), fmax(fabs(t_rd), fabs(t_ru))));
+  const int i0 = regime_of(p_prev, t_pl, t_pu), j0 = regime_of(p_prev - ph_prev, t_rd, t_ru);
+  double best = piece(i0, j0, p, ph);
+  if (best > tol) {
+#pragma unroll 1
+    for (int q = 0; q < 9; ++q) {
+      const int i = q / 3, j = q - 3 * (q / 3);
+      if (i == i0 && j == j0) continue;
+      double pc, phc;
+      const double viol = piece(i, j, pc, phc);
       if (viol < best) {
         best = viol;
         p = pc;
@@ -164,7 +174,8 @@ __global__ void __launch_bounds__(BS) k_gen(Dev S) {
 #pragma unroll
   for (int r = 0; r < 9; ++r) tg[r] = S.GT[rows[r] * NGP + gp];
   if (t == 0) tg[8] = 0.0;
-  const GenOut o = gen_solve(S.c2p[gg], S.c1p[gg], I.rpq, S.Pmax[gg], S.qlo[gg], S.qhi[gg], S.p0[gg], t > 0, tg);
+  const GenOut o = gen_solve(S.c2p[gg], S.c1p[gg], I.rpq, S.Pmax[gg], S.qlo[gg], S.qhi[gg], S.p0[gg], t > 0, tg,
+                             S.G[F_P * NGP + gp], S.G[F_PH * NGP + gp]);
   S.G[F_P * NGP + gp] = o.p;
   S.G[F_Q * NGP + gp] = o.q;
   S.G[F_PH * NGP + gp] = o.ph;
