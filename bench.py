@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--line-form", default="polar", choices=["polar", "w"])
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-1e-4 run")
     ap.add_argument("--ttc-max-sweeps", type=int, default=6000)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -234,6 +235,11 @@ def main():
     params = ucac.ucac_default_params()
     params.line_form = ucac.UCAC_LINE_POLAR if a.line_form == "polar" else ucac.UCAC_LINE_W
     h = ucac.Handle(grids, params=params, stream=stream.cuda_stream)
+    tuning, cache = None, None
+    if not a.no_autotune:
+        cache = os.path.join(os.path.expanduser("~"), ".cache", "ucac", "autotune.txt")
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        tuning = h.autotune(3, cache)
     with torch.cuda.stream(stream):
         h.enqueue(a.warmup)
         stream.synchronize()
@@ -269,10 +275,10 @@ def main():
     # read back the solution and the residual record
     e2e = None
     if not a.no_e2e:
-        e2e = e2e_run(ucac, grids, a.steps, stream, params)
+        e2e = e2e_run(ucac, grids, a.steps, stream, params, cache)
     ttc = None
     if not a.no_ttc:
-        ttc = time_to_tolerance(ucac, grids, stream, params, a.ttc_max_sweeps)
+        ttc = time_to_tolerance(ucac, grids, stream, params, a.ttc_max_sweeps, cache)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         v, sample = oracle_sweep_rate(grids, budget_s=15.0)
@@ -284,6 +290,7 @@ def main():
                 "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (seeded grids shaped like the paper's workloads)",
                 "config": {"workload": a.workload, "instances": len(grids), "line_form": a.line_form,
+                           "block_sizes": tuning,
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "state larger than L2 (no flush needed)", "r_p_inst0": r["r_p"]},
                 "gpu_launches": 6 * a.steps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
@@ -294,7 +301,7 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def time_to_tolerance(ucac, grids, stream, params, max_sweeps):
+def time_to_tolerance(ucac, grids, stream, params, max_sweeps, cache=None):
     """Cold start to convergence of every instance (r_p, r_d <= 1e-4 RMS and
     z_rms <= 1e-4, the inner and outer stops of Algorithm 1) through the public
     API: create from host arrays, ucac_iterate with host checks every 50
@@ -303,6 +310,8 @@ def time_to_tolerance(ucac, grids, stream, params, max_sweeps):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = ucac.Handle(grids, params=params, stream=stream.cuda_stream)
+    if cache:
+        h.autotune(3, cache)  # cache hit: applies the tuned block sizes
     t1 = time.perf_counter()
     done, rc = 0, 0
     while done < max_sweeps and rc != 1:
@@ -319,7 +328,7 @@ def time_to_tolerance(ucac, grids, stream, params, max_sweeps):
             "outer_max": max(r["outer"] for r in rs), "variant": "plain (no learned warm start)"}
 
 
-def e2e_run(ucac, grids, steps, stream, params):
+def e2e_run(ucac, grids, steps, stream, params, cache=None):
     import torch
     # pinned host copies of every grid array
     pinned = []
@@ -335,6 +344,8 @@ def e2e_run(ucac, grids, steps, stream, params):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = ucac.Handle(pinned, params=params, stream=stream.cuda_stream)
+    if cache:
+        h.autotune(3, cache)
     ucac.ucac_iterate(h.h, steps)
     for k, g in enumerate(grids):
         ucac.ucac_solution(h.h, k, g.T, g.n_gen, g.n_bus, g.n_branch)

@@ -199,6 +199,23 @@ int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms);
 const char *ucac_kernel_name(int32_t k);
 
 /*
+ * Autotuner (batching support; no counterpart in the paper).  Times every
+ * candidate block size of each sweep kernel (32, 64, 128, 256 threads; the
+ * persistent line kernel 32, 64, 128) on the handle's own workload --
+ * sweeps_per_trial sweeps per candidate after one warm-up sweep, CUDA events
+ * on the handle's stream, the iterate restored before every trial -- keeps
+ * the fastest per kernel and re-captures the sweep graph.  Block sizes change
+ * no result (work is split in warp-sized granules of one instance each), only
+ * the speed.  cache_path (NULL: none) is a text file of lines
+ *   <device name>|<instances>|<gen-periods>|<line-periods>|<bus-periods>|<line form> ucdp gen line bus ucbar
+ * a matching entry is applied without timing; otherwise the result is
+ * appended.  The iterate is unchanged on return.  Allocates a temporary copy
+ * of the handle's device state.  out5 (may be NULL) receives the chosen sizes
+ * {ucdp, gen, line, bus, ucbar}.  Synchronises.
+ */
+int ucac_autotune(ucac_handle *h, int32_t sweeps_per_trial, const char *cache_path, int32_t *out5);
+
+/*
  * Standalone UC dynamic program (Algorithm 2) for n_gen generators over T
  * periods, on DEVICE arrays.  tau_on/tau_su/tau_sd [T][n_gen] are the targets
  * ubar - z - y/rho of the duplicate rows; c0, c_su, c_sd [n_gen]; TU, TD, u0,

@@ -6,9 +6,11 @@
 //   branch-period  bp = inst.bpo + t * inst.nl + l
 //   bus-period     up = inst.upo + t * inst.nb + i
 // so one launch covers a whole batch and consecutive threads touch
-// consecutive addresses.  Kernels walk a block table whose blocks never
-// straddle two instances, which keeps the residual reductions per instance
-// and deterministic (fixed-order block partials, fixed-order final sum).
+// consecutive addresses.  Each warp handles one granule of 32 consecutive
+// items of one instance (granule tables never straddle two instances), so
+// residual partial sums are per warp and per instance, and the block size of
+// a launch changes neither the work split nor any result: it is free to be
+// tuned (fixed-order warp partials, fixed-order final sum).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -40,7 +42,7 @@ struct Inst {
   int nb, nl, ng, T, ref;
   int go, gpo, lo, bpo, uo, upo;
   int m_rows;
-  int blk_gen0, blk_gen1, blk_gp0, blk_gp1, blk_bp0, blk_bp1, blk_up0, blk_up1;
+  int gran_gen0, gran_gen1, gran_gp0, gran_gp1, gran_bp0, gran_bp1, gran_up0, gran_up1;
   double rpq, rva, ruc;
 };
 
@@ -49,10 +51,12 @@ struct Params {
   int K_AL, K_N, L_max, line_form;
 };
 
-struct Blocks {
+constexpr int GRAN = 32;  // items per granule (one warp)
+
+struct Granules {
   int n;
-  const int *inst;   // instance of each block
-  const int *first;  // global index of the block's first item
+  const int *inst;   // instance of each granule
+  const int *first;  // global index of the granule's first item
 };
 
 struct Dev {
@@ -85,18 +89,40 @@ struct Dev {
   double *ctrl;       // [K][NCTRL]
   double *res;        // [K][NRES]
   long long *stat;    // [K][4]: sweeps, newton, al, capped
-  double *part_up;    // [nblk_up][NQ]
-  double *part_gp;    // [nblk_gp][NQ]
+  double *part_up;    // [granules of bus-periods][NQ]
+  double *part_gp;    // [granules of gen-periods][NQ]
   long long *bstat;   // [K][3]: Newton iterations, AL rounds, capped solves (line kernel, per sweep)
   unsigned long long *bp_counter;  // work counter of the persistent line kernel
   // UC dynamic-program scratch: stage costs, cost-to-go, decisions
   double *dpL;        // [4][T][ng] per instance, instance slice at 4*gpo
   double *dpC;        // [2][T+1][ng] per instance, slice at 2*(gpo+go)
   unsigned char *dpD; // [2][T][ng] per instance, slice at 2*gpo
-  Blocks b_gen, b_gp, b_bp, b_up;
+  Granules g_gen, g_gp, g_bp, g_up;
 };
 
 __device__ __forceinline__ double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
+
+// granule of the calling warp (uniform across the warp), or -1
+template <int BS>
+__device__ __forceinline__ int warp_granule(int n) {
+  const int gr = blockIdx.x * (BS / 32) + (threadIdx.x >> 5);
+  return gr < n ? gr : -1;
+}
+
+// deterministic warp reduction of NQ doubles (sums, except Q_INF = max);
+// lane 0 writes the result
+__device__ __forceinline__ void warp_reduce_q(double (&q)[NQ], double *out) {
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    double v = q[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_down_sync(0xffffffffu, v, o);
+      v = (k == Q_INF) ? fmax(v, w) : v + w;
+    }
+    if ((threadIdx.x & 31) == 0) out[k] = v;
+  }
+}
 
 // deterministic block reduction of NQ doubles (sums, except Q_INF = max)
 template <int BS>

@@ -161,10 +161,11 @@ __device__ __forceinline__ GenOut gen_solve(double c2p, double c1p, double rho, 
 
 template <int BS>
 __global__ void __launch_bounds__(BS) k_gen(Dev S) {
-  const int b = blockIdx.x;
-  const int k = S.b_gp.inst[b];
+  const int gr = warp_granule<BS>(S.g_gp.n);
+  if (gr < 0) return;
+  const int k = S.g_gp.inst[gr];
   const Inst I = S.inst[k];
-  const long long gp = (long long)S.b_gp.first[b] + threadIdx.x;
+  const long long gp = (long long)S.g_gp.first[gr] + (threadIdx.x & 31);
   if (gp >= (long long)I.gpo + (long long)I.T * I.ng) return;
   const int loc = (int)(gp - I.gpo);
   const int t = loc / I.ng, g = loc - t * I.ng, gg = I.go + g;

@@ -101,10 +101,11 @@ __device__ __forceinline__ double uc_dp(int T, int TU, int TD, int u0, int K0, d
 // u_sd and the x-side values of the three duplicate rows.
 template <int BS>
 __global__ void __launch_bounds__(BS) k_ucdp(Dev S) {
-  const int b = blockIdx.x;
-  const int k = S.b_gen.inst[b];
+  const int gr = warp_granule<BS>(S.g_gen.n);
+  if (gr < 0) return;
+  const int k = S.g_gen.inst[gr];
   const Inst I = S.inst[k];
-  const int gg = S.b_gen.first[b] + threadIdx.x;
+  const int gg = S.g_gen.first[gr] + (threadIdx.x & 31);
   if (gg >= I.go + I.ng) return;
   const int g = gg - I.go, ng = I.ng, T = I.T;
   const long long NGP = S.NGP;

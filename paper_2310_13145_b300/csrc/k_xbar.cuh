@@ -71,9 +71,18 @@ __device__ __forceinline__ double row_target_fast(double b, double z, double y, 
   return __dsub_rn(__dsub_rn(b, z), __dmul_rn(y, irho));
 }
 
+// Explicitly rounded operations: the x-bar kernels spell out every multiply,
+// add and fused multiply-add, so that no template instantiation (block size)
+// can contract or reorder them differently -- results are bit-identical
+// whatever launch configuration the autotuner picks.
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+
 // x-bar-step target of a row from its x value a: (a + z) + y/rho
 __device__ __forceinline__ double row_mtarget(double a, double z, double y, const Fam &F) {
-  return (a + z) + y * F.irho;
+  return fma_(y, F.irho, add_(a, z));
 }
 
 template <bool EXACT>
@@ -83,18 +92,20 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
   const double a = A[idx], y = Y[idx], z = Z[idx];
   double lam = L[idx];
   if (R.pend) {
-    lam = clampd(lam + R.beta_cur * z, -R.lam_max, R.lam_max);
+    lam = clampd(fma_(R.beta_cur, z, lam), -R.lam_max, R.lam_max);
     L[idx] = lam;
   }
-  const double c = a - b_new;
-  const double zn = -(lam + y + F.rho * c) * F.ibr;
-  const double yn = y + F.rho * (c + zn);
+  const double c = sub_(a, b_new);
+  const double zn = -mul_(fma_(F.rho, c, add_(lam, y)), F.ibr);
+  const double cz = add_(c, zn);
+  const double yn = fma_(F.rho, cz, y);
   Z[idx] = zn;
   Y[idx] = yn;
   Tg[idx] = EXACT ? row_target_exact(b_new, zn, yn, F.rho) : row_target_fast(b_new, zn, yn, F.irho);
-  q[Q_SP] += (c + zn) * (c + zn);
-  q[Q_SD] += (b_new - b_old) * (b_new - b_old);
-  q[Q_SZ] += zn * zn;
+  const double db = sub_(b_new, b_old);
+  q[Q_SP] = fma_(cz, cz, q[Q_SP]);
+  q[Q_SD] = fma_(db, db, q[Q_SD]);
+  q[Q_SZ] = fma_(zn, zn, q[Q_SZ]);
   q[Q_INF] = fmax(q[Q_INF], fabs(c));
 }
 
@@ -103,11 +114,12 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
 // neighbouring lanes then loop over equally many incident rows, which keeps
 // the warp converged (the order changes no result).
 template <int BS>
-__global__ void __launch_bounds__(BS, UCAC_BUS_MINB) k_bus(Dev S) {
-  const int b = blockIdx.x;
-  const int k = S.b_up.inst[b];
+__global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
+  const int gr = warp_granule<BS>(S.g_up.n);
+  if (gr < 0) return;
+  const int k = S.g_up.inst[gr];
   const Inst I = S.inst[k];
-  const long long upl = (long long)S.b_up.first[b] + threadIdx.x;
+  const long long upl = (long long)S.g_up.first[gr] + (threadIdx.x & 31);
   double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (upl < (long long)I.upo + (long long)I.T * I.nb) {
     const int loc = (int)(upl - I.upo);
@@ -127,44 +139,44 @@ __global__ void __launch_bounds__(BS, UCAC_BUS_MINB) k_bus(Dev S) {
       double iW = irpq;
       if (!last) {
         const long long gn = gp + I.ng;
-        m = 0.5 * (m + row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], Fpq));
+        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], Fpq)));
         iW = 0.5 * irpq;
       }
-      M00 += iW;
-      r0 += m;
-      M11 += irpq;
-      r1 += row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq);
+      M00 = add_(M00, iW);
+      r0 = add_(r0, m);
+      M11 = add_(M11, irpq);
+      r1 = add_(r1, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq));
     }
 #pragma unroll kBusUnroll
     for (int e = e0; e < e1; ++e) {
       const long long bp = (long long)I.bpo + (long long)t * I.nl + S.inc_br[e];
       const int sd = S.inc_side[e];
       const int rp = sd ? 2 : 0, rw = sd ? 5 : 4;
-      M00 += irpq;
-      r0 -= row_mtarget(S.BA[rp * NBP + bp], S.BZ[rp * NBP + bp], S.BY[rp * NBP + bp], Fpq);
-      M11 += irpq;
-      r1 -= row_mtarget(S.BA[(rp + 1) * NBP + bp], S.BZ[(rp + 1) * NBP + bp], S.BY[(rp + 1) * NBP + bp], Fpq);
-      mw += row_mtarget(S.BA[rw * NBP + bp], S.BZ[rw * NBP + bp], S.BY[rw * NBP + bp], Fva);
-      mth += row_mtarget(S.BA[(rw + 2) * NBP + bp], S.BZ[(rw + 2) * NBP + bp], S.BY[(rw + 2) * NBP + bp], Fva);
+      M00 = add_(M00, irpq);
+      r0 = sub_(r0, row_mtarget(S.BA[rp * NBP + bp], S.BZ[rp * NBP + bp], S.BY[rp * NBP + bp], Fpq));
+      M11 = add_(M11, irpq);
+      r1 = sub_(r1, row_mtarget(S.BA[(rp + 1) * NBP + bp], S.BZ[(rp + 1) * NBP + bp], S.BY[(rp + 1) * NBP + bp], Fpq));
+      mw = add_(mw, row_mtarget(S.BA[rw * NBP + bp], S.BZ[rw * NBP + bp], S.BY[rw * NBP + bp], Fva));
+      mth = add_(mth, row_mtarget(S.BA[(rw + 2) * NBP + bp], S.BZ[(rw + 2) * NBP + bp], S.BY[(rw + 2) * NBP + bp], Fva));
     }
     const int deg = e1 - e0;
     const double ideg = 1.0 / deg;
-    mw *= ideg;
-    mth *= ideg;
-    const double iWw = Fva.irho * ideg, aPw = -S.Gs[ig], aQw = S.Bs[ig];
-    M00 += aPw * aPw * iWw;
-    M01 += aPw * aQw * iWw;
-    M11 += aQw * aQw * iWw;
-    r0 += aPw * mw - S.Pd[up];
-    r1 += aQw * mw - S.Qd[up];
+    mw = mul_(mw, ideg);
+    mth = mul_(mth, ideg);
+    const double iWw = mul_(Fva.irho, ideg), aPw = -S.Gs[ig], aQw = S.Bs[ig];
+    M00 = fma_(mul_(aPw, aPw), iWw, M00);
+    M01 = fma_(mul_(aPw, aQw), iWw, M01);
+    M11 = fma_(mul_(aQw, aQw), iWw, M11);
+    r0 = sub_(fma_(aPw, mw, r0), S.Pd[up]);
+    r1 = sub_(fma_(aQw, mw, r1), S.Qd[up]);
     double nuP, nuQ;
     if (M01 == 0.0) {
       nuP = (M00 > 0.0) ? r0 / M00 : 0.0;
       nuQ = (M11 > 0.0) ? r1 / M11 : 0.0;
     } else {
-      const double idet = 1.0 / (M00 * M11 - M01 * M01);
-      nuP = (M11 * r0 - M01 * r1) * idet;
-      nuQ = (M00 * r1 - M01 * r0) * idet;
+      const double idet = 1.0 / sub_(mul_(M00, M11), mul_(M01, M01));
+      nuP = mul_(sub_(mul_(M11, r0), mul_(M01, r1)), idet);
+      nuQ = mul_(sub_(mul_(M00, r1), mul_(M01, r0)), idet);
     }
     // pass 2: new x-bar values, then the rows they own
     for (int e = g0; e < g1; ++e) {
@@ -173,12 +185,12 @@ __global__ void __launch_bounds__(BS, UCAC_BUS_MINB) k_bus(Dev S) {
       double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GZ[GR_GP * NGP + gp], S.GY[GR_GP * NGP + gp], Fpq);
       double iW = irpq;
       if (!last) {
-        m = 0.5 * (m + row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], Fpq));
+        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], Fpq)));
         iW = 0.5 * irpq;
       }
-      const double pnew = m - nuP * iW;
+      const double pnew = fma_(-nuP, iW, m);
       const double qnew =
-          row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq) - nuQ * irpq;
+          fma_(-nuQ, irpq, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq));
       const double pold = S.G[F_PBAR * NGP + gp], qold = S.G[F_QBAR * NGP + gp];
       S.G[F_PBAR * NGP + gp] = pnew;
       S.G[F_QBAR * NGP + gp] = qnew;
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(BS, UCAC_BUS_MINB) k_bus(Dev S) {
                         S.GT + GR_GQ * NGP, gp, qnew, qold, Fpq, R, q);
     }
     const double wold = S.U[FU_W * NUP + up], thold = S.U[FU_TH * NUP + up];
-    const double wnew = mw - (nuP * aPw + nuQ * aQw) * iWw;
+    const double wnew = sub_(mw, mul_(fma_(nuP, aPw, mul_(nuQ, aQw)), iWw));
     const double thnew = (i == I.ref) ? 0.0 : mth;
     S.U[FU_W * NUP + up] = wnew;
     S.U[FU_TH * NUP + up] = thnew;
@@ -203,7 +215,7 @@ __global__ void __launch_bounds__(BS, UCAC_BUS_MINB) k_bus(Dev S) {
       for (int u = 0; u < 2; ++u) {
         const int r = rp + u;
         const double m = row_mtarget(S.BA[r * NBP + bp], S.BZ[r * NBP + bp], S.BY[r * NBP + bp], Fpq);
-        const double vnew = m + (u == 0 ? nuP : nuQ) * irpq;
+        const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, m);
         const double vold = S.B[(FB_FB0 + r) * NBP + bp];
         S.B[(FB_FB0 + r) * NBP + bp] = vnew;
         row_update<false>(S.BA + r * NBP, S.BY + r * NBP, S.BZ + r * NBP, S.BL + r * NBP, S.BT + r * NBP, bp, vnew,
@@ -215,7 +227,7 @@ __global__ void __launch_bounds__(BS, UCAC_BUS_MINB) k_bus(Dev S) {
                         S.BT + (rw + 2) * NBP, bp, thnew, thold, Fva, R, q);
     }
   }
-  block_reduce_q<BS>(q, S.part_up + (long long)b * NQ);
+  warp_reduce_q(q, S.part_up + (long long)gr * NQ);
 }
 
 // ------------------------------------------------------ x-bar^UC (R7) -----
@@ -334,10 +346,11 @@ __device__ __forceinline__ void boxqp3(int n, const double (&H)[3][3], const dou
 
 template <int BS>
 __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
-  const int b = blockIdx.x;
-  const int k = S.b_gp.inst[b];
+  const int gr = warp_granule<BS>(S.g_gp.n);
+  if (gr < 0) return;
+  const int k = S.g_gp.inst[gr];
   const Inst I = S.inst[k];
-  const long long gp = (long long)S.b_gp.first[b] + threadIdx.x;
+  const long long gp = (long long)S.g_gp.first[gr] + (threadIdx.x & 31);
   double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (gp < (long long)I.gpo + (long long)I.T * I.ng) {
     const int loc = (int)(gp - I.gpo);
@@ -415,7 +428,7 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
     q[Q_OBJ] = S.c2p[gg] * p * p + S.c1p[gg] * p + S.c0[gg] * S.G[F_UON * NGP + gp] +
                S.csu[gg] * S.G[F_USU * NGP + gp] + S.csd[gg] * S.G[F_USD * NGP + gp];
   }
-  block_reduce_q<BS>(q, S.part_gp + (long long)b * NQ);
+  warp_reduce_q(q, S.part_gp + (long long)gr * NQ);
 }
 
 // ------------------------------------------------------------ finish -------
@@ -429,14 +442,14 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
   const int k = blockIdx.x;
   const Inst I = S.inst[k];
   double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int bb = I.blk_up0 + threadIdx.x; bb < I.blk_up1; bb += BS) {
+  for (int bb = I.gran_up0 + threadIdx.x; bb < I.gran_up1; bb += BS) {
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
       const double v = S.part_up[(long long)bb * NQ + j];
       q[j] = (j == Q_INF) ? fmax(q[j], v) : q[j] + v;
     }
   }
-  for (int bb = I.blk_gp0 + threadIdx.x; bb < I.blk_gp1; bb += BS) {
+  for (int bb = I.gran_gp0 + threadIdx.x; bb < I.gran_gp1; bb += BS) {
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
       const double v = S.part_gp[(long long)bb * NQ + j];
@@ -495,10 +508,11 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
 // or import).  One thread per gen-period and per branch-period.
 template <int BS>
 __global__ void __launch_bounds__(BS) k_prep_gen(Dev S) {
-  const int b = blockIdx.x;
-  const int k = S.b_gp.inst[b];
+  const int gr = warp_granule<BS>(S.g_gp.n);
+  if (gr < 0) return;
+  const int k = S.g_gp.inst[gr];
   const Inst I = S.inst[k];
-  const long long gp = (long long)S.b_gp.first[b] + threadIdx.x;
+  const long long gp = (long long)S.g_gp.first[gr] + (threadIdx.x & 31);
   if (gp >= (long long)I.gpo + (long long)I.T * I.ng) return;
   const int loc = (int)(gp - I.gpo);
   const int t = loc / I.ng, g = loc - t * I.ng, gg = I.go + g;
@@ -528,10 +542,11 @@ __global__ void __launch_bounds__(BS) k_prep_gen(Dev S) {
 
 template <int BS>
 __global__ void __launch_bounds__(BS) k_prep_branch(Dev S) {
-  const int b = blockIdx.x;
-  const int k = S.b_bp.inst[b];
+  const int gr = warp_granule<BS>(S.g_bp.n);
+  if (gr < 0) return;
+  const int k = S.g_bp.inst[gr];
   const Inst I = S.inst[k];
-  const long long bp = (long long)S.b_bp.first[b] + threadIdx.x;
+  const long long bp = (long long)S.g_bp.first[gr] + (threadIdx.x & 31);
   if (bp >= (long long)I.bpo + (long long)I.T * I.nl) return;
   const int loc = (int)(bp - I.bpo);
   const int t = loc / I.nl, l = loc - t * I.nl;

@@ -12,7 +12,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <mutex>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -28,11 +30,17 @@ using namespace ucac;
 
 namespace {
 
-constexpr int BS_GEN = 64;    // UC DP: one thread per generator
-constexpr int BS_GP = 128;    // generator and x-bar^UC kernels
-constexpr int BS_BP = 64;     // line kernel (register heavy)
-constexpr int BS_UP = 128;    // bus kernel
 constexpr int BS_FIN = 256;   // finish kernel
+constexpr int BS_PREP = 128;  // target preparation after create / import
+
+// Block sizes of the sweep kernels.  With warp-granular work they change
+// neither the work split nor any result, only the speed; ucac_autotune picks
+// them per device and workload shape.
+struct Tuning {
+  int ucdp = 64, gen = 128, line = 64, bus = 128, ucbar = 128;
+};
+const int kBlockSizes[4] = {32, 64, 128, 256};
+const int kLineBlockSizes[3] = {32, 64, 128};
 
 thread_local std::string g_create_error;
 
@@ -55,8 +63,9 @@ struct ucac_handle {
   size_t arena_bytes = 0;
   Dev dev{};
   long long NGEN = 0, NGP = 0, NL = 0, NBP = 0, NB = 0, NUP = 0;
-  int nblk_gen = 0, nblk_gp = 0, nblk_bp = 0, nblk_up = 0;
+  int ngr_gen = 0, ngr_gp = 0, ngr_bp = 0, ngr_up = 0;  // granule counts
   int grid_branch = 0;  // persistent line kernel: resident blocks on the whole GPU
+  Tuning tune;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::string err;
@@ -132,8 +141,9 @@ struct Arena {
   }
 };
 
-void build_blocks(const std::vector<long long> &off, const std::vector<long long> &cnt, int bs, std::vector<int> &inst,
-                  std::vector<int> &first, std::vector<int> &b0, std::vector<int> &b1) {
+// granules of GRAN consecutive items, never straddling two instances
+void build_granules(const std::vector<long long> &off, const std::vector<long long> &cnt, int bs, std::vector<int> &inst,
+                    std::vector<int> &first, std::vector<int> &b0, std::vector<int> &b1) {
   for (size_t k = 0; k < cnt.size(); ++k) {
     b0[k] = (int)inst.size();
     for (long long j = 0; j < cnt[k]; j += bs) {
@@ -149,22 +159,85 @@ void reset_branch_work(ucac_handle *h, cudaStream_t s) {
   cudaMemsetAsync(h->dev.bstat, 0, sizeof(long long) * 3 * h->K, s);
 }
 
+inline int blocks_for(int granules, int bs) { return std::max(1, (granules + bs / 32 - 1) / (bs / 32)); }
+
+#define UCAC_DISPATCH_BS(BSV, KERNEL, NGRAN, STREAM, ARG)                                      \
+  switch (BSV) {                                                                              \
+    case 32: KERNEL<32><<<blocks_for(NGRAN, 32), 32, 0, STREAM>>>(ARG); break;                \
+    case 64: KERNEL<64><<<blocks_for(NGRAN, 64), 64, 0, STREAM>>>(ARG); break;                \
+    case 256: KERNEL<256><<<blocks_for(NGRAN, 256), 256, 0, STREAM>>>(ARG); break;            \
+    default: KERNEL<128><<<blocks_for(NGRAN, 128), 128, 0, STREAM>>>(ARG); break;             \
+  }
+
+void launch_ucdp(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.ucdp, k_ucdp, h->ngr_gen, s, h->dev); }
+void launch_gen(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.gen, k_gen, h->ngr_gp, s, h->dev); }
+void launch_bus(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.bus, k_bus, h->ngr_up, s, h->dev); }
+void launch_ucbar(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.ucbar, k_ucbar, h->ngr_gp, s, h->dev); }
+
+// resident blocks of the persistent line kernel for block size bs
+int line_grid(ucac_handle *h, int bs) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  cudaError_t e;
+  const bool polar = h->prm.line_form == UCAC_LINE_POLAR;
+#define UCAC_OCC(B)                                                                                 \
+  e = polar ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_polar<B>, B, 0)         \
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_branch<B>, B, 0)
+  switch (bs) {
+    case 32: UCAC_OCC(32); break;
+    case 128: UCAC_OCC(128); break;
+    default: UCAC_OCC(64); break;
+  }
+#undef UCAC_OCC
+  if (e != cudaSuccess) return 1;
+  const long long need = (h->NBP + bs - 1) / bs;
+  return (int)std::max(1LL, std::min<long long>((long long)sms * std::max(per_sm, 1), need));
+}
+
 void launch_line(ucac_handle *h, cudaStream_t s) {
   reset_branch_work(h, s);
-  if (h->prm.line_form == UCAC_LINE_POLAR)
-    k_line_polar<BS_BP><<<h->grid_branch, BS_BP, 0, s>>>(h->dev);
-  else
-    k_branch<BS_BP><<<h->grid_branch, BS_BP, 0, s>>>(h->dev);
+  const bool polar = h->prm.line_form == UCAC_LINE_POLAR;
+  const int g = h->grid_branch;
+  switch (h->tune.line) {
+    case 32:
+      if (polar) k_line_polar<32><<<g, 32, 0, s>>>(h->dev); else k_branch<32><<<g, 32, 0, s>>>(h->dev);
+      break;
+    case 128:
+      if (polar) k_line_polar<128><<<g, 128, 0, s>>>(h->dev); else k_branch<128><<<g, 128, 0, s>>>(h->dev);
+      break;
+    default:
+      if (polar) k_line_polar<64><<<g, 64, 0, s>>>(h->dev); else k_branch<64><<<g, 64, 0, s>>>(h->dev);
+      break;
+  }
+}
+
+void launch_prep(ucac_handle *h, cudaStream_t s) {
+  k_prep_gen<BS_PREP><<<blocks_for(h->ngr_gp, BS_PREP), BS_PREP, 0, s>>>(h->dev);
+  k_prep_branch<BS_PREP><<<blocks_for(h->ngr_bp, BS_PREP), BS_PREP, 0, s>>>(h->dev);
 }
 
 void launch_sweep(ucac_handle *h, cudaStream_t s) {
-  const Dev &D = h->dev;
-  k_ucdp<BS_GEN><<<h->nblk_gen, BS_GEN, 0, s>>>(D);
-  k_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
+  launch_ucdp(h, s);
+  launch_gen(h, s);
   launch_line(h, s);
-  k_bus<BS_UP><<<h->nblk_up, BS_UP, 0, s>>>(D);
-  k_ucbar<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
-  k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(D);
+  launch_bus(h, s);
+  launch_ucbar(h, s);
+  k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(h->dev);
+}
+
+// (re)captures one sweep into the handle's graph
+cudaError_t capture_graph(ucac_handle *h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  launch_sweep(h, h->cap);
+  e = cudaStreamEndCapture(h->cap, &h->graph);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
+  return e;
 }
 
 const char *kKernelNames[UCAC_N_KERNELS] = {"k_ucdp", "k_gen", "k_branch", "k_bus", "k_ucbar", "k_finish"};
@@ -384,25 +457,25 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
       offb[k] = I.bpo; cntb[k] = (long long)I.T * I.nl;
       offu[k] = I.upo; cntu[k] = (long long)I.T * I.nb;
     }
-    build_blocks(offg, cntg, BS_GEN, bgi, bgf, g0, g1);
-    build_blocks(offp, cntp, BS_GP, bpi, bpf, p0b, p1b);
-    build_blocks(offb, cntb, BS_BP, bbi, bbf, q0b, q1b);
-    build_blocks(offu, cntu, BS_UP, bui, buf_, u0b, u1b);
+    build_granules(offg, cntg, GRAN, bgi, bgf, g0, g1);
+    build_granules(offp, cntp, GRAN, bpi, bpf, p0b, p1b);
+    build_granules(offb, cntb, GRAN, bbi, bbf, q0b, q1b);
+    build_granules(offu, cntu, GRAN, bui, buf_, u0b, u1b);
   }
-  h->nblk_gen = (int)bgi.size();
-  h->nblk_gp = (int)bpi.size();
-  h->nblk_bp = (int)bbi.size();
-  h->nblk_up = (int)bui.size();
+  h->ngr_gen = (int)bgi.size();
+  h->ngr_gp = (int)bpi.size();
+  h->ngr_bp = (int)bbi.size();
+  h->ngr_up = (int)bui.size();
   for (int k = 0; k < n; ++k) {
     const HInst &I = h->hi[k];
     Inst D{};
     D.nb = I.nb; D.nl = I.nl; D.ng = I.ng; D.T = I.T; D.ref = I.ref;
     D.go = I.go; D.gpo = I.gpo; D.lo = I.lo; D.bpo = I.bpo; D.uo = I.uo; D.upo = I.upo;
     D.m_rows = I.T * 8 * I.nl + I.ng * (12 * I.T - 1);
-    D.blk_gen0 = g0[k]; D.blk_gen1 = g1[k];
-    D.blk_gp0 = p0b[k]; D.blk_gp1 = p1b[k];
-    D.blk_bp0 = q0b[k]; D.blk_bp1 = q1b[k];
-    D.blk_up0 = u0b[k]; D.blk_up1 = u1b[k];
+    D.gran_gen0 = g0[k]; D.gran_gen1 = g1[k];
+    D.gran_gp0 = p0b[k]; D.gran_gp1 = p1b[k];
+    D.gran_bp0 = q0b[k]; D.gran_bp1 = q1b[k];
+    D.gran_up0 = u0b[k]; D.gran_up1 = u1b[k];
     D.rpq = rhos[k].pq; D.rva = rhos[k].va; D.ruc = rhos[k].uc;
     h->inst_h.push_back(D);
   }
@@ -421,11 +494,11 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
   const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
   const size_t o_stat = A.take<long long>(4 * n);
-  const size_t o_pup = A.take<double>((size_t)NQ * h->nblk_up), o_pgp = A.take<double>((size_t)NQ * h->nblk_gp);
+  const size_t o_pup = A.take<double>((size_t)NQ * h->ngr_up), o_pgp = A.take<double>((size_t)NQ * h->ngr_gp);
   const size_t o_pbp = A.take<long long>(3 * (size_t)n + 8);
   const size_t o_dpL = A.take<double>(4 * NGP), o_dpC = A.take<double>(2 * (NGP + NGEN));
   const size_t o_dpD = A.take<unsigned char>(2 * NGP);
-  const size_t o_blk = A.take<int>(2 * ((size_t)h->nblk_gen + h->nblk_gp + h->nblk_bp + h->nblk_up));
+  const size_t o_blk = A.take<int>(2 * ((size_t)h->ngr_gen + h->ngr_gp + h->ngr_bp + h->ngr_up));
   h->arena_bytes = A.off;
   cudaError_t ce = cudaMalloc((void **)&h->arena, h->arena_bytes);
   if (ce != cudaSuccess) {
@@ -478,13 +551,13 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.dpC = (double *)(ar + o_dpC);
   D.dpD = (unsigned char *)(ar + o_dpD);
   int *blk = (int *)(ar + o_blk);
-  D.b_gen = Blocks{h->nblk_gen, blk, blk + h->nblk_gen};
-  blk += 2 * h->nblk_gen;
-  D.b_gp = Blocks{h->nblk_gp, blk, blk + h->nblk_gp};
-  blk += 2 * h->nblk_gp;
-  D.b_bp = Blocks{h->nblk_bp, blk, blk + h->nblk_bp};
-  blk += 2 * h->nblk_bp;
-  D.b_up = Blocks{h->nblk_up, blk, blk + h->nblk_up};
+  D.g_gen = Granules{h->ngr_gen, blk, blk + h->ngr_gen};
+  blk += 2 * h->ngr_gen;
+  D.g_gp = Granules{h->ngr_gp, blk, blk + h->ngr_gp};
+  blk += 2 * h->ngr_gp;
+  D.g_bp = Granules{h->ngr_bp, blk, blk + h->ngr_bp};
+  blk += 2 * h->ngr_bp;
+  D.g_up = Granules{h->ngr_up, blk, blk + h->ngr_up};
 
   auto up = [&](const void *dst, const void *src, size_t bytes) -> cudaError_t {
     if (bytes == 0) return cudaSuccess;
@@ -539,35 +612,19 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   chain(up(D.Pd, pqh.data(), pqh.size() * 8));
   chain(up(D.U, U.data(), U.size() * 8));
   chain(up(D.ctrl, ctrl.data(), ctrl.size() * 8));
-  chain(up(D.b_gen.inst, blkh.data(), blkh.size() * 4));
+  chain(up(D.g_gen.inst, blkh.data(), blkh.size() * 4));
   if (e != cudaSuccess) {
     std::string m = std::string("upload: ") + cudaGetErrorString(e);
     ucac_destroy(h);
     return fail(nullptr, UCAC_E_CUDA, m);
   }
-  {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = (h->prm.line_form == UCAC_LINE_POLAR)
-              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_polar<BS_BP>, BS_BP, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_branch<BS_BP>, BS_BP, 0);
-    const long long need = (NBP + BS_BP - 1) / BS_BP;
-    h->grid_branch = (int)std::max(1LL, std::min<long long>((long long)sms * std::max(per_sm, 1), need));
-  }
-  k_prep_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, h->stream>>>(D);
-  k_prep_branch<BS_BP><<<h->nblk_bp, BS_BP, 0, h->stream>>>(D);
+  h->grid_branch = line_grid(h, h->tune.line);
+  launch_prep(h, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   // ---- capture one sweep into a graph (capture needs a non-legacy stream)
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    launch_sweep(h, h->cap);
-    e = cudaStreamEndCapture(h->cap, &h->graph);
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
+  if (e == cudaSuccess) e = capture_graph(h);
   if (e != cudaSuccess) {
     std::string m = std::string("setup: ") + cudaGetErrorString(e);
     ucac_destroy(h);
@@ -710,8 +767,7 @@ int ucac_state_import(ucac_handle *h, int32_t k, const double *buf, size_t n) {
     CK(cudaMemcpy(sg.first, buf + o, sg.second * 8, cudaMemcpyHostToDevice));
     o += sg.second;
   }
-  k_prep_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, h->stream>>>(h->dev);
-  k_prep_branch<BS_BP><<<h->nblk_bp, BS_BP, 0, h->stream>>>(h->dev);
+  launch_prep(h, h->stream);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return UCAC_OK;
@@ -726,15 +782,15 @@ int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
   cudaStream_t s = h->stream;
   for (int it = 0; it < n_sweeps; ++it) {
     CK(cudaEventRecord(ev[0], s));
-    k_ucdp<BS_GEN><<<h->nblk_gen, BS_GEN, 0, s>>>(D);
+    launch_ucdp(h, s);
     CK(cudaEventRecord(ev[1], s));
-    k_gen<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
+    launch_gen(h, s);
     CK(cudaEventRecord(ev[2], s));
     launch_line(h, s);
     CK(cudaEventRecord(ev[3], s));
-    k_bus<BS_UP><<<h->nblk_up, BS_UP, 0, s>>>(D);
+    launch_bus(h, s);
     CK(cudaEventRecord(ev[4], s));
-    k_ucbar<BS_GP><<<h->nblk_gp, BS_GP, 0, s>>>(D);
+    launch_ucbar(h, s);
     CK(cudaEventRecord(ev[5], s));
     k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(D);
     CK(cudaEventRecord(ev[6], s));
@@ -749,6 +805,88 @@ int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
   for (auto &e : ev) cudaEventDestroy(e);
   for (int j = 0; j < UCAC_N_KERNELS; ++j) ms[j] = acc[j] / n_sweeps;
   return UCAC_OK;
+}
+
+int ucac_autotune(ucac_handle *h, int32_t sweeps_per_trial, const char *cache_path, int32_t *out5) {
+  if (!h || sweeps_per_trial < 1) return fail(h, UCAC_E_ARG, "bad arguments");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, dev));
+  std::ostringstream ks;
+  ks << prop.name << "|" << h->K << "|" << h->NGP << "|" << h->NBP << "|" << h->NUP << "|" << h->prm.line_form;
+  const std::string key = ks.str();
+  auto apply = [&](const Tuning &t) -> int {
+    h->tune = t;
+    h->grid_branch = line_grid(h, t.line);
+    CK(cudaStreamSynchronize(h->stream));
+    CK(capture_graph(h));
+    if (out5) {
+      out5[0] = t.ucdp; out5[1] = t.gen; out5[2] = t.line; out5[3] = t.bus; out5[4] = t.ucbar;
+    }
+    return UCAC_OK;
+  };
+  auto valid = [](int b, bool line) {
+    for (int c : (line ? std::vector<int>{32, 64, 128} : std::vector<int>{32, 64, 128, 256}))
+      if (b == c) return true;
+    return false;
+  };
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      const size_t sp = line.rfind('|');
+      if (sp == std::string::npos) continue;
+      const size_t ws = line.find(' ', sp);
+      if (ws == std::string::npos || line.substr(0, ws) != key) continue;
+      std::istringstream vs(line.substr(ws));
+      Tuning t;
+      if ((vs >> t.ucdp >> t.gen >> t.line >> t.bus >> t.ucbar) && valid(t.ucdp, false) && valid(t.gen, false) &&
+          valid(t.line, true) && valid(t.bus, false) && valid(t.ucbar, false))
+        return apply(t);
+    }
+  }
+  // save the iterate (the whole arena), time the candidates, restore
+  void *save = nullptr;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMalloc(&save, h->arena_bytes));
+  auto restore = [&]() { return cudaMemcpyAsync(h->arena, save, h->arena_bytes, cudaMemcpyDeviceToDevice, h->stream); };
+  cudaError_t e = cudaMemcpyAsync(save, h->arena, h->arena_bytes, cudaMemcpyDeviceToDevice, h->stream);
+  Tuning best = h->tune;
+  int* fields[5] = {&best.ucdp, &best.gen, &best.line, &best.bus, &best.ucbar};
+  const int kidx[5] = {0, 1, 2, 3, 4};  // position of each kernel in ucac_kernel_times
+  double ms[UCAC_N_KERNELS];
+  for (int f = 0; f < 5 && e == cudaSuccess; ++f) {
+    const bool line = (f == 2);
+    const int nc = line ? 3 : 4;
+    double best_ms = INFINITY;
+    int best_bs = *fields[f];
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+      const int bs = line ? kLineBlockSizes[c] : kBlockSizes[c];
+      h->tune = best;
+      int *cur[5] = {&h->tune.ucdp, &h->tune.gen, &h->tune.line, &h->tune.bus, &h->tune.ucbar};
+      *cur[f] = bs;
+      h->grid_branch = line_grid(h, h->tune.line);
+      e = restore();
+      if (e != cudaSuccess) break;
+      if (ucac_kernel_times(h, 1, ms) != UCAC_OK) { e = cudaErrorUnknown; break; }
+      if (ucac_kernel_times(h, sweeps_per_trial, ms) != UCAC_OK) { e = cudaErrorUnknown; break; }
+      if (ms[kidx[f]] < best_ms) {
+        best_ms = ms[kidx[f]];
+        best_bs = bs;
+      }
+    }
+    *fields[f] = best_bs;
+  }
+  if (e == cudaSuccess) e = restore();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(save);
+  if (e != cudaSuccess) return fail(h, UCAC_E_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  if (cache_path) {
+    std::ofstream o(cache_path, std::ios::app);
+    o << key << " " << best.ucdp << " " << best.gen << " " << best.line << " " << best.bus << " " << best.ucbar << "\n";
+  }
+  return apply(best);
 }
 
 const char *ucac_kernel_name(int32_t k) { return (k >= 0 && k < UCAC_N_KERNELS) ? kKernelNames[k] : ""; }

@@ -27,7 +27,7 @@ UCAC_LINE_W, UCAC_LINE_POLAR = 0, 1
 EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_instances", "ucac_iterate",
            "ucac_enqueue_sweeps", "ucac_residuals", "ucac_solution", "ucac_state_size", "ucac_state_export",
            "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp", "ucac_ucdp_noalloc",
-           "ucac_probe_fp64", "ucac_destroy", "ucac_last_error"]
+           "ucac_probe_fp64", "ucac_autotune", "ucac_destroy", "ucac_last_error"]
 
 
 class ucac_grid(C.Structure):
@@ -94,6 +94,7 @@ def lib():
         L.ucac_ucdp.argtypes = [C.c_int32, C.c_int32, C.c_double] + [vp] * 12 + [vp, C.c_size_t, vp]
         L.ucac_ucdp_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_double] + [vp] * 12 + [vp]
         L.ucac_probe_fp64.argtypes = [C.c_int32, vp, _dp]
+        L.ucac_autotune.argtypes = [vp, C.c_int32, C.c_char_p, _ip]
         L.ucac_destroy.argtypes = [vp]
         L.ucac_destroy.restype = None
         L.ucac_last_error.argtypes = [vp]
@@ -241,6 +242,13 @@ def ucac_probe_fp64(reps: int = 5, stream=0) -> float:
     return f.value
 
 
+def ucac_autotune(h, sweeps_per_trial: int = 3, cache_path: str | None = None) -> dict:
+    out = np.zeros(5, np.int32)
+    cp = cache_path.encode() if cache_path else None
+    _check(lib().ucac_autotune(h, int(sweeps_per_trial), cp, out.ctypes.data_as(_ip)), h)
+    return dict(zip(("ucdp", "gen", "line", "bus", "ucbar"), (int(v) for v in out)))
+
+
 def ucac_destroy(h) -> None:
     if h:
         lib().ucac_destroy(h)
@@ -286,3 +294,6 @@ class Handle:
 
     def kernel_times(self, n=5):
         return ucac_kernel_times(self.h, n)
+
+    def autotune(self, sweeps_per_trial=3, cache_path=None):
+        return ucac_autotune(self.h, sweeps_per_trial, cache_path)
