@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ucac", choices=["ucac", "reference"])
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "dp"],
+                    help="dp: the UC dynamic program alone on 1,000 and 10,000 generators (Fig. 1 workload)")
     ap.add_argument("--workload", default="c5_2000bus_T24x16", choices=sorted(synth.CONFIGS))
     ap.add_argument("--instances", type=int, default=None, help="use only the first N instances (profiling)")
     ap.add_argument("--line-form", default="polar", choices=["polar", "w"])
@@ -212,9 +214,70 @@ def reference_arm(a, grids):
 
 
 # ------------------------------------------------------------------ GPU arm
+def dp_inputs(ng, T, seed):
+    """Seeded UC subproblems: duplicate-row targets around the relaxed schedule,
+    costs and minimum up/down times of the synthetic fleet."""
+    rng = np.random.Generator(np.random.Philox(np.random.SeedSequence([seed, ng, T])))
+    return dict(tau_on=rng.uniform(-0.2, 1.2, (T, ng)), tau_su=rng.uniform(-0.2, 0.5, (T, ng)),
+                tau_sd=rng.uniform(-0.2, 0.5, (T, ng)), c0=rng.uniform(100, 500, ng), csu=rng.uniform(200, 1000, ng),
+                csd=np.zeros(ng), TU=rng.integers(1, 9, ng).astype(np.int32), TD=rng.integers(1, 9, ng).astype(np.int32),
+                u0=rng.integers(0, 2, ng).astype(np.int32), K0=np.zeros(ng, np.int32))
+
+
+def dp_mode(a):
+    """The DP-only workload of Fig. 1: time of one UC-subproblem solve for all
+    generators, GPU (ucac_ucdp) against the oracle's C loop on one core; the
+    decisions and costs are checked bit for bit."""
+    import torch
+    import oracle
+    from paper_2310_13145_b300 import build, ucac
+    build.build()
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream().cuda_stream
+    rows = []
+    rho = 1e4
+    for ng in (1000, 10000):
+        for T in (24, 48, 96, 168):
+            x = dp_inputs(ng, T, 7)
+            f64 = lambda v: torch.as_tensor(v, dtype=torch.float64, device=dev)
+            i32 = lambda v: torch.as_tensor(v, dtype=torch.int32, device=dev)
+            A = [f64(x["tau_on"]), f64(x["tau_su"]), f64(x["tau_sd"]), f64(x["c0"]), f64(x["csu"]), f64(x["csd"]),
+                 i32(x["TU"]), i32(x["TD"]), i32(x["u0"]), i32(x["K0"])]
+            u = torch.zeros((T, ng), dtype=torch.int8, device=dev)
+            cost = torch.zeros(ng, dtype=torch.float64, device=dev)
+            nb = ucac.ucac_ucdp_workspace_bytes(ng, T)
+            ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+            args = [t.data_ptr() for t in A] + [u.data_ptr(), cost.data_ptr(), ws.data_ptr(), nb, stream]
+            for _ in range(3):
+                ucac.ucac_ucdp(ng, T, rho, *args)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 50
+            e0.record()
+            for _ in range(reps):
+                ucac.ucac_ucdp(ng, T, rho, *args)
+            e1.record()
+            torch.cuda.synchronize()
+            gpu_ms = e0.elapsed_time(e1) / reps
+            t0 = time.perf_counter()
+            uo, co = oracle.ucdp_batch(rho, x["tau_on"], x["tau_su"], x["tau_sd"], x["c0"], x["csu"], x["csd"],
+                                       x["TU"], x["TD"], x["u0"], x["K0"])
+            cpu_ms = (time.perf_counter() - t0) * 1e3
+            exact = bool(np.array_equal(uo, u.cpu().numpy()) and np.array_equal(co, cost.cpu().numpy()))
+            rows.append({"n_gen": ng, "T": T, "gpu_ms": gpu_ms, "cpu_ms": cpu_ms, "speedup": cpu_ms / gpu_ms,
+                         "bit_exact": exact})
+    print(json.dumps({"metric": "UC dynamic program (Algorithm 2) time per solve of all generators",
+                      "unit": "ms", "higher_is_better": False, "workload": "dp_fig1 (1,000 and 10,000 generators, "
+                      "T = 24..168, seeded targets)", "cpu": "oracle C loop, 1 core", "rows": rows}), flush=True)
+
+
 def main():
     a = parse()
     rank, world, local = dist_info()
+    if a.mode == "dp":
+        if rank == 0:
+            dp_mode(a)
+        return
     grids = synth.config_instances(a.workload, a.instances)
     if a.impl == "reference":
         reference_arm(a, grids)

@@ -79,6 +79,8 @@ def lib():
                                            C.c_int, C.c_int, _dp, _dp, _dp, _dp, _ip]
             L.orc_bus_solve.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_double, _dp]
             L.orc_boxqp.argtypes = [C.c_int, _dp, _dp, _dp]
+            L.orc_ucdp_batch.argtypes = [C.c_int, C.c_int, C.c_double] + [_dp] * 6 + [_ip] * 4 + \
+                [C.POINTER(C.c_int8), _dp]
             _lib = L
     return _lib
 
@@ -235,6 +237,19 @@ def dp(L, TU, TD, u0, K0=0):
     u = np.zeros(T, np.int32)
     c = lib().orc_dp(T, int(TU), int(TD), int(u0), int(K0), _d(L), _i(u))
     return c, u
+
+
+def ucdp_batch(rho, tau_on, tau_su, tau_sd, c0, csu, csd, TU, TD, u0, K0):
+    """Algorithm 2 for every generator of [T][n_gen] inputs; returns (u_on int8 [T][n_gen], cost [n_gen])."""
+    tau_on, tau_su, tau_sd, c0, csu, csd = (np.ascontiguousarray(x, np.float64)
+                                            for x in (tau_on, tau_su, tau_sd, c0, csu, csd))
+    TU, TD, u0, K0 = (np.ascontiguousarray(x, np.int32) for x in (TU, TD, u0, K0))
+    T, ng = tau_on.shape
+    u = np.zeros((T, ng), np.int8)
+    cost = np.zeros(ng)
+    lib().orc_ucdp_batch(ng, T, float(rho), _d(tau_on), _d(tau_su), _d(tau_sd), _d(c0), _d(csu), _d(csd), _i(TU),
+                         _i(TD), _i(u0), _i(K0), u.ctypes.data_as(C.POINTER(C.c_int8)), _d(cost))
+    return u, cost
 
 
 def gen_solve(prm, has_prev, tg):

@@ -1452,3 +1452,30 @@ EXPORT void orc_rows(void *h, double *GA, double *GB, double *BA, double *BB) {
   memcpy(GA, I->GA, GN * 8); memcpy(GB, I->GB, GN * 8);
   memcpy(BA, I->BA, BN * 8); memcpy(BB, I->BB, BN * 8);
 }
+
+/*
+ * Algorithm 2 for n_gen generators over T periods, inputs [T][n_gen]
+ * (duplicate-row targets tau = ubar - z - y/rho), outputs u_on [T][n_gen] and
+ * the DP cost per generator: the stage costs and the DP above, one generator
+ * after another.  The CPU reference of the DP-only workload of Fig. 1.
+ */
+EXPORT void orc_ucdp_batch(int ng, int T, double rho, const double *tau_on, const double *tau_su,
+                           const double *tau_sd, const double *c0, const double *csu, const double *csd,
+                           const int32_t *TU, const int32_t *TD, const int32_t *u0, const int32_t *K0,
+                           int8_t *u_on, double *cost) {
+  double *ton = (double *)malloc(sizeof(double) * T), *tsu = (double *)malloc(sizeof(double) * T);
+  double *tsd = (double *)malloc(sizeof(double) * T), *L = (double *)malloc(sizeof(double) * 4 * T);
+  int32_t *u = (int32_t *)malloc(sizeof(int32_t) * T);
+  for (int g = 0; g < ng; ++g) {
+    for (int t = 0; t < T; ++t) {
+      ton[t] = tau_on[(size_t)t * ng + g];
+      tsu[t] = tau_su[(size_t)t * ng + g];
+      tsd[t] = tau_sd[(size_t)t * ng + g];
+    }
+    orc_uc_stagecost(T, c0[g], csu[g], csd[g], rho, ton, tsu, tsd, L);
+    int k0 = K0[g] < 0 ? 0 : (K0[g] > T ? T : K0[g]);
+    cost[g] = orc_dp(T, TU[g] < 1 ? 1 : TU[g], TD[g] < 1 ? 1 : TD[g], u0[g] ? 1 : 0, k0, L, u);
+    for (int t = 0; t < T; ++t) u_on[(size_t)t * ng + g] = (int8_t)u[t];
+  }
+  free(ton); free(tsu); free(tsd); free(L); free(u);
+}

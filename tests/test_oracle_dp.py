@@ -131,3 +131,17 @@ def test_golden_cases():
         f = bf.objective(u, c["u0"], c["c0"], c["csu"], c["csd"], c["rho"], c["ubar"], c["y"], c["z"])
         assert abs(f - c["best"]) <= 1e-9 * max(1.0, abs(c["best"])), c["name"]
         assert list(u) == c["schedule"] or abs(f - c["best"]) <= 1e-12 * abs(c["best"])
+
+
+def test_batched_dp_equals_per_generator_dp():
+    rng = np.random.default_rng(11)
+    T, ng = 24, 40
+    tau = [rng.uniform(-0.3, 1.3, (T, ng)) for _ in range(3)]
+    c0, csu, csd = rng.uniform(0, 500, ng), rng.uniform(0, 900, ng), rng.uniform(0, 100, ng)
+    TU, TD = rng.integers(1, 6, ng), rng.integers(1, 6, ng)
+    u0, K0 = rng.integers(0, 2, ng), rng.integers(0, 3, ng)
+    u, cost = oracle.ucdp_batch(1e3, *tau, c0, csu, csd, TU, TD, u0, K0)
+    for g in range(ng):
+        L = oracle.uc_stagecost(c0[g], csu[g], csd[g], 1e3, tau[0][:, g], tau[1][:, g], tau[2][:, g])
+        c, ug = oracle.dp(L, TU[g], TD[g], u0[g], K0[g])
+        assert c == cost[g] and np.array_equal(ug, u[:, g])
