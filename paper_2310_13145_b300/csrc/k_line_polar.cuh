@@ -1,38 +1,58 @@
 // k_line_polar.cuh -- line x-update per (t, line ij) solved in polar form.
 //
 // The line subproblem (variables w_i, w_j, wR, wI, theta_i, theta_j and the
-// line-limit slacks; the product equation wR^2 + wI^2 = w_i w_j and the angle
-// equation theta_i - theta_j = atan2(wI, wR) of Eq. acopf) is parametrised by
-// x = (V_i, V_j, d):
+// line-limit slacks sigma_ij, sigma_ji; the product equation wR^2 + wI^2 =
+// w_i w_j and the angle equation theta_i - theta_j = atan2(wI, wR) of
+// Eq. acopf) is parametrised by x = (V_i, V_j, d):
 //   w_i = V_i^2, w_j = V_j^2, wR = V_i V_j cos d, wI = V_i V_j sin d,
 // which satisfies both equations identically for |d| < pi.  The angle copies
 // enter only through d = theta_i - theta_j and their own consensus rows, so
 // their common mode has the closed form theta_i + theta_j = t_6 + t_7 and the
 // two angle rows contribute rho_va/4 (d - (t_6 - t_7))^2.  The line limits
-// p^2 + q^2 <= rate^2 (the slack form of Eq. uc_acopf_ij/ji_limit) are handled
-// by the augmented Lagrangian for inequalities,
-//   psi(g) = (max(0, mu + c g)^2 - mu^2) / (2c),  mu <- max(0, mu + c g),
-// and are inactive on most lines, where one Newton solve ends the subproblem.
+// keep the slack form of Eq. uc_acopf_ij/ji_limit,
+//   h_k = p_k^2 + q_k^2 + sigma_k - rate^2 = 0,  sigma_k >= 0,
+// under the augmented Lagrangian mu_k h_k + c/2 h_k^2 with the bounded slacks
+// as variables, so the inner objective over v = (V_i, V_j, d, sigma_ij,
+// sigma_ji) is smooth and the bound sigma_k >= 0 is met by projection (an
+// inequality penalty max(0, .)^2 in x alone has a curvature jump of order c
+// at the limit, which stalls the trust-region Newton once c is large).
 // This is the same subproblem as the W-form kernel (same feasible set and
-// objective, hence the same KKT points); only the coordinates differ.
+// objective, hence the same KKT points); only the coordinates differ.  The
+// W-form's upper slack bound sigma_k <= rate^2 is implied by h_k = 0 and is
+// dropped: held by an epsilon-active set on a line with almost no flow it
+// would pin h_k at the flow's square and make the multiplier oscillate.
 // The voltage bounds Vmin <= V <= Vmax are Eq. uc_acopf_w_bound; the angle
 // bounds |theta| <= 2 pi of the W-form are never active and are dropped.
 //
-// Inner solver per x (3 variables): the same projected Newton method with an
-// epsilon-active set, Cholesky (shifted only when not positive definite), a
-// trust radius and the final-step rule as the W-form kernel; in addition an
-// undamped step of size <= 1e-4 (1 + |x|) inside the radius is accepted
-// without the ratio test (its model error is at the rounding level).
+// Inner solver: the projected Newton method with an epsilon-active set,
+// Cholesky (shifted only when not positive definite), a trust radius on x and
+// the final-step rule of the W-form kernel, applied to the five variables.
+// The objective is quadratic in each slack with curvature c and coupling
+// c grad(g_k), so a free slack is eliminated from the Newton system exactly:
+// the 3x3 system in x carries c grad(g_k) grad(g_k)^T only for slacks held
+// at zero, the slack step follows from the x step, and the x-Hessian drops
+// m_k hess(g_k) of a free slack (m_k = mu_k + c h_k vanishes at the slack's
+// optimum: this is the Hessian of the problem reduced over the slack).
+// Stationarity is tested on the reduced gradient, after which each free
+// slack takes its exact step -m_k / c.  A trial step gets a second-order
+// correction before the ratio test: free slacks absorb the O(|dx|^2)
+// remainder of g_k, and a slack held at zero gets a correction in x along
+// grad g_k, so that c/2 h_k^2 sees the linear prediction instead of the
+// remainder magnified by c.  An undamped step of size <= 1e-4 (1 + |x|)
+// inside the radius that leaves every free variable inside its box is
+// accepted without the ratio test (its model error is at the rounding
+// level).
 // Precision split (B300's FP64 pipe is 1/64 of its FP32 pipe): the iterate,
 // flows, residuals, gradient and objective are FP64 -- they fix the converged
 // point -- while the Hessian and the Newton system are FP32 on lanes whose
-// line limits are inactive (condition number ~1e3-1e4, so the direction is
+// slacks are off zero (condition number ~1e3-1e4, so the direction is
 // accurate to ~1e-4 and Newton still converges in a step or two); lanes with
-// an active limit (penalty c up to 1e6 rho, condition up to ~1e9) keep the
-// FP64 Hessian.  After the last (tiny) step the flows and cos/sin are updated
-// to first order from the last evaluation instead of being re-evaluated (the
-// error is the square of a step below 1e-9).  Persistent kernel with per-lane
-// work fetching (see k_branch.cuh).
+// a slack held at zero (the c grad grad^T term, c up to 1e6 rho) keep the
+// FP64 Hessian.  After a final step below 1e-8 the flows and cos/sin are
+// updated to first order from the last evaluation, and h_k in FP64 from
+// grad g_k (the gradient the slack step was taken from), instead of being
+// re-evaluated (the error is the square of the step).  Persistent kernel
+// with per-lane work fetching (see k_branch.cuh).
 #pragma once
 #include "common.cuh"
 
@@ -47,24 +67,35 @@ struct PolP {
   double tg[8];
   double rpq, rva;
   double mu[2];  // line-limit multipliers (ij, ji)
-  double c;
+  double c, ic;  // penalty and its reciprocal
 };
 
 // last full evaluation: flows, their gradients (FP32: used only for the
-// first-order update after a tiny step), cos/sin and the point
+// first-order update after a tiny step), cos/sin, the point, the limit
+// gradients grad(g_k) and the multiplier estimates m_k = mu_k + c h_k
 struct PolLast {
-  double a[4], c, s, x[3];
+  double a[4], c, s, v[5];
+  double dg[2][3], m[2], h[2];
   float da[4][3];
-  bool lim;  // a line-limit term is active: the FP64 Hessian is in use
+  bool lim;  // a slack is held at zero: the FP64 Hessian is in use
 };
 
-__device__ __forceinline__ double pol_lo(const PolK &K, int i) { return i == 0 ? K.lo0 : (i == 1 ? K.lo1 : -3.14159265358979); }
-__device__ __forceinline__ double pol_hi(const PolK &K, int i) { return i == 0 ? K.hi0 : (i == 1 ? K.hi1 : 3.14159265358979); }
+constexpr int POL_NV = 5;  // V_i, V_j, d, sigma_ij, sigma_ji
 
-// objective (and flows, cos/sin) at x
-__device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, const double (&x)[3], double (&a)[4],
-                                          double &c, double &s) {
-  const double Vi = x[0], Vj = x[1], d = x[2];
+__device__ __forceinline__ double pol_lo(const PolK &K, int i) {
+  return i == 0 ? K.lo0 : (i == 1 ? K.lo1 : (i == 2 ? -3.14159265358979 : 0.0));
+}
+__device__ __forceinline__ double pol_hi(const PolK &K, int i) {
+  return i == 0 ? K.hi0 : (i == 1 ? K.hi1 : (i == 2 ? 3.14159265358979 : INFINITY));
+}
+
+// objective (and flows, cos/sin) at v.  Slacks in free_mask are first set
+// to max(0, ht_k - g_k(x)), so that h_k takes its predicted value ht_k (the
+// second-order correction of a trial step: without it the c/2 h_k^2 term
+// sees the O(|dx|^2) remainder of g_k magnified by c)
+__device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, double (&v)[POL_NV], double (&a)[4],
+                                          double &c, double &s, const double (&ht)[2], int free_mask) {
+  const double Vi = v[0], Vj = v[1], d = v[2];
   sincos(d, &s, &c);
   const double Pv = Vi * Vj;
   double f = 0.0;
@@ -78,28 +109,32 @@ __device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, const do
   f += 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const double gk = a[2 * k] * a[2 * k] + a[2 * k + 1] * a[2 * k + 1] - K.rate2;
-    const double m = P.mu[k] + P.c * gk;
-    f += (m > 0.0) ? (m * m - P.mu[k] * P.mu[k]) / (2.0 * P.c) : -P.mu[k] * P.mu[k] / (2.0 * P.c);
+    const double g = a[2 * k] * a[2 * k] + a[2 * k + 1] * a[2 * k + 1] - K.rate2;
+    if ((free_mask >> k) & 1) v[3 + k] = fmax(ht[k] - g, 0.0);
+    const double h = g + v[3 + k];
+    f += h * (P.mu[k] + 0.5 * P.c * h);
   }
   return f;
 }
 
-// objective, gradient (FP64) and Hessian (FP32 Hf, or FP64 Hd when a line
-// limit is active) at x; fills L
-__device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, const double (&x)[3], double (&g)[3],
+// objective, x-gradient gx (FP64) and the x-Hessian without the c grad grad^T
+// terms (FP32 Hf, or FP64 Hd when a slack is held at zero) at v; fills L.
+// With m_k = mu_k + c h_k the x-Hessian is
+//   sum_r (w_r grad a_r grad a_r^T + u_r hess a_r) + (angle/voltage rows)
+//   + sum_k c grad g_k grad g_k^T,
+// w_r = rho_pq + 2 m_k, u_r = rho_pq (a_r - t_r) + 2 m_k a_r (k = r / 2).
+__device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, const double (&v)[POL_NV], double (&gx)[3],
                                            float (&Hf)[6], double (&Hd)[6], PolLast &L) {
-  const double Vi = x[0], Vj = x[1], d = x[2];
+  const double Vi = v[0], Vj = v[1], d = v[2];
   double s, c;
   sincos(d, &s, &c);
   L.c = c;
   L.s = s;
-  L.x[0] = Vi;
-  L.x[1] = Vj;
-  L.x[2] = d;
+#pragma unroll
+  for (int i = 0; i < POL_NV; ++i) L.v[i] = v[i];
   const double Pv = Vi * Vj;
   double f = 0.0;
-  g[0] = g[1] = g[2] = 0.0;
+  gx[0] = gx[1] = gx[2] = 0.0;
   double da[4][3], E[4], Ed[4], pe[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
@@ -114,45 +149,56 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, const d
     da[r][2] = Pv * Ed[r];
     pe[r] = P.rpq * e;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      g[i] += pe[r] * da[r][i];
-      L.da[r][i] = (float)da[r][i];
-    }
+    for (int i = 0; i < 3; ++i) L.da[r][i] = (float)da[r][i];
   }
   const double ewi = Vi * Vi - P.tg[4], ewj = Vj * Vj - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
   f += 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
-  g[0] += 2.0 * P.rva * ewi * Vi;
-  g[1] += 2.0 * P.rva * ewj * Vj;
-  g[2] += 0.5 * P.rva * et;
-  double m[2];
+  double w[4], u[4];
   bool lim = false;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int r0 = 2 * k, r1 = 2 * k + 1;
-    const double gk = L.a[r0] * L.a[r0] + L.a[r1] * L.a[r1] - K.rate2;
-    m[k] = P.mu[k] + P.c * gk;
-    if (m[k] > 0.0) {
-      lim = true;
-      f += (m[k] * m[k] - P.mu[k] * P.mu[k]) / (2.0 * P.c);
+    const double sk = v[3 + k];
+    const double h = L.a[r0] * L.a[r0] + L.a[r1] * L.a[r1] - K.rate2 + sk;
+    const double m = P.mu[k] + P.c * h;
+    f += h * (P.mu[k] + 0.5 * P.c * h);
+    L.m[k] = m;
+    L.h[k] = h;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) g[i] += m[k] * 2.0 * (L.a[r0] * da[r0][i] + L.a[r1] * da[r1][i]);
-    } else {
-      f -= P.mu[k] * P.mu[k] / (2.0 * P.c);
+    for (int i = 0; i < 3; ++i) {
+      L.dg[k][i] = 2.0 * (L.a[r0] * da[r0][i] + L.a[r1] * da[r1][i]);
+      gx[i] += m * L.dg[k][i];
     }
+    // a free slack's optimum has m_k = 0, so the Newton model takes the
+    // reduced x-Hessian there; m_k hess g_k stays only for a slack that may
+    // be held at zero
+    const bool held = sk <= 1e-6 && m > 0.0;
+    const double mh = held ? m : 0.0;
+    w[r0] = w[r1] = P.rpq + 2.0 * mh;
+    u[r0] = pe[r0] + 2.0 * mh * L.a[r0];
+    u[r1] = pe[r1] + 2.0 * mh * L.a[r1];
+    lim = lim || held;
   }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gx[i] += pe[r] * da[r][i];
+  gx[0] += 2.0 * P.rva * ewi * Vi;
+  gx[1] += 2.0 * P.rva * ewj * Vj;
+  gx[2] += 0.5 * P.rva * et;
   L.lim = lim;
   // packed symmetric index: 0:(0,0) 1:(0,1) 2:(0,2) 3:(1,1) 4:(1,2) 5:(2,2)
   const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
   if (!lim) {
-    const float fVi = (float)Vi, fVj = (float)Vj, fP = (float)Pv, rpq = (float)P.rpq, rva = (float)P.rva;
+    const float fVi = (float)Vi, fVj = (float)Vj, fP = (float)Pv, rva = (float)P.rva;
 #pragma unroll
     for (int q = 0; q < 6; ++q) Hf[q] = 0.0f;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const float fE = (float)E[r], fEd = (float)Ed[r], fpe = (float)pe[r];
+      const float fE = (float)E[r], fEd = (float)Ed[r], fu = (float)u[r], fw = (float)w[r];
       const float d2[6] = {2.0f * (float)K.al[r], fE, fVj * fEd, 2.0f * (float)K.be[r], fVi * fEd, -fP * fE};
 #pragma unroll
-      for (int q = 0; q < 6; ++q) Hf[q] += rpq * L.da[r][pi_[q]] * L.da[r][pj_[q]] + fpe * d2[q];
+      for (int q = 0; q < 6; ++q) Hf[q] += fw * L.da[r][pi_[q]] * L.da[r][pj_[q]] + fu * d2[q];
     }
     Hf[0] += rva * (4.0f * fVi * fVi + 2.0f * (float)ewi);
     Hf[3] += rva * (4.0f * fVj * fVj + 2.0f * (float)ewj);
@@ -164,29 +210,11 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, const d
     for (int r = 0; r < 4; ++r) {
       const double d2[6] = {2.0 * K.al[r], E[r], Vj * Ed[r], 2.0 * K.be[r], Vi * Ed[r], -Pv * E[r]};
 #pragma unroll
-      for (int q = 0; q < 6; ++q) Hd[q] += P.rpq * da[r][pi_[q]] * da[r][pj_[q]] + pe[r] * d2[q];
+      for (int q = 0; q < 6; ++q) Hd[q] += w[r] * da[r][pi_[q]] * da[r][pj_[q]] + u[r] * d2[q];
     }
     Hd[0] += P.rva * (4.0 * Vi * Vi + 2.0 * ewi);
     Hd[3] += P.rva * (4.0 * Vj * Vj + 2.0 * ewj);
     Hd[5] += 0.5 * P.rva;
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      if (m[k] > 0.0) {
-        const int r0 = 2 * k, r1 = 2 * k + 1;
-        double dg[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) dg[i] = 2.0 * (L.a[r0] * da[r0][i] + L.a[r1] * da[r1][i]);
-        const double d2r0[6] = {2.0 * K.al[r0], E[r0], Vj * Ed[r0], 2.0 * K.be[r0], Vi * Ed[r0], -Pv * E[r0]};
-        const double d2r1[6] = {2.0 * K.al[r1], E[r1], Vj * Ed[r1], 2.0 * K.be[r1], Vi * Ed[r1], -Pv * E[r1]};
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-          const int i = pi_[q], j = pj_[q];
-          const double d2g = 2.0 * (da[r0][i] * da[r0][j] + L.a[r0] * d2r0[q] + da[r1][i] * da[r1][j] +
-                                    L.a[r1] * d2r1[q]);
-          Hd[q] += m[k] * d2g + P.c * dg[i] * dg[j];
-        }
-      }
-    }
   }
   return f;
 }
@@ -218,45 +246,104 @@ __device__ __forceinline__ T hq(const T (&H)[6], int i, int j) {
   return H[q];
 }
 
-// one Newton iteration with the Hessian H of type T (see newton_iter of the
-// W-form kernel for the steps)
+
+// one projected Newton iteration over v = (V_i, V_j, d, sigma_ij, sigma_ji)
+// with the x-Hessian H of type T (see newton_iter of the W-form kernel for
+// the steps); free slacks are eliminated from the Newton system exactly
 template <typename T>
-__device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&x)[3], double &f, const double (&g)[3],
-                                        const T (&H)[6], double &Delta, double omega, bool &accepted, int &counted) {
+__device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v)[POL_NV], double &f,
+                                        const double (&gx)[3], const PolLast &L, const T (&H)[6], double &Delta,
+                                        double omega, bool &accepted, int &counted) {
   accepted = false;
   counted = 0;
-  double pg = 0.0, xmax = 0.0;
-  T hmax = T(0), eps = T(0), dlo[3], dhi[3], gt[3];
+  const double c = P.c;
+  const double gr[POL_NV] = {gx[0], gx[1], gx[2], L.m[0], L.m[1]};
+  double xmax = 0.0, dlo[POL_NV], dhi[POL_NV];
+  T hmax = T(0), epst = T(0);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < POL_NV; ++i) {
     const double lo = pol_lo(K, i), hi = pol_hi(K, i);
-    pg = fmax(pg, fabs(clampd(x[i] - g[i], lo, hi) - x[i]));
-    xmax = fmax(xmax, fabs(x[i]));
-    dlo[i] = (T)(x[i] - lo);
-    dhi[i] = (T)(hi - x[i]);
-    gt[i] = (T)g[i];
-    const T hii = hq(H, i, i);
-    hmax = hmax > hii ? hmax : hii;
-    const T di = (hii > T(0)) ? gt[i] / hii : gt[i];
-    const T st = (-di < -dlo[i]) ? -dlo[i] : ((-di > dhi[i]) ? dhi[i] : -di);
+    dlo[i] = v[i] - lo;
+    dhi[i] = hi - v[i];
+    // diagonal Newton step (the epsilon of the active set), in T
+    T di;
+    if (i < 3) {
+      xmax = fmax(xmax, fabs(v[i]));
+      const T h = hq(H, i, i);
+      hmax = hmax > h ? hmax : h;
+      di = (h > T(0)) ? (T)gr[i] / h : (T)gr[i];
+    } else {
+      di = (T)(gr[i] * P.ic);
+    }
+    const T st = (-di < (T)-dlo[i]) ? (T)-dlo[i] : ((-di > (T)dhi[i]) ? (T)dhi[i] : -di);
     const T ast = st < T(0) ? -st : st;
-    eps = eps > ast ? eps : ast;
+    epst = epst > ast ? epst : ast;
   }
-  if (pg <= omega) return NI_CONV;
-  eps = eps < T(1e-6) ? eps : T(1e-6);
-  bool act[3];
-  T d[3];
+  const double eps = fmin((double)epst, 1e-6);
+  bool act[POL_NV];
+  double d[POL_NV];
+#pragma unroll
+  for (int i = 0; i < POL_NV; ++i) {
+    act[i] = false;
+    d[i] = 0.0;
+    if (dlo[i] <= eps && gr[i] > 0.0) {
+      act[i] = true;
+      d[i] = -dlo[i] * 1.000001;  // onto the bound (clamped below)
+    } else if (dhi[i] <= eps && gr[i] < 0.0) {
+      act[i] = true;
+      d[i] = dhi[i] * 1.000001;
+    }
+  }
+  // stationarity on the reduced gradient (free slacks eliminated: their
+  // m_k grad g_k leaves the x-gradient); at a stationary x each free slack
+  // takes its exact step -m_k / c (the objective is quadratic in it) -- m_k
+  // itself carries c times the rounding of h_k and never reaches omega
+  double rg[3], pg = 0.0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    act[i] = false;
-    d[i] = T(0);
-    if (dlo[i] <= eps && gt[i] > T(0)) {
-      act[i] = true;
-      d[i] = -dlo[i] * T(1.000001);  // onto the bound (clamped below)
-    } else if (dhi[i] <= eps && gt[i] < T(0)) {
-      act[i] = true;
-      d[i] = dhi[i] * T(1.000001);
+    rg[i] = gx[i];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (!act[3 + k]) rg[i] -= L.m[k] * L.dg[k][i];
+    pg = fmax(pg, fabs(clampd(v[i] - rg[i], pol_lo(K, i), pol_hi(K, i)) - v[i]));
+  }
+  double sn[2];
+  bool sok = true;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    sn[k] = v[3 + k];
+    if (act[3 + k]) {
+      pg = fmax(pg, fabs(clampd(v[3 + k] - L.m[k], 0.0, INFINITY) - v[3 + k]));
+    } else {
+      sn[k] = v[3 + k] - L.m[k] * P.ic;
+      sok = sok && sn[k] >= 0.0;
     }
+  }
+  if (pg <= omega && sok) {
+    v[3] = sn[0];
+    v[4] = sn[1];
+    return NI_CONV;
+  }
+  // 3x3 system in x: H plus c grad g_k grad g_k^T of the slacks held at a
+  // bound; a free slack's row gives d_sigma_k = -m_k / c - grad g_k . d_x,
+  // which turns its m_k grad g_k out of the right-hand side
+  const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
+  T Hr[6], rb[3];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    double add = 0.0;
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (act[3 + k]) add += c * L.dg[k][pi_[q]] * L.dg[k][pj_[q]];
+    Hr[q] = H[q] + (T)add;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double r = -rg[i];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (act[3 + k]) r -= c * L.dg[k][i] * d[3 + k];
+    rb[i] = (T)r;
   }
   T lm = T(0), y[3];
   bool ok = false;
@@ -264,76 +351,130 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&x
     T A[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      const int i = (q < 3) ? 0 : ((q < 5) ? 1 : 2), j = (q == 0) ? 0 : ((q == 1 || q == 3) ? 1 : 2);
-      A[q] = (act[i] || act[j]) ? ((i == j) ? T(1) : T(0)) : H[q];
+      const int i = pi_[q], j = pj_[q];
+      A[q] = (act[i] || act[j]) ? ((i == j) ? T(1) : T(0)) : Hr[q];
       if (i == j && !act[i]) A[q] += lm;
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      T r = -gt[i];
+      T r = rb[i];
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        if (act[j]) r -= hq(H, i, j) * d[j];
-      y[i] = act[i] ? d[i] : r;
+        if (act[j]) r -= hq(Hr, i, j) * (T)d[j];
+      y[i] = act[i] ? (T)d[i] : r;
     }
     if (chol3p(A, y)) {
       ok = true;
       break;
     }
-    lm = (lm == T(0)) ? T(1e-10) * hmax : T(10) * lm;
+    lm = (lm == T(0)) ? T(1e-10) * (hmax > T(0) ? hmax : T(1)) : T(10) * lm;
   }
   if (!ok) return NI_STOP;
-  T dn = T(0);
+  double dn = 0.0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    d[i] = y[i];
-    const T ad = d[i] < T(0) ? -d[i] : d[i];
-    dn = dn > ad ? dn : ad;
+    if (!act[i]) d[i] = (double)y[i];
+    dn = fmax(dn, fabs(d[i]));
   }
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    if (!act[3 + k]) d[3 + k] = -L.m[k] * P.ic - (L.dg[k][0] * d[0] + L.dg[k][1] * d[1] + L.dg[k][2] * d[2]);
   counted = 1;
-  if (lm == T(0)) {
-    T gd = T(0), dHd = T(0);
+  // model decrease of a step sg: -(gr . sg + 1/2 sg^T H5 sg), where
+  // sg^T H5 sg = sx^T H sx + sum_k c (grad g_k . sx + s_sigma_k)^2
+  auto model = [&](const double (&sg)[POL_NV]) -> double {
+    double lin = 0.0;
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      gd += gt[i] * d[i];
-      dHd += d[i] * (hq(H, i, 0) * d[0] + hq(H, i, 1) * d[1] + hq(H, i, 2) * d[2]);
+    for (int i = 0; i < POL_NV; ++i) lin += gr[i] * sg[i];
+    const T s0 = (T)sg[0], s1 = (T)sg[1], s2 = (T)sg[2];
+    const T sHs = s0 * (H[0] * s0 + H[1] * s1 + H[2] * s2) + s1 * (H[1] * s0 + H[3] * s1 + H[4] * s2) +
+                  s2 * (H[2] * s0 + H[4] * s1 + H[5] * s2);
+    double quad = (double)sHs;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double e = L.dg[k][0] * sg[0] + L.dg[k][1] * sg[1] + L.dg[k][2] * sg[2] + sg[3 + k];
+      quad += c * e * e;
     }
-    const T predN = -(gd + T(0.5) * dHd);
-    if ((double)dn <= 1e-9 * (1.0 + xmax) || (double)predN <= 1e-12 * (1.0 + fabs(f))) {
+    return -(lin + 0.5 * quad);
+  };
+  if (lm == T(0)) {
+    const double predN = model(d);
+    if (dn <= 1e-9 * (1.0 + xmax) || predN <= 1e-12 * (1.0 + fabs(f))) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) x[i] = clampd(x[i] + (double)d[i], pol_lo(K, i), pol_hi(K, i));
+      for (int i = 0; i < POL_NV; ++i) v[i] = clampd(v[i] + d[i], pol_lo(K, i), pol_hi(K, i));
       return NI_CONV;
     }
-    if ((double)dn <= 1e-4 * (1.0 + xmax) && (double)dn <= Delta) {
+    bool inside = true;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) x[i] = clampd(x[i] + (double)d[i], pol_lo(K, i), pol_hi(K, i));
+    for (int i = 0; i < POL_NV; ++i)
+      inside = inside && (act[i] || (d[i] >= -dlo[i] && d[i] <= dhi[i]));
+    if (inside && dn <= 1e-4 * (1.0 + xmax) && dn <= Delta) {
+#pragma unroll
+      for (int i = 0; i < POL_NV; ++i) v[i] = clampd(v[i] + d[i], pol_lo(K, i), pol_hi(K, i));
       accepted = true;
       return NI_CONT;
     }
   }
-  const double scale = ((double)dn > Delta) ? Delta / (double)dn : 1.0;
-  double xt[3], smax = 0.0;
-  T sv[3];
+  const double scale = (dn > Delta) ? Delta / dn : 1.0;
+  double vt[POL_NV], sg[POL_NV], smax = 0.0;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    xt[i] = clampd(x[i] + scale * (double)d[i], pol_lo(K, i), pol_hi(K, i));
-    const double si = xt[i] - x[i];
-    sv[i] = (T)si;
-    smax = fmax(smax, fabs(si));
+  for (int i = 0; i < POL_NV; ++i) {
+    vt[i] = clampd(v[i] + scale * d[i], pol_lo(K, i), pol_hi(K, i));
+    sg[i] = vt[i] - v[i];
+    if (i < 3) smax = fmax(smax, fabs(sg[i]));
   }
-  T gs = T(0), sHs = T(0);
+  const double pred = model(sg);
+  // predicted h_k of the trial step; free slacks absorb the remainder of
+  // g_k exactly, a slack held at zero gets the correction
+  // dx = -sum_k alpha_k grad g_k (Gram system of the held gradients) that
+  // restores the linear prediction of its g_k to second order
+  double ht[2];
+  int free_mask = 0, nheld = 0;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    gs += gt[i] * sv[i];
-    sHs += sv[i] * (hq(H, i, 0) * sv[0] + hq(H, i, 1) * sv[1] + hq(H, i, 2) * sv[2]);
+  for (int k = 0; k < 2; ++k) {
+    ht[k] = L.h[k] + L.dg[k][0] * sg[0] + L.dg[k][1] * sg[1] + L.dg[k][2] * sg[2] + sg[3 + k];
+    if (act[3 + k]) ++nheld; else free_mask |= 1 << k;
   }
-  const double pred = -(double)(gs + T(0.5) * sHs);
   double at[4], ct, stn;
-  const double ft = pol_obj(K, P, xt, at, ct, stn);
+  double ft = pol_obj(K, P, vt, at, ct, stn, ht, free_mask);
+  if (nheld > 0) {
+    double r[2], G[3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      r[k] = act[3 + k] ? (at[2 * k] * at[2 * k] + at[2 * k + 1] * at[2 * k + 1] - K.rate2 + vt[3 + k]) - ht[k] : 0.0;
+    G[0] = L.dg[0][0] * L.dg[0][0] + L.dg[0][1] * L.dg[0][1] + L.dg[0][2] * L.dg[0][2];
+    G[1] = L.dg[0][0] * L.dg[1][0] + L.dg[0][1] * L.dg[1][1] + L.dg[0][2] * L.dg[1][2];
+    G[2] = L.dg[1][0] * L.dg[1][0] + L.dg[1][1] * L.dg[1][1] + L.dg[1][2] * L.dg[1][2];
+    double al0 = 0.0, al1 = 0.0;
+    if (nheld == 2) {
+      const double det = G[0] * G[2] - G[1] * G[1];
+      if (det > 1e-12 * G[0] * G[2]) {
+        al0 = (G[2] * r[0] - G[1] * r[1]) / det;
+        al1 = (G[0] * r[1] - G[1] * r[0]) / det;
+      }
+    } else if (act[3]) {
+      al0 = G[0] > 0.0 ? r[0] / G[0] : 0.0;
+    } else {
+      al1 = G[2] > 0.0 ? r[1] / G[2] : 0.0;
+    }
+    double vc[POL_NV];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      vc[i] = clampd(vt[i] - al0 * L.dg[0][i] - al1 * L.dg[1][i], pol_lo(K, i), pol_hi(K, i));
+    vc[3] = vt[3];
+    vc[4] = vt[4];
+    double ac[4], cc, sc;
+    const double fc = pol_obj(K, P, vc, ac, cc, sc, ht, free_mask);
+    if (fc < ft) {
+      ft = fc;
+#pragma unroll
+      for (int i = 0; i < POL_NV; ++i) vt[i] = vc[i];
+    }
+  }
   const double ared = f - ft;
   if (pred > 0.0 && ared >= 1e-4 * pred) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) x[i] = xt[i];
+    for (int i = 0; i < POL_NV; ++i) v[i] = vt[i];
     f = ft;
     accepted = true;
     if (ared >= 0.75 * pred && scale < 1.0) Delta = 2.0 * Delta;
@@ -372,7 +513,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   };
   bool need_full = false;
   double f = 0.0, Delta = 1.0, hprev = INFINITY, omega = 0.0, cmax = 0.0;
-  double x[3], g[3], Hd[6];
+  double v[POL_NV], gx[3], Hd[6];
   float Hf[6];
   PolLast L;
   PolK K;
@@ -418,13 +559,16 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           for (int r = 0; r < 8; ++r) P.tg[r] = S.BT[r * NBP + bp];
           P.rpq = I.rpq;
           P.rva = I.rva;
-          P.mu[0] = fmax(S.B[(FB_MU0 + 2) * NBP + bp], 0.0);
-          P.mu[1] = fmax(S.B[(FB_MU0 + 3) * NBP + bp], 0.0);
+          P.mu[0] = S.B[(FB_MU0 + 2) * NBP + bp];
+          P.mu[1] = S.B[(FB_MU0 + 3) * NBP + bp];
           P.c = S.B[FB_C * NBP + bp];
-          // warm start from the stored iterate: V = sqrt(w), d = theta_i - theta_j
-          x[0] = clampd(sqrt(fmax(S.B[(FB_V0 + 0) * NBP + bp], 0.0)), K.lo0, K.hi0);
-          x[1] = clampd(sqrt(fmax(S.B[(FB_V0 + 1) * NBP + bp], 0.0)), K.lo1, K.hi1);
-          x[2] = clampd(S.B[(FB_V0 + 4) * NBP + bp] - S.B[(FB_V0 + 5) * NBP + bp], pol_lo(K, 2), pol_hi(K, 2));
+          P.ic = 1.0 / P.c;
+          // warm start from the stored iterate: V = sqrt(w), d = theta_i - theta_j, the slacks
+          v[0] = clampd(sqrt(fmax(S.B[(FB_V0 + 0) * NBP + bp], 0.0)), K.lo0, K.hi0);
+          v[1] = clampd(sqrt(fmax(S.B[(FB_V0 + 1) * NBP + bp], 0.0)), K.lo1, K.hi1);
+          v[2] = clampd(S.B[(FB_V0 + 4) * NBP + bp] - S.B[(FB_V0 + 5) * NBP + bp], pol_lo(K, 2), pol_hi(K, 2));
+          v[3] = fmax(S.B[(FB_V0 + 6) * NBP + bp], 0.0);
+          v[4] = fmax(S.B[(FB_V0 + 7) * NBP + bp], 0.0);
           const double rmax = fmax(I.rpq, I.rva);
           omega = S.prm.omega_rel * rmax;
           cmax = S.prm.c_max_rel * rmax;
@@ -437,45 +581,53 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
     }
     if (__ballot_sync(FULL, active) == 0) break;
     if (active) {
-      if (need_full) f = pol_full(K, P, x, g, Hf, Hd, L);
+      if (need_full) f = pol_full(K, P, v, gx, Hf, Hd, L);
       need_full = false;
       bool accepted;
       int counted;
-      const int out = L.lim ? pol_iter<double>(K, P, x, f, g, Hd, Delta, omega, accepted, counted)
-                            : pol_iter<float>(K, P, x, f, g, Hf, Delta, omega, accepted, counted);
+      const int out = L.lim ? pol_iter<double>(K, P, v, f, gx, L, Hd, Delta, omega, accepted, counted)
+                            : pol_iter<float>(K, P, v, f, gx, L, Hf, Delta, omega, accepted, counted);
       newton += counted;
       need_full = accepted;
       ++itn;
       if (out != NI_CONT || itn >= K_N) {
         const bool conv = (out == NI_CONV);
-        // flows and cos/sin at x: first order from the last evaluation after a
-        // converged (tiny final) step, a fresh evaluation otherwise
-        double a[4], c, sn;
-        if (conv) {
-          const double dx0 = x[0] - L.x[0], dx1 = x[1] - L.x[1], dx2 = x[2] - L.x[2];
+        // flows, cos/sin and h_k at v: first order from the last evaluation
+        // after a converged tiny final step (h_k in FP64 from grad g_k, so
+        // that it matches the slack step taken from the same gradient), a
+        // fresh evaluation otherwise
+        const double dx0 = v[0] - L.v[0], dx1 = v[1] - L.v[1], dx2 = v[2] - L.v[2];
+        const bool tiny = conv && fmax(fmax(fabs(dx0), fabs(dx1)), fabs(dx2)) <= 1e-8;
+        double a[4], c, sn, h[2];
+        if (tiny) {
 #pragma unroll
           for (int r = 0; r < 4; ++r)
             a[r] = L.a[r] + (double)L.da[r][0] * dx0 + (double)L.da[r][1] * dx1 + (double)L.da[r][2] * dx2;
           c = L.c - L.s * dx2;
           sn = L.s + L.c * dx2;
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+            h[q] = L.h[q] + L.dg[q][0] * dx0 + L.dg[q][1] * dx1 + L.dg[q][2] * dx2 + (v[3 + q] - L.v[3 + q]);
         } else {
-          pol_obj(K, P, x, a, c, sn);
+          const double ht0[2] = {0.0, 0.0};
+          pol_obj(K, P, v, a, c, sn, ht0, 0);
+#pragma unroll
+          for (int q = 0; q < 2; ++q)
+            h[q] = a[2 * q] * a[2 * q] + a[2 * q + 1] * a[2 * q + 1] - K.rate2 + v[3 + q];
         }
+        // equality multiplier step on h_k = p_k^2 + q_k^2 + sigma_k - rate^2
         double hn = 0.0;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const double gk = a[2 * q] * a[2 * q] + a[2 * q + 1] * a[2 * q + 1] - K.rate2;
-          const double mn = fmax(0.0, P.mu[q] + P.c * gk);
-          hn = fmax(hn, fabs(mn - P.mu[q]) / P.c);
-          P.mu[q] = mn;
+          hn = fmax(hn, fabs(h[q]));
+          P.mu[q] += P.c * h[q];
         }
         ++al;
         const bool done = (hn <= eta && conv);
         if (done || al >= K_AL) {
-          const double Pv = x[0] * x[1], tm = 0.5 * (P.tg[6] + P.tg[7]);
-          const double v8[8] = {x[0] * x[0], x[1] * x[1], Pv * c, Pv * sn, tm + 0.5 * x[2], tm - 0.5 * x[2],
-                                clampd(K.rate2 - a[0] * a[0] - a[1] * a[1], 0.0, K.rate2),
-                                clampd(K.rate2 - a[2] * a[2] - a[3] * a[3], 0.0, K.rate2)};
+          const double Pv = v[0] * v[1], tm = 0.5 * (P.tg[6] + P.tg[7]);
+          const double v8[8] = {v[0] * v[0], v[1] * v[1], Pv * c, Pv * sn, tm + 0.5 * v[2], tm - 0.5 * v[2],
+                                v[3], v[4]};
 #pragma unroll
           for (int i = 0; i < 8; ++i) S.B[(FB_V0 + i) * NBP + bp] = v8[i];
           S.B[(FB_MU0 + 0) * NBP + bp] = 0.0;
@@ -494,7 +646,10 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           acc_cap += done ? 0ull : 1ull;
           bp = -1;
         } else {
-          if (hn > 0.25 * hprev) P.c = fmin(10.0 * P.c, cmax);
+          if (hn > 0.25 * hprev) {
+            P.c = fmin(10.0 * P.c, cmax);
+            P.ic = 1.0 / P.c;
+          }
           hprev = hn;
           Delta = fmax(Delta, 1e-3);
           itn = 0;

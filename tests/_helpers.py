@@ -14,7 +14,7 @@ RTOL = 1e-9
 ATOL = 1e-12
 
 
-def field_atol(name, g, cpen_max):
+def field_atol(name, g, cpen_max, mu_eta=None):
     rho_pq, rho_va, rho_uc = g.rho
     if name.startswith("gy_") or name.startswith("glam_"):
         r = name.split("_", 1)[1]
@@ -23,13 +23,16 @@ def field_atol(name, g, cpen_max):
         r = name.split("_", 1)[1]
         return ATOL * (rho_pq if r in ("pij", "qij", "pji", "qji") else rho_va)
     if name.startswith("mu"):
-        return 1e-14 * cpen_max
+        # a solver that reaches the line subproblem's KKT point by another
+        # path (mu_eta = its stopping tolerance eta on |h|) fixes mu = mu + c h
+        # only to within c eta on each side
+        return (2.0 * mu_eta if mu_eta is not None else 1e-14) * cpen_max
     if name in ("beta", "beta_next", "zprev"):
         return 0.0
     return ATOL
 
 
-def compare_states(a, b, g, rtol=RTOL, skip=()):
+def compare_states(a, b, g, rtol=RTOL, skip=(), mu_eta=None):
     """Returns a list of (field, err, bound) that violate the bound."""
     dims = (g.T, g.n_gen, g.n_branch, g.n_bus)
     A = oracle.unpack_state(a, *dims)
@@ -46,7 +49,7 @@ def compare_states(a, b, g, rtol=RTOL, skip=()):
             continue
         err = float(np.abs(x - y).max()) if x.size else 0.0
         scale = max(float(np.abs(x).max()) if x.size else 0.0, float(np.abs(y).max()) if y.size else 0.0)
-        bound = rtol * scale + field_atol(name, g, cmax)
+        bound = rtol * scale + field_atol(name, g, cmax, mu_eta)
         if not err <= bound:
             bad.append((name, err, bound))
     return bad

@@ -21,7 +21,8 @@ def _dims(g):
 # The polar line solver keeps no multipliers for the product and angle
 # equations (they hold identically in its coordinates), so those two W-form
 # multipliers and the W-form penalty are not compared for it; everything the
-# ADMM iterates on is.
+# ADMM iterates on is.  Its line-limit multipliers come from another path to
+# the same KKT point and agree up to the inner stopping rule |h| <= eta.
 POLAR_SKIP = ("mu0", "mu1", "cpen")
 
 
@@ -34,7 +35,9 @@ def _lockstep(ucac, grids, sweeps, params=None, oparams=None, warm=0, check_inst
     if line_form is not None:
         params = params if params is not None else ucac.ucac_default_params()
         params.line_form = line_form
-    skip = POLAR_SKIP if (params is None or params.line_form == ucac.UCAC_LINE_POLAR) else ()
+    polar = params is None or params.line_form == ucac.UCAC_LINE_POLAR
+    skip = POLAR_SKIP if polar else ()
+    mu_eta = (params.eta if params is not None else ucac.ucac_default_params().eta) if polar else None
     h = ucac.Handle(grids, params=params)
     if warm:
         h.enqueue(warm)
@@ -52,7 +55,7 @@ def _lockstep(ucac, grids, sweeps, params=None, oparams=None, warm=0, check_inst
             o = orcs[k]
             o.set_state(pre[k])
             o.sweep()
-            bad = compare_states(h.export(k), o.state_vector(), grids[k], skip=skip)
+            bad = compare_states(h.export(k), o.state_vector(), grids[k], skip=skip, mu_eta=mu_eta)
             assert not bad, f"sweep {s} instance {k}: {bad[:6]}"
     h.close()
 
@@ -150,7 +153,8 @@ def test_full_size_2000bus_one_instance_lockstep(ucac_mod, line_form):
     o = oracle.Oracle(grids[k])
     o.set_state(pre)
     o.sweep()
-    skip = POLAR_SKIP if line_form == ucac_mod.UCAC_LINE_POLAR else ()
-    bad = compare_states(h.export(k), o.state_vector(), grids[k], skip=skip)
+    polar = line_form == ucac_mod.UCAC_LINE_POLAR
+    bad = compare_states(h.export(k), o.state_vector(), grids[k], skip=POLAR_SKIP if polar else (),
+                         mu_eta=p.eta if polar else None)
     assert not bad, bad[:6]
     h.close()
