@@ -6,7 +6,15 @@
 //   branch-period  bp = inst.bpo + t * inst.nl + l
 //   bus-period     up = inst.upo + t * inst.nb + i
 // so one launch covers a whole batch and consecutive threads touch
-// consecutive addresses.  Each warp handles one granule of 32 consecutive
+// consecutive addresses.  The coupling rows of the line ends (p, q, w, theta
+// of one end of a line, owned by the bus at that end) are stored in a slot
+// layout instead: per instance and period, the buses in degree order are cut
+// into blocks of 32 (one warp of the bus kernel), and block b owns W_b slots
+// per lane (W_b = its largest degree), slot j of lane l at
+//   e = inst.eo + t * inst.spp + blk_off[b] + 32 j + l,
+// so the bus kernel's loads of its j-th incident line end are one contiguous
+// 256-byte line per warp; the line kernels find their two ends through
+// eslot[side][line].  Each warp handles one granule of 32 consecutive
 // items of one instance (granule tables never straddle two instances), so
 // residual partial sums are per warp and per instance, and the block size of
 // a launch changes neither the work split nor any result: it is free to be
@@ -41,6 +49,8 @@ enum { BC_Y0 = 0, BC_RATE2 = 8, BC_LO = 9, BC_HI = 17, BC_VB = 25, BC_N = 29 };
 struct Inst {
   int nb, nl, ng, T, ref;
   int go, gpo, lo, bpo, uo, upo;
+  long long eo;    // first line-end slot of the instance
+  int spp, nblk, bo;  // slots per period, bus blocks per period, first bus block (global)
   int m_rows;
   int gran_gen0, gran_gen1, gran_gp0, gran_gp1, gran_bp0, gran_bp1, gran_up0, gran_up1;
   double rpq, rva, ruc;
@@ -73,14 +83,21 @@ struct Dev {
   long long NL;
   const double *BC;
   const int *bf, *bt;  // local bus index of the from / to end
-  // branch-period state [NBF][NBP], rows [NBR][NBP]
+  // branch-period state [FB_FB0][NBP] (the x-bar values of the flow rows
+  // live with the line-end rows)
   long long NBP;
-  double *B, *BA, *BY, *BZ, *BL, *BT;
+  double *B;
+  // line-end rows in the slot layout: [4][NEP] (p, q, w, theta of the end)
+  // for x values, y, z, lambda and x-step targets; x-bar of p, q [2][NEP]
+  long long NEP;
+  double *EA, *EY, *EZ, *EL, *ET, *EFB;
+  const int *eslot;             // [2][NL]: slot of the from / to end within its period
+  const int *blk_off, *blk_w;   // per bus block: slot offset within the period, width
   // buses
   long long NB;
   const double *Gs, *Bs;
-  const int *inc_ptr, *inc_br, *inc_side;  // CSR over global buses; branch index local
-  const int *gen_ptr, *gen_idx;            // CSR over global buses; generator index local
+  const int *inc_ptr;            // CSR row pointers over global buses (degree)
+  const int *gen_ptr, *gen_idx;  // CSR over global buses; generator index local
   const int *bus_order;                    // [NB] per instance: local buses sorted by (degree, generators)
   long long NUP;
   const double *Pd, *Qd;
@@ -101,6 +118,19 @@ struct Dev {
 };
 
 __device__ __forceinline__ double clampd(double x, double lo, double hi) { return fmin(fmax(x, lo), hi); }
+
+// slots of the from / to end of line lg at period t of instance I
+__device__ __forceinline__ void line_ends(const Dev &S, const Inst &I, int t, long long lg, long long &ef,
+                                          long long &et) {
+  const long long base = I.eo + (long long)t * I.spp;
+  ef = base + S.eslot[lg];
+  et = base + S.eslot[S.NL + lg];
+}
+
+// canonical line row r (p_ij, q_ij, p_ji, q_ji, w_i, w_j, theta_i, theta_j)
+// -> row type u (p, q, w, theta) at its end and the end (0 from, 1 to)
+__host__ __device__ __forceinline__ int erow_u(int r) { return r < 4 ? (r & 1) : (r < 6 ? 2 : 3); }
+__host__ __device__ __forceinline__ int erow_end(int r) { return r < 4 ? (r >> 1) : (r & 1); }
 
 // granule of the calling warp (uniform across the warp), or -1
 template <int BS>

@@ -372,11 +372,11 @@ template <int BS>
 __global__ void __launch_bounds__(BS) k_branch(Dev S) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const long long NBP = S.NBP, NL = S.NL;
+  const long long NBP = S.NBP, NL = S.NL, NEP = S.NEP;
   const double eta = S.prm.eta;
   const int K_N = S.prm.K_N, K_AL = S.prm.K_AL;
   bool active = true;
-  long long bp = -1;
+  long long bp = -1, lef = 0, let = 0;  // item, slots of its from / to end
   int k = 0, itn = 0, al = 0, newton = 0;
   bool need_f = false, need_gH = false;
   double f = 0.0, Delta = 1.0, hprev = INFINITY, omega = 0.0, cmax = 0.0;
@@ -417,8 +417,9 @@ __global__ void __launch_bounds__(BS) k_branch(Dev S) {
             K.lo[i] = S.BC[(BC_LO + i) * NL + lg];
             K.hi[i] = S.BC[(BC_HI + i) * NL + lg];
           }
+          line_ends(S, I, t, lg, lef, let);
 #pragma unroll
-          for (int r = 0; r < 8; ++r) P.tg[r] = S.BT[r * NBP + bp];
+          for (int r = 0; r < 8; ++r) P.tg[r] = S.ET[erow_u(r) * NEP + (erow_end(r) ? let : lef)];
           P.rpq = I.rpq;
           P.rva = I.rva;
 #pragma unroll
@@ -469,11 +470,11 @@ __global__ void __launch_bounds__(BS) k_branch(Dev S) {
           for (int q = 0; q < 4; ++q) S.B[(FB_MU0 + q) * NBP + bp] = P.mu[q];
           S.B[FB_C * NBP + bp] = P.c;
 #pragma unroll
-          for (int r = 0; r < 4; ++r) S.BA[r * NBP + bp] = a[r];
-          S.BA[4 * NBP + bp] = v[0];
-          S.BA[5 * NBP + bp] = v[1];
-          S.BA[6 * NBP + bp] = v[4];
-          S.BA[7 * NBP + bp] = v[5];
+          for (int r = 0; r < 4; ++r) S.EA[erow_u(r) * NEP + (erow_end(r) ? let : lef)] = a[r];
+          S.EA[2 * NEP + lef] = v[0];
+          S.EA[2 * NEP + let] = v[1];
+          S.EA[3 * NEP + lef] = v[4];
+          S.EA[3 * NEP + let] = v[5];
           long long *st = S.bstat + (long long)k * 3;
           atomicAdd((unsigned long long *)&st[0], (unsigned long long)newton);
           atomicAdd((unsigned long long *)&st[1], (unsigned long long)al);

@@ -492,11 +492,11 @@ template <int BS>
 __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const long long NBP = S.NBP, NL = S.NL;
+  const long long NBP = S.NBP, NL = S.NL, NEP = S.NEP;
   const double eta = S.prm.eta;
   const int K_N = S.prm.K_N, K_AL = S.prm.K_AL;
   bool active = true;
-  long long bp = -1;
+  long long bp = -1, lef = 0, let = 0;  // item, slots of its from / to end
   int k = 0, itn = 0, al = 0, newton = 0;
   // per-lane statistics, flushed to the instance's counters when the lane
   // moves to another instance or retires (consecutive items mostly share one)
@@ -555,8 +555,9 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           K.hi0 = S.BC[(BC_VB + 1) * NL + lg];
           K.lo1 = S.BC[(BC_VB + 2) * NL + lg];
           K.hi1 = S.BC[(BC_VB + 3) * NL + lg];
+          line_ends(S, I, t, lg, lef, let);
 #pragma unroll
-          for (int r = 0; r < 8; ++r) P.tg[r] = S.BT[r * NBP + bp];
+          for (int r = 0; r < 8; ++r) P.tg[r] = S.ET[erow_u(r) * NEP + (erow_end(r) ? let : lef)];
           P.rpq = I.rpq;
           P.rva = I.rva;
           P.mu[0] = S.B[(FB_MU0 + 2) * NBP + bp];
@@ -636,11 +637,11 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           S.B[(FB_MU0 + 3) * NBP + bp] = P.mu[1];
           S.B[FB_C * NBP + bp] = P.c;
 #pragma unroll
-          for (int r = 0; r < 4; ++r) S.BA[r * NBP + bp] = a[r];
-          S.BA[4 * NBP + bp] = v8[0];
-          S.BA[5 * NBP + bp] = v8[1];
-          S.BA[6 * NBP + bp] = v8[4];
-          S.BA[7 * NBP + bp] = v8[5];
+          for (int r = 0; r < 4; ++r) S.EA[erow_u(r) * NEP + (erow_end(r) ? let : lef)] = a[r];
+          S.EA[2 * NEP + lef] = v8[0];
+          S.EA[2 * NEP + let] = v8[1];
+          S.EA[3 * NEP + lef] = v8[4];
+          S.EA[3 * NEP + let] = v8[5];
           acc_nw += (unsigned long long)newton;
           acc_al += (unsigned long long)al;
           acc_cap += done ? 0ull : 1ull;

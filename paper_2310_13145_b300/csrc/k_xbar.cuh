@@ -110,27 +110,30 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
 }
 
 // ------------------------------------------------------------ bus (R8) ----
-// Buses are visited in a per-instance order sorted by (degree, generators):
-// neighbouring lanes then loop over equally many incident rows, which keeps
-// the warp converged (the order changes no result).
+// One warp per (period, block of 32 buses in the instance's degree order):
+// the lanes' j-th incident line ends are adjacent slots, so every load and
+// store of a line-end row is one coalesced 256-byte access; the lanes of a
+// block have (nearly) equal degrees, which keeps the warp converged.
 template <int BS>
 __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
   const int gr = warp_granule<BS>(S.g_up.n);
   if (gr < 0) return;
   const int k = S.g_up.inst[gr];
   const Inst I = S.inst[k];
-  const long long upl = (long long)S.g_up.first[gr] + (threadIdx.x & 31);
+  const int tb = S.g_up.first[gr];  // t * nblk + block
+  const int t = tb / I.nblk, blk = tb - t * I.nblk;
+  const int lane = threadIdx.x & 31, pos = blk * 32 + lane;
   double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (upl < (long long)I.upo + (long long)I.T * I.nb) {
-    const int loc = (int)(upl - I.upo);
-    const int t = loc / I.nb, i = S.bus_order[I.uo + (loc - t * I.nb)], ig = I.uo + i;
+  if (pos < I.nb) {
+    const int i = S.bus_order[I.uo + pos], ig = I.uo + i;
     const long long up = (long long)I.upo + (long long)t * I.nb + i;
-    const long long NGP = S.NGP, NBP = S.NBP, NUP = S.NUP;
+    const long long NGP = S.NGP, NEP = S.NEP, NUP = S.NUP;
+    const long long e0 = I.eo + (long long)t * I.spp + S.blk_off[I.bo + blk] + lane;  // slot 0 of this bus
     const RowCtx R = row_ctx(S, k);
     const Fam Fpq = fam(I.rpq, R), Fva = fam(I.rva, R);
     const double irpq = Fpq.irho;
     const bool last = (t == I.T - 1);
-    const int g0 = S.gen_ptr[ig], g1 = S.gen_ptr[ig + 1], e0 = S.inc_ptr[ig], e1 = S.inc_ptr[ig + 1];
+    const int g0 = S.gen_ptr[ig], g1 = S.gen_ptr[ig + 1], deg = S.inc_ptr[ig + 1] - S.inc_ptr[ig];
     // pass 1: targets m_v, weights W_v and the 2x2 multiplier system
     double M00 = 0.0, M01 = 0.0, M11 = 0.0, r0 = 0.0, r1 = 0.0, mw = 0.0, mth = 0.0;
     for (int e = g0; e < g1; ++e) {
@@ -148,18 +151,15 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
       r1 = add_(r1, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq));
     }
 #pragma unroll kBusUnroll
-    for (int e = e0; e < e1; ++e) {
-      const long long bp = (long long)I.bpo + (long long)t * I.nl + S.inc_br[e];
-      const int sd = S.inc_side[e];
-      const int rp = sd ? 2 : 0, rw = sd ? 5 : 4;
+    for (int j = 0; j < deg; ++j) {
+      const long long e = e0 + 32LL * j;
       M00 = add_(M00, irpq);
-      r0 = sub_(r0, row_mtarget(S.BA[rp * NBP + bp], S.BZ[rp * NBP + bp], S.BY[rp * NBP + bp], Fpq));
+      r0 = sub_(r0, row_mtarget(S.EA[e], S.EZ[e], S.EY[e], Fpq));
       M11 = add_(M11, irpq);
-      r1 = sub_(r1, row_mtarget(S.BA[(rp + 1) * NBP + bp], S.BZ[(rp + 1) * NBP + bp], S.BY[(rp + 1) * NBP + bp], Fpq));
-      mw = add_(mw, row_mtarget(S.BA[rw * NBP + bp], S.BZ[rw * NBP + bp], S.BY[rw * NBP + bp], Fva));
-      mth = add_(mth, row_mtarget(S.BA[(rw + 2) * NBP + bp], S.BZ[(rw + 2) * NBP + bp], S.BY[(rw + 2) * NBP + bp], Fva));
+      r1 = sub_(r1, row_mtarget(S.EA[NEP + e], S.EZ[NEP + e], S.EY[NEP + e], Fpq));
+      mw = add_(mw, row_mtarget(S.EA[2 * NEP + e], S.EZ[2 * NEP + e], S.EY[2 * NEP + e], Fva));
+      mth = add_(mth, row_mtarget(S.EA[3 * NEP + e], S.EZ[3 * NEP + e], S.EY[3 * NEP + e], Fva));
     }
-    const int deg = e1 - e0;
     const double ideg = 1.0 / deg;
     mw = mul_(mw, ideg);
     mth = mul_(mth, ideg);
@@ -207,24 +207,19 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const double thnew = (i == I.ref) ? 0.0 : mth;
     S.U[FU_W * NUP + up] = wnew;
     S.U[FU_TH * NUP + up] = thnew;
-    for (int e = e0; e < e1; ++e) {
-      const long long bp = (long long)I.bpo + (long long)t * I.nl + S.inc_br[e];
-      const int sd = S.inc_side[e];
-      const int rp = sd ? 2 : 0, rw = sd ? 5 : 4;
+    for (int j = 0; j < deg; ++j) {
+      const long long e = e0 + 32LL * j;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        const int r = rp + u;
-        const double m = row_mtarget(S.BA[r * NBP + bp], S.BZ[r * NBP + bp], S.BY[r * NBP + bp], Fpq);
+        const long long eu = u * NEP + e;
+        const double m = row_mtarget(S.EA[eu], S.EZ[eu], S.EY[eu], Fpq);
         const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, m);
-        const double vold = S.B[(FB_FB0 + r) * NBP + bp];
-        S.B[(FB_FB0 + r) * NBP + bp] = vnew;
-        row_update<false>(S.BA + r * NBP, S.BY + r * NBP, S.BZ + r * NBP, S.BL + r * NBP, S.BT + r * NBP, bp, vnew,
-                          vold, Fpq, R, q);
+        const double vold = S.EFB[eu];
+        S.EFB[eu] = vnew;
+        row_update<false>(S.EA, S.EY, S.EZ, S.EL, S.ET, eu, vnew, vold, Fpq, R, q);
       }
-      row_update<false>(S.BA + rw * NBP, S.BY + rw * NBP, S.BZ + rw * NBP, S.BL + rw * NBP, S.BT + rw * NBP, bp,
-                        wnew, wold, Fva, R, q);
-      row_update<false>(S.BA + (rw + 2) * NBP, S.BY + (rw + 2) * NBP, S.BZ + (rw + 2) * NBP, S.BL + (rw + 2) * NBP,
-                        S.BT + (rw + 2) * NBP, bp, thnew, thold, Fva, R, q);
+      row_update<false>(S.EA, S.EY, S.EZ, S.EL, S.ET, 2 * NEP + e, wnew, wold, Fva, R, q);
+      row_update<false>(S.EA, S.EY, S.EZ, S.EL, S.ET, 3 * NEP + e, thnew, thold, Fva, R, q);
     }
   }
   warp_reduce_q(q, S.part_up + (long long)gr * NQ);
@@ -550,20 +545,46 @@ __global__ void __launch_bounds__(BS) k_prep_branch(Dev S) {
   if (bp >= (long long)I.bpo + (long long)I.T * I.nl) return;
   const int loc = (int)(bp - I.bpo);
   const int t = loc / I.nl, l = loc - t * I.nl;
-  const long long NBP = S.NBP, NUP = S.NUP, lg = (long long)I.lo + l;
+  const long long NEP = S.NEP, NUP = S.NUP, lg = (long long)I.lo + l;
   const long long uf = (long long)I.upo + (long long)t * I.nb + S.bf[lg];
   const long long ut = (long long)I.upo + (long long)t * I.nb + S.bt[lg];
+  long long ef, et;
+  line_ends(S, I, t, lg, ef, et);
   double bv[8];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) bv[r] = S.B[(FB_FB0 + r) * NBP + bp];
+  for (int r = 0; r < 4; ++r) bv[r] = S.EFB[erow_u(r) * NEP + (erow_end(r) ? et : ef)];
   bv[4] = S.U[FU_W * NUP + uf];
   bv[5] = S.U[FU_W * NUP + ut];
   bv[6] = S.U[FU_TH * NUP + uf];
   bv[7] = S.U[FU_TH * NUP + ut];
   const double irpq = 1.0 / I.rpq, irva = 1.0 / I.rva;
 #pragma unroll
-  for (int r = 0; r < 8; ++r)
-    S.BT[r * NBP + bp] = row_target_fast(bv[r], S.BZ[r * NBP + bp], S.BY[r * NBP + bp], (r < 4) ? irpq : irva);
+  for (int r = 0; r < 8; ++r) {
+    const long long e = erow_u(r) * NEP + (erow_end(r) ? et : ef);
+    S.ET[e] = row_target_fast(bv[r], S.EZ[e], S.EY[e], (r < 4) ? irpq : irva);
+  }
+}
+
+// Line-end rows of instance k between the slot layout and the canonical
+// [r][t * nl + l] order of the state vector (dir 0: slots -> canon, 1: back).
+// arr is a [4][NEP] (or [2][NEP] for the x-bar of p, q) slot array; rows r
+// of the canonical block follow erow_u / erow_end (nrows = 8 or 4).
+template <int BS>
+__global__ void __launch_bounds__(BS) k_edge_canon(Dev S, int k, int dir, double *arr, int nrows, double *canon) {
+  const Inst I = S.inst[k];
+  const long long n = (long long)I.T * I.nl;
+  const long long loc = (long long)blockIdx.x * BS + threadIdx.x;
+  if (loc >= n) return;
+  const int t = (int)(loc / I.nl), l = (int)(loc - (long long)t * I.nl);
+  long long ef, et;
+  line_ends(S, I, t, (long long)I.lo + l, ef, et);
+  for (int r = 0; r < nrows; ++r) {
+    const long long e = erow_u(r) * S.NEP + (erow_end(r) ? et : ef);
+    if (dir == 0)
+      canon[(long long)r * n + loc] = arr[e];
+    else
+      arr[e] = canon[(long long)r * n + loc];
+  }
 }
 
 }  // namespace ucac

@@ -47,7 +47,13 @@ thread_local std::string g_create_error;
 struct HInst {
   int nb, nl, ng, T, ref;
   int go, gpo, lo, bpo, uo, upo;
+  long long eo = 0;
+  int spp = 0, nblk = 0, bo = 0;
 };
+
+// staging rows of the canonical line-end blocks: x-bar of p, q (4), y, z,
+// lambda (8 each), x values (8, for the solution read-back)
+constexpr int NSTAGE = 4 + 3 * NBR + NBR;
 
 }  // namespace
 
@@ -62,7 +68,8 @@ struct ucac_handle {
   char *arena = nullptr;
   size_t arena_bytes = 0;
   Dev dev{};
-  long long NGEN = 0, NGP = 0, NL = 0, NBP = 0, NB = 0, NUP = 0;
+  long long NGEN = 0, NGP = 0, NL = 0, NBP = 0, NB = 0, NUP = 0, NEP = 0, max_nbp = 0;
+  double *stage = nullptr;  // [NSTAGE][max_nbp]: line-end rows of one instance in canonical order
   int ngr_gen = 0, ngr_gp = 0, ngr_bp = 0, ngr_up = 0;  // granule counts
   int grid_branch = 0;  // persistent line kernel: resident blocks on the whole GPU
   Tuning tune;
@@ -319,7 +326,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   std::vector<int> bf(NL), bt(NL);
   std::vector<double> Gs(NB), Bs(NB), Pd(NUP), Qd(NUP);
   std::vector<int> inc_ptr(NB + 1, 0), inc_br(2 * NL), inc_side(2 * NL), gen_ptr(NB + 1, 0), gen_idx(NGEN);
-  std::vector<double> G((size_t)NGF * NGP, 0.0), B((size_t)NBF * NBP, 0.0), U((size_t)NUF * NUP, 0.0);
+  std::vector<double> G((size_t)NGF * NGP, 0.0), B((size_t)FB_FB0 * NBP, 0.0), U((size_t)NUF * NUP, 0.0);
+  std::vector<double> fb0((size_t)4 * NBP, 0.0);  // cold-start x-bar of the flow rows, canonical [r][bp]
   std::vector<double> ctrl((size_t)NCTRL * n, 0.0);
   const double twopi = 6.283185307179586476925286766559;
   for (int k = 0; k < n; ++k) {
@@ -412,10 +420,10 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
         v[7] = std::min(std::max(rate2 - a2 * a2 - a3 * a3, 0.0), rate2);
         for (int q = 0; q < 8; ++q) B[(FB_V0 + q) * NBP + bp] = v[q];
         B[FB_C * NBP + bp] = cpen0;
-        B[(FB_FB0 + 0) * NBP + bp] = a0;
-        B[(FB_FB0 + 1) * NBP + bp] = a1;
-        B[(FB_FB0 + 2) * NBP + bp] = a2;
-        B[(FB_FB0 + 3) * NBP + bp] = a3;
+        fb0[0 * NBP + bp] = a0;
+        fb0[1 * NBP + bp] = a1;
+        fb0[2 * NBP + bp] = a2;
+        fb0[3 * NBP + bp] = a3;
       }
     }
     ctrl[(size_t)k * NCTRL + C_BETA] = P.beta0;
@@ -445,6 +453,61 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
       }
     }
   }
+  // ---- bus order and the line-end slot layout
+  // per instance: local bus indices sorted by (degree, generator count),
+  // stable; blocks of 32 consecutive buses in that order, block b with W_b
+  // slots per lane (its largest degree); the j-th incident line end of the
+  // bus at order position p = 32 b + l sits at slot blk_off[b] + 32 j + l.
+  std::vector<int> order(NB), eslot(2 * NL), blk_off, blk_w;
+  long long NEP = 0;
+  long long max_nbp = 0;
+  for (int k = 0; k < n; ++k) {
+    const HInst &I = h->hi[k];
+    auto deg = [&](int i) { return inc_ptr[I.uo + i + 1] - inc_ptr[I.uo + i]; };
+    std::vector<int> o(I.nb);
+    for (int i = 0; i < I.nb; ++i) o[i] = i;
+    auto key = [&](int i) { return std::make_pair(deg(i), gen_ptr[I.uo + i + 1] - gen_ptr[I.uo + i]); };
+    std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return key(a) < key(b); });
+    for (int p = 0; p < I.nb; ++p) order[I.uo + p] = o[p];
+    HInst &Hm = h->hi[k];
+    Hm.nblk = (I.nb + 31) / 32;
+    Hm.bo = (int)blk_off.size();
+    int off = 0;
+    for (int b = 0; b < Hm.nblk; ++b) {
+      int w = 0;
+      for (int p = 32 * b; p < std::min(32 * b + 32, I.nb); ++p) w = std::max(w, deg(o[p]));
+      blk_off.push_back(off);
+      blk_w.push_back(w);
+      off += 32 * w;
+    }
+    Hm.spp = off;
+    Hm.eo = NEP;
+    NEP += (long long)I.T * off;
+    for (int p = 0; p < I.nb; ++p) {
+      const int i = o[p], b = p / 32, l = p % 32, ig = I.uo + i;
+      for (int j = 0; j < deg(i); ++j) {
+        const int e = inc_ptr[ig] + j;
+        eslot[(size_t)inc_side[e] * NL + I.lo + inc_br[e]] = blk_off[Hm.bo + b] + 32 * j + l;
+      }
+    }
+    max_nbp = std::max(max_nbp, (long long)I.T * I.nl);
+  }
+  if (NEP > 2000000000LL) {
+    delete h;
+    return fail(nullptr, UCAC_E_ARG, "batch too large for 32-bit item indices");
+  }
+  h->NEP = NEP;
+  h->max_nbp = max_nbp;
+  std::vector<double> efb((size_t)2 * NEP, 0.0);
+  for (int k = 0; k < n; ++k) {
+    const HInst &I = h->hi[k];
+    for (int t = 0; t < I.T; ++t)
+      for (int l = 0; l < I.nl; ++l) {
+        const long long bp = I.bpo + (long long)t * I.nl + l, base = I.eo + (long long)t * I.spp;
+        const long long ee[2] = {base + eslot[I.lo + l], base + eslot[NL + I.lo + l]};
+        for (int r = 0; r < 4; ++r) efb[(size_t)erow_u(r) * NEP + ee[erow_end(r)]] = fb0[(size_t)r * NBP + bp];
+      }
+  }
   // ---- block tables
   std::vector<int> bgi, bgf, bpi, bpf, bbi, bbf, bui, buf_;
   std::vector<int> g0(n), g1(n), p0b(n), p1b(n), q0b(n), q1b(n), u0b(n), u1b(n);
@@ -460,7 +523,17 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     build_granules(offg, cntg, GRAN, bgi, bgf, g0, g1);
     build_granules(offp, cntp, GRAN, bpi, bpf, p0b, p1b);
     build_granules(offb, cntb, GRAN, bbi, bbf, q0b, q1b);
-    build_granules(offu, cntu, GRAN, bui, buf_, u0b, u1b);
+    (void)offu;
+    (void)cntu;
+    for (int k = 0; k < n; ++k) {
+      const HInst &I = h->hi[k];
+      u0b[k] = (int)bui.size();
+      for (int tb = 0; tb < I.T * I.nblk; ++tb) {
+        bui.push_back(k);
+        buf_.push_back(tb);
+      }
+      u1b[k] = (int)bui.size();
+    }
   }
   h->ngr_gen = (int)bgi.size();
   h->ngr_gp = (int)bpi.size();
@@ -471,6 +544,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     Inst D{};
     D.nb = I.nb; D.nl = I.nl; D.ng = I.ng; D.T = I.T; D.ref = I.ref;
     D.go = I.go; D.gpo = I.gpo; D.lo = I.lo; D.bpo = I.bpo; D.uo = I.uo; D.upo = I.upo;
+    D.eo = I.eo; D.spp = I.spp; D.nblk = I.nblk; D.bo = I.bo;
     D.m_rows = I.T * 8 * I.nl + I.ng * (12 * I.T - 1);
     D.gran_gen0 = g0[k]; D.gran_gen1 = g1[k];
     D.gran_gp0 = p0b[k]; D.gran_gp1 = p1b[k];
@@ -487,10 +561,12 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_G = A.take<double>((size_t)NGF * NGP);
   const size_t o_GR = A.take<double>((size_t)5 * NGR * NGP);
   const size_t o_BC = A.take<double>((size_t)BC_N * NL), o_bft = A.take<int>(2 * NL);
-  const size_t o_B = A.take<double>((size_t)NBF * NBP);
-  const size_t o_BR = A.take<double>((size_t)5 * NBR * NBP);
+  const size_t o_B = A.take<double>((size_t)FB_FB0 * NBP);
+  const size_t o_E = A.take<double>((size_t)22 * NEP);
+  const size_t o_es = A.take<int>(2 * NL + 2 * blk_off.size());
+  const size_t o_stage = A.take<double>((size_t)NSTAGE * max_nbp);
   const size_t o_bus = A.take<double>(2 * NB);
-  const size_t o_csr = A.take<int>((NB + 1) * 2 + 4 * NL + NGEN + NB);
+  const size_t o_csr = A.take<int>((NB + 1) * 2 + NGEN + NB);
   const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
   const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
   const size_t o_stat = A.take<long long>(4 * n);
@@ -528,14 +604,18 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.bf = (const int *)(ar + o_bft); D.bt = D.bf + NL;
   D.NBP = NBP;
   D.B = (double *)(ar + o_B);
-  double *br = (double *)(ar + o_BR);
-  D.BA = br; D.BY = br + (size_t)NBR * NBP; D.BZ = br + (size_t)2 * NBR * NBP; D.BL = br + (size_t)3 * NBR * NBP;
-  D.BT = br + (size_t)4 * NBR * NBP;
+  D.NEP = NEP;
+  double *er = (double *)(ar + o_E);
+  D.EA = er; D.EY = er + (size_t)4 * NEP; D.EZ = er + (size_t)8 * NEP; D.EL = er + (size_t)12 * NEP;
+  D.ET = er + (size_t)16 * NEP; D.EFB = er + (size_t)20 * NEP;
+  const int *es = (const int *)(ar + o_es);
+  D.eslot = es; D.blk_off = es + 2 * NL; D.blk_w = D.blk_off + blk_off.size();
+  h->stage = (double *)(ar + o_stage);
   D.NB = NB;
   D.Gs = (const double *)(ar + o_bus); D.Bs = D.Gs + NB;
   const int *csr = (const int *)(ar + o_csr);
-  D.inc_ptr = csr; D.gen_ptr = csr + (NB + 1); D.inc_br = csr + 2 * (NB + 1); D.inc_side = D.inc_br + 2 * NL;
-  D.gen_idx = D.inc_side + 2 * NL;
+  D.inc_ptr = csr; D.gen_ptr = csr + (NB + 1);
+  D.gen_idx = D.gen_ptr + (NB + 1);
   D.bus_order = D.gen_idx + NGEN;
   D.NUP = NUP;
   D.Pd = (const double *)(ar + o_pq); D.Qd = D.Pd + NUP;
@@ -574,25 +654,11 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   bush.insert(bush.end(), Bs.begin(), Bs.end());
   std::vector<int> csrh(inc_ptr);
   csrh.insert(csrh.end(), gen_ptr.begin(), gen_ptr.end());
-  csrh.insert(csrh.end(), inc_br.begin(), inc_br.end());
-  csrh.insert(csrh.end(), inc_side.begin(), inc_side.end());
   csrh.insert(csrh.end(), gen_idx.begin(), gen_idx.end());
-  {
-    // per instance: local bus indices sorted by (degree, generator count), stable
-    std::vector<int> order(NB);
-    for (int k = 0; k < n; ++k) {
-      const HInst &I = h->hi[k];
-      std::vector<int> o(I.nb);
-      for (int i = 0; i < I.nb; ++i) o[i] = i;
-      auto key = [&](int i) {
-        const int b = I.uo + i;
-        return std::make_pair(inc_ptr[b + 1] - inc_ptr[b], gen_ptr[b + 1] - gen_ptr[b]);
-      };
-      std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return key(a) < key(b); });
-      for (int i = 0; i < I.nb; ++i) order[I.uo + i] = o[i];
-    }
-    csrh.insert(csrh.end(), order.begin(), order.end());
-  }
+  csrh.insert(csrh.end(), order.begin(), order.end());
+  std::vector<int> esh(eslot);
+  esh.insert(esh.end(), blk_off.begin(), blk_off.end());
+  esh.insert(esh.end(), blk_w.begin(), blk_w.end());
   std::vector<double> pqh(Pd);
   pqh.insert(pqh.end(), Qd.begin(), Qd.end());
   std::vector<int> blkh;
@@ -607,6 +673,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   chain(up(D.BC, BC.data(), BC.size() * 8));
   chain(up(D.bf, bfth.data(), bfth.size() * 4));
   chain(up(D.B, B.data(), B.size() * 8));
+  chain(up(D.EFB, efb.data(), efb.size() * 8));
+  chain(up(D.eslot, esh.data(), esh.size() * 4));
   chain(up(D.Gs, bush.data(), bush.size() * 8));
   chain(up(csr, csrh.data(), csrh.size() * 4));
   chain(up(D.Pd, pqh.data(), pqh.size() * 8));
@@ -694,6 +762,10 @@ int ucac_residuals(const ucac_handle *hc, int32_t instance, ucac_report *out) {
   return UCAC_OK;
 }
 
+namespace {
+void edge_stage(ucac_handle *h, int k, int dir, bool with_x, cudaStream_t s);
+}  // namespace
+
 int ucac_solution(const ucac_handle *hc, int32_t k, double *p, double *q, double *w, double *theta, double *pf,
                   uint8_t *u_on) {
   ucac_handle *h = const_cast<ucac_handle *>(hc);
@@ -707,9 +779,12 @@ int ucac_solution(const ucac_handle *hc, int32_t k, double *p, double *q, double
   if (w) CK(cudaMemcpy(w, D.U + FU_W * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost));
   if (theta) CK(cudaMemcpy(theta, D.U + FU_TH * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost));
   if (pf) {
+    edge_stage(h, k, 0, true, h->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));
     std::vector<double> tmp(nbp);
     for (int r = 0; r < 4; ++r) {
-      CK(cudaMemcpy(tmp.data(), D.BA + r * D.NBP + I.bpo, nbp * 8, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(tmp.data(), h->stage + (size_t)(4 + 3 * NBR + r) * nbp, nbp * 8, cudaMemcpyDeviceToHost));
       for (size_t j = 0; j < nbp; ++j) pf[j * 4 + r] = tmp[j];
     }
   }
@@ -729,7 +804,9 @@ size_t ucac_state_size(const ucac_handle *h, int32_t k) {
 }
 
 namespace {
-// (device pointer, element count) of each canonical state segment of instance k
+// (device pointer, element count) of each canonical state segment of instance
+// k; the line-end blocks (x-bar of the flow rows, y, z, lambda of the line
+// rows) point into the staging rows, which edge_stage fills or drains
 std::vector<std::pair<double *, size_t>> state_segments(ucac_handle *h, int k) {
   const HInst &I = h->hi[k];
   const Dev &D = h->dev;
@@ -738,18 +815,37 @@ std::vector<std::pair<double *, size_t>> state_segments(ucac_handle *h, int k) {
   for (int f = 0; f < NGF; ++f) s.push_back({D.G + f * D.NGP + I.gpo, ngp});
   for (double *arr : {D.GY, D.GZ, D.GL})
     for (int r = 0; r < NGR; ++r) s.push_back({arr + r * D.NGP + I.gpo, ngp});
-  for (int f = 0; f < NBF; ++f) s.push_back({D.B + f * D.NBP + I.bpo, nbp});
-  for (double *arr : {D.BY, D.BZ, D.BL})
-    for (int r = 0; r < NBR; ++r) s.push_back({arr + r * D.NBP + I.bpo, nbp});
+  for (int f = 0; f < NBF; ++f)
+    s.push_back({f < FB_FB0 ? D.B + f * D.NBP + I.bpo : h->stage + (size_t)(f - FB_FB0) * nbp, nbp});
+  for (int a = 0; a < 3; ++a)
+    for (int r = 0; r < NBR; ++r) s.push_back({h->stage + (size_t)(4 + a * NBR + r) * nbp, nbp});
   for (int f = 0; f < NUF; ++f) s.push_back({D.U + f * D.NUP + I.upo, nup});
   s.push_back({D.ctrl + (size_t)k * NCTRL, (size_t)NCTRL});
   return s;
+}
+
+// line-end slot arrays of instance k <-> staging rows in canonical order
+// (dir 0: slots -> staging, 1: staging -> slots); with_x adds the x values
+// (rows 28..35, slots -> staging only)
+void edge_stage(ucac_handle *h, int k, int dir, bool with_x, cudaStream_t s) {
+  const HInst &I = h->hi[k];
+  const size_t nbp = (size_t)I.T * I.nl;
+  const int nblk = (int)((nbp + 255) / 256);
+  const Dev &D = h->dev;
+  k_edge_canon<256><<<nblk, 256, 0, s>>>(D, k, dir, D.EFB, 4, h->stage);
+  k_edge_canon<256><<<nblk, 256, 0, s>>>(D, k, dir, D.EY, NBR, h->stage + 4 * nbp);
+  k_edge_canon<256><<<nblk, 256, 0, s>>>(D, k, dir, D.EZ, NBR, h->stage + (4 + NBR) * nbp);
+  k_edge_canon<256><<<nblk, 256, 0, s>>>(D, k, dir, D.EL, NBR, h->stage + (4 + 2 * NBR) * nbp);
+  if (with_x) k_edge_canon<256><<<nblk, 256, 0, s>>>(D, k, 0, D.EA, NBR, h->stage + (4 + 3 * NBR) * nbp);
 }
 }  // namespace
 
 int ucac_state_export(const ucac_handle *hc, int32_t k, double *buf, size_t n) {
   ucac_handle *h = const_cast<ucac_handle *>(hc);
   if (!h || !buf || k < 0 || k >= h->K || n < ucac_state_size(h, k)) return fail(h, UCAC_E_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  edge_stage(h, k, 0, false, h->stream);
+  CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   size_t o = 0;
   for (auto &sg : state_segments(h, k)) {
@@ -767,6 +863,7 @@ int ucac_state_import(ucac_handle *h, int32_t k, const double *buf, size_t n) {
     CK(cudaMemcpy(sg.first, buf + o, sg.second * 8, cudaMemcpyHostToDevice));
     o += sg.second;
   }
+  edge_stage(h, k, 1, false, h->stream);
   launch_prep(h, h->stream);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
