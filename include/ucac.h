@@ -192,9 +192,11 @@ int ucac_state_import(ucac_handle *h, int32_t instance, const double *buf, size_
  * Average device time per sweep of each kernel over n_sweeps sweeps, timed
  * with CUDA events on the handle's stream (kernels launched one by one, not
  * from the graph).  ms[] receives UCAC_N_KERNELS values in the order of
- * ucac_kernel_name().  Synchronises.
+ * ucac_kernel_name(): k_ucdp, k_gen, k_branch (the line kernel of either
+ * form), k_bus, k_ucbar, k_finish, k_mlp (0 unless the learned warm start is
+ * enabled).  Synchronises.
  */
-#define UCAC_N_KERNELS 6
+#define UCAC_N_KERNELS 7
 int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms);
 const char *ucac_kernel_name(int32_t k);
 
@@ -257,6 +259,51 @@ int ucac_ucdp_noalloc(int32_t n_gen, int32_t T, double rho_uc, const double *tau
                       const double *tau_sd, const double *c0, const double *c_su, const double *c_sd,
                       const int32_t *TU, const int32_t *TD, const int32_t *u0, const int32_t *K0, int8_t *u_on,
                       double *cost, void *cuda_stream);
+
+/*
+ * Learned warm start of the line subproblems (no counterpart in the paper,
+ * which starts every line solve from the previous ADMM iterate).  A 12-64-64-6
+ * MLP with SiLU activations maps 12 features of a line-period -- its voltage
+ * magnitudes and angle difference at the previous iterate, the direction of
+ * its series admittance, and the unit direction r / |r| of its target
+ * residual r (flow residuals divided by |y|, w and angle residuals) -- to the
+ * change of its W-form iterate (w_i, w_j, wR, wI, theta_i, theta_j) divided
+ * by |r|.  Parameters are one flat FP32 vector of ucac_mlp_param_count()
+ * values: W1 [64][12], b1 [64], W2 [64][64], b2 [64], W3 [6][64], b3 [6]
+ * (row-major, output index first).
+ *
+ * ucac_mlp_forward: inference on the tensor cores (BF16 operands, FP32
+ * accumulation, BF16 hidden activations) of n rows x [n][12] into y [n][6];
+ * DEVICE pointers; workspace of ucac_mlp_workspace_bytes(n) bytes.
+ * Synchronises; UCAC_E_CUDA if an mbarrier wait of the kernel timed out.
+ * ucac_mlp_grad: FP32 loss (1/n) sum |y - labels|^2 into *loss and its
+ * gradient into grad [param_count] (DEVICE pointers; sums over the batch in
+ * sample order, so the result is reproducible).  Enqueued, not synchronised.
+ * ucac_mlp_adam: one Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step >= 1)
+ * on DEVICE params / moments m, v.  Enqueued, not synchronised.
+ * ucac_line_features: features [T*n_branch][12] (FP32) and residual norms
+ * |r| [T*n_branch] of instance k at the handle's current iterate, into HOST
+ * buffers (training data: label = (x_after_sweep - x_before) / |r|).
+ * ucac_set_warm_start: params (HOST, FP32) enable the learned start: every
+ * sweep then runs the network over all line-periods before the line kernel,
+ * and a line solve starts from the proposal when the proposal's objective is
+ * lower than the previous iterate's (polar form; the W-form line solver
+ * always starts from the previous iterate).  NULL disables it.  Re-captures
+ * the sweep graph; synchronises.
+ * ucac_warm_start_stats: line solves of instance k started from the
+ * proposal since the last ucac_set_warm_start; *mma_error (may be NULL) is
+ * non-zero if a tensor-core wait timed out.
+ */
+int32_t ucac_mlp_param_count(void);
+size_t ucac_mlp_workspace_bytes(int64_t n);
+int ucac_mlp_forward(int64_t n, const float *params, const float *x, float *y, void *workspace,
+                     size_t workspace_bytes, void *cuda_stream);
+int ucac_mlp_grad(int64_t n, const float *params, const float *x, const float *labels, float *grad, float *loss,
+                  void *workspace, size_t workspace_bytes, void *cuda_stream);
+int ucac_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr, void *cuda_stream);
+int ucac_line_features(const ucac_handle *h, int32_t instance, float *feat, double *scale);
+int ucac_set_warm_start(ucac_handle *h, const float *params);
+int ucac_warm_start_stats(const ucac_handle *h, int32_t instance, int64_t *taken, int32_t *mma_error);
 
 /*
  * Measures the device's FP64 fused multiply-add throughput (FLOP/s, 2 per

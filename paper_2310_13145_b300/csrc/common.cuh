@@ -109,6 +109,12 @@ struct Dev {
   double *part_up;    // [granules of bus-periods][NQ]
   double *part_gp;    // [granules of gen-periods][NQ]
   long long *bstat;   // [K][3]: Newton iterations, AL rounds, capped solves (line kernel, per sweep)
+  // learned warm start: proposed change of each line-period's iterate
+  // [6][NBP] (W coordinates, written by the MLP kernel of the same sweep),
+  // enabled flag, and the count of line solves started from it [K]
+  const float *prop;
+  int warm;
+  unsigned long long *wstat;
   unsigned long long *bp_counter;  // work counter of the persistent line kernel
   // UC dynamic-program scratch: stage costs, cost-to-go, decisions
   double *dpL;        // [4][T][ng] per instance, instance slice at 4*gpo

@@ -501,15 +501,16 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   // per-lane statistics, flushed to the instance's counters when the lane
   // moves to another instance or retires (consecutive items mostly share one)
   int acc_k = -1;
-  unsigned long long acc_nw = 0, acc_al = 0, acc_cap = 0;
+  unsigned long long acc_nw = 0, acc_al = 0, acc_cap = 0, acc_w = 0;
   auto flush = [&]() {
     if (acc_k >= 0) {
       unsigned long long *st = (unsigned long long *)(S.bstat + (long long)acc_k * 3);
       atomicAdd(&st[0], acc_nw);
       atomicAdd(&st[1], acc_al);
       if (acc_cap) atomicAdd(&st[2], acc_cap);
+      if (acc_w) atomicAdd(&S.wstat[acc_k], acc_w);
     }
-    acc_nw = acc_al = acc_cap = 0;
+    acc_nw = acc_al = acc_cap = acc_w = 0;
   };
   bool need_full = false;
   double f = 0.0, Delta = 1.0, hprev = INFINITY, omega = 0.0, cmax = 0.0;
@@ -570,6 +571,31 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           v[2] = clampd(S.B[(FB_V0 + 4) * NBP + bp] - S.B[(FB_V0 + 5) * NBP + bp], pol_lo(K, 2), pol_hi(K, 2));
           v[3] = fmax(S.B[(FB_V0 + 6) * NBP + bp], 0.0);
           v[4] = fmax(S.B[(FB_V0 + 7) * NBP + bp], 0.0);
+          if (S.warm) {
+            // learned warm start: the network's proposal x0 + s y (W
+            // coordinates) is taken when its objective is below the plain
+            // start's, both with the slacks at their exact minimiser; the
+            // Newton solve that follows is the same either way
+            const double ht[2] = {-P.mu[0] * P.ic, -P.mu[1] * P.ic};
+            double vm[POL_NV];
+            const double wi = S.B[(FB_V0 + 0) * NBP + bp] + (double)S.prop[0 * NBP + bp];
+            const double wj = S.B[(FB_V0 + 1) * NBP + bp] + (double)S.prop[1 * NBP + bp];
+            const double thi = S.B[(FB_V0 + 4) * NBP + bp] + (double)S.prop[4 * NBP + bp];
+            const double thj = S.B[(FB_V0 + 5) * NBP + bp] + (double)S.prop[5 * NBP + bp];
+            vm[0] = clampd(sqrt(fmax(wi, 0.0)), K.lo0, K.hi0);
+            vm[1] = clampd(sqrt(fmax(wj, 0.0)), K.lo1, K.hi1);
+            vm[2] = clampd(thi - thj, pol_lo(K, 2), pol_hi(K, 2));
+            vm[3] = v[3];
+            vm[4] = v[4];
+            double at[4], ct, st;
+            const double fp = pol_obj(K, P, v, at, ct, st, ht, 3);
+            const double fm = pol_obj(K, P, vm, at, ct, st, ht, 3);
+            if (fm < fp) {
+#pragma unroll
+              for (int i = 0; i < POL_NV; ++i) v[i] = vm[i];
+              ++acc_w;
+            }
+          }
           const double rmax = fmax(I.rpq, I.rva);
           omega = S.prm.omega_rel * rmax;
           cmax = S.prm.c_max_rel * rmax;

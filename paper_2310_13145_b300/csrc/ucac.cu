@@ -23,6 +23,7 @@
 #include "k_branch.cuh"
 #include "k_gen.cuh"
 #include "k_line_polar.cuh"
+#include "k_mlp.cuh"
 #include "k_ucdp.cuh"
 #include "k_xbar.cuh"
 
@@ -70,6 +71,8 @@ struct ucac_handle {
   Dev dev{};
   long long NGEN = 0, NGP = 0, NL = 0, NBP = 0, NB = 0, NUP = 0, NEP = 0, max_nbp = 0;
   double *stage = nullptr;  // [NSTAGE][max_nbp]: line-end rows of one instance in canonical order
+  uint8_t *mlp_pack = nullptr;  // packed warm-start network (BF16 operands, FP32 biases)
+  int *mlp_err = nullptr;       // set by the MLP kernel on a timed-out wait
   int ngr_gen = 0, ngr_gp = 0, ngr_bp = 0, ngr_up = 0;  // granule counts
   int grid_branch = 0;  // persistent line kernel: resident blocks on the whole GPU
   Tuning tune;
@@ -224,9 +227,20 @@ void launch_prep(ucac_handle *h, cudaStream_t s) {
   k_prep_branch<BS_PREP><<<blocks_for(h->ngr_bp, BS_PREP), BS_PREP, 0, s>>>(h->dev);
 }
 
+// persistent tensor-core MLP over all line-periods (learned warm start)
+void launch_mlp(ucac_handle *h, cudaStream_t s) {
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long tiles = (h->NBP + 127) / 128;
+  const int grid = (int)std::max(1LL, std::min(tiles, 4LL * sms));
+  k_mlp<true><<<grid, 128, 0, s>>>(h->dev, h->mlp_pack, h->NBP, nullptr, const_cast<float *>(h->dev.prop),
+                                   h->mlp_err);
+}
+
 void launch_sweep(ucac_handle *h, cudaStream_t s) {
   launch_ucdp(h, s);
   launch_gen(h, s);
+  if (h->dev.warm) launch_mlp(h, s);
   launch_line(h, s);
   launch_bus(h, s);
   launch_ucbar(h, s);
@@ -247,7 +261,7 @@ cudaError_t capture_graph(ucac_handle *h) {
   return e;
 }
 
-const char *kKernelNames[UCAC_N_KERNELS] = {"k_ucdp", "k_gen", "k_branch", "k_bus", "k_ucbar", "k_finish"};
+const char *kKernelNames[UCAC_N_KERNELS] = {"k_ucdp", "k_gen", "k_branch", "k_bus", "k_ucbar", "k_finish", "k_mlp"};
 
 }  // namespace
 
@@ -574,6 +588,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_pbp = A.take<long long>(3 * (size_t)n + 8);
   const size_t o_dpL = A.take<double>(4 * NGP), o_dpC = A.take<double>(2 * (NGP + NGEN));
   const size_t o_dpD = A.take<unsigned char>(2 * NGP);
+  const size_t o_prop = A.take<float>((size_t)MLP_OUT * NBP), o_pack = A.take<uint8_t>(MLP_PACK_BYTES);
+  const size_t o_wst = A.take<unsigned long long>(n), o_merr = A.take<int>(1);
   const size_t o_blk = A.take<int>(2 * ((size_t)h->ngr_gen + h->ngr_gp + h->ngr_bp + h->ngr_up));
   h->arena_bytes = A.off;
   cudaError_t ce = cudaMalloc((void **)&h->arena, h->arena_bytes);
@@ -630,6 +646,11 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.dpL = (double *)(ar + o_dpL);
   D.dpC = (double *)(ar + o_dpC);
   D.dpD = (unsigned char *)(ar + o_dpD);
+  D.prop = (const float *)(ar + o_prop);
+  D.warm = 0;
+  D.wstat = (unsigned long long *)(ar + o_wst);
+  h->mlp_pack = (uint8_t *)(ar + o_pack);
+  h->mlp_err = (int *)(ar + o_merr);
   int *blk = (int *)(ar + o_blk);
   D.g_gen = Granules{h->ngr_gen, blk, blk + h->ngr_gen};
   blk += 2 * h->ngr_gen;
@@ -872,9 +893,12 @@ int ucac_state_import(ucac_handle *h, int32_t k, const double *buf, size_t n) {
 
 int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
   if (!h || !ms || n_sweeps < 1) return fail(h, UCAC_E_ARG, "bad arguments");
-  cudaEvent_t ev[UCAC_N_KERNELS + 1];
+  // events around each launch of one sweep, in launch order:
+  // ucdp, gen, mlp (warm start only), line, bus, ucbar, finish
+  cudaEvent_t ev[8];
   for (auto &e : ev) CK(cudaEventCreate(&e));
   double acc[UCAC_N_KERNELS] = {0};
+  const int slot[7] = {0, 1, 6, 2, 3, 4, 5};  // launch position -> kernel index
   const Dev &D = h->dev;
   cudaStream_t s = h->stream;
   for (int it = 0; it < n_sweeps; ++it) {
@@ -883,19 +907,21 @@ int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
     CK(cudaEventRecord(ev[1], s));
     launch_gen(h, s);
     CK(cudaEventRecord(ev[2], s));
-    launch_line(h, s);
+    if (h->dev.warm) launch_mlp(h, s);
     CK(cudaEventRecord(ev[3], s));
-    launch_bus(h, s);
+    launch_line(h, s);
     CK(cudaEventRecord(ev[4], s));
-    launch_ucbar(h, s);
+    launch_bus(h, s);
     CK(cudaEventRecord(ev[5], s));
-    k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(D);
+    launch_ucbar(h, s);
     CK(cudaEventRecord(ev[6], s));
-    CK(cudaEventSynchronize(ev[6]));
-    for (int j = 0; j < UCAC_N_KERNELS; ++j) {
+    k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(D);
+    CK(cudaEventRecord(ev[7], s));
+    CK(cudaEventSynchronize(ev[7]));
+    for (int j = 0; j < 7; ++j) {
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, ev[j], ev[j + 1]));
-      acc[j] += t;
+      acc[slot[j]] += t;
     }
   }
   CK(cudaGetLastError());
@@ -984,6 +1010,139 @@ int ucac_autotune(ucac_handle *h, int32_t sweeps_per_trial, const char *cache_pa
     o << key << " " << best.ucdp << " " << best.gen << " " << best.line << " " << best.bus << " " << best.ucbar << "\n";
   }
   return apply(best);
+}
+
+// ------------------------------------------------ learned warm start (MLP)
+int32_t ucac_mlp_param_count(void) { return MLP_NPARAM; }
+
+namespace {
+size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+// workspace: Z1, Z2, dZ1, dZ2 [n][64], dY [n][6], sq [n] (FP32), packed weights, error flag
+struct MlpWs {
+  float *Z1, *Z2, *dZ1, *dZ2, *dY, *sq;
+  uint8_t *pack;
+  int *err;
+};
+MlpWs mlp_ws(void *ws, int64_t n) {
+  char *b = (char *)ws;
+  MlpWs w;
+  const size_t h = (size_t)n * MLP_H * 4;
+  w.Z1 = (float *)b;
+  w.Z2 = (float *)(b + h);
+  w.dZ1 = (float *)(b + 2 * h);
+  w.dZ2 = (float *)(b + 3 * h);
+  w.dY = (float *)(b + 4 * h);
+  w.sq = (float *)(b + 4 * h + (size_t)n * MLP_OUT * 4);
+  const size_t o = up256(4 * h + (size_t)n * (MLP_OUT + 1) * 4);
+  w.pack = (uint8_t *)(b + o);
+  w.err = (int *)(b + o + up256(MLP_PACK_BYTES));
+  return w;
+}
+}  // namespace
+
+size_t ucac_mlp_workspace_bytes(int64_t n) {
+  if (n < 1) return 0;
+  return up256((size_t)n * (4 * MLP_H + MLP_OUT + 1) * 4) + up256(MLP_PACK_BYTES) + 256;
+}
+
+int ucac_mlp_forward(int64_t n, const float *params, const float *x, float *y, void *workspace,
+                     size_t workspace_bytes, void *cuda_stream) {
+  ucac_handle *h = nullptr;
+  if (n < 1 || !params || !x || !y || !workspace || workspace_bytes < ucac_mlp_workspace_bytes(n))
+    return fail(h, UCAC_E_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const MlpWs w = mlp_ws(workspace, n);
+  int dev = 0, sms = 148;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  k_mlp_pack<<<16, 256, 0, s>>>(params, w.pack);
+  CK(cudaMemsetAsync(w.err, 0, sizeof(int), s));
+  const long long tiles = (n + 127) / 128;
+  const int grid = (int)std::max(1LL, std::min(tiles, 4LL * sms));
+  Dev none{};
+  k_mlp<false><<<grid, 128, 0, s>>>(none, w.pack, n, x, y, w.err);
+  CK(cudaGetLastError());
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, w.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (err) return fail(h, UCAC_E_CUDA, "tensor-core MLP: an mbarrier wait timed out");
+  return UCAC_OK;
+}
+
+int ucac_mlp_grad(int64_t n, const float *params, const float *x, const float *labels, float *grad, float *loss,
+                  void *workspace, size_t workspace_bytes, void *cuda_stream) {
+  ucac_handle *h = nullptr;
+  if (n < 1 || !params || !x || !labels || !grad || !loss || !workspace ||
+      workspace_bytes < ucac_mlp_workspace_bytes(n))
+    return fail(h, UCAC_E_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const MlpWs w = mlp_ws(workspace, n);
+  const int nb = (int)((n + 127) / 128);
+  k_mlp_fwd_train<<<nb, 128, 0, s>>>(n, x, labels, params, w.Z1, w.Z2, w.dY, w.sq);
+  k_mlp_bwd_train<<<nb, 128, 0, s>>>(n, params, w.Z1, w.Z2, w.dY, w.dZ1, w.dZ2);
+  k_mlp_wgrad<<<(MLP_NPARAM + 127) / 128, 128, 0, s>>>(n, x, w.Z1, w.Z2, w.dZ1, w.dZ2, w.dY, grad);
+  k_sum_fixed<<<1, 256, 0, s>>>(n, w.sq, 1.0f / (float)n, loss);
+  CK(cudaGetLastError());
+  return UCAC_OK;
+}
+
+int ucac_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr, void *cuda_stream) {
+  ucac_handle *h = nullptr;
+  if (!params || !grad || !m || !v || step < 1 || !(lr > 0.0f)) return fail(h, UCAC_E_ARG, "bad arguments");
+  const double b1 = 0.9, b2 = 0.999;
+  k_mlp_adam<<<(MLP_NPARAM + 255) / 256, 256, 0, (cudaStream_t)cuda_stream>>>(
+      grad, params, m, v, lr, (float)b1, (float)b2, (float)(1.0 - b1), (float)(1.0 - b2),
+      (float)(1.0 - std::pow(b1, step)), (float)(1.0 - std::pow(b2, step)), 1e-8f);
+  CK(cudaGetLastError());
+  return UCAC_OK;
+}
+
+int ucac_line_features(const ucac_handle *hc, int32_t k, float *feat, double *scale) {
+  ucac_handle *h = const_cast<ucac_handle *>(hc);
+  if (!h || k < 0 || k >= h->K || !feat || !scale) return fail(h, UCAC_E_ARG, "bad arguments");
+  const HInst &I = h->hi[k];
+  const size_t n = (size_t)I.T * I.nl;
+  float *f = (float *)h->stage;
+  double *sc = h->stage + (n * MLP_IN + 1) / 2 + 1;
+  CK(cudaStreamSynchronize(h->stream));
+  k_line_features<256><<<(int)((n + 255) / 256), 256, 0, h->stream>>>(h->dev, k, f, sc);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(feat, f, n * MLP_IN * sizeof(float), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(scale, sc, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return UCAC_OK;
+}
+
+int ucac_set_warm_start(ucac_handle *h, const float *params) {
+  if (!h) return fail(h, UCAC_E_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  if (params) {
+    float *dp = nullptr;
+    CK(cudaMalloc((void **)&dp, MLP_NPARAM * sizeof(float)));
+    cudaError_t e = cudaMemcpy(dp, params, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      k_mlp_pack<<<16, 256, 0, h->stream>>>(dp, h->mlp_pack);
+      e = cudaStreamSynchronize(h->stream);
+    }
+    cudaFree(dp);
+    CK(e);
+    CK(cudaMemset(h->mlp_err, 0, sizeof(int)));
+  }
+  h->dev.warm = params ? 1 : 0;
+  CK(cudaMemset(h->dev.wstat, 0, sizeof(unsigned long long) * h->K));
+  CK(capture_graph(h));
+  return UCAC_OK;
+}
+
+int ucac_warm_start_stats(const ucac_handle *hc, int32_t k, int64_t *taken, int32_t *mma_error) {
+  ucac_handle *h = const_cast<ucac_handle *>(hc);
+  if (!h || k < 0 || k >= h->K || !taken) return fail(h, UCAC_E_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  unsigned long long t = 0;
+  CK(cudaMemcpy(&t, h->dev.wstat + k, sizeof(t), cudaMemcpyDeviceToHost));
+  *taken = (int64_t)t;
+  if (mma_error) CK(cudaMemcpy(mma_error, h->mlp_err, sizeof(int), cudaMemcpyDeviceToHost));
+  return UCAC_OK;
 }
 
 const char *ucac_kernel_name(int32_t k) { return (k >= 0 && k < UCAC_N_KERNELS) ? kKernelNames[k] : ""; }

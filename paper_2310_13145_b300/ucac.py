@@ -20,14 +20,16 @@ _ip = C.POINTER(C.c_int32)
 
 UCAC_OK, UCAC_CONVERGED = 0, 1
 UCAC_E_ARG, UCAC_E_GRID, UCAC_E_CUDA, UCAC_E_NEWTON_MAXIT, UCAC_E_NAN, UCAC_E_DIVERGED = -1, -2, -3, -4, -5, -6
-UCAC_N_KERNELS = 6
+UCAC_N_KERNELS = 7
 UCAC_LINE_W, UCAC_LINE_POLAR = 0, 1
 
 # symbols declared in include/ucac.h
 EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_instances", "ucac_iterate",
            "ucac_enqueue_sweeps", "ucac_residuals", "ucac_solution", "ucac_state_size", "ucac_state_export",
            "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp", "ucac_ucdp_noalloc",
-           "ucac_probe_fp64", "ucac_autotune", "ucac_destroy", "ucac_last_error"]
+           "ucac_probe_fp64", "ucac_autotune", "ucac_mlp_param_count", "ucac_mlp_workspace_bytes", "ucac_mlp_forward",
+           "ucac_mlp_grad", "ucac_mlp_adam", "ucac_line_features", "ucac_set_warm_start", "ucac_warm_start_stats",
+           "ucac_destroy", "ucac_last_error"]
 
 
 class ucac_grid(C.Structure):
@@ -95,6 +97,16 @@ def lib():
         L.ucac_ucdp_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_double] + [vp] * 12 + [vp]
         L.ucac_probe_fp64.argtypes = [C.c_int32, vp, _dp]
         L.ucac_autotune.argtypes = [vp, C.c_int32, C.c_char_p, _ip]
+        L.ucac_mlp_param_count.argtypes = []
+        L.ucac_mlp_param_count.restype = C.c_int32
+        L.ucac_mlp_workspace_bytes.argtypes = [C.c_int64]
+        L.ucac_mlp_workspace_bytes.restype = C.c_size_t
+        L.ucac_mlp_forward.argtypes = [C.c_int64, vp, vp, vp, vp, C.c_size_t, vp]
+        L.ucac_mlp_grad.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
+        L.ucac_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_float, vp]
+        L.ucac_line_features.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), _dp]
+        L.ucac_set_warm_start.argtypes = [vp, C.POINTER(C.c_float)]
+        L.ucac_warm_start_stats.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), _ip]
         L.ucac_destroy.argtypes = [vp]
         L.ucac_destroy.restype = None
         L.ucac_last_error.argtypes = [vp]
@@ -249,6 +261,55 @@ def ucac_autotune(h, sweeps_per_trial: int = 3, cache_path: str | None = None) -
     return dict(zip(("ucdp", "gen", "line", "bus", "ucbar"), (int(v) for v in out)))
 
 
+def ucac_mlp_param_count() -> int:
+    return int(lib().ucac_mlp_param_count())
+
+
+def ucac_mlp_workspace_bytes(n: int) -> int:
+    return int(lib().ucac_mlp_workspace_bytes(int(n)))
+
+
+def ucac_mlp_forward(n, params, x, y, workspace, workspace_bytes, stream=0):
+    """Tensor-core inference on DEVICE pointers (ints); synchronises."""
+    _check(lib().ucac_mlp_forward(int(n), params, x, y, workspace, int(workspace_bytes), stream))
+
+
+def ucac_mlp_grad(n, params, x, labels, grad, loss, workspace, workspace_bytes, stream=0):
+    """FP32 loss and gradient on DEVICE pointers (ints); enqueued."""
+    _check(lib().ucac_mlp_grad(int(n), params, x, labels, grad, loss, workspace, int(workspace_bytes), stream))
+
+
+def ucac_mlp_adam(params, grad, m, v, step, lr, stream=0):
+    _check(lib().ucac_mlp_adam(params, grad, m, v, int(step), float(lr), stream))
+
+
+def ucac_line_features(h, instance: int, n_rows: int):
+    """(features [n_rows][12] float32, residual norms [n_rows] float64) of the
+    instance's line-periods (n_rows = horizon * n_branch) at the current iterate."""
+    f = np.zeros((n_rows, 12), np.float32)
+    sc = np.zeros(n_rows)
+    _check(lib().ucac_line_features(h, int(instance), f.ctypes.data_as(C.POINTER(C.c_float)), sc.ctypes.data_as(_dp)),
+           h)
+    return f, sc
+
+
+def ucac_set_warm_start(h, params) -> None:
+    if params is None:
+        _check(lib().ucac_set_warm_start(h, None), h)
+        return
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.size != ucac_mlp_param_count():
+        raise UcacError(f"warm-start parameters: expected {ucac_mlp_param_count()} values, got {p.size}")
+    _check(lib().ucac_set_warm_start(h, p.ctypes.data_as(C.POINTER(C.c_float))), h)
+
+
+def ucac_warm_start_stats(h, instance: int = 0):
+    taken = C.c_int64(0)
+    err = C.c_int32(0)
+    _check(lib().ucac_warm_start_stats(h, int(instance), C.byref(taken), C.byref(err)), h)
+    return int(taken.value), int(err.value)
+
+
 def ucac_destroy(h) -> None:
     if h:
         lib().ucac_destroy(h)
@@ -264,6 +325,7 @@ class Handle:
 
     def __init__(self, grids, params=None, stream=0, horizons=None):
         self.grids = list(grids)
+        self.horizons = list(horizons) if horizons is not None else None
         self.h = ucac_create_batch(self.grids, horizons=horizons, params=params, stream=stream)
 
     def close(self):
@@ -297,3 +359,13 @@ class Handle:
 
     def autotune(self, sweeps_per_trial=3, cache_path=None):
         return ucac_autotune(self.h, sweeps_per_trial, cache_path)
+
+    def line_features(self, k=0):
+        T = self.horizons[k] if self.horizons is not None else self.grids[k].T
+        return ucac_line_features(self.h, k, T * self.grids[k].n_branch)
+
+    def set_warm_start(self, params):
+        ucac_set_warm_start(self.h, params)
+
+    def warm_start_stats(self, k=0):
+        return ucac_warm_start_stats(self.h, k)

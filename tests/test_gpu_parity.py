@@ -31,7 +31,8 @@ def line_form(request, ucac_mod):
     return ucac_mod.UCAC_LINE_POLAR if request.param == "polar" else ucac_mod.UCAC_LINE_W
 
 
-def _lockstep(ucac, grids, sweeps, params=None, oparams=None, warm=0, check_instances=None, line_form=None):
+def _lockstep(ucac, grids, sweeps, params=None, oparams=None, warm=0, check_instances=None, line_form=None,
+              setup=None):
     if line_form is not None:
         params = params if params is not None else ucac.ucac_default_params()
         params.line_form = line_form
@@ -39,6 +40,8 @@ def _lockstep(ucac, grids, sweeps, params=None, oparams=None, warm=0, check_inst
     skip = POLAR_SKIP if polar else ()
     mu_eta = (params.eta if params is not None else ucac.ucac_default_params().eta) if polar else None
     h = ucac.Handle(grids, params=params)
+    if setup is not None:
+        setup(h)
     if warm:
         h.enqueue(warm)
     orcs = {}
