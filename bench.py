@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start arm")
     return ap.parse_args()
 
 
@@ -342,6 +343,9 @@ def main():
     ttc = None
     if not a.no_ttc:
         ttc = time_to_tolerance(ucac, grids, stream, params, a.ttc_max_sweeps, cache)
+    learned = None
+    if not a.no_learned:
+        learned = learned_arm(ucac, h, grids, stream, params, a, cache)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         v, sample = oracle_sweep_rate(grids, budget_s=15.0)
@@ -357,24 +361,57 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "state larger than L2 (no flush needed)", "r_p_inst0": r["r_p"]},
                 "gpu_launches": 6 * a.steps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "time_to_1e-4": ttc,
+                "time_to_1e-4": ttc, "learned": learned,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def time_to_tolerance(ucac, grids, stream, params, max_sweeps, cache=None):
+def learned_arm(ucac, h, grids, stream, params, a, cache):
+    """The learned warm start: train the default network (outside any timed
+    region), then sweeps/s on the bench handle with it switched on, and the
+    time to 1e-4 from a cold start with it."""
+    import torch
+    from paper_2310_13145_b300 import warmstart
+    t0 = time.perf_counter()
+    wp, info = warmstart.train_default()
+    info["seconds"] = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        h.set_warm_start(wp)
+        h.enqueue(a.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h.enqueue(a.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = h.kernel_times(3)
+    taken = sum(h.warm_start_stats(k)[0] for k in range(len(grids)))
+    errs = sum(h.warm_start_stats(k)[1] for k in range(len(grids)))
+    h.set_warm_start(None)
+    out = {"sweeps_per_s": a.steps / (ms * 1e-3), "ms_per_step": ms / a.steps, "kernel_ms": kt,
+           "starts_from_network": taken, "tensor_core_errors": errs, "training": info}
+    if not a.no_ttc:
+        out["time_to_1e-4"] = time_to_tolerance(ucac, grids, stream, params, a.ttc_max_sweeps, cache, warm=wp)
+    return out
+
+
+def time_to_tolerance(ucac, grids, stream, params, max_sweeps, cache=None, warm=None):
     """Cold start to convergence of every instance (r_p, r_d <= 1e-4 RMS and
     z_rms <= 1e-4, the inner and outer stops of Algorithm 1) through the public
     API: create from host arrays, ucac_iterate with host checks every 50
-    sweeps (the checks are inside the timed region)."""
+    sweeps (the checks are inside the timed region).  warm: parameters of the
+    learned warm start (loaded inside the timed region) or None."""
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = ucac.Handle(grids, params=params, stream=stream.cuda_stream)
     if cache:
         h.autotune(3, cache)  # cache hit: applies the tuned block sizes
+    if warm is not None:
+        h.set_warm_start(warm)
     t1 = time.perf_counter()
     done, rc = 0, 0
     while done < max_sweeps and rc != 1:
@@ -382,13 +419,17 @@ def time_to_tolerance(ucac, grids, stream, params, max_sweeps, cache=None):
         done += params.check_every
     t2 = time.perf_counter()
     rs = [h.residuals(k) for k in range(len(grids))]
+    taken = sum(h.warm_start_stats(k)[0] for k in range(len(grids))) if warm is not None else 0
     h.close()
     return {"converged": rc == 1, "seconds": t2 - t0, "create_s": t1 - t0, "iterate_s": t2 - t1,
+            "newton_total": sum(r["newton_total"] for r in rs), "al_total": sum(r["al_total"] for r in rs),
+            "starts_from_network": taken,
             "sweeps": done, "check_every": params.check_every,
             "objective_mean": statistics.mean(r["objective"] for r in rs),
             "r_p_max": max(r["r_p"] for r in rs), "r_d_max": max(r["r_d"] for r in rs),
             "z_rms_max": max(r["z_rms"] for r in rs), "inf_norm_max": max(r["inf_norm_viol"] for r in rs),
-            "outer_max": max(r["outer"] for r in rs), "variant": "plain (no learned warm start)"}
+            "outer_max": max(r["outer"] for r in rs),
+            "variant": "learned warm start + batched" if warm is not None else "plain (no learned warm start)"}
 
 
 def e2e_run(ucac, grids, steps, stream, params, cache=None):

@@ -105,13 +105,15 @@ typedef struct ucac_params {
  * inf_norm_viol = |Ax + Bxbar|_inf (the primal infeasibility of Sec. IV-C),
  * objective = sum of generation, no-load, start-up and shut-down costs at the
  * current x.  newton / al = line-subproblem Newton / multiplier iterations in
- * the last sweep; n_newton_maxit = line subproblems that stopped on a cap.
- * status: 0 running, 1 converged, or a negative UCAC_E_* code.
+ * the last sweep; n_newton_maxit = line subproblems that stopped on a cap;
+ * newton_total / al_total = the same counts summed over every sweep since
+ * create.  status: 0 running, 1 converged, or a negative UCAC_E_* code.
  */
 typedef struct ucac_report {
   double r_p, r_d, z_norm, z_rms, inf_norm_viol, objective, beta;
   int64_t sweeps, outer, newton, al;
   int32_t status, n_newton_maxit;
+  int64_t newton_total, al_total;
 } ucac_report;
 
 typedef struct ucac_handle ucac_handle;
@@ -302,6 +304,10 @@ int ucac_mlp_grad(int64_t n, const float *params, const float *x, const float *l
                   void *workspace, size_t workspace_bytes, void *cuda_stream);
 int ucac_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr, void *cuda_stream);
 int ucac_line_features(const ucac_handle *h, int32_t instance, float *feat, double *scale);
+/* Features [NBP][12], residual norms [NBP] and W-form iterates [NBP][6] of
+ * every line-period of every instance (instance-major, then period, then
+ * line), into HOST buffers; any of the three may be NULL.  Synchronises. */
+int ucac_line_samples(const ucac_handle *h, float *feat, double *scale, double *iterate);
 int ucac_set_warm_start(ucac_handle *h, const float *params);
 int ucac_warm_start_stats(const ucac_handle *h, int32_t instance, int64_t *taken, int32_t *mma_error);
 

@@ -105,7 +105,7 @@ struct Dev {
   // control and records
   double *ctrl;       // [K][NCTRL]
   double *res;        // [K][NRES]
-  long long *stat;    // [K][4]: sweeps, newton, al, capped
+  long long *stat;    // [K][6]: sweeps, newton, al, capped (last sweep), newton, al (all sweeps)
   double *part_up;    // [granules of bus-periods][NQ]
   double *part_gp;    // [granules of gen-periods][NQ]
   long long *bstat;   // [K][3]: Newton iterations, AL rounds, capped solves (line kernel, per sweep)

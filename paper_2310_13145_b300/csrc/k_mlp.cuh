@@ -501,4 +501,24 @@ __global__ void __launch_bounds__(BS) k_line_features(Dev S, int k, float *__res
   sc[loc] = s;
 }
 
+// features of every line-period of the handle (global item order)
+template <int BS>
+__global__ void __launch_bounds__(BS) k_line_features_all(Dev S, float *__restrict__ feat, double *__restrict__ sc) {
+  const long long bp = (long long)blockIdx.x * BS + threadIdx.x;
+  if (bp >= S.NBP) return;
+  int lo = 0, hi = S.K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((long long)S.inst[mid].bpo <= bp) lo = mid; else hi = mid - 1;
+  }
+  const Inst &I = S.inst[lo];
+  const int loc = (int)(bp - I.bpo), t = loc / I.nl, l = loc - t * I.nl;
+  float f[MLP_IN];
+  double s;
+  line_features(S, I, bp, t, l, f, s);
+#pragma unroll
+  for (int j = 0; j < MLP_IN; ++j) feat[bp * MLP_IN + j] = f[j];
+  sc[bp] = s;
+}
+
 }  // namespace ucac

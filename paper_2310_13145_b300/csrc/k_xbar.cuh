@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
     const Params &P = S.prm;
     double *c = S.ctrl + (long long)k * NCTRL;
     double *r = S.res + (long long)k * NRES;
-    long long *s = S.stat + (long long)k * 4;
+    long long *s = S.stat + (long long)k * 6;
     const double m = (double)I.m_rows;
     const double rp = sqrt(out[Q_SP] / m), rd = sqrt(out[Q_SD] / m), zn = sqrt(out[Q_SZ]);
     const double zr = sqrt(out[Q_SZ] / m);
@@ -474,6 +474,8 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
     s[1] = nw;
     s[2] = na;
     s[3] = nc;
+    s[4] += nw;
+    s[5] += na;
     if (c[C_PEND] != 0.0) {
       c[C_BETA] = c[C_BNEXT];
       c[C_PEND] = 0.0;

@@ -583,7 +583,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_csr = A.take<int>((NB + 1) * 2 + NGEN + NB);
   const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
   const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
-  const size_t o_stat = A.take<long long>(4 * n);
+  const size_t o_stat = A.take<long long>(6 * n);
   const size_t o_pup = A.take<double>((size_t)NQ * h->ngr_up), o_pgp = A.take<double>((size_t)NQ * h->ngr_gp);
   const size_t o_pbp = A.take<long long>(3 * (size_t)n + 8);
   const size_t o_dpL = A.take<double>(4 * NGP), o_dpC = A.take<double>(2 * (NGP + NGEN));
@@ -762,11 +762,11 @@ int ucac_residuals(const ucac_handle *hc, int32_t instance, ucac_report *out) {
   ucac_handle *h = const_cast<ucac_handle *>(hc);
   if (!h || !out || instance < 0 || instance >= h->K) return fail(h, UCAC_E_ARG, "bad arguments");
   double r[NRES], c[NCTRL];
-  long long s[4];
+  long long s[6];
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(r, h->dev.res + (size_t)instance * NRES, sizeof(r), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(c, h->dev.ctrl + (size_t)instance * NCTRL, sizeof(c), cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(s, h->dev.stat + (size_t)instance * 4, sizeof(s), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(s, h->dev.stat + (size_t)instance * 6, sizeof(s), cudaMemcpyDeviceToHost));
   out->r_p = r[R_RP];
   out->r_d = r[R_RD];
   out->z_norm = r[R_ZN];
@@ -779,6 +779,8 @@ int ucac_residuals(const ucac_handle *hc, int32_t instance, ucac_report *out) {
   out->newton = s[1];
   out->al = s[2];
   out->n_newton_maxit = (int32_t)s[3];
+  out->newton_total = s[4];
+  out->al_total = s[5];
   out->status = (int32_t)r[R_STATUS];
   return UCAC_OK;
 }
@@ -1110,6 +1112,34 @@ int ucac_line_features(const ucac_handle *hc, int32_t k, float *feat, double *sc
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(feat, f, n * MLP_IN * sizeof(float), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(scale, sc, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return UCAC_OK;
+}
+
+int ucac_line_samples(const ucac_handle *hc, float *feat, double *scale, double *iterate) {
+  ucac_handle *h = const_cast<ucac_handle *>(hc);
+  if (!h) return fail(h, UCAC_E_ARG, "bad arguments");
+  const size_t n = (size_t)h->NBP;
+  CK(cudaStreamSynchronize(h->stream));
+  if (feat || scale) {
+    char *tmp = nullptr;
+    CK(cudaMalloc((void **)&tmp, n * (MLP_IN * sizeof(float) + sizeof(double))));
+    double *sc = (double *)tmp;
+    float *f = (float *)(tmp + n * sizeof(double));
+    k_line_features_all<256><<<(int)((n + 255) / 256), 256, 0, h->stream>>>(h->dev, f, sc);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && feat) e = cudaMemcpy(feat, f, n * MLP_IN * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && scale) e = cudaMemcpy(scale, sc, n * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(tmp);
+    CK(e);
+  }
+  if (iterate) {
+    std::vector<double> col(n);
+    for (int q = 0; q < 6; ++q) {
+      CK(cudaMemcpy(col.data(), h->dev.B + (size_t)(FB_V0 + q) * n, n * sizeof(double), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < n; ++i) iterate[i * 6 + q] = col[i];
+    }
+  }
   return UCAC_OK;
 }
 

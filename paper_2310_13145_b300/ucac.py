@@ -28,7 +28,7 @@ EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_inst
            "ucac_enqueue_sweeps", "ucac_residuals", "ucac_solution", "ucac_state_size", "ucac_state_export",
            "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp", "ucac_ucdp_noalloc",
            "ucac_probe_fp64", "ucac_autotune", "ucac_mlp_param_count", "ucac_mlp_workspace_bytes", "ucac_mlp_forward",
-           "ucac_mlp_grad", "ucac_mlp_adam", "ucac_line_features", "ucac_set_warm_start", "ucac_warm_start_stats",
+           "ucac_mlp_grad", "ucac_mlp_adam", "ucac_line_features", "ucac_line_samples", "ucac_set_warm_start", "ucac_warm_start_stats",
            "ucac_destroy", "ucac_last_error"]
 
 
@@ -57,7 +57,8 @@ class ucac_params(C.Structure):
 class ucac_report(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("r_p", "r_d", "z_norm", "z_rms", "inf_norm_viol", "objective", "beta")] + \
         [(n, C.c_int64) for n in ("sweeps", "outer", "newton", "al")] + \
-        [("status", C.c_int32), ("n_newton_maxit", C.c_int32)]
+        [("status", C.c_int32), ("n_newton_maxit", C.c_int32)] + \
+        [(n, C.c_int64) for n in ("newton_total", "al_total")]
 
 
 class UcacError(RuntimeError):
@@ -105,6 +106,7 @@ def lib():
         L.ucac_mlp_grad.argtypes = [C.c_int64, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
         L.ucac_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_float, vp]
         L.ucac_line_features.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), _dp]
+        L.ucac_line_samples.argtypes = [vp, C.POINTER(C.c_float), _dp, _dp]
         L.ucac_set_warm_start.argtypes = [vp, C.POINTER(C.c_float)]
         L.ucac_warm_start_stats.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), _ip]
         L.ucac_destroy.argtypes = [vp]
@@ -293,6 +295,18 @@ def ucac_line_features(h, instance: int, n_rows: int):
     return f, sc
 
 
+def ucac_line_samples(h, n_rows: int, features=True, iterate=True):
+    """(features [n][12] float32 or None, norms [n] or None, W iterates [n][6] or None)
+    of all line-periods of the handle (n_rows = sum of horizon * n_branch)."""
+    f = np.zeros((n_rows, 12), np.float32) if features else None
+    sc = np.zeros(n_rows) if features else None
+    x = np.zeros((n_rows, 6)) if iterate else None
+    _check(lib().ucac_line_samples(h, f.ctypes.data_as(C.POINTER(C.c_float)) if features else None,
+                                   sc.ctypes.data_as(_dp) if features else None,
+                                   x.ctypes.data_as(_dp) if iterate else None), h)
+    return f, sc, x
+
+
 def ucac_set_warm_start(h, params) -> None:
     if params is None:
         _check(lib().ucac_set_warm_start(h, None), h)
@@ -363,6 +377,13 @@ class Handle:
     def line_features(self, k=0):
         T = self.horizons[k] if self.horizons is not None else self.grids[k].T
         return ucac_line_features(self.h, k, T * self.grids[k].n_branch)
+
+    def line_rows(self):
+        return sum((self.horizons[k] if self.horizons is not None else g.T) * g.n_branch
+                   for k, g in enumerate(self.grids))
+
+    def line_samples(self, features=True, iterate=True):
+        return ucac_line_samples(self.h, self.line_rows(), features, iterate)
 
     def set_warm_start(self, params):
         ucac_set_warm_start(self.h, params)

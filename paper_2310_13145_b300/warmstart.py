@@ -15,44 +15,41 @@ import torch
 
 from . import ucac
 
-# canonical state layout of ucac_state_export: generator fields and rows
-# (17 + 3 x 12 arrays of [T][n_gen]) come first, then the branch fields
-# v0..v7 (the W-form iterate), mu0..mu3, cpen, fb0..fb3, each [T][n_branch]
-_GEN_ARRAYS = 17 + 3 * 12
-
-
-def iterate_w(buf, T, n_gen, n_branch):
-    """The W-form line iterate [T*n_branch][6] from an exported state vector."""
-    o = _GEN_ARRAYS * T * n_gen
-    n = T * n_branch
-    return np.stack([buf[o + k * n:o + (k + 1) * n] for k in range(6)], 1)
-
 
 def collect(handle: ucac.Handle, n_sweeps: int, stride: int = 1, min_scale: float = 1e-12):
     """Runs n_sweeps sweeps on the handle and returns (X [N][12], Y [N][6])
-    float32 from every `stride`-th sweep's line solves (rows with a residual
-    norm below min_scale are skipped: the solve does not move there)."""
+    float32 from every `stride`-th sweep's line solves of all its instances
+    (rows with a residual norm below min_scale are skipped: the solve does
+    not move there)."""
     xs, ys = [], []
-    K = ucac.ucac_instances(handle.h)
     for s in range(n_sweeps):
-        take = (s % stride) == 0
-        if take:
-            pre = []
-            for k in range(K):
-                g = handle.grids[k]
-                T = handle.horizons[k] if handle.horizons is not None else g.T
-                f, sc = handle.line_features(k)
-                pre.append((f, sc, iterate_w(handle.export(k), T, g.n_gen, g.n_branch), T))
+        if s % stride:
+            handle.enqueue(1)
+            continue
+        f, sc, x0 = handle.line_samples()
         handle.enqueue(1)
-        if take:
-            for k in range(K):
-                g = handle.grids[k]
-                f, sc, x0, T = pre[k]
-                x1 = iterate_w(handle.export(k), T, g.n_gen, g.n_branch)
-                keep = sc > min_scale
-                xs.append(f[keep])
-                ys.append(((x1[keep] - x0[keep]) / sc[keep, None]).astype(np.float32))
+        _, _, x1 = handle.line_samples(features=False)
+        keep = sc > min_scale
+        xs.append(f[keep])
+        ys.append(((x1[keep] - x0[keep]) / sc[keep, None]).astype(np.float32))
     return np.concatenate(xs), np.concatenate(ys)
+
+
+def train_default(n_instances: int = 100, sweeps: int = 300, stride: int = 2, epochs: int = 6, batch: int = 4096,
+                  lr: float = 2e-3, seed: int = 0):
+    """The default network: trained on line solves logged from runs of
+    9-bus grids (T = 6, seeds 100, 101, ...; all instances batched in one
+    handle).  Returns (params, info)."""
+    from . import synth
+    grids = [synth.make_grid(9, 9, 3, 6, seed=100 + i, load_seed=100 + i, name="c1_9bus_T6_train%d" % i)
+             for i in range(n_instances)]
+    h = ucac.Handle(grids)
+    X, Y = collect(h, sweeps, stride)
+    h.close()
+    tr = Trainer(init_params(seed), batch=batch, lr=lr)
+    hist = tr.fit(X, Y, epochs=epochs, seed=seed)
+    return tr.params(), {"samples": int(X.shape[0]), "epochs": epochs, "loss_first": hist[0], "loss_last": hist[-1],
+                         "train_grids": "%d x 9-bus T=6 (seeds 100..%d)" % (n_instances, 99 + n_instances)}
 
 
 def init_params(seed: int = 0) -> np.ndarray:
