@@ -38,19 +38,26 @@ METRIC = "ADMM sweeps/s (one sweep = all instances of the workload)"
 UNIT = "sweeps/s"
 
 # Algorithmic FP64 operation counts of the line kernel, counted from its
-# source (divisions, square roots, sincos/atan2 count as one operation each).
-# Polar form (default): objective+gradient+Hessian at the current point 315
-# (four flows with first and second derivatives 272, voltage/angle rows 20,
-# line limits 20, products 3), one Newton iteration 258 (projected-gradient
-# and active-set scan 42, masked 3x3 Cholesky and solves 49, Newton decrement
-# 30, trial step 15, model decrease 27, objective at the trial point 90, ratio
-# test 5); one multiplier round 100 (objective at the point, two inequality
-# multiplier updates).
+# source (a multiply-add counts 2; divisions, square roots, sin and cos count
+# one each; FP32 work -- the Hessian and the 3x3 Newton system of lanes
+# without a slack held at zero -- is not counted: the FP64 pipe is the
+# bound and FP32 runs at 64x its rate).
+# Polar form (default), per counted Newton iteration 425: evaluation at the
+# point 242 (sincos 2, four flows with their x-gradients 112, voltage/angle
+# rows 27, two line-limit rows with slack, multiplier estimate and gradient
+# 76, x-gradient 24, product 1), the iteration 100 (bound distances 10,
+# reduced gradient and stationarity 22, exact slack steps 4, slack steps of
+# the Newton direction 14, model decrease 31, step and rules 19), and a trial
+# point on half the iterations (measured: the rest take the final-step or
+# the small-step rule) 0.5 x 166 (step and projection 16, model 31, predicted
+# h 16, objective at the trial point 101, ratio 2); per multiplier round 200
+# (the stationarity check that ends half of the solves without a counted
+# step, 0.5 x 274; first-order finish, multiplier step and outputs 63).
 # W-form: one damped-Newton iteration 1229 (projected-gradient and active-set
 # scan 64, masked Cholesky build 64 + factor 168 + 2 triangular solves 112,
 # Newton-decrement and model terms 288, trial step 24, objective at the trial
 # point 85, gradient and Hessian at the accepted point 280); one AL round 60.
-FLOPS = {"polar": (315 + 258, 100), "w": (1229, 60)}
+FLOPS = {"polar": (425, 200), "w": (1229, 60)}
 FP64_NOMINAL_TFLOPS = 1.25
 
 
