@@ -88,14 +88,18 @@ typedef struct ucac_rho {
  * UCAC_LINE_POLAR (default: (V_i, V_j, theta_i - theta_j), where the product
  * and angle equations hold identically) or UCAC_LINE_W (the W-form variables
  * with an augmented Lagrangian on all four equalities).  Both solve the same
- * subproblem.
+ * subproblem.  uc_relax: 0 (default) solves the UC subproblem by Algorithm 2;
+ * 1 replaces it by its box relaxation (u_on, u_su, u_sd in [0, 1] each, the
+ * start-up/shut-down equation and the minimum up/down times dropped:
+ * u = clamp(tau - c/rho_uc, 0, 1) per row), the first phase of the UC warm
+ * start (ucac_uc_warm_start).
  */
 #define UCAC_LINE_W 0
 #define UCAC_LINE_POLAR 1
 typedef struct ucac_params {
   double eps_in, eps_out, tau, theta, beta0, lambda_max;
   double eta, omega_rel, c_init_rel, c_max_rel;
-  int32_t K_AL, K_N, L_max, check_every, line_form, reserved;
+  int32_t K_AL, K_N, L_max, check_every, line_form, uc_relax;
 } ucac_params;
 
 /*
@@ -261,6 +265,20 @@ int ucac_ucdp_noalloc(int32_t n_gen, int32_t T, double rho_uc, const double *tau
                       const double *tau_sd, const double *c0, const double *c_su, const double *c_sd,
                       const int32_t *TU, const int32_t *TD, const int32_t *u0, const int32_t *K0, int8_t *u_on,
                       double *cost, void *cuda_stream);
+
+/*
+ * UC warm start (Sec. IV-A: the UC variables start from a solve of the
+ * multiperiod ACOPF, set to 0 or 1 by the generation levels).  Call right
+ * after create: runs relax_sweeps sweeps with the UC subproblem relaxed to
+ * the box (params.uc_relax = 1), marks unit g committed at period t when its
+ * dispatch p_{t,g} >= p_frac * Pmin_g, repairs the minimum up/down times with
+ * Algorithm 2 (zero costs, targets the marks and their start-up/shut-down
+ * indicators: the feasible schedule nearest to the marks), and restarts every
+ * instance from the cold start with that schedule as its UC variables (u and
+ * its x-bar copy; y = z = lambda = 0, beta = beta0).  Sweep counters restart
+ * at 0.  Synchronises.  Errors: UCAC_E_ARG, UCAC_E_CUDA.
+ */
+int ucac_uc_warm_start(ucac_handle *h, int32_t relax_sweeps, double p_frac);
 
 /*
  * Learned warm start of the line subproblems (no counterpart in the paper,

@@ -52,7 +52,7 @@ class OrcGrid(C.Structure):
 class OrcParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("rho_pq", "rho_va", "rho_uc", "eps_in", "eps_out", "tau", "theta",
                                           "beta0", "lam_max", "eta", "omega_rel", "c_init_rel", "c_max_rel")] + \
-        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "pad")]
+        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "uc_relax")]
 
 
 def lib():

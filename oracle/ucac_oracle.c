@@ -50,7 +50,7 @@ typedef struct orc_params {
   double rho_pq, rho_va, rho_uc;
   double eps_in, eps_out, tau, theta, beta0, lam_max;
   double eta, omega_rel, c_init_rel, c_max_rel;
-  int32_t K_AL, K_N, L_max, pad;
+  int32_t K_AL, K_N, L_max, uc_relax; /* uc_relax: box relaxation of the UC step */
 } orc_params;
 
 /* ------------------------------------------------------- UC DP (Alg. 2) -- */
@@ -865,7 +865,7 @@ EXPORT void orc_default_params(orc_params *p) {
   p->eps_in = 1e-4; p->eps_out = 1e-4; p->tau = 6.0; p->theta = 0.8;
   p->beta0 = 1e3; p->lam_max = 1e12;
   p->eta = 1e-12; p->omega_rel = 1e-12; p->c_init_rel = 1e4; p->c_max_rel = 1e6;
-  p->K_AL = 50; p->K_N = 50; p->L_max = 1000; p->pad = 0;
+  p->K_AL = 50; p->K_N = 50; p->L_max = 1000; p->uc_relax = 0;
 }
 
 EXPORT long orc_state_size(const void *h) {
@@ -1195,6 +1195,20 @@ EXPORT void orc_sweep(void *h) {
         ton[t] = tgt_of(I->GB[GIX(I, GR_ON, t, g)], I->GZ[GIX(I, GR_ON, t, g)], I->GY[GIX(I, GR_ON, t, g)], P->rho_uc);
         tsu[t] = tgt_of(I->GB[GIX(I, GR_SU, t, g)], I->GZ[GIX(I, GR_SU, t, g)], I->GY[GIX(I, GR_SU, t, g)], P->rho_uc);
         tsd[t] = tgt_of(I->GB[GIX(I, GR_SD, t, g)], I->GZ[GIX(I, GR_SD, t, g)], I->GY[GIX(I, GR_SD, t, g)], P->rho_uc);
+      }
+      if (P->uc_relax) {
+        /* box relaxation of Eq. set:UC (integrality, the start-up/shut-down
+           equation and the minimum times dropped): each row minimises
+           c u + rho/2 (u - tau)^2 over [0, 1] */
+        for (int t = 0; t < T; ++t) {
+          const double on = clampd(ton[t] - I->c0[g] / P->rho_uc, 0.0, 1.0);
+          const double su = clampd(tsu[t] - I->csu[g] / P->rho_uc, 0.0, 1.0);
+          const double sd = clampd(tsd[t] - I->csd[g] / P->rho_uc, 0.0, 1.0);
+          I->G[GIX(I, F_UON, t, g)] = on;
+          I->G[GIX(I, F_USU, t, g)] = su;
+          I->G[GIX(I, F_USD, t, g)] = sd;
+        }
+        continue;
       }
       orc_uc_stagecost(T, I->c0[g], I->csu[g], I->csd[g], P->rho_uc, ton, tsu, tsd, L);
       int K0 = I->u0[g] ? I->L0[g] : I->F0[g];

@@ -58,7 +58,7 @@ struct Inst {
 
 struct Params {
   double eps_in, eps_out, tau, theta, beta0, lam_max, eta, omega_rel, c_init_rel, c_max_rel;
-  int K_AL, K_N, L_max, line_form;
+  int K_AL, K_N, L_max, line_form, uc_relax;
 };
 
 constexpr int GRAN = 32;  // items per granule (one warp)

@@ -116,6 +116,22 @@ __global__ void __launch_bounds__(BS) k_ucdp(Dev S) {
   double *L = S.dpL + 4LL * I.gpo + g;
   double *C = S.dpC + 2LL * (I.gpo + I.go) + g;
   unsigned char *D = S.dpD + 2LL * I.gpo + g;
+  if (S.prm.uc_relax) {
+    // box relaxation of Eq. set:UC (first phase of the UC warm start): each
+    // row minimises c u + rho/2 (u - tau)^2 over [0, 1]
+    const double c[3] = {S.c0[gg], S.csu[gg], S.csd[gg]};
+    const int fl[3] = {F_UON, F_USU, F_USD}, rw[3] = {GR_ON, GR_SU, GR_SD};
+    for (int t = 0; t < T; ++t) {
+      const long long i = base + (long long)t * ng;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const double u = clampd(__dsub_rn(S.GT[rw[q] * NGP + i], __ddiv_rn(c[q], I.ruc)), 0.0, 1.0);
+        S.G[fl[q] * NGP + i] = u;
+        S.GA[rw[q] * NGP + i] = u;
+      }
+    }
+    return;
+  }
   double *uon_a = S.G + (long long)F_UON * NGP + base;
   uc_dp(T, TU, TD, u0, K0, S.c0[gg], S.csu[gg], S.csd[gg], hr, S.GT + GR_ON * NGP + base,
         S.GT + GR_SU * NGP + base, S.GT + GR_SD * NGP + base, (long long)ng, L, C, D,
@@ -130,6 +146,48 @@ __global__ void __launch_bounds__(BS) k_ucdp(Dev S) {
     S.GA[GR_ON * NGP + i] = (double)u;
     S.GA[GR_SU * NGP + i] = su;
     S.GA[GR_SD * NGP + i] = sd;
+    prev = u;
+  }
+}
+
+// Second phase of the UC warm start, one thread per generator: marks
+// m_t = [p_{t,g} >= p_frac Pmin_g], then Algorithm 2 with zero costs on the
+// targets (m_t, m_t > m_{t-1}, m_{t-1} > m_t) -- the feasible schedule
+// nearest to the marks -- into u_on / u_su / u_sd.  The duplicate-row
+// targets are used as scratch (the state is re-imported afterwards).
+template <int BS>
+__global__ void __launch_bounds__(BS) k_uc_round(Dev S, double p_frac) {
+  const int gr = warp_granule<BS>(S.g_gen.n);
+  if (gr < 0) return;
+  const int k = S.g_gen.inst[gr];
+  const Inst I = S.inst[k];
+  const int gg = S.g_gen.first[gr] + (threadIdx.x & 31);
+  if (gg >= I.go + I.ng) return;
+  const int g = gg - I.go, ng = I.ng, T = I.T;
+  const long long NGP = S.NGP, base = (long long)I.gpo + g;
+  const int TU = max(S.TU[gg], 1), TD = max(S.TD[gg], 1), u0 = S.u0[gg];
+  const int K0 = min(max(S.K0[gg], 0), T);
+  int prev = u0;
+  for (int t = 0; t < T; ++t) {
+    const long long i = base + (long long)t * ng;
+    const int m = S.G[F_P * NGP + i] >= p_frac * S.Pmin[gg] ? 1 : 0;
+    S.GT[GR_ON * NGP + i] = (double)m;
+    S.GT[GR_SU * NGP + i] = (m > prev) ? 1.0 : 0.0;
+    S.GT[GR_SD * NGP + i] = (prev > m) ? 1.0 : 0.0;
+    prev = m;
+  }
+  double *L = S.dpL + 4LL * I.gpo + g;
+  double *C = S.dpC + 2LL * (I.gpo + I.go) + g;
+  unsigned char *D = S.dpD + 2LL * I.gpo + g;
+  double *uon_a = S.G + (long long)F_UON * NGP + base;
+  uc_dp(T, TU, TD, u0, K0, 0.0, 0.0, 0.0, 0.5, S.GT + GR_ON * NGP + base, S.GT + GR_SU * NGP + base,
+        S.GT + GR_SD * NGP + base, (long long)ng, L, C, D, [&](int t, int u) { uon_a[(long long)t * ng] = (double)u; });
+  prev = u0;
+  for (int t = 0; t < T; ++t) {
+    const long long i = base + (long long)t * ng;
+    const int u = (int)S.G[F_UON * NGP + i];
+    S.G[F_USU * NGP + i] = (u > prev) ? 1.0 : 0.0;
+    S.G[F_USD * NGP + i] = (prev > u) ? 1.0 : 0.0;
     prev = u;
   }
 }

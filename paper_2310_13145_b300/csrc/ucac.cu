@@ -284,7 +284,7 @@ void ucac_default_params(ucac_params *p) {
   p->L_max = 1000;
   p->check_every = 50;
   p->line_form = UCAC_LINE_POLAR;
-  p->reserved = 0;
+  p->uc_relax = 0;
 }
 
 int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, const ucac_rho *rhos, int32_t n,
@@ -302,7 +302,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   ucac_default_params(&P);
   if (params) P = *params;
   if (P.K_AL < 1 || P.K_N < 1 || P.L_max < 1 || P.check_every < 1 || !(P.beta0 > 0) ||
-      (P.line_form != UCAC_LINE_W && P.line_form != UCAC_LINE_POLAR))
+      (P.line_form != UCAC_LINE_W && P.line_form != UCAC_LINE_POLAR) || (P.uc_relax != 0 && P.uc_relax != 1))
     return fail(nullptr, UCAC_E_ARG, "bad parameters");
 
   h = new ucac_handle();
@@ -310,7 +310,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   h->stream = (cudaStream_t)cuda_stream;
   h->check_every = P.check_every;
   h->prm = Params{P.eps_in, P.eps_out, P.tau, P.theta, P.beta0, P.lambda_max, P.eta, P.omega_rel, P.c_init_rel,
-                  P.c_max_rel, P.K_AL, P.K_N, P.L_max, P.line_form};
+                  P.c_max_rel, P.K_AL, P.K_N, P.L_max, P.line_form, P.uc_relax};
   // ---- sizes and offsets
   long long go = 0, gpo = 0, lo = 0, bpo = 0, uo = 0, upo = 0;
   for (int k = 0; k < n; ++k) {
@@ -1012,6 +1012,50 @@ int ucac_autotune(ucac_handle *h, int32_t sweeps_per_trial, const char *cache_pa
     o << key << " " << best.ucdp << " " << best.gen << " " << best.line << " " << best.bus << " " << best.ucbar << "\n";
   }
   return apply(best);
+}
+
+// ------------------------------------------------------- UC warm start
+int ucac_uc_warm_start(ucac_handle *h, int32_t relax_sweeps, double p_frac) {
+  if (!h || relax_sweeps < 0 || !(p_frac >= 0.0)) return fail(h, UCAC_E_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(h->stream));
+  // the cold start of every instance (the state right after create)
+  std::vector<std::vector<double>> cold(h->K);
+  for (int k = 0; k < h->K; ++k) {
+    cold[k].resize(ucac_state_size(h, k));
+    const int rc = ucac_state_export(h, k, cold[k].data(), cold[k].size());
+    if (rc != UCAC_OK) return rc;
+  }
+  // phase 1: relaxed sweeps
+  h->prm.uc_relax = 1;
+  h->dev.prm.uc_relax = 1;
+  CK(capture_graph(h));
+  for (int s = 0; s < relax_sweeps; ++s) CK(cudaGraphLaunch(h->exec, h->stream));
+  // phase 2: marks from the generation levels, repaired by Algorithm 2
+  k_uc_round<128><<<blocks_for(h->ngr_gen, 128), 128, 0, h->stream>>>(h->dev, p_frac);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  h->prm.uc_relax = 0;
+  h->dev.prm.uc_relax = 0;
+  CK(capture_graph(h));
+  // phase 3: every instance restarts from its cold start with the schedule
+  for (int k = 0; k < h->K; ++k) {
+    const HInst &I = h->hi[k];
+    const size_t ngp = (size_t)I.T * I.ng;
+    std::vector<double> u(3 * ngp);
+    for (int q = 0; q < 3; ++q)
+      CK(cudaMemcpy(u.data() + q * ngp, h->dev.G + (size_t)(F_UON + q) * h->NGP + I.gpo, ngp * 8,
+                    cudaMemcpyDeviceToHost));
+    // canonical order: generator fields first, F_UON..F_USD and their
+    // x-bar copies F_UBON..F_UBSD
+    for (int q = 0; q < 3; ++q) {
+      std::copy(u.begin() + q * ngp, u.begin() + (q + 1) * ngp, cold[k].begin() + (size_t)(F_UON + q) * ngp);
+      std::copy(u.begin() + q * ngp, u.begin() + (q + 1) * ngp, cold[k].begin() + (size_t)(F_UBON + q) * ngp);
+    }
+    const int rc = ucac_state_import(h, k, cold[k].data(), cold[k].size());
+    if (rc != UCAC_OK) return rc;
+  }
+  CK(cudaMemset(h->dev.stat, 0, sizeof(long long) * 6 * h->K));
+  return UCAC_OK;
 }
 
 // ------------------------------------------------ learned warm start (MLP)

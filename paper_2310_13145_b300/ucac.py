@@ -27,7 +27,7 @@ UCAC_LINE_W, UCAC_LINE_POLAR = 0, 1
 EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_instances", "ucac_iterate",
            "ucac_enqueue_sweeps", "ucac_residuals", "ucac_solution", "ucac_state_size", "ucac_state_export",
            "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp", "ucac_ucdp_noalloc",
-           "ucac_probe_fp64", "ucac_autotune", "ucac_mlp_param_count", "ucac_mlp_workspace_bytes", "ucac_mlp_forward",
+           "ucac_probe_fp64", "ucac_autotune", "ucac_uc_warm_start", "ucac_mlp_param_count", "ucac_mlp_workspace_bytes", "ucac_mlp_forward",
            "ucac_mlp_grad", "ucac_mlp_adam", "ucac_line_features", "ucac_line_samples", "ucac_set_warm_start", "ucac_warm_start_stats",
            "ucac_destroy", "ucac_last_error"]
 
@@ -51,7 +51,7 @@ class ucac_rho(C.Structure):
 class ucac_params(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("eps_in", "eps_out", "tau", "theta", "beta0", "lambda_max", "eta",
                                           "omega_rel", "c_init_rel", "c_max_rel")] + \
-        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "check_every", "line_form", "reserved")]
+        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "check_every", "line_form", "uc_relax")]
 
 
 class ucac_report(C.Structure):
@@ -98,6 +98,7 @@ def lib():
         L.ucac_ucdp_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_double] + [vp] * 12 + [vp]
         L.ucac_probe_fp64.argtypes = [C.c_int32, vp, _dp]
         L.ucac_autotune.argtypes = [vp, C.c_int32, C.c_char_p, _ip]
+        L.ucac_uc_warm_start.argtypes = [vp, C.c_int32, C.c_double]
         L.ucac_mlp_param_count.argtypes = []
         L.ucac_mlp_param_count.restype = C.c_int32
         L.ucac_mlp_workspace_bytes.argtypes = [C.c_int64]
@@ -263,6 +264,10 @@ def ucac_autotune(h, sweeps_per_trial: int = 3, cache_path: str | None = None) -
     return dict(zip(("ucdp", "gen", "line", "bus", "ucbar"), (int(v) for v in out)))
 
 
+def ucac_uc_warm_start(h, relax_sweeps: int = 300, p_frac: float = 0.5) -> None:
+    _check(lib().ucac_uc_warm_start(h, int(relax_sweeps), float(p_frac)), h)
+
+
 def ucac_mlp_param_count() -> int:
     return int(lib().ucac_mlp_param_count())
 
@@ -377,6 +382,9 @@ class Handle:
     def line_features(self, k=0):
         T = self.horizons[k] if self.horizons is not None else self.grids[k].T
         return ucac_line_features(self.h, k, T * self.grids[k].n_branch)
+
+    def uc_warm_start(self, relax_sweeps=300, p_frac=0.5):
+        ucac_uc_warm_start(self.h, relax_sweeps, p_frac)
 
     def line_rows(self):
         return sum((self.horizons[k] if self.horizons is not None else g.T) * g.n_branch

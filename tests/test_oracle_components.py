@@ -283,3 +283,29 @@ def test_line_kkt_second_order_and_polar_grid(seed):
                         continue
                     best = min(best, consensus((Vi2, Vj2, th_i + a3, th_j + a4), gs, bs, tgt, rpq, rva))
     assert best >= f_or - 1e-9 * max(1.0, f_or)
+
+
+def test_relaxed_uc_step_is_the_box_minimiser():
+    """The oracle's relaxed UC step (first phase of the UC warm start) puts
+    each duplicate row at the minimiser of c u + rho/2 (u - tau)^2 on [0, 1],
+    checked against a dense grid."""
+    from paper_2310_13145_b300 import synth
+    g = synth.config_instances("c1_9bus_T6")[0]
+    o = oracle.Oracle(g)
+    o.sweep(15)
+    st = oracle.unpack_state(o.state_vector(), g.T, g.n_gen, g.n_branch, g.n_bus)
+    rel = oracle.Oracle(g, oracle.default_params(rho=g.rho, uc_relax=1))
+    rel.set_state(st)
+    rel.sweep()
+    out = oracle.unpack_state(rel.state_vector(), g.T, g.n_gen, g.n_branch, g.n_bus)
+    rho = g.rho[2]
+    grid = np.linspace(0.0, 1.0, 20001)
+    for row, cost in (("on", g.c0), ("su", g.c_su), ("sd", g.c_sd)):
+        tau = (st["ub_" + row] - st["gz_" + row]) - st["gy_" + row] / rho
+        u = out["u_" + row]
+        for t in range(g.T):
+            for k in range(g.n_gen):
+                f = cost[k] * grid + 0.5 * rho * (grid - tau[t, k]) ** 2
+                best = grid[np.argmin(f)]
+                assert abs(u[t, k] - best) <= 1e-4 + 1e-12, (row, t, k, u[t, k], best)
+                assert 0.0 <= u[t, k] <= 1.0
