@@ -354,14 +354,17 @@ def main():
         ttc = time_to_tolerance(ucac, grids, stream, params, a.ttc_max_sweeps, cache)
     ucw = None
     if not a.no_ttc and not a.no_uc_warm:
-        # the UC warm start (Sec. IV-A) against the all-on start, on the
-        # 3 x 118-bus batch (on the 2000-bus scenarios it does not converge
-        # within the sweep cap, see the design notes)
+        # start and penalty variants on the 3 x 118-bus batch: the UC warm
+        # start (Sec. IV-A) against the all-on start, and the adaptive
+        # penalty (on the 2000-bus scenarios the UC warm start does not
+        # converge within the sweep cap)
         g2 = synth.config_instances("c2_118bus_T24x3")
+        pa = ucac.ucac_default_params(line_form=params.line_form, rho_every=10)
         ucw = {"workload": "c2_118bus_T24x3",
                "all_on_start": time_to_tolerance(ucac, g2, stream, params, a.ttc_max_sweeps),
                "uc_warm_start": time_to_tolerance(ucac, g2, stream, params, a.ttc_max_sweeps,
-                                                  uc_warm=a.uc_warm_sweeps)}
+                                                  uc_warm=a.uc_warm_sweeps),
+               "adaptive_penalty_every10": time_to_tolerance(ucac, g2, stream, pa, a.ttc_max_sweeps)}
     learned = None
     if not a.no_learned:
         learned = learned_arm(ucac, h, grids, stream, params, a, cache)
@@ -380,7 +383,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "state larger than L2 (no flush needed)", "r_p_inst0": r["r_p"]},
                 "gpu_launches": 6 * a.steps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "time_to_1e-4": ttc, "uc_warm_start": ucw, "learned": learned,
+                "time_to_1e-4": ttc, "variants_118bus": ucw, "learned": learned,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -92,14 +92,20 @@ typedef struct ucac_rho {
  * 1 replaces it by its box relaxation (u_on, u_su, u_sd in [0, 1] each, the
  * start-up/shut-down equation and the minimum up/down times dropped:
  * u = clamp(tau - c/rho_uc, 0, 1) per row), the first phase of the UC warm
- * start (ucac_uc_warm_start).
+ * start (ucac_uc_warm_start).  rho_every: 0 (default) keeps the penalties of
+ * create; k > 0 adapts them every k sweeps by residual balancing (the
+ * adaptive rules Sec. V names as future work): all three penalties are
+ * multiplied by rho_tau (2) when r_p > rho_mu r_d (rho_mu = 10) and divided
+ * by it when r_d > rho_mu r_p, at most 6 net steps either way from the
+ * penalties of create; the current penalties are part of the state.
  */
 #define UCAC_LINE_W 0
 #define UCAC_LINE_POLAR 1
 typedef struct ucac_params {
   double eps_in, eps_out, tau, theta, beta0, lambda_max;
   double eta, omega_rel, c_init_rel, c_max_rel;
-  int32_t K_AL, K_N, L_max, check_every, line_form, uc_relax;
+  double rho_mu, rho_tau;
+  int32_t K_AL, K_N, L_max, check_every, line_form, uc_relax, rho_every, reserved;
 } ucac_params;
 
 /*

@@ -51,8 +51,9 @@ class OrcGrid(C.Structure):
 
 class OrcParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("rho_pq", "rho_va", "rho_uc", "eps_in", "eps_out", "tau", "theta",
-                                          "beta0", "lam_max", "eta", "omega_rel", "c_init_rel", "c_max_rel")] + \
-        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "uc_relax")]
+                                          "beta0", "lam_max", "eta", "omega_rel", "c_init_rel", "c_max_rel",
+                                          "rho_mu", "rho_tau")] + \
+        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "uc_relax", "rho_every", "pad")]
 
 
 def lib():
@@ -110,7 +111,8 @@ GEN_ROWS = ["on", "su", "sd", "pl", "pu", "ql", "qu", "rd", "ru", "gp", "gq", "t
 BR_FIELDS = ["v%d" % k for k in range(8)] + ["mu%d" % k for k in range(4)] + ["cpen"] + ["fb%d" % k for k in range(4)]
 BR_ROWS = ["pij", "qij", "pji", "qji", "wi", "wj", "thi", "thj"]
 BUS_FIELDS = ["wbar", "thbar"]
-CTRL = ["beta", "zprev", "l_inner", "k_outer", "pending", "beta_next", "done"]
+CTRL = ["beta", "zprev", "l_inner", "k_outer", "pending", "beta_next", "done", "rho_pq", "rho_va", "rho_uc",
+        "rho_cnt", "rho_log"]
 
 
 def state_layout(T, ng, nl, nb):

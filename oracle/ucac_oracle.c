@@ -50,7 +50,9 @@ typedef struct orc_params {
   double rho_pq, rho_va, rho_uc;
   double eps_in, eps_out, tau, theta, beta0, lam_max;
   double eta, omega_rel, c_init_rel, c_max_rel;
+  double rho_mu, rho_tau;             /* adaptive penalty: balance ratio and factor */
   int32_t K_AL, K_N, L_max, uc_relax; /* uc_relax: box relaxation of the UC step */
+  int32_t rho_every, pad;             /* adaptive penalty: check period (0: off) */
 } orc_params;
 
 /* ------------------------------------------------------- UC DP (Alg. 2) -- */
@@ -812,12 +814,12 @@ EXPORT void orc_boxqp(int n, const double *Hf, const double *gv, double *x) {
  */
 enum { GR_ON, GR_SU, GR_SD, GR_PL, GR_PU, GR_QL, GR_QU, GR_RD, GR_RU, GR_GP, GR_GQ, GR_TC, NGR };
 enum { NBR = 8 };
-enum { NG_FIELDS = 17, NB_FIELDS = 17, NU_FIELDS = 2, NCTRL = 7 };
+enum { NG_FIELDS = 17, NB_FIELDS = 17, NU_FIELDS = 2, NCTRL = 12 };
 enum { F_P, F_Q, F_PH, F_SPL, F_SPU, F_SQL, F_SQU, F_SRD, F_SRU, F_UON, F_USU, F_USD, F_PBAR, F_QBAR,
        F_UBON, F_UBSU, F_UBSD };
 enum { FB_V0 = 0, FB_MU0 = 8, FB_C = 12, FB_FB0 = 13 };
 enum { FU_W, FU_TH };
-enum { C_BETA, C_ZPREV, C_LIN, C_KOUT, C_PEND, C_BNEXT, C_DONE };
+enum { C_BETA, C_ZPREV, C_LIN, C_KOUT, C_PEND, C_BNEXT, C_DONE, C_RPQ, C_RVA, C_RUC, C_RCNT, C_RLOG };
 
 typedef struct {
   int nb, nl, ng, T, ref;
@@ -866,6 +868,7 @@ EXPORT void orc_default_params(orc_params *p) {
   p->beta0 = 1e3; p->lam_max = 1e12;
   p->eta = 1e-12; p->omega_rel = 1e-12; p->c_init_rel = 1e4; p->c_max_rel = 1e6;
   p->K_AL = 50; p->K_N = 50; p->L_max = 1000; p->uc_relax = 0;
+  p->rho_every = 0; p->pad = 0; p->rho_mu = 10.0; p->rho_tau = 2.0;
 }
 
 EXPORT long orc_state_size(const void *h) {
@@ -1114,6 +1117,9 @@ EXPORT void *orc_create(const orc_grid *g, const orc_params *prm) {
   I->ctrl[C_BETA] = I->P.beta0;
   I->ctrl[C_ZPREV] = -1.0;
   I->ctrl[C_BNEXT] = I->P.beta0;
+  I->ctrl[C_RPQ] = I->P.rho_pq;
+  I->ctrl[C_RVA] = I->P.rho_va;
+  I->ctrl[C_RUC] = I->P.rho_uc;
   return I;
 }
 
@@ -1158,6 +1164,10 @@ EXPORT void orc_state_set(void *h, const double *buf) {
   memcpy(I->BL, buf + o, NBR * BN * 8); o += NBR * BN;
   memcpy(I->U, buf + o, NU_FIELDS * UN * 8); o += NU_FIELDS * UN;
   memcpy(I->ctrl, buf + o, NCTRL * 8);
+  /* the current penalties travel with the state (adaptive penalty) */
+  I->P.rho_pq = I->ctrl[C_RPQ];
+  I->P.rho_va = I->ctrl[C_RVA];
+  I->P.rho_uc = I->ctrl[C_RUC];
 }
 
 /* Kahan-compensated accumulator */
@@ -1441,6 +1451,28 @@ EXPORT void orc_sweep(void *h) {
       I->ctrl[C_ZPREV] = zn;
       I->ctrl[C_KOUT] += 1.0;
       I->ctrl[C_LIN] = 0.0;
+    }
+  }
+  /* adaptive penalty by residual balancing (future work named in Sec. V):
+     every rho_every sweeps the three penalties grow by rho_tau when
+     r_p > rho_mu r_d and shrink by it when r_d > rho_mu r_p, at most 6 net
+     steps either way from the initial penalties */
+  if (P->rho_every > 0 && I->ctrl[C_DONE] == 0.0) {
+    I->ctrl[C_RCNT] += 1.0;
+    if (I->ctrl[C_RCNT] >= (double)P->rho_every) {
+      I->ctrl[C_RCNT] = 0.0;
+      double sc = 1.0;
+      if (I->res[0] > P->rho_mu * I->res[1] && I->ctrl[C_RLOG] < 6.0) sc = P->rho_tau;
+      else if (I->res[1] > P->rho_mu * I->res[0] && I->ctrl[C_RLOG] > -6.0) sc = 1.0 / P->rho_tau;
+      if (sc != 1.0) {
+        I->ctrl[C_RLOG] += (sc > 1.0) ? 1.0 : -1.0;
+        I->ctrl[C_RPQ] *= sc;
+        I->ctrl[C_RVA] *= sc;
+        I->ctrl[C_RUC] *= sc;
+        I->P.rho_pq = I->ctrl[C_RPQ];
+        I->P.rho_va = I->ctrl[C_RVA];
+        I->P.rho_uc = I->ctrl[C_RUC];
+      }
     }
   }
 }

@@ -37,9 +37,13 @@ enum { FB_V0 = 0, FB_MU0 = 8, FB_C = 12, FB_FB0 = 13, NBF = 17 };
 // bus-period fields
 enum { FU_W, FU_TH, NUF };
 // per-instance control scalars
-enum { C_BETA, C_ZPREV, C_LIN, C_KOUT, C_PEND, C_BNEXT, C_DONE, NCTRL };
+// (C_RPQ..C_RUC: the current penalties, C_RCNT: sweeps since the last
+// adaptive-penalty check, C_RLOG: net doublings so far, kept in [-6, 6];
+// part of the canonical state)
+enum { C_BETA, C_ZPREV, C_LIN, C_KOUT, C_PEND, C_BNEXT, C_DONE, C_RPQ, C_RVA, C_RUC, C_RCNT, C_RLOG, NCTRL };
 // residual record
-enum { R_RP, R_RD, R_ZN, R_ZRMS, R_INF, R_OBJ, R_STATUS, NRES };
+// (R_RCHG: the penalties changed at the end of this sweep)
+enum { R_RP, R_RD, R_ZN, R_ZRMS, R_INF, R_OBJ, R_STATUS, R_RCHG, NRES };
 // block partial quantities of the x-bar kernels
 enum { Q_SP, Q_SD, Q_SZ, Q_INF, Q_OBJ, NQ };
 // branch constant table [BC_N][NL]
@@ -58,7 +62,8 @@ struct Inst {
 
 struct Params {
   double eps_in, eps_out, tau, theta, beta0, lam_max, eta, omega_rel, c_init_rel, c_max_rel;
-  int K_AL, K_N, L_max, line_form, uc_relax;
+  double rho_mu, rho_tau;
+  int K_AL, K_N, L_max, line_form, uc_relax, rho_every;
 };
 
 constexpr int GRAN = 32;  // items per granule (one warp)

@@ -497,17 +497,58 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
         c[C_LIN] = 0.0;
       }
     }
+    // adaptive penalty by residual balancing (Sec. V names adaptive rules as
+    // the way past the penalty sensitivity): every rho_every sweeps, all
+    // three penalties grow by rho_tau when r_p > rho_mu r_d and shrink by it
+    // when r_d > rho_mu r_p, at most 6 net steps either way from the
+    // penalties of create (unbounded, the rule can run away: r_d shrinks as
+    // the penalty grows); the sweep's target preparation then rewrites the
+    // x-step targets with the new penalties
+    r[R_RCHG] = 0.0;
+    if (P.rho_every > 0 && c[C_DONE] == 0.0) {
+      c[C_RCNT] += 1.0;
+      if (c[C_RCNT] >= (double)P.rho_every) {
+        c[C_RCNT] = 0.0;
+        const int up = (rp > P.rho_mu * rd && c[C_RLOG] < 6.0) ? 1 : ((rd > P.rho_mu * rp && c[C_RLOG] > -6.0) ? -1 : 0);
+        const double sc = up > 0 ? P.rho_tau : (up < 0 ? 1.0 / P.rho_tau : 1.0);
+        if (up != 0) {
+          c[C_RLOG] += (double)up;
+          c[C_RPQ] *= sc;
+          c[C_RVA] *= sc;
+          c[C_RUC] *= sc;
+          Inst *Iw = const_cast<Inst *>(S.inst) + k;
+          Iw->rpq = c[C_RPQ];
+          Iw->rva = c[C_RVA];
+          Iw->ruc = c[C_RUC];
+          r[R_RCHG] = 1.0;
+        }
+      }
+    }
+  }
+}
+
+// instance penalties from the control record (after a state import)
+__global__ void k_sync_rho(Dev S, int k) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const double *c = S.ctrl + (long long)k * NCTRL;
+    Inst *Iw = const_cast<Inst *>(S.inst) + k;
+    Iw->rpq = c[C_RPQ];
+    Iw->rva = c[C_RVA];
+    Iw->ruc = c[C_RUC];
   }
 }
 
 // ----------------------------------------------------------- targets ------
 // x-step targets of every row from the current x-bar, z and y (after create
-// or import).  One thread per gen-period and per branch-period.
+// or import, and after an adaptive-penalty change: changed_only limits the
+// pass to instances whose penalties changed in this sweep).  One thread per
+// gen-period and per branch-period.
 template <int BS>
-__global__ void __launch_bounds__(BS) k_prep_gen(Dev S) {
+__global__ void __launch_bounds__(BS) k_prep_gen(Dev S, int changed_only) {
   const int gr = warp_granule<BS>(S.g_gp.n);
   if (gr < 0) return;
   const int k = S.g_gp.inst[gr];
+  if (changed_only && S.res[(long long)k * NRES + R_RCHG] == 0.0) return;
   const Inst I = S.inst[k];
   const long long gp = (long long)S.g_gp.first[gr] + (threadIdx.x & 31);
   if (gp >= (long long)I.gpo + (long long)I.T * I.ng) return;
@@ -538,10 +579,11 @@ __global__ void __launch_bounds__(BS) k_prep_gen(Dev S) {
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS) k_prep_branch(Dev S) {
+__global__ void __launch_bounds__(BS) k_prep_branch(Dev S, int changed_only) {
   const int gr = warp_granule<BS>(S.g_bp.n);
   if (gr < 0) return;
   const int k = S.g_bp.inst[gr];
+  if (changed_only && S.res[(long long)k * NRES + R_RCHG] == 0.0) return;
   const Inst I = S.inst[k];
   const long long bp = (long long)S.g_bp.first[gr] + (threadIdx.x & 31);
   if (bp >= (long long)I.bpo + (long long)I.T * I.nl) return;

@@ -222,9 +222,9 @@ void launch_line(ucac_handle *h, cudaStream_t s) {
   }
 }
 
-void launch_prep(ucac_handle *h, cudaStream_t s) {
-  k_prep_gen<BS_PREP><<<blocks_for(h->ngr_gp, BS_PREP), BS_PREP, 0, s>>>(h->dev);
-  k_prep_branch<BS_PREP><<<blocks_for(h->ngr_bp, BS_PREP), BS_PREP, 0, s>>>(h->dev);
+void launch_prep(ucac_handle *h, cudaStream_t s, int changed_only = 0) {
+  k_prep_gen<BS_PREP><<<blocks_for(h->ngr_gp, BS_PREP), BS_PREP, 0, s>>>(h->dev, changed_only);
+  k_prep_branch<BS_PREP><<<blocks_for(h->ngr_bp, BS_PREP), BS_PREP, 0, s>>>(h->dev, changed_only);
 }
 
 // persistent tensor-core MLP over all line-periods (learned warm start)
@@ -245,6 +245,7 @@ void launch_sweep(ucac_handle *h, cudaStream_t s) {
   launch_bus(h, s);
   launch_ucbar(h, s);
   k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(h->dev);
+  if (h->prm.rho_every > 0) launch_prep(h, s, 1);
 }
 
 // (re)captures one sweep into the handle's graph
@@ -285,6 +286,9 @@ void ucac_default_params(ucac_params *p) {
   p->check_every = 50;
   p->line_form = UCAC_LINE_POLAR;
   p->uc_relax = 0;
+  p->rho_every = 0;
+  p->rho_mu = 10.0;
+  p->rho_tau = 2.0;
 }
 
 int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, const ucac_rho *rhos, int32_t n,
@@ -302,7 +306,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   ucac_default_params(&P);
   if (params) P = *params;
   if (P.K_AL < 1 || P.K_N < 1 || P.L_max < 1 || P.check_every < 1 || !(P.beta0 > 0) ||
-      (P.line_form != UCAC_LINE_W && P.line_form != UCAC_LINE_POLAR) || (P.uc_relax != 0 && P.uc_relax != 1))
+      (P.line_form != UCAC_LINE_W && P.line_form != UCAC_LINE_POLAR) || (P.uc_relax != 0 && P.uc_relax != 1) ||
+      P.rho_every < 0 || (P.rho_every > 0 && !(P.rho_mu > 1.0 && P.rho_tau > 1.0)))
     return fail(nullptr, UCAC_E_ARG, "bad parameters");
 
   h = new ucac_handle();
@@ -310,7 +315,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   h->stream = (cudaStream_t)cuda_stream;
   h->check_every = P.check_every;
   h->prm = Params{P.eps_in, P.eps_out, P.tau, P.theta, P.beta0, P.lambda_max, P.eta, P.omega_rel, P.c_init_rel,
-                  P.c_max_rel, P.K_AL, P.K_N, P.L_max, P.line_form, P.uc_relax};
+                  P.c_max_rel, P.rho_mu, P.rho_tau, P.K_AL, P.K_N, P.L_max, P.line_form, P.uc_relax,
+                  P.rho_every};
   // ---- sizes and offsets
   long long go = 0, gpo = 0, lo = 0, bpo = 0, uo = 0, upo = 0;
   for (int k = 0; k < n; ++k) {
@@ -443,6 +449,9 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     ctrl[(size_t)k * NCTRL + C_BETA] = P.beta0;
     ctrl[(size_t)k * NCTRL + C_ZPREV] = -1.0;
     ctrl[(size_t)k * NCTRL + C_BNEXT] = P.beta0;
+    ctrl[(size_t)k * NCTRL + C_RPQ] = rhos[k].pq;
+    ctrl[(size_t)k * NCTRL + C_RVA] = rhos[k].va;
+    ctrl[(size_t)k * NCTRL + C_RUC] = rhos[k].uc;
   }
   for (long long i = 0; i < NB; ++i) {
     inc_ptr[i + 1] += inc_ptr[i];
@@ -887,6 +896,7 @@ int ucac_state_import(ucac_handle *h, int32_t k, const double *buf, size_t n) {
     o += sg.second;
   }
   edge_stage(h, k, 1, false, h->stream);
+  k_sync_rho<<<1, 32, 0, h->stream>>>(h->dev, k);
   launch_prep(h, h->stream);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));

@@ -50,8 +50,9 @@ class ucac_rho(C.Structure):
 
 class ucac_params(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("eps_in", "eps_out", "tau", "theta", "beta0", "lambda_max", "eta",
-                                          "omega_rel", "c_init_rel", "c_max_rel")] + \
-        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "check_every", "line_form", "uc_relax")]
+                                          "omega_rel", "c_init_rel", "c_max_rel", "rho_mu", "rho_tau")] + \
+        [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "check_every", "line_form", "uc_relax", "rho_every",
+                                  "reserved")]
 
 
 class ucac_report(C.Structure):

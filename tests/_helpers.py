@@ -4,7 +4,8 @@ import numpy as np
 import oracle
 
 # UC decisions and counters are compared bit for bit.
-EXACT_FIELDS = {"u_on", "u_su", "u_sd", "l_inner", "k_outer", "pending", "done"}
+EXACT_FIELDS = {"u_on", "u_su", "u_sd", "l_inner", "k_outer", "pending", "done", "rho_pq", "rho_va", "rho_uc",
+                "rho_cnt", "rho_log"}
 # Per-iterate bound of the FP64 path against the oracle: normwise relative
 # 1e-9 per field, plus an absolute floor at the FP64 noise level of the
 # quantity (positions and powers are O(1) p.u.; multipliers y carry a factor

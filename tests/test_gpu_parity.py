@@ -161,3 +161,37 @@ def test_full_size_2000bus_one_instance_lockstep(ucac_mod, line_form):
                          mu_eta=p.eta if polar else None)
     assert not bad, bad[:6]
     h.close()
+
+
+@pytest.mark.parametrize("every", [1, 5])
+def test_lockstep_9bus_adaptive_penalty(ucac_mod, every):
+    """Residual-balancing penalties (every `every` sweeps), in lockstep with
+    the oracle: the decisions, the penalties and the rewritten targets."""
+    g = synth.config_instances("c1_9bus_T6")[0]
+    p = ucac_mod.ucac_default_params(rho_every=every)
+    _lockstep(ucac_mod, [g], 40, params=p, oparams=lambda gg: oracle.default_params(rho=gg.rho, rho_every=every))
+
+
+def test_lockstep_118bus_adaptive_penalty(ucac_mod):
+    grids = synth.config_instances("c2_118bus_T24x3")
+    p = ucac_mod.ucac_default_params(rho_every=10)
+    _lockstep(ucac_mod, grids, 12, params=p, oparams=lambda gg: oracle.default_params(rho=gg.rho, rho_every=10),
+              warm=35)
+
+
+def test_adaptive_penalty_resume_bitwise(ucac_mod):
+    g = synth.config_instances("c1_9bus_T6")[0].copy()
+    g.rho = tuple(100.0 * r for r in g.rho)  # mismatched on purpose: the balancing must act
+    p = ucac_mod.ucac_default_params(rho_every=3)
+    a = ucac_mod.Handle([g], params=p)
+    a.enqueue(31)
+    snap = a.export(0)
+    st = oracle.unpack_state(snap, g.T, g.n_gen, g.n_branch, g.n_bus)
+    assert st["rho_pq"] != g.rho[0]  # the penalties did move
+    a.enqueue(20)
+    b = ucac_mod.Handle([g], params=p)
+    b.import_(0, snap)
+    b.enqueue(20)
+    assert np.array_equal(a.export(0), b.export(0))
+    a.close()
+    b.close()

@@ -179,3 +179,36 @@ def test_uc_step_is_bruteforce_optimal(swept):
         assert f <= best + 1e-12 * abs(best)
         su, sd = bf.derived(u, int(g.u0[gi]))
         assert np.array_equal(post["u_su"][:, gi], su) and np.array_equal(post["u_sd"][:, gi], sd)
+
+
+def test_adaptive_penalty_rule_and_state():
+    """Residual balancing: after each check the three penalties are scaled by
+    2 when r_p > 10 r_d, by 1/2 when r_d > 10 r_p, else kept; the penalties
+    travel with the state (an oracle created with the scaled penalties, given
+    the same state, sweeps identically)."""
+    from paper_2310_13145_b300 import synth
+    g = synth.config_instances("c1_9bus_T6")[0]
+    o = oracle.Oracle(g, oracle.default_params(rho=g.rho, rho_every=1))
+    changes = 0
+    for _ in range(60):
+        st0 = oracle.unpack_state(o.state_vector(), g.T, g.n_gen, g.n_branch, g.n_bus)
+        o.sweep()
+        st1 = oracle.unpack_state(o.state_vector(), g.T, g.n_gen, g.n_branch, g.n_bus)
+        r = o.residuals()
+        want = 2.0 if (r["r_p"] > 10 * r["r_d"] and st0["rho_log"] < 6) else (
+            0.5 if (r["r_d"] > 10 * r["r_p"] and st0["rho_log"] > -6) else 1.0)
+        if st1["done"]:
+            want = 1.0
+        assert abs(st1["rho_log"]) <= 6
+        for name in ("rho_pq", "rho_va", "rho_uc"):
+            assert st1[name] == st0[name] * want
+        changes += want != 1.0
+    assert changes > 0
+    # the state's penalties drive the sweep
+    st = o.state_vector()
+    s = oracle.unpack_state(st, g.T, g.n_gen, g.n_branch, g.n_bus)
+    o2 = oracle.Oracle(g, oracle.default_params(rho=(s["rho_pq"], s["rho_va"], s["rho_uc"]), rho_every=1))
+    o2.set_state(st)
+    o.sweep()
+    o2.sweep()
+    assert np.array_equal(o.state_vector(), o2.state_vector())
