@@ -64,11 +64,11 @@ __device__ __forceinline__ double row_target_exact(double b, double z, double y,
   return __dsub_rn(__dsub_rn(b, z), __ddiv_rn(y, rho));
 }
 
-// x-step target of every other row: (b - z) - y * (1/rho), also separately
-// rounded so that the sweep kernels and the target preparation after an
-// import produce the same bits.
+// x-step target of every other row: (b - z) - y * (1/rho) as one
+// multiply-add, with explicit rounding so that the sweep kernels and the
+// target preparation after an import produce the same bits.
 __device__ __forceinline__ double row_target_fast(double b, double z, double y, double irho) {
-  return __dsub_rn(__dsub_rn(b, z), __dmul_rn(y, irho));
+  return __fma_rn(-y, irho, __dsub_rn(b, z));
 }
 
 // Explicitly rounded operations: the x-bar kernels spell out every multiply,
@@ -85,7 +85,17 @@ __device__ __forceinline__ double row_mtarget(double a, double z, double y, cons
   return fma_(y, F.irho, add_(a, z));
 }
 
-template <bool EXACT>
+// max(q, |c|) for q >= 0 on the bit patterns (order-preserving for
+// non-negative doubles): integer work instead of an FP64 min/max
+__device__ __forceinline__ double max_abs_bits(double q, double c) {
+  const unsigned long long bc = (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffULL;
+  const unsigned long long bq = (unsigned long long)__double_as_longlong(q);
+  return __longlong_as_double((long long)(bc > bq ? bc : bq));
+}
+
+// SD: accumulate this row's (b_new - b_old)^2 here (false when the caller
+// adds it once for rows that share b, as a bus's w and theta rows do)
+template <bool EXACT, bool SD = true>
 __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, double *L, double *Tg, long long idx,
                                            double b_new, double b_old, const Fam &F, const RowCtx &R,
                                            double (&q)[NQ]) {
@@ -102,11 +112,13 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
   Z[idx] = zn;
   Y[idx] = yn;
   Tg[idx] = EXACT ? row_target_exact(b_new, zn, yn, F.rho) : row_target_fast(b_new, zn, yn, F.irho);
-  const double db = sub_(b_new, b_old);
   q[Q_SP] = fma_(cz, cz, q[Q_SP]);
-  q[Q_SD] = fma_(db, db, q[Q_SD]);
+  if (SD) {
+    const double db = sub_(b_new, b_old);
+    q[Q_SD] = fma_(db, db, q[Q_SD]);
+  }
   q[Q_SZ] = fma_(zn, zn, q[Q_SZ]);
-  q[Q_INF] = fmax(q[Q_INF], fabs(c));
+  q[Q_INF] = max_abs_bits(q[Q_INF], c);
 }
 
 // ------------------------------------------------------------ bus (R8) ----
@@ -150,16 +162,23 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
       M11 = add_(M11, irpq);
       r1 = add_(r1, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq));
     }
+    // (the p, q x-bar-step targets are parked in the target slots for pass
+    // 2, which overwrites them with the next x-step targets)
 #pragma unroll kBusUnroll
     for (int j = 0; j < deg; ++j) {
       const long long e = e0 + 32LL * j;
-      M00 = add_(M00, irpq);
-      r0 = sub_(r0, row_mtarget(S.EA[e], S.EZ[e], S.EY[e], Fpq));
-      M11 = add_(M11, irpq);
-      r1 = sub_(r1, row_mtarget(S.EA[NEP + e], S.EZ[NEP + e], S.EY[NEP + e], Fpq));
+      const double mp = row_mtarget(S.EA[e], S.EZ[e], S.EY[e], Fpq);
+      const double mq = row_mtarget(S.EA[NEP + e], S.EZ[NEP + e], S.EY[NEP + e], Fpq);
+      S.ET[e] = mp;
+      S.ET[NEP + e] = mq;
+      r0 = sub_(r0, mp);
+      r1 = sub_(r1, mq);
       mw = add_(mw, row_mtarget(S.EA[2 * NEP + e], S.EZ[2 * NEP + e], S.EY[2 * NEP + e], Fva));
       mth = add_(mth, row_mtarget(S.EA[3 * NEP + e], S.EZ[3 * NEP + e], S.EY[3 * NEP + e], Fva));
     }
+    const double fdeg = (double)deg;
+    M00 = fma_(fdeg, irpq, M00);
+    M11 = fma_(fdeg, irpq, M11);
     const double ideg = 1.0 / deg;
     mw = mul_(mw, ideg);
     mth = mul_(mth, ideg);
@@ -207,19 +226,23 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const double thnew = (i == I.ref) ? 0.0 : mth;
     S.U[FU_W * NUP + up] = wnew;
     S.U[FU_TH * NUP + up] = thnew;
+    // every incident w (theta) row has the bus's w (theta) as its x-bar:
+    // their x-bar changes enter the dual residual as deg times one square
+    const double dw = sub_(wnew, wold), dth = sub_(thnew, thold);
+    q[Q_SD] = fma_(mul_(fdeg, dw), dw, q[Q_SD]);
+    q[Q_SD] = fma_(mul_(fdeg, dth), dth, q[Q_SD]);
     for (int j = 0; j < deg; ++j) {
       const long long e = e0 + 32LL * j;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const long long eu = u * NEP + e;
-        const double m = row_mtarget(S.EA[eu], S.EZ[eu], S.EY[eu], Fpq);
-        const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, m);
+        const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, S.ET[eu]);
         const double vold = S.EFB[eu];
         S.EFB[eu] = vnew;
         row_update<false>(S.EA, S.EY, S.EZ, S.EL, S.ET, eu, vnew, vold, Fpq, R, q);
       }
-      row_update<false>(S.EA, S.EY, S.EZ, S.EL, S.ET, 2 * NEP + e, wnew, wold, Fva, R, q);
-      row_update<false>(S.EA, S.EY, S.EZ, S.EL, S.ET, 3 * NEP + e, thnew, thold, Fva, R, q);
+      row_update<false, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, 2 * NEP + e, wnew, wold, Fva, R, q);
+      row_update<false, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, 3 * NEP + e, thnew, thold, Fva, R, q);
     }
   }
   warp_reduce_q(q, S.part_up + (long long)gr * NQ);
