@@ -58,9 +58,19 @@
 
 namespace ucac {
 
+// a_r = q_r V'^2 + V_i V_j (ga_r cos d + ka_r sin d) with V' = V_i for the
+// from-end rows r = 0, 1 and V_j for the to-end rows r = 2, 3.  FP32 copies
+// of q, ga, ka for the mixed-precision Hessian sit in shared memory (f[j *
+// fs], j = 0..11), so they cost neither registers nor per-evaluation
+// conversions on the FP64 pipe
 struct PolK {
-  double al[4], be[4], ga[4], ka[4];  // a_r = al V_i^2 + be V_j^2 + V_i V_j (ga cos d + ka sin d)
+  double q[4], ga[4], ka[4];
   double rate2, lo0, hi0, lo1, hi1;
+  const float *f;
+  int fs;
+  __device__ __forceinline__ float fq(int r) const { return f[r * fs]; }
+  __device__ __forceinline__ float fga(int r) const { return f[(4 + r) * fs]; }
+  __device__ __forceinline__ float fka(int r) const { return f[(8 + r) * fs]; }
 };
 
 struct PolP {
@@ -97,15 +107,15 @@ __device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, double (
                                           double &c, double &s, const double (&ht)[2], int free_mask) {
   const double Vi = v[0], Vj = v[1], d = v[2];
   sincos(d, &s, &c);
-  const double Pv = Vi * Vj;
+  const double Pv = Vi * Vj, Vi2 = Vi * Vi, Vj2 = Vj * Vj;
   double f = 0.0;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    a[r] = K.al[r] * Vi * Vi + K.be[r] * Vj * Vj + Pv * (K.ga[r] * c + K.ka[r] * s);
+    a[r] = K.q[r] * (r < 2 ? Vi2 : Vj2) + Pv * (K.ga[r] * c + K.ka[r] * s);
     const double e = a[r] - P.tg[r];
     f += 0.5 * P.rpq * e * e;
   }
-  const double ewi = Vi * Vi - P.tg[4], ewj = Vj * Vj - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
+  const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
   f += 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
@@ -132,26 +142,33 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, const d
   L.s = s;
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) L.v[i] = v[i];
-  const double Pv = Vi * Vj;
+  const double Pv = Vi * Vj, Vi2 = Vi * Vi, Vj2 = Vj * Vj;
+  const float fVi = (float)Vi, fVj = (float)Vj, fP = fVi * fVj;
   double f = 0.0;
   gx[0] = gx[1] = gx[2] = 0.0;
   double da[4][3], E[4], Ed[4], pe[4];
+  float fE[4], fEd[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     E[r] = K.ga[r] * c + K.ka[r] * s;
     Ed[r] = K.ka[r] * c - K.ga[r] * s;
-    const double a = K.al[r] * Vi * Vi + K.be[r] * Vj * Vj + Pv * E[r];
+    const double a = K.q[r] * (r < 2 ? Vi2 : Vj2) + Pv * E[r];
     L.a[r] = a;
     const double e = a - P.tg[r];
     f += 0.5 * P.rpq * e * e;
-    da[r][0] = 2.0 * K.al[r] * Vi + Vj * E[r];
-    da[r][1] = 2.0 * K.be[r] * Vj + Vi * E[r];
+    da[r][0] = r < 2 ? 2.0 * K.q[r] * Vi + Vj * E[r] : Vj * E[r];
+    da[r][1] = r < 2 ? Vi * E[r] : 2.0 * K.q[r] * Vj + Vi * E[r];
     da[r][2] = Pv * Ed[r];
     pe[r] = P.rpq * e;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) L.da[r][i] = (float)da[r][i];
+    // FP32 gradient of the flow from FP32-rounded E, Ed (two conversions
+    // per row instead of three, and the products in FP32)
+    fE[r] = (float)E[r];
+    fEd[r] = (float)Ed[r];
+    L.da[r][0] = r < 2 ? 2.0f * K.fq(r) * fVi + fVj * fE[r] : fVj * fE[r];
+    L.da[r][1] = r < 2 ? fVi * fE[r] : 2.0f * K.fq(r) * fVj + fVi * fE[r];
+    L.da[r][2] = fP * fEd[r];
   }
-  const double ewi = Vi * Vi - P.tg[4], ewj = Vj * Vj - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
+  const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
   f += 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
   double w[4], u[4];
   bool lim = false;
@@ -190,13 +207,14 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, const d
   // packed symmetric index: 0:(0,0) 1:(0,1) 2:(0,2) 3:(1,1) 4:(1,2) 5:(2,2)
   const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
   if (!lim) {
-    const float fVi = (float)Vi, fVj = (float)Vj, fP = (float)Pv, rva = (float)P.rva;
+    const float rva = (float)P.rva, fw0 = (float)w[0], fw2 = (float)w[2];
 #pragma unroll
     for (int q = 0; q < 6; ++q) Hf[q] = 0.0f;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const float fE = (float)E[r], fEd = (float)Ed[r], fu = (float)u[r], fw = (float)w[r];
-      const float d2[6] = {2.0f * (float)K.al[r], fE, fVj * fEd, 2.0f * (float)K.be[r], fVi * fEd, -fP * fE};
+      const float fu = (float)u[r], fw = r < 2 ? fw0 : fw2;
+      const float d2[6] = {r < 2 ? 2.0f * K.fq(r) : 0.0f, fE[r], fVj * fEd[r], r < 2 ? 0.0f : 2.0f * K.fq(r),
+                           fVi * fEd[r], -fP * fE[r]};
 #pragma unroll
       for (int q = 0; q < 6; ++q) Hf[q] += fw * L.da[r][pi_[q]] * L.da[r][pj_[q]] + fu * d2[q];
     }
@@ -208,7 +226,8 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, const d
     for (int q = 0; q < 6; ++q) Hd[q] = 0.0;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const double d2[6] = {2.0 * K.al[r], E[r], Vj * Ed[r], 2.0 * K.be[r], Vi * Ed[r], -Pv * E[r]};
+      const double d2[6] = {r < 2 ? 2.0 * K.q[r] : 0.0, E[r], Vj * Ed[r], r < 2 ? 0.0 : 2.0 * K.q[r], Vi * Ed[r],
+                            -Pv * E[r]};
 #pragma unroll
       for (int q = 0; q < 6; ++q) Hd[q] += w[r] * da[r][pi_[q]] * da[r][pj_[q]] + u[r] * d2[q];
     }
@@ -259,39 +278,55 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   const double c = P.c;
   const double gr[POL_NV] = {gx[0], gx[1], gx[2], L.m[0], L.m[1]};
   double xmax = 0.0, dlo[POL_NV], dhi[POL_NV];
-  T hmax = T(0), epst = T(0);
+  T hmax = T(0);
+  // a variable can only be epsilon-active within 1e-6 of a bound (epsilon
+  // <= 1e-6), so the epsilon estimate is skipped when none is that close
+  bool near = false;
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) {
     const double lo = pol_lo(K, i), hi = pol_hi(K, i);
     dlo[i] = v[i] - lo;
     dhi[i] = hi - v[i];
-    // diagonal Newton step (the epsilon of the active set), in T
-    T di;
     if (i < 3) {
       xmax = fmax(xmax, fabs(v[i]));
       const T h = hq(H, i, i);
       hmax = hmax > h ? hmax : h;
-      di = (h > T(0)) ? (T)gr[i] / h : (T)gr[i];
-    } else {
-      di = (T)(gr[i] * P.ic);
     }
-    const T st = (-di < (T)-dlo[i]) ? (T)-dlo[i] : ((-di > (T)dhi[i]) ? (T)dhi[i] : -di);
-    const T ast = st < T(0) ? -st : st;
-    epst = epst > ast ? epst : ast;
+    near = near || (dlo[i] <= 1e-6 && gr[i] > 0.0) || (dhi[i] <= 1e-6 && gr[i] < 0.0);
   }
-  const double eps = fmin((double)epst, 1e-6);
   bool act[POL_NV];
   double d[POL_NV];
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) {
     act[i] = false;
     d[i] = 0.0;
-    if (dlo[i] <= eps && gr[i] > 0.0) {
-      act[i] = true;
-      d[i] = -dlo[i] * 1.000001;  // onto the bound (clamped below)
-    } else if (dhi[i] <= eps && gr[i] < 0.0) {
-      act[i] = true;
-      d[i] = dhi[i] * 1.000001;
+  }
+  if (near) {
+    // epsilon: largest clamped diagonal Newton step, in T
+    T epst = T(0);
+#pragma unroll
+    for (int i = 0; i < POL_NV; ++i) {
+      T di;
+      if (i < 3) {
+        const T h = hq(H, i, i);
+        di = (h > T(0)) ? (T)gr[i] / h : (T)gr[i];
+      } else {
+        di = (T)(gr[i] * P.ic);
+      }
+      const T st = (-di < (T)-dlo[i]) ? (T)-dlo[i] : ((-di > (T)dhi[i]) ? (T)dhi[i] : -di);
+      const T ast = st < T(0) ? -st : st;
+      epst = epst > ast ? epst : ast;
+    }
+    const double eps = fmin((double)epst, 1e-6);
+#pragma unroll
+    for (int i = 0; i < POL_NV; ++i) {
+      if (dlo[i] <= eps && gr[i] > 0.0) {
+        act[i] = true;
+        d[i] = -dlo[i] * 1.000001;  // onto the bound (clamped below)
+      } else if (dhi[i] <= eps && gr[i] < 0.0) {
+        act[i] = true;
+        d[i] = dhi[i] * 1.000001;
+      }
     }
   }
   // stationarity on the reduced gradient (free slacks eliminated: their
@@ -329,13 +364,17 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   // which turns its m_k grad g_k out of the right-hand side
   const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
   T Hr[6], rb[3];
+  const bool sheld = act[3] || act[4];
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
-    double add = 0.0;
+    Hr[q] = H[q];
+    if (sheld) {
+      double add = 0.0;
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (act[3 + k]) add += c * L.dg[k][pi_[q]] * L.dg[k][pj_[q]];
-    Hr[q] = H[q] + (T)add;
+      for (int k = 0; k < 2; ++k)
+        if (act[3 + k]) add += c * L.dg[k][pi_[q]] * L.dg[k][pj_[q]];
+      Hr[q] += (T)add;
+    }
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -492,6 +531,7 @@ template <int BS>
 __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  __shared__ float kf[12][BS];  // FP32 copies of the lane's line constants
   const long long NBP = S.NBP, NL = S.NL, NEP = S.NEP;
   const double eta = S.prm.eta;
   const int K_N = S.prm.K_N, K_AL = S.prm.K_AL;
@@ -518,6 +558,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   float Hf[6];
   PolLast L;
   PolK K;
+  K.f = &kf[0][threadIdx.x];
+  K.fs = BS;
   PolP P;
   while (true) {
     const bool want = active && bp < 0;
@@ -547,10 +589,16 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           const double Gij = S.BC[(BC_Y0 + 2) * NL + lg], Bij = S.BC[(BC_Y0 + 3) * NL + lg];
           const double Gjj = S.BC[(BC_Y0 + 4) * NL + lg], Bjj = S.BC[(BC_Y0 + 5) * NL + lg];
           const double Gji = S.BC[(BC_Y0 + 6) * NL + lg], Bji = S.BC[(BC_Y0 + 7) * NL + lg];
-          K.al[0] = Gii;  K.be[0] = 0.0;  K.ga[0] = Gij;  K.ka[0] = Bij;
-          K.al[1] = -Bii; K.be[1] = 0.0;  K.ga[1] = -Bij; K.ka[1] = Gij;
-          K.al[2] = 0.0;  K.be[2] = Gjj;  K.ga[2] = Gji;  K.ka[2] = -Bji;
-          K.al[3] = 0.0;  K.be[3] = -Bjj; K.ga[3] = -Bji; K.ka[3] = -Gji;
+          K.q[0] = Gii;  K.ga[0] = Gij;  K.ka[0] = Bij;
+          K.q[1] = -Bii; K.ga[1] = -Bij; K.ka[1] = Gij;
+          K.q[2] = Gjj;  K.ga[2] = Gji;  K.ka[2] = -Bji;
+          K.q[3] = -Bjj; K.ga[3] = -Bji; K.ka[3] = -Gji;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            kf[r][threadIdx.x] = (float)K.q[r];
+            kf[4 + r][threadIdx.x] = (float)K.ga[r];
+            kf[8 + r][threadIdx.x] = (float)K.ka[r];
+          }
           K.rate2 = S.BC[BC_RATE2 * NL + lg];
           K.lo0 = S.BC[(BC_VB + 0) * NL + lg];
           K.hi0 = S.BC[(BC_VB + 1) * NL + lg];
