@@ -98,6 +98,10 @@ __device__ __forceinline__ double pol_lo(const PolK &K, int i) {
 __device__ __forceinline__ double pol_hi(const PolK &K, int i) {
   return i == 0 ? K.hi0 : (i == 1 ? K.hi1 : (i == 2 ? 3.14159265358979 : INFINITY));
 }
+// projection of variable i onto its bounds (a slack has only its lower bound)
+__device__ __forceinline__ double pol_clamp(const PolK &K, int i, double x) {
+  return i < 3 ? clampd(x, pol_lo(K, i), pol_hi(K, i)) : fmax(x, 0.0);
+}
 
 // objective (and flows, cos/sin) at v.  Slacks in free_mask are first set
 // to max(0, ht_k - g_k(x)), so that h_k takes its predicted value ht_k (the
@@ -333,15 +337,19 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   // m_k grad g_k leaves the x-gradient); at a stationary x each free slack
   // takes its exact step -m_k / c (the objective is quadratic in it) -- m_k
   // itself carries c times the rounding of h_k and never reaches omega
-  double rg[3], pg = 0.0;
+  // (|P(v - g) - v| <= omega holds when |g| <= omega or the bound that -g
+  // points at is within omega)
+  double rg[3];
+  bool stat = true;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     rg[i] = gx[i];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
       if (!act[3 + k]) rg[i] -= L.m[k] * L.dg[k][i];
-    pg = fmax(pg, fabs(clampd(v[i] - rg[i], pol_lo(K, i), pol_hi(K, i)) - v[i]));
+    stat = stat && (fabs(rg[i]) <= omega || (rg[i] > 0.0 ? dlo[i] : dhi[i]) <= omega);
   }
+  double pg = stat ? 0.0 : INFINITY;
   double sn[2];
   bool sok = true;
 #pragma unroll
@@ -440,7 +448,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     const double predN = model(d);
     if (dn <= 1e-9 * (1.0 + xmax) || predN <= 1e-12 * (1.0 + fabs(f))) {
 #pragma unroll
-      for (int i = 0; i < POL_NV; ++i) v[i] = clampd(v[i] + d[i], pol_lo(K, i), pol_hi(K, i));
+      for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
       return NI_CONV;
     }
     bool inside = true;
@@ -449,7 +457,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
       inside = inside && (act[i] || (d[i] >= -dlo[i] && d[i] <= dhi[i]));
     if (inside && dn <= 1e-4 * (1.0 + xmax) && dn <= Delta) {
 #pragma unroll
-      for (int i = 0; i < POL_NV; ++i) v[i] = clampd(v[i] + d[i], pol_lo(K, i), pol_hi(K, i));
+      for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
       accepted = true;
       return NI_CONT;
     }
@@ -458,7 +466,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   double vt[POL_NV], sg[POL_NV], smax = 0.0;
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) {
-    vt[i] = clampd(v[i] + scale * d[i], pol_lo(K, i), pol_hi(K, i));
+    vt[i] = pol_clamp(K, i, v[i] + scale * d[i]);
     sg[i] = vt[i] - v[i];
     if (i < 3) smax = fmax(smax, fabs(sg[i]));
   }
@@ -675,9 +683,11 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         const bool tiny = conv && fmax(fmax(fabs(dx0), fabs(dx1)), fabs(dx2)) <= 1e-8;
         double a[4], c, sn, h[2];
         if (tiny) {
+          // (dx <= 1e-8: the FP32 product carries ~1e-15 absolute error)
+          const float fx0 = (float)dx0, fx1 = (float)dx1, fx2 = (float)dx2;
 #pragma unroll
           for (int r = 0; r < 4; ++r)
-            a[r] = L.a[r] + (double)L.da[r][0] * dx0 + (double)L.da[r][1] * dx1 + (double)L.da[r][2] * dx2;
+            a[r] = L.a[r] + (double)(L.da[r][0] * fx0 + L.da[r][1] * fx1 + L.da[r][2] * fx2);
           c = L.c - L.s * dx2;
           sn = L.s + L.c * dx2;
 #pragma unroll
