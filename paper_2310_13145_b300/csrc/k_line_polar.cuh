@@ -137,8 +137,9 @@ __device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, double (
 //   sum_r (w_r grad a_r grad a_r^T + u_r hess a_r) + (angle/voltage rows)
 //   + sum_k c grad g_k grad g_k^T,
 // w_r = rho_pq + 2 m_k, u_r = rho_pq (a_r - t_r) + 2 m_k a_r (k = r / 2).
-__device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, const double (&v)[POL_NV], double (&gx)[3],
-                                           float (&Hf)[6], double (&Hd)[6], PolLast &L) {
+__device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double (&v)[POL_NV], double (&gx)[3],
+                                           float (&Hf)[6], double (&Hd)[6], PolLast &L, const double (&ht)[2],
+                                           int free_mask) {
   const double Vi = v[0], Vj = v[1], d = v[2];
   double s, c;
   sincos(d, &s, &c);
@@ -179,8 +180,13 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, const d
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int r0 = 2 * k, r1 = 2 * k + 1;
+    const double g = L.a[r0] * L.a[r0] + L.a[r1] * L.a[r1] - K.rate2;
+    if ((free_mask >> k) & 1) {  // second-order correction of a trial point (see pol_obj)
+      v[3 + k] = fmax(ht[k] - g, 0.0);
+      L.v[3 + k] = v[3 + k];
+    }
     const double sk = v[3 + k];
-    const double h = L.a[r0] * L.a[r0] + L.a[r1] * L.a[r1] - K.rate2 + sk;
+    const double h = g + sk;
     const double m = P.mu[k] + P.c * h;
     f += h * (P.mu[k] + 0.5 * P.c * h);
     L.m[k] = m;
@@ -270,13 +276,20 @@ __device__ __forceinline__ T hq(const T (&H)[6], int i, int j) {
 }
 
 
+// a pending trial point: evaluated in full at the next trip, then accepted or
+// rejected by the ratio test against the model decrease pred
+struct PolTrial {
+  double v[POL_NV], ht[2], pred, scale, smax;
+};
+enum { NI_TRIAL = 3 };
+
 // one projected Newton iteration over v = (V_i, V_j, d, sigma_ij, sigma_ji)
 // with the x-Hessian H of type T (see newton_iter of the W-form kernel for
 // the steps); free slacks are eliminated from the Newton system exactly
 template <typename T>
 __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v)[POL_NV], double &f,
                                         const double (&gx)[3], const PolLast &L, const T (&H)[6], double &Delta,
-                                        double omega, bool &accepted, int &counted) {
+                                        double omega, bool &accepted, int &counted, PolTrial &tr) {
   accepted = false;
   counted = 0;
   const double c = P.c;
@@ -482,9 +495,22 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     ht[k] = L.h[k] + L.dg[k][0] * sg[0] + L.dg[k][1] * sg[1] + L.dg[k][2] * sg[2] + sg[3 + k];
     if (act[3 + k]) ++nheld; else free_mask |= 1 << k;
   }
+  if (nheld == 0) {
+    // the trial point becomes the next trip's evaluation point: every lane
+    // of the warp then runs one full evaluation per trip, and the ratio test
+    // follows it (a rejection re-evaluates the current point)
+#pragma unroll
+    for (int i = 0; i < POL_NV; ++i) tr.v[i] = vt[i];
+    tr.ht[0] = ht[0];
+    tr.ht[1] = ht[1];
+    tr.pred = pred;
+    tr.scale = scale;
+    tr.smax = smax;
+    return NI_TRIAL;
+  }
   double at[4], ct, stn;
   double ft = pol_obj(K, P, vt, at, ct, stn, ht, free_mask);
-  if (nheld > 0) {
+  {
     double r[2], G[3];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
@@ -560,7 +586,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
     }
     acc_nw = acc_al = acc_cap = acc_w = 0;
   };
-  bool need_full = false;
+  bool need_full = false, trial = false;
+  PolTrial tr;
   double f = 0.0, Delta = 1.0, hprev = INFINITY, omega = 0.0, cmax = 0.0;
   double v[POL_NV], gx[3], Hd[6];
   float Hf[6];
@@ -659,21 +686,62 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           Delta = 1.0;
           itn = al = newton = 0;
           need_full = true;
+          trial = false;
         }
       }
     }
     if (__ballot_sync(FULL, active) == 0) break;
     if (active) {
-      if (need_full) f = pol_full(K, P, v, gx, Hf, Hd, L);
-      need_full = false;
-      bool accepted;
-      int counted;
-      const int out = L.lim ? pol_iter<double>(K, P, v, f, gx, L, Hd, Delta, omega, accepted, counted)
-                            : pol_iter<float>(K, P, v, f, gx, L, Hf, Delta, omega, accepted, counted);
-      newton += counted;
-      need_full = accepted;
+      // one full evaluation per trip: at a pending trial point (then the
+      // ratio test), else at the current point when it moved
+      int out = NI_CONT;
+      bool step_now = true;
+      if (need_full) {
+        // one call site for every lane: the point is the trial point or the
+        // current point (two call sites would split the warp between copies)
+        if (!trial) {
+#pragma unroll
+          for (int i = 0; i < POL_NV; ++i) tr.v[i] = v[i];
+          tr.ht[0] = tr.ht[1] = 0.0;
+        }
+        const double fe = pol_full(K, P, tr.v, gx, Hf, Hd, L, tr.ht, trial ? 3 : 0);
+        if (trial) {
+          trial = false;
+          const double ared = f - fe;
+          if (tr.pred > 0.0 && ared >= 1e-4 * tr.pred) {
+#pragma unroll
+            for (int i = 0; i < POL_NV; ++i) v[i] = tr.v[i];
+            f = fe;
+            if (ared >= 0.75 * tr.pred && tr.scale < 1.0) Delta = 2.0 * Delta;
+          } else {
+            // rejected: the evaluation describes the trial point, so the
+            // current point is evaluated again at the next trip
+            Delta = 0.25 * tr.smax;
+            step_now = false;
+            if (Delta <= 1e-15 * (1.0 + fmax(fmax(fabs(v[0]), fabs(v[1])), fabs(v[2])))) out = NI_STOP;
+          }
+        } else {
+          f = fe;
+        }
+      }
+      need_full = !step_now;
+      if (step_now) {
+        bool accepted;
+        int counted;
+        out = L.lim ? pol_iter<double>(K, P, v, f, gx, L, Hd, Delta, omega, accepted, counted, tr)
+                    : pol_iter<float>(K, P, v, f, gx, L, Hf, Delta, omega, accepted, counted, tr);
+        newton += counted;
+        if (out == NI_TRIAL) {
+          trial = true;
+          need_full = true;
+          out = NI_CONT;
+        } else {
+          need_full = accepted;
+        }
+      }
       ++itn;
       if (out != NI_CONT || itn >= K_N) {
+        trial = false;
         const bool conv = (out == NI_CONV);
         // flows, cos/sin and h_k at v: first order from the last evaluation
         // after a converged tiny final step (h_k in FP64 from grad g_k, so
