@@ -59,6 +59,10 @@ UNIT = "sweeps/s"
 # point 85, gradient and Hessian at the accepted point 280); one AL round 60.
 FLOPS = {"polar": (425, 200), "w": (1229, 60)}
 FP64_NOMINAL_TFLOPS = 1.25
+# DRAM bytes (read + write) of one launch of the polar line kernel on the
+# 16 x 2000-bus workload, from an ncu capture of sweep 31 (the summary under
+# profiles/ gives the command); None for a form or workload not captured
+LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 333.6e6}
 
 
 def parse():
@@ -331,7 +335,7 @@ def main():
     value = whole_job_value(a.steps, world, ms)
     # per-kernel device times (events on the handle's stream) and iteration counts
     r = h.residuals(0)
-    kt = h.kernel_times(3)
+    kt = h.kernel_times(4)
     newton = sum(h.residuals(k)["newton"] for k in range(len(grids)))
     al = sum(h.residuals(k)["al"] for k in range(len(grids)))
     fp64 = ucac.ucac_probe_fp64(5, stream.cuda_stream)
@@ -341,7 +345,8 @@ def main():
     flops = newton * f_newton + al * f_al
     achieved = flops / t_br / 1e12
     roofline = {"bound": "alu", "kernel": "k_branch (line subproblems, %s form)" % a.line_form, "achieved": achieved, "peak": fp64 / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / (fp64 / 1e12), "traffic": None,
+                "frac": achieved / (fp64 / 1e12), "traffic": LINE_TRAFFIC.get((a.line_form, a.workload)) if a.instances is None else None,
+                "traffic_unit": "bytes per launch (ncu, sweep 31)",
                 "peak_source": "measured FP64 FMA probe on this GPU (nominal %.2f)" % FP64_NOMINAL_TFLOPS,
                 "newton_per_sweep": newton, "al_per_sweep": al, "kernel_ms": kt}
     # end to end through the public API: create from pinned host arrays, sweeps,
@@ -409,7 +414,7 @@ def learned_arm(ucac, h, grids, stream, params, a, cache):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    kt = h.kernel_times(3)
+    kt = h.kernel_times(4)
     taken = sum(h.warm_start_stats(k)[0] for k in range(len(grids)))
     errs = sum(h.warm_start_stats(k)[1] for k in range(len(grids)))
     h.set_warm_start(None)

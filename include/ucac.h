@@ -201,9 +201,11 @@ int ucac_state_export(const ucac_handle *h, int32_t instance, double *buf, size_
 int ucac_state_import(ucac_handle *h, int32_t instance, const double *buf, size_t n_doubles);
 
 /*
- * Average device time per sweep of each kernel over n_sweeps sweeps, timed
- * with CUDA events on the handle's stream (kernels launched one by one, not
- * from the graph).  ms[] receives UCAC_N_KERNELS values in the order of
+ * Runs n_sweeps sweeps with the kernels launched one by one (not from the
+ * graph) and returns each kernel's average device time per sweep, timed
+ * with CUDA events on the handle's stream; when n_sweeps >= 2 the first
+ * sweep is untimed (it carries the first-launch costs of the one-by-one
+ * launches).  ms[] receives UCAC_N_KERNELS values in the order of
  * ucac_kernel_name(): k_ucdp, k_gen, k_branch (the line kernel of either
  * form), k_bus, k_ucbar, k_finish, k_mlp (0 unless the learned warm start is
  * enabled).  Synchronises.
