@@ -87,6 +87,9 @@ struct Dev {
   // branch constants [BC_N][NL]
   long long NL;
   const double *BC;
+  // FP32 copies of the polar line constants [12][NL]: q_r (Gii, -Bii, Gjj,
+  // -Bjj), ga_r (Gij, -Bij, Gji, -Bji), ka_r (Bij, Gij, -Bji, -Gji)
+  const float *BCF;
   const int *bf, *bt;  // local bus index of the from / to end
   // branch-period state [FB_FB0][NBP] (the x-bar values of the flow rows
   // live with the line-end rows)

@@ -561,12 +561,42 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   return NI_CONT;
 }
 
+// starting point of line-period `it` (instance k): V = sqrt(w) and
+// d = theta_i - theta_j of the stored iterate, clamped to their bounds, the
+// slacks, and 1 / c
+__device__ __forceinline__ void pol_start(const Dev &S, int k, long long it, double (&v)[POL_NV], double &ic) {
+  const Inst &I = S.inst[k];
+  const long long NBP = S.NBP, NL = S.NL;
+  const int loc = (int)(it - I.bpo);
+  const long long lg = (long long)I.lo + (loc - (loc / I.nl) * I.nl);
+  v[0] = clampd(sqrt(fmax(S.B[(FB_V0 + 0) * NBP + it], 0.0)), S.BC[(BC_VB + 0) * NL + lg], S.BC[(BC_VB + 1) * NL + lg]);
+  v[1] = clampd(sqrt(fmax(S.B[(FB_V0 + 1) * NBP + it], 0.0)), S.BC[(BC_VB + 2) * NL + lg], S.BC[(BC_VB + 3) * NL + lg]);
+  v[2] = clampd(S.B[(FB_V0 + 4) * NBP + it] - S.B[(FB_V0 + 5) * NBP + it], -3.14159265358979, 3.14159265358979);
+  v[3] = fmax(S.B[(FB_V0 + 6) * NBP + it], 0.0);
+  v[4] = fmax(S.B[(FB_V0 + 7) * NBP + it], 0.0);
+  ic = 1.0 / S.B[FB_C * NBP + it];
+}
+
 template <int BS>
 __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   __shared__ float kf[12][BS];  // FP32 copies of the lane's line constants
+  // Per-warp ring of prepared starts (item, instance, v, 1 / c).  Lanes that
+  // finish a solve take their next item from the ring; when it runs short,
+  // the warp fetches 32 items at once and all 32 lanes prepare one each, so
+  // the start's square roots and division run with every lane active
+  // instead of with the ~1/3 of the lanes that finish in a given trip.  In
+  // the last 2 x (resident threads) items the warp fetches only what its
+  // lanes need, so that no warp holds a backlog while others run dry.
+  constexpr int QN = 64;
+  __shared__ double qv[BS / 32][POL_NV + 1][QN];
+  __shared__ long long qit[BS / 32][QN];
+  __shared__ int qk[BS / 32][QN];
+  int qhead = 0, qcount = 0;  // warp-uniform
+  bool drained = false;       // warp-uniform: the work counter has passed NBP
   const long long NBP = S.NBP, NL = S.NL, NEP = S.NEP;
+  const long long tail = 2LL * gridDim.x * BS;
   const double eta = S.prm.eta;
   const int K_N = S.prm.K_N, K_AL = S.prm.K_AL;
   bool active = true;
@@ -600,18 +630,49 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
     const bool want = active && bp < 0;
     const unsigned m = __ballot_sync(FULL, want);
     if (m) {
-      const int leader = __ffs(m) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(S.bp_counter, (unsigned long long)__popc(m));
-      base = __shfl_sync(FULL, base, leader);
+      const int nw = __popc(m);
+      if (qcount < nw && !drained) {
+        __syncwarp();
+        unsigned long long base = 0;
+        int nb = 0;
+        if (lane == 0) {
+          const unsigned long long cur = *(volatile unsigned long long *)S.bp_counter;
+          nb = ((long long)cur + tail < NBP) ? 32 : nw - qcount;
+          base = atomicAdd(S.bp_counter, (unsigned long long)nb);
+        }
+        base = __shfl_sync(FULL, base, 0);
+        nb = __shfl_sync(FULL, nb, 0);
+        const long long left = NBP - (long long)base;
+        const int got = left <= 0 ? 0 : (left < nb ? (int)left : nb);
+        if (left <= nb) drained = true;
+        if (lane < got) {
+          const long long it = (long long)base + lane;
+          const int ki = find_instance(S, it);
+          double vs[POL_NV], ic;
+          pol_start(S, ki, it, vs, ic);
+          const int sl = (qhead + qcount + lane) & (QN - 1);
+          qit[wib][sl] = it;
+          qk[wib][sl] = ki;
+#pragma unroll
+          for (int i = 0; i < POL_NV; ++i) qv[wib][i][sl] = vs[i];
+          qv[wib][POL_NV][sl] = ic;
+        }
+        qcount += got;
+        __syncwarp();
+      }
       if (want) {
-        const long long item = (long long)base + __popc(m & ((1u << lane) - 1u));
-        if (item >= NBP) {
+        const int r = __popc(m & ((1u << lane) - 1u));
+        if (r >= qcount) {
+          // the ring is empty and the counter has passed NBP
           active = false;
           flush();
         } else {
-          bp = item;
-          k = find_instance(S, bp);
+          const int sl = (qhead + r) & (QN - 1);
+          bp = qit[wib][sl];
+          k = qk[wib][sl];
+#pragma unroll
+          for (int i = 0; i < POL_NV; ++i) v[i] = qv[wib][i][sl];
+          P.ic = qv[wib][POL_NV][sl];
           if (k != acc_k) {
             flush();
             acc_k = k;
@@ -629,11 +690,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           K.q[2] = Gjj;  K.ga[2] = Gji;  K.ka[2] = -Bji;
           K.q[3] = -Bjj; K.ga[3] = -Bji; K.ka[3] = -Gji;
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            kf[r][threadIdx.x] = (float)K.q[r];
-            kf[4 + r][threadIdx.x] = (float)K.ga[r];
-            kf[8 + r][threadIdx.x] = (float)K.ka[r];
-          }
+          for (int j = 0; j < 12; ++j) kf[j][threadIdx.x] = S.BCF[j * NL + lg];
           K.rate2 = S.BC[BC_RATE2 * NL + lg];
           K.lo0 = S.BC[(BC_VB + 0) * NL + lg];
           K.hi0 = S.BC[(BC_VB + 1) * NL + lg];
@@ -641,19 +698,12 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           K.hi1 = S.BC[(BC_VB + 3) * NL + lg];
           line_ends(S, I, t, lg, lef, let);
 #pragma unroll
-          for (int r = 0; r < 8; ++r) P.tg[r] = S.ET[erow_u(r) * NEP + (erow_end(r) ? let : lef)];
+          for (int r8 = 0; r8 < 8; ++r8) P.tg[r8] = S.ET[erow_u(r8) * NEP + (erow_end(r8) ? let : lef)];
           P.rpq = I.rpq;
           P.rva = I.rva;
           P.mu[0] = S.B[(FB_MU0 + 2) * NBP + bp];
           P.mu[1] = S.B[(FB_MU0 + 3) * NBP + bp];
           P.c = S.B[FB_C * NBP + bp];
-          P.ic = 1.0 / P.c;
-          // warm start from the stored iterate: V = sqrt(w), d = theta_i - theta_j, the slacks
-          v[0] = clampd(sqrt(fmax(S.B[(FB_V0 + 0) * NBP + bp], 0.0)), K.lo0, K.hi0);
-          v[1] = clampd(sqrt(fmax(S.B[(FB_V0 + 1) * NBP + bp], 0.0)), K.lo1, K.hi1);
-          v[2] = clampd(S.B[(FB_V0 + 4) * NBP + bp] - S.B[(FB_V0 + 5) * NBP + bp], pol_lo(K, 2), pol_hi(K, 2));
-          v[3] = fmax(S.B[(FB_V0 + 6) * NBP + bp], 0.0);
-          v[4] = fmax(S.B[(FB_V0 + 7) * NBP + bp], 0.0);
           if (S.warm) {
             // learned warm start: the network's proposal x0 + s y (W
             // coordinates) is taken when its objective is below the plain
@@ -689,6 +739,9 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           trial = false;
         }
       }
+      const int used = nw < qcount ? nw : qcount;
+      qhead = (qhead + used) & (QN - 1);
+      qcount -= used;
     }
     if (__ballot_sync(FULL, active) == 0) break;
     if (active) {

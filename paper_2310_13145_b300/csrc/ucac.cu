@@ -343,6 +343,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
       Qmax(NGEN), qlo(NGEN), qhi(NGEN), RU(NGEN), RD(NGEN), SU(NGEN), SD(NGEN), p0(NGEN);
   std::vector<int> TU(NGEN), TD(NGEN), u0(NGEN), K0(NGEN);
   std::vector<double> BC((size_t)BC_N * NL);
+  std::vector<float> BCF((size_t)12 * NL);
   std::vector<int> bf(NL), bt(NL);
   std::vector<double> Gs(NB), Bs(NB), Pd(NUP), Qd(NUP);
   std::vector<int> inc_ptr(NB + 1, 0), inc_br(2 * NL), inc_side(2 * NL), gen_ptr(NB + 1, 0), gen_idx(NGEN);
@@ -373,6 +374,11 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
       const double gs = r / z2, bs = -x / z2, bc = g->br_b[l];
       const double Y[8] = {gs, bs + 0.5 * bc, -gs, -bs, gs, bs + 0.5 * bc, -gs, -bs};
       for (int q = 0; q < 8; ++q) BC[(BC_Y0 + q) * NL + lg] = Y[q];
+      {
+        // Y = (Gii, Bii, Gij, Bij, Gjj, Bjj, Gji, Bji)
+        const double f12[12] = {Y[0], -Y[1], Y[4], -Y[5], Y[2], -Y[3], Y[6], -Y[7], Y[3], Y[2], -Y[7], -Y[6]};
+        for (int q = 0; q < 12; ++q) BCF[(size_t)q * NL + lg] = (float)f12[q];
+      }
       const double rate2 = g->br_rate[l] * g->br_rate[l];
       BC[BC_RATE2 * NL + lg] = rate2;
       const int i = g->br_from[l], j = g->br_to[l];
@@ -584,6 +590,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_G = A.take<double>((size_t)NGF * NGP);
   const size_t o_GR = A.take<double>((size_t)5 * NGR * NGP);
   const size_t o_BC = A.take<double>((size_t)BC_N * NL), o_bft = A.take<int>(2 * NL);
+  const size_t o_BCF = A.take<float>((size_t)12 * NL);
   const size_t o_B = A.take<double>((size_t)FB_FB0 * NBP);
   const size_t o_E = A.take<double>((size_t)22 * NEP);
   const size_t o_es = A.take<int>(2 * NL + 2 * blk_off.size());
@@ -626,6 +633,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.GT = gr + (size_t)4 * NGR * NGP;
   D.NL = NL;
   D.BC = (const double *)(ar + o_BC);
+  D.BCF = (const float *)(ar + o_BCF);
   D.bf = (const int *)(ar + o_bft); D.bt = D.bf + NL;
   D.NBP = NBP;
   D.B = (double *)(ar + o_B);
@@ -701,6 +709,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   chain(up(gi, gih.data(), gih.size() * 4));
   chain(up(D.G, G.data(), G.size() * 8));
   chain(up(D.BC, BC.data(), BC.size() * 8));
+  chain(up(D.BCF, BCF.data(), BCF.size() * 4));
   chain(up(D.bf, bfth.data(), bfth.size() * 4));
   chain(up(D.B, B.data(), B.size() * 8));
   chain(up(D.EFB, efb.data(), efb.size() * 8));
