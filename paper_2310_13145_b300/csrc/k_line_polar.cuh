@@ -199,7 +199,8 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
     // a free slack's optimum has m_k = 0, so the Newton model takes the
     // reduced x-Hessian there; m_k hess g_k stays only for a slack that may
     // be held at zero
-    const bool held = sk <= 1e-6 && m > 0.0;
+    // (sk >= 0: compared on its bit pattern, on the integer units)
+    const bool held = __double_as_longlong(sk) <= __double_as_longlong(1e-6) && __double_as_longlong(m) > 0;
     const double mh = held ? m : 0.0;
     w[r0] = w[r1] = P.rpq + 2.0 * mh;
     u[r0] = pe[r0] + 2.0 * mh * L.a[r0];
@@ -297,8 +298,12 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   double xmax = 0.0, dlo[POL_NV], dhi[POL_NV];
   T hmax = T(0);
   // a variable can only be epsilon-active within 1e-6 of a bound (epsilon
-  // <= 1e-6), so the epsilon estimate is skipped when none is that close
+  // <= 1e-6), so the epsilon estimate is skipped when none is that close.
+  // v lies in its box, so dlo, dhi >= 0 and their order is the signed order
+  // of their bit patterns: the test runs on the integer units (a negative
+  // or NaN operand can only make it pass, which is the safe side)
   bool near = false;
+  const long long b6 = __double_as_longlong(1e-6);
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) {
     const double lo = pol_lo(K, i), hi = pol_hi(K, i);
@@ -309,7 +314,8 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
       const T h = hq(H, i, i);
       hmax = hmax > h ? hmax : h;
     }
-    near = near || (dlo[i] <= 1e-6 && gr[i] > 0.0) || (dhi[i] <= 1e-6 && gr[i] < 0.0);
+    const long long bg = __double_as_longlong(gr[i]);
+    near = near || (__double_as_longlong(dlo[i]) <= b6 && bg > 0) || (__double_as_longlong(dhi[i]) <= b6 && bg < 0);
   }
   bool act[POL_NV];
   double d[POL_NV];
@@ -352,15 +358,19 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   // itself carries c times the rounding of h_k and never reaches omega
   // (|P(v - g) - v| <= omega holds when |g| <= omega or the bound that -g
   // points at is within omega)
+  // (compares of non-negative doubles on their bit patterns, as above)
   double rg[3];
   bool stat = true;
+  const long long bom = __double_as_longlong(omega);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     rg[i] = gx[i];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
       if (!act[3 + k]) rg[i] -= L.m[k] * L.dg[k][i];
-    stat = stat && (fabs(rg[i]) <= omega || (rg[i] > 0.0 ? dlo[i] : dhi[i]) <= omega);
+    const long long br = __double_as_longlong(rg[i]);
+    const long long bd = __double_as_longlong(br > 0 ? dlo[i] : dhi[i]);
+    stat = stat && ((br & 0x7fffffffffffffffLL) <= bom || bd <= bom);
   }
   double pg = stat ? 0.0 : INFINITY;
   double sn[2];
@@ -458,7 +468,17 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     return -(lin + 0.5 * quad);
   };
   if (lm == T(0)) {
-    const double predN = model(d);
+    // with no bound active d minimises the quadratic model exactly, where
+    // the model decrease is -(1/2) gr . d
+    double predN;
+    if (near) {
+      predN = model(d);
+    } else {
+      double lin = 0.0;
+#pragma unroll
+      for (int i = 0; i < POL_NV; ++i) lin += gr[i] * d[i];
+      predN = -0.5 * lin;
+    }
     if (dn <= 1e-9 * (1.0 + xmax) || predN <= 1e-12 * (1.0 + fabs(f))) {
 #pragma unroll
       for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
