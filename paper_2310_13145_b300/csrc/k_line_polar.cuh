@@ -303,20 +303,22 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   // of their bit patterns: the test runs on the integer units (a negative
   // or NaN operand can only make it pass, which is the safe side)
   bool near = false;
-  const long long b6 = __double_as_longlong(1e-6);
+  const long long b6 = __double_as_longlong(1e-6), ABS = 0x7fffffffffffffffLL;
+  long long bx = 0;
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) {
-    const double lo = pol_lo(K, i), hi = pol_hi(K, i);
-    dlo[i] = v[i] - lo;
-    dhi[i] = hi - v[i];
+    dlo[i] = v[i] - pol_lo(K, i);
+    dhi[i] = i < 3 ? pol_hi(K, i) - v[i] : INFINITY;  // a slack has no upper bound
     if (i < 3) {
-      xmax = fmax(xmax, fabs(v[i]));
+      const long long b = __double_as_longlong(v[i]) & ABS;
+      bx = b > bx ? b : bx;
       const T h = hq(H, i, i);
       hmax = hmax > h ? hmax : h;
     }
     const long long bg = __double_as_longlong(gr[i]);
     near = near || (__double_as_longlong(dlo[i]) <= b6 && bg > 0) || (__double_as_longlong(dhi[i]) <= b6 && bg < 0);
   }
+  xmax = __longlong_as_double(bx);  // max |x_i| (order of non-negative doubles = order of their bits)
   bool act[POL_NV];
   double d[POL_NV];
 #pragma unroll
@@ -370,22 +372,22 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
       if (!act[3 + k]) rg[i] -= L.m[k] * L.dg[k][i];
     const long long br = __double_as_longlong(rg[i]);
     const long long bd = __double_as_longlong(br > 0 ? dlo[i] : dhi[i]);
-    stat = stat && ((br & 0x7fffffffffffffffLL) <= bom || bd <= bom);
+    stat = stat && ((br & ABS) <= bom || bd <= bom);
   }
-  double pg = stat ? 0.0 : INFINITY;
   double sn[2];
   bool sok = true;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     sn[k] = v[3 + k];
     if (act[3 + k]) {
-      pg = fmax(pg, fabs(clampd(v[3 + k] - L.m[k], 0.0, INFINITY) - v[3 + k]));
+      stat = stat && fabs(clampd(v[3 + k] - L.m[k], 0.0, INFINITY) - v[3 + k]) <= omega;
     } else {
       sn[k] = v[3 + k] - L.m[k] * P.ic;
-      sok = sok && sn[k] >= 0.0;
+      const long long b = __double_as_longlong(sn[k]);
+      sok = sok && (b >= 0 || b == (long long)0x8000000000000000ULL);  // sn >= 0 (-0 included)
     }
   }
-  if (pg <= omega && sok) {
+  if (stat && sok) {
     v[3] = sn[0];
     v[4] = sn[1];
     return NI_CONV;
@@ -440,12 +442,14 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     lm = (lm == T(0)) ? T(1e-10) * (hmax > T(0) ? hmax : T(1)) : T(10) * lm;
   }
   if (!ok) return NI_STOP;
-  double dn = 0.0;
+  long long bn = 0;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (!act[i]) d[i] = (double)y[i];
-    dn = fmax(dn, fabs(d[i]));
+    const long long b = __double_as_longlong(d[i]) & ABS;
+    bn = b > bn ? b : bn;
   }
+  const double dn = __longlong_as_double(bn);  // max |d_i| over x
 #pragma unroll
   for (int k = 0; k < 2; ++k)
     if (!act[3 + k]) d[3 + k] = -L.m[k] * P.ic - (L.dg[k][0] * d[0] + L.dg[k][1] * d[1] + L.dg[k][2] * d[2]);
@@ -484,11 +488,16 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
       for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
       return NI_CONV;
     }
+    // d_i in [-dlo_i, dhi_i] with dlo, dhi >= 0: a negative d_i against dlo_i
+    // by magnitude, a non-negative one against dhi_i (bit-pattern compares)
     bool inside = true;
 #pragma unroll
-    for (int i = 0; i < POL_NV; ++i)
-      inside = inside && (act[i] || (d[i] >= -dlo[i] && d[i] <= dhi[i]));
-    if (inside && dn <= 1e-4 * (1.0 + xmax) && dn <= Delta) {
+    for (int i = 0; i < POL_NV; ++i) {
+      const long long b = __double_as_longlong(d[i]);
+      const bool in = b < 0 ? (b & ABS) <= __double_as_longlong(dlo[i]) : b <= __double_as_longlong(dhi[i]);
+      inside = inside && (act[i] || in);
+    }
+    if (inside && dn <= 1e-4 * (1.0 + xmax) && bn <= __double_as_longlong(Delta)) {
 #pragma unroll
       for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
       accepted = true;
