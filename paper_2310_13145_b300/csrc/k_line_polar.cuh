@@ -98,9 +98,32 @@ __device__ __forceinline__ double pol_lo(const PolK &K, int i) {
 __device__ __forceinline__ double pol_hi(const PolK &K, int i) {
   return i == 0 ? K.hi0 : (i == 1 ? K.hi1 : (i == 2 ? 3.14159265358979 : INFINITY));
 }
-// projection of variable i onto its bounds (a slack has only its lower bound)
+// Compares and clamps on the integer units.  B300's FP64 pipe also runs
+// FP64 compares and min/max, at the FP64 rate; the signed 64-bit key below
+// orders non-NaN doubles like their values (a negative double's magnitude
+// bits are flipped), so the same decisions cost only integer operations.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
+}
+__device__ __forceinline__ double dunkey(long long k) { return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k); }
+// x <= y for a non-negative y: the bit patterns compare the same way (a
+// negative x, -0 included, has a negative pattern)
+__device__ __forceinline__ bool le_nn(double x, double y) { return __double_as_longlong(x) <= __double_as_longlong(y); }
+// max |x_i| of non-negative magnitudes, by bit pattern
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+
+// projection of variable i onto its bounds (a slack has only its lower
+// bound); the same values as fmin(fmax(x, lo), hi) and fmax(x, 0)
 __device__ __forceinline__ double pol_clamp(const PolK &K, int i, double x) {
-  return i < 3 ? clampd(x, pol_lo(K, i), pol_hi(K, i)) : fmax(x, 0.0);
+  if (i < 3) {
+    long long k = dkey(x);
+    const long long kl = dkey(pol_lo(K, i)), kh = dkey(pol_hi(K, i));
+    k = k < kl ? kl : k;
+    k = k > kh ? kh : k;
+    return dunkey(k);
+  }
+  return __double_as_longlong(x) > 0 ? x : 0.0;
 }
 
 // objective (and flows, cos/sin) at v.  Slacks in free_mask are first set
@@ -483,7 +506,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
       for (int i = 0; i < POL_NV; ++i) lin += gr[i] * d[i];
       predN = -0.5 * lin;
     }
-    if (dn <= 1e-9 * (1.0 + xmax) || predN <= 1e-12 * (1.0 + fabs(f))) {
+    if (le_nn(dn, 1e-9 * (1.0 + xmax)) || le_nn(predN, 1e-12 * (1.0 + fabs(f)))) {
 #pragma unroll
       for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
       return NI_CONV;
@@ -497,14 +520,14 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
       const bool in = b < 0 ? (b & ABS) <= __double_as_longlong(dlo[i]) : b <= __double_as_longlong(dhi[i]);
       inside = inside && (act[i] || in);
     }
-    if (inside && dn <= 1e-4 * (1.0 + xmax) && bn <= __double_as_longlong(Delta)) {
+    if (inside && le_nn(dn, 1e-4 * (1.0 + xmax)) && le_nn(dn, Delta)) {
 #pragma unroll
       for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
       accepted = true;
       return NI_CONT;
     }
   }
-  const double scale = (dn > Delta) ? Delta / dn : 1.0;
+  const double scale = le_nn(dn, Delta) ? 1.0 : Delta / dn;
   double vt[POL_NV], sg[POL_NV], smax = 0.0;
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) {
@@ -830,7 +853,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         // that it matches the slack step taken from the same gradient), a
         // fresh evaluation otherwise
         const double dx0 = v[0] - L.v[0], dx1 = v[1] - L.v[1], dx2 = v[2] - L.v[2];
-        const bool tiny = conv && fmax(fmax(fabs(dx0), fabs(dx1)), fabs(dx2)) <= 1e-8;
+        const long long b8 = __double_as_longlong(1e-8);
+        const bool tiny = conv && abs_bits(dx0) <= b8 && abs_bits(dx1) <= b8 && abs_bits(dx2) <= b8;
         double a[4], c, sn, h[2];
         if (tiny) {
           // (dx <= 1e-8: the FP32 product carries ~1e-15 absolute error)
@@ -851,14 +875,16 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
             h[q] = a[2 * q] * a[2 * q] + a[2 * q + 1] * a[2 * q + 1] - K.rate2 + v[3 + q];
         }
         // equality multiplier step on h_k = p_k^2 + q_k^2 + sigma_k - rate^2
-        double hn = 0.0;
+        long long bh = 0;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          hn = fmax(hn, fabs(h[q]));
+          const long long b = abs_bits(h[q]);
+          bh = b > bh ? b : bh;
           P.mu[q] += P.c * h[q];
         }
+        const double hn = __longlong_as_double(bh);  // max |h_k|
         ++al;
-        const bool done = (hn <= eta && conv);
+        const bool done = le_nn(hn, eta) && conv;
         if (done || al >= K_AL) {
           const double Pv = v[0] * v[1], tm = 0.5 * (P.tg[6] + P.tg[7]);
           const double v8[8] = {v[0] * v[0], v[1] * v[1], Pv * c, Pv * sn, tm + 0.5 * v[2], tm - 0.5 * v[2],
