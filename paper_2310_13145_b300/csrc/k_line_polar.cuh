@@ -76,6 +76,7 @@ struct PolK {
 struct PolP {
   double tg[8];
   double rpq, rva;
+  float frpq, frva;  // FP32 copies for the Hessian
   double mu[2];  // line-limit multipliers (ij, ji)
   double c, ic;  // penalty and its reciprocal
 };
@@ -198,7 +199,7 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
   }
   const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
   f += 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
-  double w[4], u[4];
+  double mhk[2];
   bool lim = false;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
@@ -224,10 +225,7 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
     // be held at zero
     // (sk >= 0: compared on its bit pattern, on the integer units)
     const bool held = __double_as_longlong(sk) <= __double_as_longlong(1e-6) && __double_as_longlong(m) > 0;
-    const double mh = held ? m : 0.0;
-    w[r0] = w[r1] = P.rpq + 2.0 * mh;
-    u[r0] = pe[r0] + 2.0 * mh * L.a[r0];
-    u[r1] = pe[r1] + 2.0 * mh * L.a[r1];
+    mhk[k] = held ? m : 0.0;
     lim = lim || held;
   }
 #pragma unroll
@@ -241,12 +239,13 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
   // packed symmetric index: 0:(0,0) 1:(0,1) 2:(0,2) 3:(1,1) 4:(1,2) 5:(2,2)
   const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
   if (!lim) {
-    const float rva = (float)P.rva, fw0 = (float)w[0], fw2 = (float)w[2];
+    // no slack held: the row weights are w_r = rho_pq, u_r = rho_pq (a_r - t_r)
+    const float rva = P.frva, fw = P.frpq;
 #pragma unroll
     for (int q = 0; q < 6; ++q) Hf[q] = 0.0f;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const float fu = (float)u[r], fw = r < 2 ? fw0 : fw2;
+      const float fu = (float)pe[r];
       const float d2[6] = {r < 2 ? 2.0f * K.fq(r) : 0.0f, fE[r], fVj * fEd[r], r < 2 ? 0.0f : 2.0f * K.fq(r),
                            fVi * fEd[r], -fP * fE[r]};
 #pragma unroll
@@ -256,6 +255,13 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
     Hf[3] += rva * (4.0f * fVj * fVj + 2.0f * (float)ewj);
     Hf[5] += 0.5f * rva;
   } else {
+    double w[4], u[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const double mh = mhk[r >> 1];
+      w[r] = P.rpq + 2.0 * mh;
+      u[r] = pe[r] + 2.0 * mh * L.a[r];
+    }
 #pragma unroll
     for (int q = 0; q < 6; ++q) Hd[q] = 0.0;
 #pragma unroll
@@ -753,6 +759,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           for (int r8 = 0; r8 < 8; ++r8) P.tg[r8] = S.ET[erow_u(r8) * NEP + (erow_end(r8) ? let : lef)];
           P.rpq = I.rpq;
           P.rva = I.rva;
+          P.frpq = (float)I.rpq;
+          P.frva = (float)I.rva;
           P.mu[0] = S.B[(FB_MU0 + 2) * NBP + bp];
           P.mu[1] = S.B[(FB_MU0 + 3) * NBP + bp];
           P.c = S.B[FB_C * NBP + bp];
