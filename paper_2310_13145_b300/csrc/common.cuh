@@ -68,6 +68,12 @@ struct Params {
 
 constexpr int GRAN = 32;  // items per granule (one warp)
 
+// cos(k / 64), sin(k / 64) for k = -TRIG_K..TRIG_K (|k / 64| <= pi + 1/64),
+// filled from the host's libm when a handle is created (the same values on
+// every device and handle)
+constexpr int TRIG_K = 202;
+__device__ double2 g_trig[2 * TRIG_K + 1];
+
 struct Granules {
   int n;
   const int *inst;   // instance of each granule

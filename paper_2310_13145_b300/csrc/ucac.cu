@@ -185,6 +185,16 @@ void launch_bus(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.bus, 
 void launch_ucbar(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.ucbar, k_ucbar, h->ngr_gp, s, h->dev); }
 
 // resident blocks of the persistent line kernel for block size bs
+// the cos/sin table of the polar line kernel (see g_trig)
+cudaError_t upload_trig() {
+  std::vector<double> t(2 * (2 * TRIG_K + 1));
+  for (int k = -TRIG_K; k <= TRIG_K; ++k) {
+    t[2 * (k + TRIG_K)] = std::cos(k / 64.0);
+    t[2 * (k + TRIG_K) + 1] = std::sin(k / 64.0);
+  }
+  return cudaMemcpyToSymbol(g_trig, t.data(), t.size() * sizeof(double));
+}
+
 int line_grid(ucac_handle *h, int bs) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -703,6 +713,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   for (auto *pr : {&bgi, &bgf, &bpi, &bpf, &bbi, &bbf, &bui, &buf_}) blkh.insert(blkh.end(), pr->begin(), pr->end());
   cudaError_t e = cudaSuccess;
   auto chain = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+  chain(upload_trig());
   chain(cudaMemset(h->arena, 0, h->arena_bytes));
   chain(up(D.inst, h->inst_h.data(), sizeof(Inst) * n));
   chain(up(gd, gdh.data(), gdh.size() * 8));
@@ -1365,6 +1376,32 @@ extern "C" int ucac_probe_fp64(int32_t reps, void *cuda_stream, double *flops) {
   cudaEventDestroy(e1);
   cudaFree(sink);
   *flops = best;
+  return UCAC_OK;
+}
+
+namespace {
+__global__ void k_cossin_probe(const double *d, double *c, double *s, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) pol_cossin(d[i], c[i], s[i]);
+}
+}  // namespace
+
+extern "C" int ucac_probe_cossin(int32_t n, const double *d, double *c, double *s) {
+  ucac_handle *h = nullptr;
+  if (n < 0 || (n > 0 && (!d || !c || !s))) return fail(nullptr, UCAC_E_ARG, "bad arguments");
+  if (n == 0) return UCAC_OK;
+  double *buf = nullptr;
+  CK(upload_trig());
+  CK(cudaMalloc(&buf, 3 * (size_t)n * sizeof(double)));
+  cudaError_t e = cudaMemcpy(buf, d, (size_t)n * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_cossin_probe<<<(n + 255) / 256, 256>>>(buf, buf + n, buf + 2 * (size_t)n, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(c, buf + n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(s, buf + 2 * (size_t)n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(nullptr, UCAC_E_CUDA, std::string("probe_cossin: ") + cudaGetErrorString(e));
   return UCAC_OK;
 }
 
