@@ -93,8 +93,9 @@ struct Dev {
   // branch constants [BC_N][NL]
   long long NL;
   const double *BC;
-  // FP32 copies of the polar line constants [12][NL]: q_r (Gii, -Bii, Gjj,
-  // -Bjj), ga_r (Gij, -Bij, Gji, -Bji), ka_r (Bij, Gij, -Bji, -Gji)
+  // FP32 copies of the polar line constants [8][NL]: q_r (Gii, -Bii, Gjj,
+  // -Bjj), then ga, ka of the from end (Gij, Bij) and the to end (Gji, -Bji)
+  // as ga_0, ga_1, ka_0, ka_1
   const float *BCF;
   const int *bf, *bt;  // local bus index of the from / to end
   // branch-period state [FB_FB0][NBP] (the x-bar values of the flow rows

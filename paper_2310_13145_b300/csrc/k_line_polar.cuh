@@ -58,20 +58,38 @@
 
 namespace ucac {
 
-// a_r = q_r V'^2 + V_i V_j (ga_r cos d + ka_r sin d) with V' = V_i for the
-// from-end rows r = 0, 1 and V_j for the to-end rows r = 2, 3.  FP32 copies
-// of q, ga, ka for the mixed-precision Hessian sit in shared memory (f[j *
-// fs], j = 0..11), so they cost neither registers nor per-evaluation
+// a_r = q_r V'^2 + V_i V_j E_r with E_r = ga_r cos d + ka_r sin d and V' =
+// V_i for the from-end rows r = 0, 1 and V_j for the to-end rows r = 2, 3.
+// Within each end the coefficients pair up, (ga_1, ka_1) = (-ka_0, ga_0) and
+// (ga_3, ka_3) = (ka_2, -ga_2), so with Ed_r = dE_r/dd only E and Ed of rows 0
+// and 2 are formed: E_1 = -Ed_0, Ed_1 = E_0, E_3 = Ed_2, Ed_3 = -E_2.  ga[e],
+// ka[e] hold the coefficients of row 2e.  FP32 copies of q, ga, ka for the
+// mixed-precision Hessian sit in shared memory (f[j * fs]: q_0..q_3, ga_0,
+// ga_1, ka_0, ka_1), so they cost neither registers nor per-evaluation
 // conversions on the FP64 pipe
 struct PolK {
-  double q[4], ga[4], ka[4];
+  double q[4], ga[2], ka[2];
   double rate2, lo0, hi0, lo1, hi1;
   const float *f;
   int fs;
   __device__ __forceinline__ float fq(int r) const { return f[r * fs]; }
-  __device__ __forceinline__ float fga(int r) const { return f[(4 + r) * fs]; }
-  __device__ __forceinline__ float fka(int r) const { return f[(8 + r) * fs]; }
+  __device__ __forceinline__ float fga(int e) const { return f[(4 + e) * fs]; }
+  __device__ __forceinline__ float fka(int e) const { return f[(6 + e) * fs]; }
 };
+
+// E_r and Ed_r of the four flow rows from those of rows 0 and 2 (T = double
+// or float; the negations fold into the consuming operations)
+template <typename T>
+__device__ __forceinline__ void pol_angle_terms(T ga0, T ka0, T ga2, T ka2, T c, T s, T (&E)[4], T (&Ed)[4]) {
+  E[0] = ga0 * c + ka0 * s;
+  Ed[0] = ka0 * c - ga0 * s;
+  E[2] = ga2 * c + ka2 * s;
+  Ed[2] = ka2 * c - ga2 * s;
+  E[1] = -Ed[0];
+  Ed[1] = E[0];
+  E[3] = Ed[2];
+  Ed[3] = -E[2];
+}
 
 struct PolP {
   double tg[8];
@@ -154,15 +172,16 @@ __device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, double (
   const double Vi = v[0], Vj = v[1], d = v[2];
   pol_cossin(d, c, s);
   const double Pv = Vi * Vj, Vi2 = Vi * Vi, Vj2 = Vj * Vj;
-  double f = 0.0;
+  double E[4], Ed[4], spe = 0.0;  // spe = sum_r rho_pq (a_r - t_r)^2
+  pol_angle_terms(K.ga[0], K.ka[0], K.ga[1], K.ka[1], c, s, E, Ed);
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    a[r] = K.q[r] * (r < 2 ? Vi2 : Vj2) + Pv * (K.ga[r] * c + K.ka[r] * s);
+    a[r] = K.q[r] * (r < 2 ? Vi2 : Vj2) + Pv * E[r];
     const double e = a[r] - P.tg[r];
-    f += 0.5 * P.rpq * e * e;
+    spe = fma(P.rpq * e, e, spe);
   }
   const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
-  f += 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
+  double f = 0.5 * spe + 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const double g = a[2 * k] * a[2 * k] + a[2 * k + 1] * a[2 * k + 1] - K.rate2;
@@ -195,30 +214,29 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
   gx[0] = gx[1] = gx[2] = 0.0;
   double da[4][3], E[4], Ed[4], pe[4];
   float fE[4], fEd[4];
+  // FP32 gradient of the flow (for the FP32 Hessian and the first-order
+  // finish) from FP32 cos/sin and constants: two conversions per
+  // evaluation, the products on the FP32 pipe
   const float fc = (float)c, fs = (float)s;
+  pol_angle_terms(K.ga[0], K.ka[0], K.ga[1], K.ka[1], c, s, E, Ed);
+  pol_angle_terms(K.fga(0), K.fka(0), K.fga(1), K.fka(1), fc, fs, fE, fEd);
+  double spe = 0.0;  // sum_r rho_pq (a_r - t_r)^2
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    E[r] = K.ga[r] * c + K.ka[r] * s;
-    Ed[r] = K.ka[r] * c - K.ga[r] * s;
     const double a = K.q[r] * (r < 2 ? Vi2 : Vj2) + Pv * E[r];
     L.a[r] = a;
     const double e = a - P.tg[r];
-    f += 0.5 * P.rpq * e * e;
+    pe[r] = P.rpq * e;
+    spe = fma(pe[r], e, spe);
     da[r][0] = r < 2 ? 2.0 * K.q[r] * Vi + Vj * E[r] : Vj * E[r];
     da[r][1] = r < 2 ? Vi * E[r] : 2.0 * K.q[r] * Vj + Vi * E[r];
     da[r][2] = Pv * Ed[r];
-    pe[r] = P.rpq * e;
-    // FP32 gradient of the flow (for the FP32 Hessian and the first-order
-    // finish) from FP32 cos/sin and constants: two conversions per
-    // evaluation, the products on the FP32 pipe
-    fE[r] = fmaf(K.fga(r), fc, K.fka(r) * fs);
-    fEd[r] = fmaf(K.fka(r), fc, -(K.fga(r) * fs));
     L.da[r][0] = r < 2 ? 2.0f * K.fq(r) * fVi + fVj * fE[r] : fVj * fE[r];
     L.da[r][1] = r < 2 ? fVi * fE[r] : 2.0f * K.fq(r) * fVj + fVi * fE[r];
     L.da[r][2] = fP * fEd[r];
   }
   const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
-  f += 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
+  f = 0.5 * spe + 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
   double mhk[2];
   bool lim = false;
 #pragma unroll
@@ -659,7 +677,7 @@ template <int BS>
 __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  __shared__ float kf[12][BS];  // FP32 copies of the lane's line constants
+  __shared__ float kf[8][BS];  // FP32 copies of the lane's line constants
   // Per-warp ring of prepared starts (item, instance, v, 1 / c).  Lanes that
   // finish a solve take their next item from the ring; when it runs short,
   // the warp fetches 32 items at once and all 32 lanes prepare one each, so
@@ -763,12 +781,10 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           const double Gij = S.BC[(BC_Y0 + 2) * NL + lg], Bij = S.BC[(BC_Y0 + 3) * NL + lg];
           const double Gjj = S.BC[(BC_Y0 + 4) * NL + lg], Bjj = S.BC[(BC_Y0 + 5) * NL + lg];
           const double Gji = S.BC[(BC_Y0 + 6) * NL + lg], Bji = S.BC[(BC_Y0 + 7) * NL + lg];
-          K.q[0] = Gii;  K.ga[0] = Gij;  K.ka[0] = Bij;
-          K.q[1] = -Bii; K.ga[1] = -Bij; K.ka[1] = Gij;
-          K.q[2] = Gjj;  K.ga[2] = Gji;  K.ka[2] = -Bji;
-          K.q[3] = -Bjj; K.ga[3] = -Bji; K.ka[3] = -Gji;
+          K.q[0] = Gii;  K.q[1] = -Bii; K.q[2] = Gjj;  K.q[3] = -Bjj;
+          K.ga[0] = Gij; K.ka[0] = Bij;  K.ga[1] = Gji; K.ka[1] = -Bji;
 #pragma unroll
-          for (int j = 0; j < 12; ++j) kf[j][threadIdx.x] = S.BCF[j * NL + lg];
+          for (int j = 0; j < 8; ++j) kf[j][threadIdx.x] = S.BCF[j * NL + lg];
           K.rate2 = S.BC[BC_RATE2 * NL + lg];
           K.lo0 = S.BC[(BC_VB + 0) * NL + lg];
           K.hi0 = S.BC[(BC_VB + 1) * NL + lg];

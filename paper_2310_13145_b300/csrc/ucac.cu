@@ -353,7 +353,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
       Qmax(NGEN), qlo(NGEN), qhi(NGEN), RU(NGEN), RD(NGEN), SU(NGEN), SD(NGEN), p0(NGEN);
   std::vector<int> TU(NGEN), TD(NGEN), u0(NGEN), K0(NGEN);
   std::vector<double> BC((size_t)BC_N * NL);
-  std::vector<float> BCF((size_t)12 * NL);
+  std::vector<float> BCF((size_t)8 * NL);
   std::vector<int> bf(NL), bt(NL);
   std::vector<double> Gs(NB), Bs(NB), Pd(NUP), Qd(NUP);
   std::vector<int> inc_ptr(NB + 1, 0), inc_br(2 * NL), inc_side(2 * NL), gen_ptr(NB + 1, 0), gen_idx(NGEN);
@@ -386,8 +386,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
       for (int q = 0; q < 8; ++q) BC[(BC_Y0 + q) * NL + lg] = Y[q];
       {
         // Y = (Gii, Bii, Gij, Bij, Gjj, Bjj, Gji, Bji)
-        const double f12[12] = {Y[0], -Y[1], Y[4], -Y[5], Y[2], -Y[3], Y[6], -Y[7], Y[3], Y[2], -Y[7], -Y[6]};
-        for (int q = 0; q < 12; ++q) BCF[(size_t)q * NL + lg] = (float)f12[q];
+        const double f8[8] = {Y[0], -Y[1], Y[4], -Y[5], Y[2], Y[6], Y[3], -Y[7]};
+        for (int q = 0; q < 8; ++q) BCF[(size_t)q * NL + lg] = (float)f8[q];
       }
       const double rate2 = g->br_rate[l] * g->br_rate[l];
       BC[BC_RATE2 * NL + lg] = rate2;
@@ -600,7 +600,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_G = A.take<double>((size_t)NGF * NGP);
   const size_t o_GR = A.take<double>((size_t)5 * NGR * NGP);
   const size_t o_BC = A.take<double>((size_t)BC_N * NL), o_bft = A.take<int>(2 * NL);
-  const size_t o_BCF = A.take<float>((size_t)12 * NL);
+  const size_t o_BCF = A.take<float>((size_t)8 * NL);
   const size_t o_B = A.take<double>((size_t)FB_FB0 * NBP);
   const size_t o_E = A.take<double>((size_t)22 * NEP);
   const size_t o_es = A.take<int>(2 * NL + 2 * blk_off.size());
