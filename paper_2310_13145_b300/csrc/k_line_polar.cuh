@@ -673,6 +673,50 @@ __device__ __forceinline__ void pol_start(const Dev &S, int k, long long it, dou
   ic = 1.0 / S.B[FB_C * NBP + it];
 }
 
+// Finish ring: a lane whose solve is done records what the outputs need
+// (flows, FP32 flow gradients and the last step for the first-order update,
+// cos/sin, V_i, V_j, d, the angle targets, item and slots) and the warp
+// writes the outputs of 32 records at a time with every lane active.  Per
+// warp POL_QF records in dynamic shared memory, laid out for all warps of
+// the block as doubles [warp][12][QF], floats [warp][15][QF], ints
+// [warp][3][QF]; the record fields:
+//   doubles 0-3 flows a_r, 4 cos, 5 sin, 6 V_i, 7 V_j, 8 d, 9 step in d, 10-11 t_6, t_7
+//   floats 0-11 grad a_r (FP32, r * 3 + i), 12-14 the step in x (FP32)
+//   ints 0 item, 1-2 slots of the from / to end
+constexpr int POL_QF = 64;
+constexpr int POL_FD = 12, POL_FF = 15, POL_FI = 3;
+__host__ __device__ constexpr size_t pol_dyn_smem(int bs) {
+  return (size_t)(bs / 32) * POL_QF * (POL_FD * sizeof(double) + POL_FF * sizeof(float) + POL_FI * sizeof(int));
+}
+
+// outputs of finish record sl: flows to first order after the final step,
+// the W-form iterate (w_i, w_j, wR, wI, theta_i, theta_j) and the line-end
+// rows (the slacks, multipliers and penalty are written by the lane itself)
+__device__ __forceinline__ void pol_finish_out(const Dev &S, const double *fd, const float *ff, const int *fi,
+                                               int sl) {
+  const long long NBP = S.NBP, NEP = S.NEP;
+  const long long bp = fi[sl], lef = fi[POL_QF + sl], let = fi[2 * POL_QF + sl];
+  const float fx0 = ff[12 * POL_QF + sl], fx1 = ff[13 * POL_QF + sl], fx2 = ff[14 * POL_QF + sl];
+  double a[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    a[r] = fd[r * POL_QF + sl] + (double)(ff[(3 * r) * POL_QF + sl] * fx0 + ff[(3 * r + 1) * POL_QF + sl] * fx1 +
+                                          ff[(3 * r + 2) * POL_QF + sl] * fx2);
+  const double c0 = fd[4 * POL_QF + sl], s0 = fd[5 * POL_QF + sl], dx2 = fd[9 * POL_QF + sl];
+  const double c = c0 - s0 * dx2, sn = s0 + c0 * dx2;
+  const double Vi = fd[6 * POL_QF + sl], Vj = fd[7 * POL_QF + sl], d = fd[8 * POL_QF + sl];
+  const double Pv = Vi * Vj, tm = 0.5 * (fd[10 * POL_QF + sl] + fd[11 * POL_QF + sl]);
+  const double v6[6] = {Vi * Vi, Vj * Vj, Pv * c, Pv * sn, tm + 0.5 * d, tm - 0.5 * d};
+#pragma unroll
+  for (int i = 0; i < 6; ++i) S.B[(FB_V0 + i) * NBP + bp] = v6[i];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) S.EA[erow_u(r) * NEP + (erow_end(r) ? let : lef)] = a[r];
+  S.EA[2 * NEP + lef] = v6[0];
+  S.EA[2 * NEP + let] = v6[1];
+  S.EA[3 * NEP + lef] = v6[4];
+  S.EA[3 * NEP + let] = v6[5];
+}
+
 template <int BS>
 __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   const unsigned FULL = 0xffffffffu;
@@ -691,6 +735,15 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   __shared__ int qk[BS / 32][QN];
   int qhead = 0, qcount = 0;  // warp-uniform
   bool drained = false;       // warp-uniform: the work counter has passed NBP
+  extern __shared__ double pol_dsm[];
+  double *frd = pol_dsm + (size_t)wib * POL_FD * POL_QF;
+  float *frf = (float *)(pol_dsm + (size_t)(BS / 32) * POL_FD * POL_QF) + (size_t)wib * POL_FF * POL_QF;
+  int *fri = (int *)(pol_dsm + (size_t)(BS / 32) * POL_FD * POL_QF) + (size_t)(BS / 32) * POL_FF * POL_QF +
+             (size_t)wib * POL_FI * POL_QF;
+  __shared__ int ftail[BS / 32];  // records pushed by each warp (monotone)
+  int fhead = 0;                  // warp-uniform: records written out
+  if (lane == 0) ftail[wib] = 0;
+  __syncwarp();
   const long long NBP = S.NBP, NL = S.NL, NEP = S.NEP;
   const long long tail = 2LL * gridDim.x * BS;
   const double eta = S.prm.eta;
@@ -839,7 +892,11 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
       qhead = (qhead + used) & (QN - 1);
       qcount -= used;
     }
-    if (__ballot_sync(FULL, active) == 0) break;
+    if (__ballot_sync(FULL, active) == 0) {
+      __syncwarp();
+      if (lane < ftail[wib] - fhead) pol_finish_out(S, frd, frf, fri, (fhead + lane) & (POL_QF - 1));
+      break;
+    }
     if (active) {
       // one full evaluation per trip: at a pending trial point (then the
       // ratio test), else at the current point when it moved
@@ -896,27 +953,34 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         // after a converged tiny final step (h_k in FP64 from grad g_k, so
         // that it matches the slack step taken from the same gradient), a
         // fresh evaluation otherwise
+        // (the flows and cos/sin themselves are formed from the base values
+        // ab, cb, sb and the step fx, dxs by the finish ring: with dx <= 1e-8
+        // the FP32 product carries ~1e-15 absolute error)
         const double dx0 = v[0] - L.v[0], dx1 = v[1] - L.v[1], dx2 = v[2] - L.v[2];
         const long long b8 = __double_as_longlong(1e-8);
         const bool tiny = conv && abs_bits(dx0) <= b8 && abs_bits(dx1) <= b8 && abs_bits(dx2) <= b8;
-        double a[4], c, sn, h[2];
+        double ab[4], cb, sb, dxs, h[2];
+        float fx[3];
         if (tiny) {
-          // (dx <= 1e-8: the FP32 product carries ~1e-15 absolute error)
-          const float fx0 = (float)dx0, fx1 = (float)dx1, fx2 = (float)dx2;
 #pragma unroll
-          for (int r = 0; r < 4; ++r)
-            a[r] = L.a[r] + (double)(L.da[r][0] * fx0 + L.da[r][1] * fx1 + L.da[r][2] * fx2);
-          c = L.c - L.s * dx2;
-          sn = L.s + L.c * dx2;
+          for (int r = 0; r < 4; ++r) ab[r] = L.a[r];
+          cb = L.c;
+          sb = L.s;
+          fx[0] = (float)dx0;
+          fx[1] = (float)dx1;
+          fx[2] = (float)dx2;
+          dxs = dx2;
 #pragma unroll
           for (int q = 0; q < 2; ++q)
             h[q] = L.h[q] + L.dg[q][0] * dx0 + L.dg[q][1] * dx1 + L.dg[q][2] * dx2 + (v[3 + q] - L.v[3 + q]);
         } else {
           const double ht0[2] = {0.0, 0.0};
-          pol_obj(K, P, v, a, c, sn, ht0, 0);
+          pol_obj(K, P, v, ab, cb, sb, ht0, 0);
+          fx[0] = fx[1] = fx[2] = 0.0f;
+          dxs = 0.0;
 #pragma unroll
           for (int q = 0; q < 2; ++q)
-            h[q] = a[2 * q] * a[2 * q] + a[2 * q + 1] * a[2 * q + 1] - K.rate2 + v[3 + q];
+            h[q] = ab[2 * q] * ab[2 * q] + ab[2 * q + 1] * ab[2 * q + 1] - K.rate2 + v[3 + q];
         }
         // equality multiplier step on h_k = p_k^2 + q_k^2 + sigma_k - rate^2
         long long bh = 0;
@@ -930,22 +994,36 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         ++al;
         const bool done = le_nn(hn, eta) && conv;
         if (done || al >= K_AL) {
-          const double Pv = v[0] * v[1], tm = 0.5 * (P.tg[6] + P.tg[7]);
-          const double v8[8] = {v[0] * v[0], v[1] * v[1], Pv * c, Pv * sn, tm + 0.5 * v[2], tm - 0.5 * v[2],
-                                v[3], v[4]};
-#pragma unroll
-          for (int i = 0; i < 8; ++i) S.B[(FB_V0 + i) * NBP + bp] = v8[i];
+          S.B[(FB_V0 + 6) * NBP + bp] = v[3];
+          S.B[(FB_V0 + 7) * NBP + bp] = v[4];
           S.B[(FB_MU0 + 0) * NBP + bp] = 0.0;
           S.B[(FB_MU0 + 1) * NBP + bp] = 0.0;
           S.B[(FB_MU0 + 2) * NBP + bp] = P.mu[0];
           S.B[(FB_MU0 + 3) * NBP + bp] = P.mu[1];
           S.B[FB_C * NBP + bp] = P.c;
+          {
+            const int sl = atomicAdd(&ftail[wib], 1) & (POL_QF - 1);
 #pragma unroll
-          for (int r = 0; r < 4; ++r) S.EA[erow_u(r) * NEP + (erow_end(r) ? let : lef)] = a[r];
-          S.EA[2 * NEP + lef] = v8[0];
-          S.EA[2 * NEP + let] = v8[1];
-          S.EA[3 * NEP + lef] = v8[4];
-          S.EA[3 * NEP + let] = v8[5];
+            for (int r = 0; r < 4; ++r) frd[r * POL_QF + sl] = ab[r];
+            frd[4 * POL_QF + sl] = cb;
+            frd[5 * POL_QF + sl] = sb;
+            frd[6 * POL_QF + sl] = v[0];
+            frd[7 * POL_QF + sl] = v[1];
+            frd[8 * POL_QF + sl] = v[2];
+            frd[9 * POL_QF + sl] = dxs;
+            frd[10 * POL_QF + sl] = P.tg[6];
+            frd[11 * POL_QF + sl] = P.tg[7];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int i = 0; i < 3; ++i) frf[(3 * r + i) * POL_QF + sl] = L.da[r][i];
+            frf[12 * POL_QF + sl] = fx[0];
+            frf[13 * POL_QF + sl] = fx[1];
+            frf[14 * POL_QF + sl] = fx[2];
+            fri[sl] = (int)bp;
+            fri[POL_QF + sl] = (int)lef;
+            fri[2 * POL_QF + sl] = (int)let;
+          }
           acc_nw += (unsigned long long)newton;
           acc_al += (unsigned long long)al;
           acc_cap += done ? 0ull : 1ull;
@@ -961,6 +1039,13 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           need_full = true;
         }
       }
+    }
+    // the outputs of 32 finish records, with every lane active
+    __syncwarp();
+    if (ftail[wib] - fhead >= 32) {
+      pol_finish_out(S, frd, frf, fri, (fhead + lane) & (POL_QF - 1));
+      fhead += 32;
+      __syncwarp();
     }
   }
 }

@@ -184,7 +184,6 @@ void launch_gen(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.gen, 
 void launch_bus(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.bus, k_bus, h->ngr_up, s, h->dev); }
 void launch_ucbar(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.ucbar, k_ucbar, h->ngr_gp, s, h->dev); }
 
-// resident blocks of the persistent line kernel for block size bs
 // the cos/sin table of the polar line kernel (see g_trig)
 cudaError_t upload_trig() {
   std::vector<double> t(2 * (2 * TRIG_K + 1));
@@ -195,15 +194,22 @@ cudaError_t upload_trig() {
   return cudaMemcpyToSymbol(g_trig, t.data(), t.size() * sizeof(double));
 }
 
+// resident blocks of the persistent line kernel for block size bs (the
+// polar kernel's finish ring lives in dynamic shared memory: opted in here)
 int line_grid(ucac_handle *h, int bs) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 1;
   cudaError_t e;
   const bool polar = h->prm.line_form == UCAC_LINE_POLAR;
-#define UCAC_OCC(B)                                                                                 \
-  e = polar ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_polar<B>, B, 0)         \
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_branch<B>, B, 0)
+#define UCAC_OCC(B)                                                                                              \
+  if (polar) {                                                                                                   \
+    e = cudaFuncSetAttribute(k_line_polar<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, pol_dyn_smem(B));     \
+    if (e == cudaSuccess)                                                                                        \
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_polar<B>, B, pol_dyn_smem(B));          \
+  } else {                                                                                                       \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_branch<B>, B, 0);                               \
+  }
   switch (bs) {
     case 32: UCAC_OCC(32); break;
     case 128: UCAC_OCC(128); break;
@@ -221,13 +227,13 @@ void launch_line(ucac_handle *h, cudaStream_t s) {
   const int g = h->grid_branch;
   switch (h->tune.line) {
     case 32:
-      if (polar) k_line_polar<32><<<g, 32, 0, s>>>(h->dev); else k_branch<32><<<g, 32, 0, s>>>(h->dev);
+      if (polar) k_line_polar<32><<<g, 32, pol_dyn_smem(32), s>>>(h->dev); else k_branch<32><<<g, 32, 0, s>>>(h->dev);
       break;
     case 128:
-      if (polar) k_line_polar<128><<<g, 128, 0, s>>>(h->dev); else k_branch<128><<<g, 128, 0, s>>>(h->dev);
+      if (polar) k_line_polar<128><<<g, 128, pol_dyn_smem(128), s>>>(h->dev); else k_branch<128><<<g, 128, 0, s>>>(h->dev);
       break;
     default:
-      if (polar) k_line_polar<64><<<g, 64, 0, s>>>(h->dev); else k_branch<64><<<g, 64, 0, s>>>(h->dev);
+      if (polar) k_line_polar<64><<<g, 64, pol_dyn_smem(64), s>>>(h->dev); else k_branch<64><<<g, 64, 0, s>>>(h->dev);
       break;
   }
 }
