@@ -192,8 +192,18 @@ __device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, double (
   return f;
 }
 
-// objective, x-gradient gx (FP64) and the x-Hessian without the c grad grad^T
-// terms (FP32 Hf, or FP64 Hd when a slack is held at zero) at v; fills L.
+// objective, reduced x-gradient gx (FP64; the slack terms m_k grad g_k are
+// left out -- pol_iter adds them where a slack is held at its bound) and the
+// x-Hessian without the c grad grad^T terms (FP32 Hf, or FP64 Hd when a slack
+// is held at zero) at v; fills L.  The gradients come from sums over the
+// rows, with grad a_r = (2 q_r V_i [r < 2] + V_j E_r, V_i E_r + 2 q_r V_j
+// [r >= 2], V_i V_j Ed_r):
+//   gx = (2 V_i (pe_0 q_0 + pe_1 q_1) + V_j sum pe_r E_r,
+//         2 V_j (pe_2 q_2 + pe_3 q_3) + V_i sum pe_r E_r, V_i V_j sum pe_r Ed_r)
+//        + (angle/voltage rows), pe_r = rho_pq (a_r - t_r);
+//   grad g_0 = (4 V_i A_q + 2 V_j A_E, 2 V_i A_E, 2 V_i V_j A_Ed) and
+//   grad g_1 = (2 V_j A_E, 4 V_j A_q + 2 V_i A_E, 2 V_i V_j A_Ed) with the
+//   end's sums A_E = sum a_r E_r, A_Ed = sum a_r Ed_r, A_q = sum a_r q_r.
 // With m_k = mu_k + c h_k the x-Hessian is
 //   sum_r (w_r grad a_r grad a_r^T + u_r hess a_r) + (angle/voltage rows)
 //   + sum_k c grad g_k grad g_k^T,
@@ -210,9 +220,9 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
   for (int i = 0; i < POL_NV; ++i) L.v[i] = v[i];
   const double Pv = Vi * Vj, Vi2 = Vi * Vi, Vj2 = Vj * Vj;
   const float fVi = (float)Vi, fVj = (float)Vj, fP = fVi * fVj;
+  const double Vi2x = 2.0 * Vi, Vj2x = 2.0 * Vj;
   double f = 0.0;
-  gx[0] = gx[1] = gx[2] = 0.0;
-  double da[4][3], E[4], Ed[4], pe[4];
+  double E[4], Ed[4], pe[4];
   float fE[4], fEd[4];
   // FP32 gradient of the flow (for the FP32 Hessian and the first-order
   // finish) from FP32 cos/sin and constants: two conversions per
@@ -228,9 +238,6 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
     const double e = a - P.tg[r];
     pe[r] = P.rpq * e;
     spe = fma(pe[r], e, spe);
-    da[r][0] = r < 2 ? 2.0 * K.q[r] * Vi + Vj * E[r] : Vj * E[r];
-    da[r][1] = r < 2 ? Vi * E[r] : 2.0 * K.q[r] * Vj + Vi * E[r];
-    da[r][2] = Pv * Ed[r];
     L.da[r][0] = r < 2 ? 2.0f * K.fq(r) * fVi + fVj * fE[r] : fVj * fE[r];
     L.da[r][1] = r < 2 ? fVi * fE[r] : 2.0f * K.fq(r) * fVj + fVi * fE[r];
     L.da[r][2] = fP * fEd[r];
@@ -253,11 +260,17 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
     f += h * (P.mu[k] + 0.5 * P.c * h);
     L.m[k] = m;
     L.h[k] = h;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      L.dg[k][i] = 2.0 * (L.a[r0] * da[r0][i] + L.a[r1] * da[r1][i]);
-      gx[i] += m * L.dg[k][i];
+    const double AE = fma(L.a[r0], E[r0], L.a[r1] * E[r1]);
+    const double AEd = fma(L.a[r0], Ed[r0], L.a[r1] * Ed[r1]);
+    const double Aq = fma(L.a[r0], K.q[r0], L.a[r1] * K.q[r1]);
+    if (k == 0) {
+      L.dg[0][0] = fma(2.0 * Vi2x, Aq, Vj2x * AE);
+      L.dg[0][1] = Vi2x * AE;
+    } else {
+      L.dg[1][0] = Vj2x * AE;
+      L.dg[1][1] = fma(2.0 * Vj2x, Aq, Vi2x * AE);
     }
+    L.dg[k][2] = 2.0 * Pv * AEd;
     // a free slack's optimum has m_k = 0, so the Newton model takes the
     // reduced x-Hessian there; m_k hess g_k stays only for a slack that may
     // be held at zero
@@ -266,13 +279,18 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
     mhk[k] = held ? m : 0.0;
     lim = lim || held;
   }
+  {
+    double SE = pe[0] * E[0], SEd = pe[0] * Ed[0];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
-#pragma unroll
-    for (int i = 0; i < 3; ++i) gx[i] += pe[r] * da[r][i];
-  gx[0] += 2.0 * P.rva * ewi * Vi;
-  gx[1] += 2.0 * P.rva * ewj * Vj;
-  gx[2] += 0.5 * P.rva * et;
+    for (int r = 1; r < 4; ++r) {
+      SE = fma(pe[r], E[r], SE);
+      SEd = fma(pe[r], Ed[r], SEd);
+    }
+    const double Sq0 = fma(pe[0], K.q[0], pe[1] * K.q[1]), Sq1 = fma(pe[2], K.q[2], pe[3] * K.q[3]);
+    gx[0] = fma(Vi2x, Sq0, Vj * SE) + 2.0 * P.rva * ewi * Vi;
+    gx[1] = fma(Vj2x, Sq1, Vi * SE) + 2.0 * P.rva * ewj * Vj;
+    gx[2] = Pv * SEd + 0.5 * P.rva * et;
+  }
   L.lim = lim;
   // packed symmetric index: 0:(0,0) 1:(0,1) 2:(0,2) 3:(1,1) 4:(1,2) 5:(2,2)
   const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
@@ -293,12 +311,15 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
     Hf[3] += rva * (4.0f * fVj * fVj + 2.0f * (float)ewj);
     Hf[5] += 0.5f * rva;
   } else {
-    double w[4], u[4];
+    double w[4], u[4], da[4][3];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const double mh = mhk[r >> 1];
       w[r] = P.rpq + 2.0 * mh;
       u[r] = pe[r] + 2.0 * mh * L.a[r];
+      da[r][0] = r < 2 ? fma(K.q[r], Vi2x, Vj * E[r]) : Vj * E[r];
+      da[r][1] = r < 2 ? Vi * E[r] : fma(K.q[r], Vj2x, Vi * E[r]);
+      da[r][2] = Pv * Ed[r];
     }
 #pragma unroll
     for (int q = 0; q < 6; ++q) Hd[q] = 0.0;
@@ -361,7 +382,16 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   accepted = false;
   counted = 0;
   const double c = P.c;
-  const double gr[POL_NV] = {gx[0], gx[1], gx[2], L.m[0], L.m[1]};
+  // gx is the reduced x-gradient; the full gradient gr over v adds
+  // m_k grad g_k to it -- formed only near a bound and for the model of a
+  // trust-region step
+  double gr[POL_NV];
+  gr[3] = L.m[0];
+  gr[4] = L.m[1];
+  auto full_grad = [&]() {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) gr[i] = fma(L.m[0], L.dg[0][i], fma(L.m[1], L.dg[1][i], gx[i]));
+  };
   double xmax = 0.0, dlo[POL_NV], dhi[POL_NV];
   T hmax = T(0);
   // a variable can only be epsilon-active within 1e-6 of a bound (epsilon
@@ -369,7 +399,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   // v lies in its box, so dlo, dhi >= 0 and their order is the signed order
   // of their bit patterns: the test runs on the integer units (a negative
   // or NaN operand can only make it pass, which is the safe side)
-  bool near = false;
+  bool near = false, prox = false;  // prox: an x variable within 1e-6 of a bound
   const long long b6 = __double_as_longlong(1e-6), ABS = 0x7fffffffffffffffLL;
   long long bx = 0;
 #pragma unroll
@@ -381,11 +411,20 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
       bx = b > bx ? b : bx;
       const T h = hq(H, i, i);
       hmax = hmax > h ? hmax : h;
+      prox = prox || __double_as_longlong(dlo[i]) <= b6 || __double_as_longlong(dhi[i]) <= b6;
+    } else {
+      near = near || (__double_as_longlong(dlo[i]) <= b6 && __double_as_longlong(gr[i]) > 0);
     }
-    const long long bg = __double_as_longlong(gr[i]);
-    near = near || (__double_as_longlong(dlo[i]) <= b6 && bg > 0) || (__double_as_longlong(dhi[i]) <= b6 && bg < 0);
   }
   xmax = __longlong_as_double(bx);  // max |x_i| (order of non-negative doubles = order of their bits)
+  if (prox) {
+    full_grad();
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const long long bg = __double_as_longlong(gr[i]);
+      near = near || (__double_as_longlong(dlo[i]) <= b6 && bg > 0) || (__double_as_longlong(dhi[i]) <= b6 && bg < 0);
+    }
+  }
   bool act[POL_NV];
   double d[POL_NV];
 #pragma unroll
@@ -394,6 +433,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     d[i] = 0.0;
   }
   if (near) {
+    if (!prox) full_grad();
     // epsilon: largest clamped diagonal Newton step, in T
     T epst = T(0);
 #pragma unroll
@@ -432,11 +472,16 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   bool stat = true;
   const long long bom = __double_as_longlong(omega);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    rg[i] = gx[i];
+  for (int i = 0; i < 3; ++i) rg[i] = gx[i];
+  if (near) {  // a slack held at its bound keeps its m_k grad g_k
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (!act[3 + k]) rg[i] -= L.m[k] * L.dg[k][i];
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (act[3 + k]) rg[i] = fma(L.m[k], L.dg[k][i], rg[i]);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
     const long long br = __double_as_longlong(rg[i]);
     const long long bd = __double_as_longlong(br > 0 ? dlo[i] : dhi[i]);
     stat = stat && ((br & ABS) <= bom || bd <= bom);
@@ -540,14 +585,14 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   };
   if (lm == T(0)) {
     // with no bound active d minimises the quadratic model exactly, where
-    // the model decrease is -(1/2) gr . d
+    // the model decrease is -(1/2) gr . d = -(1/2) (gx . dx - sum_k m_k^2 / c)
+    // (the free slacks' steps d_k = -m_k / c - grad g_k . dx)
     double predN;
     if (near) {
       predN = model(d);
     } else {
-      double lin = 0.0;
-#pragma unroll
-      for (int i = 0; i < POL_NV; ++i) lin += gr[i] * d[i];
+      const double lin = fma(gx[0], d[0], fma(gx[1], d[1], gx[2] * d[2])) -
+                         P.ic * fma(L.m[0], L.m[0], L.m[1] * L.m[1]);
       predN = -0.5 * lin;
     }
     if (le_nn(dn, 1e-9 * (1.0 + xmax)) || le_nn(predN, 1e-12 * (1.0 + fabs(f)))) {
@@ -579,6 +624,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     sg[i] = vt[i] - v[i];
     if (i < 3) smax = fmax(smax, fabs(sg[i]));
   }
+  full_grad();
   const double pred = model(sg);
   // predicted h_k of the trial step; free slacks absorb the remainder of
   // g_k exactly, a slack held at zero gets the correction
