@@ -205,7 +205,8 @@ int ucac_state_import(ucac_handle *h, int32_t instance, const double *buf, size_
  * graph) and returns each kernel's average device time per sweep, timed
  * with CUDA events on the handle's stream; when n_sweeps >= 2 the first
  * sweep is untimed (it carries the first-launch costs of the one-by-one
- * launches).  ms[] receives UCAC_N_KERNELS values in the order of
+ * launches), and each sweep is queued behind a ~0.2 ms device delay so that
+ * no host launch latency enters the times.  ms[] receives UCAC_N_KERNELS values in the order of
  * ucac_kernel_name(): k_ucdp, k_gen, k_branch (the line kernel of either
  * form), k_bus, k_ucbar, k_finish, k_mlp (0 unless the learned warm start is
  * enabled).  Synchronises.

@@ -117,21 +117,6 @@ __device__ __forceinline__ double pol_lo(const PolK &K, int i) {
 __device__ __forceinline__ double pol_hi(const PolK &K, int i) {
   return i == 0 ? K.hi0 : (i == 1 ? K.hi1 : (i == 2 ? 3.14159265358979 : INFINITY));
 }
-// Compares and clamps on the integer units.  B300's FP64 pipe also runs
-// FP64 compares and min/max, at the FP64 rate; the signed 64-bit key below
-// orders non-NaN doubles like their values (a negative double's magnitude
-// bits are flipped), so the same decisions cost only integer operations.
-__device__ __forceinline__ long long dkey(double x) {
-  const long long b = __double_as_longlong(x);
-  return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
-}
-__device__ __forceinline__ double dunkey(long long k) { return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k); }
-// x <= y for a non-negative y: the bit patterns compare the same way (a
-// negative x, -0 included, has a negative pattern)
-__device__ __forceinline__ bool le_nn(double x, double y) { return __double_as_longlong(x) <= __double_as_longlong(y); }
-// max |x_i| of non-negative magnitudes, by bit pattern
-__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
-
 // projection of variable i onto its bounds (a slack has only its lower
 // bound); the same values as fmin(fmax(x, lo), hi) and fmax(x, 0)
 __device__ __forceinline__ double pol_clamp(const PolK &K, int i, double x) {

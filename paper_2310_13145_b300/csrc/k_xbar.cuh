@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
 struct FaceRes {
   double x[3], f;
   bool inbox, kkt;
+  int next[3];  // block principal pivoting: the face to try next
 };
 
 __device__ __forceinline__ FaceRes solve_face(int n, const int (&st)[3], const double (&H)[3][3],
@@ -280,25 +281,34 @@ __device__ __forceinline__ FaceRes solve_face(int n, const int (&st)[3], const d
     }
     rhs[i] = fi ? r : ((st[i] == 2) ? 1.0 : 0.0);
   }
-  const double L00 = sqrt(A[0][0]), i00 = 1.0 / L00;
-  const double L10 = A[1][0] * i00, L20 = A[2][0] * i00;
-  const double L11 = sqrt(A[1][1] - L10 * L10), i11 = 1.0 / L11;
-  const double L21 = (A[2][1] - L20 * L10) * i11;
-  const double L22 = sqrt(A[2][2] - L20 * L20 - L21 * L21), i22 = 1.0 / L22;
-  const double y0 = rhs[0] * i00;
-  const double y1 = (rhs[1] - L10 * y0) * i11;
-  const double y2 = (rhs[2] - L20 * y0 - L21 * y1) * i22;
-  R.x[2] = y2 * i22;
-  R.x[1] = (y1 - L21 * R.x[2]) * i11;
-  R.x[0] = (y0 - L10 * R.x[1] - L20 * R.x[2]) * i00;
+  // A = L D L^T (no square roots: three reciprocals instead of three square
+  // roots and three reciprocals of the Cholesky factor)
+  const double iD0 = 1.0 / A[0][0];
+  const double L10 = A[1][0] * iD0, L20 = A[2][0] * iD0;
+  const double iD1 = 1.0 / (A[1][1] - L10 * A[1][0]);
+  const double A21r = A[2][1] - L20 * A[1][0];
+  const double L21 = A21r * iD1;
+  const double iD2 = 1.0 / (A[2][2] - L20 * A[2][0] - L21 * A21r);
+  const double y0 = rhs[0];
+  const double y1 = rhs[1] - L10 * y0;
+  const double y2 = rhs[2] - L20 * y0 - L21 * y1;
+  R.x[2] = y2 * iD2;
+  R.x[1] = y1 * iD1 - L21 * R.x[2];
+  R.x[0] = y0 * iD0 - L10 * R.x[1] - L20 * R.x[2];
   R.inbox = true;
   R.kkt = true;
   R.f = 0.0;
+  // (box and sign tests on the integer units, see dkey)
+  const long long klo = dkey(-tolx), khi = dkey(1.0 + tolx);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
+    R.next[i] = st[i];
     if (i >= n) continue;
     if (st[i] != 0) R.x[i] = (st[i] == 2) ? 1.0 : 0.0;
-    if (!(R.x[i] >= -tolx && R.x[i] <= 1.0 + tolx)) R.inbox = false;
+    const long long kx = dkey(R.x[i]);
+    if (!(kx >= klo && kx <= khi)) R.inbox = false;  // (a NaN's key lies outside)
+    if (st[i] == 0 && kx < klo) R.next[i] = 1;       // left the box: fix at the bound crossed
+    if (st[i] == 0 && kx > khi) R.next[i] = 2;
   }
   if (n == 2) R.x[2] = 0.0;
 #pragma unroll
@@ -310,32 +320,46 @@ __device__ __forceinline__ FaceRes solve_face(int n, const int (&st)[3], const d
       if (j < n) t += H[i][j] * R.x[j];
     const double gr = t - gv[i];
     R.f += 0.5 * R.x[i] * t - gv[i] * R.x[i];
-    if (st[i] == 1 && gr < -tolg) R.kkt = false;
-    if (st[i] == 2 && gr > tolg) R.kkt = false;
+    if (st[i] == 1 && dkey(gr) < dkey(-tolg)) {
+      R.kkt = false;
+      R.next[i] = 0;  // the gradient pulls it off its bound: free it
+    }
+    if (st[i] == 2 && dkey(gr) > dkey(tolg)) {
+      R.kkt = false;
+      R.next[i] = 0;
+    }
   }
   return R;
 }
 
 __device__ __forceinline__ void boxqp3(int n, const double (&H)[3][3], const double (&gv)[3], const double (&x0)[3],
                                        double (&x)[3]) {
-  double scale = 0.0;
+  long long bs = 0;  // max |gv_i|, |H_ij| by bit pattern
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    if (i < n) scale = fmax(scale, fabs(gv[i]));
+    if (i < n) bs = abs_bits(gv[i]) > bs ? abs_bits(gv[i]) : bs;
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      if (i < n && j < n) scale = fmax(scale, fabs(H[i][j]));
+      if (i < n && j < n) bs = abs_bits(H[i][j]) > bs ? abs_bits(H[i][j]) : bs;
   }
-  const double tolx = 1e-12, tolg = 1e-12 * scale;
+  const double tolx = 1e-12, tolg = 1e-12 * __longlong_as_double(bs);
   {
+    // the previous iterate's face, then up to three block-principal-pivoting
+    // steps from it: H is positive definite, so a face whose point is in the
+    // box with KKT-consistent signs holds the unique minimiser
     int st[3];
+    const long long k0 = dkey(0.0), k1 = dkey(1.0);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) st[i] = (i >= n) ? 1 : (x0[i] <= 0.0 ? 1 : (x0[i] >= 1.0 ? 2 : 0));
-    const FaceRes R = solve_face(n, st, H, gv, tolx, tolg);
-    if (R.inbox && R.kkt) {
+    for (int i = 0; i < 3; ++i) st[i] = (i >= n) ? 1 : (dkey(x0[i]) <= k0 ? 1 : (dkey(x0[i]) >= k1 ? 2 : 0));
+    for (int it = 0; it < 4; ++it) {
+      const FaceRes R = solve_face(n, st, H, gv, tolx, tolg);
+      if (R.inbox && R.kkt) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) x[i] = clampd(R.x[i], 0.0, 1.0);
-      return;
+        for (int i = 0; i < 3; ++i) x[i] = clampd(R.x[i], 0.0, 1.0);
+        return;
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) st[i] = R.next[i];
     }
   }
   double best = INFINITY, bestf = INFINITY;

@@ -929,6 +929,17 @@ int ucac_state_import(ucac_handle *h, int32_t k, const double *buf, size_t n) {
   return UCAC_OK;
 }
 
+namespace {
+// holds the stream for a fixed number of clock cycles (bounded by
+// construction), so that the host has queued a whole sweep of launches before
+// the device reaches them and no launch latency enters the event deltas
+__global__ void k_delay(long long cycles) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < cycles) {
+  }
+}
+}  // namespace
+
 int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
   if (!h || !ms || n_sweeps < 1) return fail(h, UCAC_E_ARG, "bad arguments");
   // events around each launch of one sweep, in launch order:
@@ -940,6 +951,7 @@ int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
   const Dev &D = h->dev;
   cudaStream_t s = h->stream;
   for (int it = 0; it < n_sweeps; ++it) {
+    k_delay<<<1, 1, 0, s>>>(400000LL);  // ~0.2 ms at 2 GHz
     CK(cudaEventRecord(ev[0], s));
     launch_ucdp(h, s);
     CK(cudaEventRecord(ev[1], s));
