@@ -315,10 +315,12 @@ int ucac_uc_warm_start(ucac_handle *h, int32_t relax_sweeps, double p_frac);
  * buffers (training data: label = (x_after_sweep - x_before) / |r|).
  * ucac_set_warm_start: params (HOST, FP32) enable the learned start: every
  * sweep then runs the network over all line-periods before the line kernel,
- * and a line solve starts from the proposal when the proposal's objective is
- * lower than the previous iterate's (polar form; the W-form line solver
- * always starts from the previous iterate).  NULL disables it.  Re-captures
- * the sweep graph; synchronises.
+ * and a line solve starts from the proposal when the proposal's objective
+ * (slacks at their minimiser) is lower than the previous iterate's, as the
+ * network kernel's epilogue estimates it in FP32 from the differences of the
+ * objective's terms (polar form; the W-form line solver always starts from
+ * the previous iterate).  NULL disables it.  Re-captures the sweep graph;
+ * synchronises.
  * ucac_warm_start_stats: line solves of instance k started from the
  * proposal since the last ucac_set_warm_start; *mma_error (may be NULL) is
  * non-zero if a tensor-core wait timed out.

@@ -124,8 +124,9 @@ struct Dev {
   double *part_up;    // [granules of bus-periods][NQ]
   double *part_gp;    // [granules of gen-periods][NQ]
   long long *bstat;   // [K][3]: Newton iterations, AL rounds, capped solves (line kernel, per sweep)
-  // learned warm start: proposed change of each line-period's iterate
-  // [6][NBP] (W coordinates, written by the MLP kernel of the same sweep),
+  // learned warm start: the start of each line-period's solve [4][NBP]
+  // written by the MLP kernel of the same sweep (1 when the network's
+  // proposal is taken, then its changes of V_i, V_j, d from the plain start),
   // enabled flag, and the count of line solves started from it [K]
   const float *prop;
   int warm;

@@ -884,30 +884,14 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           P.mu[0] = S.B[(FB_MU0 + 2) * NBP + bp];
           P.mu[1] = S.B[(FB_MU0 + 3) * NBP + bp];
           P.c = S.B[FB_C * NBP + bp];
-          if (S.warm) {
-            // learned warm start: the network's proposal x0 + s y (W
-            // coordinates) is taken when its objective is below the plain
-            // start's, both with the slacks at their exact minimiser; the
-            // Newton solve that follows is the same either way
-            const double ht[2] = {-P.mu[0] * P.ic, -P.mu[1] * P.ic};
-            double vm[POL_NV];
-            const double wi = S.B[(FB_V0 + 0) * NBP + bp] + (double)S.prop[0 * NBP + bp];
-            const double wj = S.B[(FB_V0 + 1) * NBP + bp] + (double)S.prop[1 * NBP + bp];
-            const double thi = S.B[(FB_V0 + 4) * NBP + bp] + (double)S.prop[4 * NBP + bp];
-            const double thj = S.B[(FB_V0 + 5) * NBP + bp] + (double)S.prop[5 * NBP + bp];
-            vm[0] = clampd(sqrt(fmax(wi, 0.0)), K.lo0, K.hi0);
-            vm[1] = clampd(sqrt(fmax(wj, 0.0)), K.lo1, K.hi1);
-            vm[2] = clampd(thi - thj, pol_lo(K, 2), pol_hi(K, 2));
-            vm[3] = v[3];
-            vm[4] = v[4];
-            double at[4], ct, st;
-            const double fp = pol_obj(K, P, v, at, ct, st, ht, 3);
-            const double fm = pol_obj(K, P, vm, at, ct, st, ht, 3);
-            if (fm < fp) {
-#pragma unroll
-              for (int i = 0; i < POL_NV; ++i) v[i] = vm[i];
-              ++acc_w;
-            }
+          if (S.warm && S.prop[bp] != 0.0f) {
+            // learned warm start: the MLP kernel of this sweep chose the
+            // network's proposal over the plain start and left its changes
+            // of V_i, V_j, d; the Newton solve that follows is the same
+            v[0] = pol_clamp(K, 0, v[0] + (double)S.prop[1 * NBP + bp]);
+            v[1] = pol_clamp(K, 1, v[1] + (double)S.prop[2 * NBP + bp]);
+            v[2] = pol_clamp(K, 2, v[2] + (double)S.prop[3 * NBP + bp]);
+            ++acc_w;
           }
           const double rmax = fmax(I.rpq, I.rva);
           omega = S.prm.omega_rel * rmax;

@@ -32,10 +32,15 @@ constexpr int MLP_IN = 12, MLP_H = 64, MLP_OUT = 6;
 constexpr int MLP_OW1 = 0, MLP_OB1 = MLP_OW1 + MLP_H * MLP_IN, MLP_OW2 = MLP_OB1 + MLP_H,
               MLP_OB2 = MLP_OW2 + MLP_H * MLP_H, MLP_OW3 = MLP_OB2 + MLP_H, MLP_OB3 = MLP_OW3 + MLP_OUT * MLP_H,
               MLP_NPARAM = MLP_OB3 + MLP_OUT;
-// packed inference weights: BF16 W1 [64 x 16] (K padded), W2 [64 x 64],
-// W3 [16 x 64] (N padded) in the canonical layout, then FP32 b1, b2, b3 (16)
-constexpr int MLP_PK_W1 = 0, MLP_PK_W2 = 2048, MLP_PK_W3 = 2048 + 8192, MLP_PK_B = 2048 + 8192 + 2048,
-              MLP_PACK_BYTES = MLP_PK_B + 4 * (64 + 64 + 16);
+// packed inference weights in the canonical layout: BF16 W1 [64 x 16] (K
+// padded; columns 12, 13 hold b1 as a BF16 pair hi + lo), W2 [64 x 64], W3
+// [16 x 64] (N padded), B2 [64 x 16] (b2 as a pair in columns 12, 13, zero
+// elsewhere), then FP32 b1, b2, b3 (16).  The feature tile carries ones in
+// columns 12, 13, so layer 1 adds b1 inside its MMA and an extra 16-deep
+// MMA of the feature tile against B2 adds b2 to layer 2 (to ~2^-16 of the
+// bias: BF16 hi + lo)
+constexpr int MLP_PK_W1 = 0, MLP_PK_W2 = 2048, MLP_PK_W3 = 2048 + 8192, MLP_PK_B2 = 2048 + 8192 + 2048,
+              MLP_PK_B = MLP_PK_B2 + 2048, MLP_PACK_BYTES = MLP_PK_B + 4 * (64 + 64 + 16);
 
 // byte offset of element (row, k) of a K-major operand with KG 8-element K
 // groups: core matrix (row / 8, k / 8) is 128 contiguous bytes, 16 per row
@@ -45,9 +50,66 @@ __host__ __device__ __forceinline__ int canon_off(int row, int k, int KG) {
 
 // ---------------------------------------------------------------- features
 // Features of line-period (t, l) of instance I and the scale s; false when
-// the residual vanishes (the network then proposes no change).
+// the residual vanishes (the network then proposes no change).  The flows
+// and the residuals' subtractions are FP64 (the residual is a small
+// difference of O(1) values); the rest of the features, which the network
+// takes in BF16, is FP32 unless EXACT (the feature API, whose scale s is
+// compared with FP64 definitions).  aflow (may be NULL) receives the flows
+// and the line-limit values g_k = p_k^2 + q_k^2 - rate^2 (formed in FP64:
+// the difference is small against its terms) as aflow[4], aflow[5].
+template <bool EXACT>
 __device__ __forceinline__ bool line_features(const Dev &S, const Inst &I, long long bp, int t, int l,
-                                              float (&f)[MLP_IN], double &s) {
+                                              float (&f)[MLP_IN], double &s, float *aflow = nullptr) {
+  if (!EXACT) {
+    const long long NBP = S.NBP, NL = S.NL, NEP = S.NEP, lg = (long long)I.lo + l;
+    const double wi = S.B[(FB_V0 + 0) * NBP + bp], wj = S.B[(FB_V0 + 1) * NBP + bp];
+    const double wR = S.B[(FB_V0 + 2) * NBP + bp], wI = S.B[(FB_V0 + 3) * NBP + bp];
+    const double thi = S.B[(FB_V0 + 4) * NBP + bp], thj = S.B[(FB_V0 + 5) * NBP + bp];
+    double Y[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) Y[q] = S.BC[(BC_Y0 + q) * NL + lg];
+    const double a[4] = {Y[0] * wi + Y[2] * wR + Y[3] * wI, -Y[1] * wi - Y[3] * wR + Y[2] * wI,
+                         Y[4] * wj + Y[6] * wR - Y[7] * wI, -Y[5] * wj - Y[7] * wR - Y[6] * wI};
+    long long ef, et;
+    line_ends(S, I, t, lg, ef, et);
+    double tg[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) tg[r] = S.ET[erow_u(r) * NEP + (erow_end(r) ? et : ef)];
+    if (aflow) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) aflow[r] = (float)a[r];
+      const double rate2 = S.BC[BC_RATE2 * NL + lg];
+      aflow[4] = (float)(a[0] * a[0] + a[1] * a[1] - rate2);
+      aflow[5] = (float)(a[2] * a[2] + a[3] * a[3] - rate2);
+    }
+    const float g = (float)Y[2], b = (float)Y[3], iym = rsqrtf(g * g + b * b);
+    float res[7];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) res[r] = (float)(tg[r] - a[r]) * iym;
+    res[4] = (float)(tg[4] - wi);
+    res[5] = (float)(tg[5] - wj);
+    const double dth = thi - thj;
+    res[6] = (float)((tg[6] - tg[7]) - dth);
+    float n2 = 0.0f;
+#pragma unroll
+    for (int r = 0; r < 7; ++r) n2 = fmaf(res[r], res[r], n2);
+    const float sf = sqrtf(n2);
+    s = (double)sf;
+    f[0] = sqrtf(fmaxf((float)wi, 0.0f));
+    f[1] = sqrtf(fmaxf((float)wj, 0.0f));
+    f[2] = (float)dth;
+    f[3] = -g * iym;  // g / |y| (Y_ij = -y)
+    f[4] = -b * iym;  // b / |y|
+    if (!(sf > 1e-30f)) {
+#pragma unroll
+      for (int r = 0; r < 7; ++r) f[5 + r] = 0.0f;
+      return false;
+    }
+    const float is = __frcp_rn(sf);
+#pragma unroll
+    for (int r = 0; r < 7; ++r) f[5 + r] = res[r] * is;
+    return true;
+  }
   const long long NBP = S.NBP, NL = S.NL, NEP = S.NEP, lg = (long long)I.lo + l;
   const double wi = S.B[(FB_V0 + 0) * NBP + bp], wj = S.B[(FB_V0 + 1) * NBP + bp];
   const double wR = S.B[(FB_V0 + 2) * NBP + bp], wI = S.B[(FB_V0 + 3) * NBP + bp];
@@ -155,6 +217,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
+// inference: z sigma(z) = h + h tanh(h) with h = z / 2, on the hardware
+// tanh (relative error ~5e-4, below the BF16 rounding of the activation
+// that follows): three instructions instead of an exponential and an IEEE
+// division, 128 activations per row
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float silu_fast(float z) {
+  const float h = 0.5f * z;
+  return fmaf(h, tanh_approx(h), h);
+}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
@@ -171,9 +246,87 @@ __device__ __forceinline__ void st_row8(uint8_t *base, int row, int k0, int KG, 
   *reinterpret_cast<uint4 *>(base + canon_off(row, k0, KG)) = q;
 }
 
+// ------------------------------------------------------ start choice
+// Whether the polar line solve of row bp should start from the network's
+// proposal, and the proposal as changes (dVi, dVj, dd) of the plain start
+// V = sqrt(w), d = theta_i - theta_j.  The test is the sign of the change of
+// the line objective (slacks at their minimiser) between the two starts,
+// formed in FP32 from differences so that no term cancels: the flows change
+// by da_r = q_r d(V'^2) + dP E_r + P' dE_r with dE from the half-angle
+// formulas, the residual terms by rho da (e + da/2) with the plain residuals
+// e rebuilt from the features f and the scale s, and the line-limit terms
+// through the change of h = max(g, -mu/c).  A wrong choice between two
+// nearly equal starts costs only Newton steps: the solve polishes either to
+// the same tolerance.
+__device__ __forceinline__ bool warm_choice(const Dev &S, const Inst &I, long long bp, long long lg,
+                                            const float (&f)[16], float s, const float (&af)[6],
+                                            const float (&dw)[MLP_OUT], float &dVi, float &dVj, float &dd) {
+  const long long NBP = S.NBP, NL = S.NL;
+  const float Vi = f[0], Vj = f[1], d = f[2];
+  // proposal: w + dw, theta + dtheta, projected on the voltage bounds
+  const float lo0 = (float)S.BC[(BC_VB + 0) * NL + lg], hi0 = (float)S.BC[(BC_VB + 1) * NL + lg];
+  const float lo1 = (float)S.BC[(BC_VB + 2) * NL + lg], hi1 = (float)S.BC[(BC_VB + 3) * NL + lg];
+  const float wim = fmaxf(Vi * Vi + dw[0], 0.0f), wjm = fmaxf(Vj * Vj + dw[1], 0.0f);
+  dVi = fminf(fmaxf(Vi + __fdividef(dw[0], Vi + sqrtf(wim)), lo0), hi0) - Vi;
+  dVj = fminf(fmaxf(Vj + __fdividef(dw[1], Vj + sqrtf(wjm)), lo1), hi1) - Vj;
+  dd = dw[4] - dw[5];
+  const float dVi2 = dVi * (2.0f * Vi + dVi), dVj2 = dVj * (2.0f * Vj + dVj);
+  const float P = Vi * Vj, dP = dVi * Vj + Vi * dVj + dVi * dVj, Pm = P + dP;
+  // cos/sin at the plain start and their changes (hardware sin/cos, ~1e-6
+  // absolute; the half-angle sine of a small change from its odd series,
+  // which keeps its relative accuracy)
+  float sn, c, smid, cmid;
+  __sincosf(d, &sn, &c);
+  const float hh = 0.5f * dd, hh2 = hh * hh;
+  const float shh = fabsf(hh) < 0.25f ? hh * (1.0f - hh2 * (1.0f / 6.0f - hh2 * (1.0f / 120.0f))) : __sinf(hh);
+  __sincosf(d + hh, &smid, &cmid);
+  const float dc = -2.0f * smid * shh, ds = 2.0f * cmid * shh;
+  // FP32 line constants: q_0..q_3, ga, ka of the from and the to end
+  float q[4], ga[2], ka[2];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) q[r] = S.BCF[r * NL + lg];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    ga[e] = S.BCF[(4 + e) * NL + lg];
+    ka[e] = S.BCF[(6 + e) * NL + lg];
+  }
+  float E[4], dE[4];
+  {
+    const float E0 = ga[0] * c + ka[0] * sn, Ed0 = ka[0] * c - ga[0] * sn;
+    const float E2 = ga[1] * c + ka[1] * sn, Ed2 = ka[1] * c - ga[1] * sn;
+    const float dE0 = ga[0] * dc + ka[0] * ds, dEd0 = ka[0] * dc - ga[0] * ds;
+    const float dE2 = ga[1] * dc + ka[1] * ds, dEd2 = ka[1] * dc - ga[1] * ds;
+    E[0] = E0; E[1] = -Ed0; E[2] = E2; E[3] = Ed2;
+    dE[0] = dE0; dE[1] = -dEd0; dE[2] = dE2; dE[3] = dEd2;
+  }
+  const float ym = sqrtf(ga[0] * ga[0] + ka[0] * ka[0]);
+  const float rpq = (float)I.rpq, rva = (float)I.rva;
+  float da[4], df = 0.0f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    da[r] = q[r] * (r < 2 ? dVi2 : dVj2) + dP * E[r] + Pm * dE[r];
+    const float e = -f[5 + r] * s * ym;  // a_r - t_r at the plain start
+    df += rpq * da[r] * (e + 0.5f * da[r]);
+  }
+  const float e4 = -f[9] * s, e5 = -f[10] * s, e6 = -f[11] * s;
+  df += 0.5f * rva * (dVi2 * (2.0f * e4 + dVi2) + dVj2 * (2.0f * e5 + dVj2));
+  df += 0.25f * rva * dd * (2.0f * e6 + dd);
+  const float cpen = (float)S.B[FB_C * NBP + bp];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int r0 = 2 * k, r1 = 2 * k + 1;
+    const float mu = (float)S.B[(FB_MU0 + 2 + k) * NBP + bp];
+    const float gp = af[4 + k];
+    const float dg = da[r0] * (2.0f * af[r0] + da[r0]) + da[r1] * (2.0f * af[r1] + da[r1]);
+    const float hc = -__fdividef(mu, cpen), hp = fmaxf(gp, hc), hm = fmaxf(gp + dg, hc);
+    df += (hm - hp) * (mu + 0.5f * cpen * (hm + hp));
+  }
+  return df < 0.0f;
+}
+
 // ------------------------------------------------------------ inference
 struct MlpSmem {
-  alignas(128) uint8_t w[MLP_PK_B];  // W1 | W2 | W3
+  alignas(128) uint8_t w[MLP_PK_B];  // W1 | W2 | W3 | B2
   float b1[64], b2[64], b3[16];
   alignas(128) uint8_t a1[128 * 16 * 2];
   alignas(128) uint8_t a2[128 * 64 * 2];
@@ -181,14 +334,18 @@ struct MlpSmem {
   uint32_t tmem;
 };
 
-constexpr uint32_t MLP_TMEM_COLS = 128;  // D1 cols 0-63, D2 64-127, D3 0-15 (after D1 is read)
+// one 64-column accumulator reused by the three layers (each layer's MMA is
+// issued after the previous layer's accumulator has been read back), so six
+// CTAs fit in an SM's 512 TMEM columns
+constexpr uint32_t MLP_TMEM_COLS = 64;
+constexpr int MLP_CTAS_PER_SM = 6;
 
 // One persistent CTA of 4 warps per 128-row tile.  FUSED: features from the
 // sweep state, output the proposed change s * y of each line-period's
 // iterate into prop [6][NBP]; otherwise features feat [n][12] and raw
 // outputs out [n][6].  err is set on a timed-out wait.
 template <bool FUSED>
-__global__ void __launch_bounds__(128) k_mlp(Dev S, const uint8_t *__restrict__ pack, long long n,
+__global__ void __launch_bounds__(128, MLP_CTAS_PER_SM) k_mlp(Dev S, const uint8_t *__restrict__ pack, long long n,
                                              const float *__restrict__ feat, float *__restrict__ out, int *err) {
   __shared__ MlpSmem sm;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -223,10 +380,12 @@ __global__ void __launch_bounds__(128) k_mlp(Dev S, const uint8_t *__restrict__ 
 #pragma unroll
     for (int j = 0; j < 16; ++j) f[j] = 0.0f;
     double sc = 0.0;
+    float af[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    int k = 0;
+    long long lgr = 0;
     bool live = row < n;
     if (live) {
       if (FUSED) {
-        int k = 0;
         {
           int lo = 0, hi = S.K - 1;
           while (lo < hi) {
@@ -237,8 +396,9 @@ __global__ void __launch_bounds__(128) k_mlp(Dev S, const uint8_t *__restrict__ 
         }
         const Inst &I = S.inst[k];
         const int loc = (int)(row - I.bpo), t = loc / I.nl, l = loc - t * I.nl;
+        lgr = (long long)I.lo + l;
         float ff[MLP_IN];
-        live = line_features(S, I, row, t, l, ff, sc);
+        live = line_features<false>(S, I, row, t, l, ff, sc, af);
 #pragma unroll
         for (int j = 0; j < MLP_IN; ++j) f[j] = ff[j];
       } else {
@@ -246,6 +406,7 @@ __global__ void __launch_bounds__(128) k_mlp(Dev S, const uint8_t *__restrict__ 
         for (int j = 0; j < MLP_IN; ++j) f[j] = feat[row * MLP_IN + j];
       }
     }
+    f[12] = f[13] = 1.0f;  // the bias columns
     st_row8(sm.a1, tid, 0, 2, f);
     st_row8(sm.a1, tid, 8, 2, f + 8);
     fence_async_smem();
@@ -265,7 +426,7 @@ __global__ void __launch_bounds__(128) k_mlp(Dev S, const uint8_t *__restrict__ 
       float z[16];
       tmem_ld16(tmem + lane_base + 16 * c, z);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) z[j] = silu(z[j] + sm.b1[16 * c + j]);
+      for (int j = 0; j < 16; ++j) z[j] = silu_fast(z[j]);  // (b1 added by the MMA)
       st_row8(sm.a2, tid, 16 * c, 8, z);
       st_row8(sm.a2, tid, 16 * c + 8, 8, z + 8);
     }
@@ -277,8 +438,10 @@ __global__ void __launch_bounds__(128) k_mlp(Dev S, const uint8_t *__restrict__ 
       tc_fence_after();
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        umma_bf16(tmem + 64, umma_desc(sa2 + 256 * kk, 128, 1024), umma_desc(sw + MLP_PK_W2 + 256 * kk, 128, 1024),
+        umma_bf16(tmem, umma_desc(sa2 + 256 * kk, 128, 1024), umma_desc(sw + MLP_PK_W2 + 256 * kk, 128, 1024),
                   ID64, kk > 0);
+      // + b2: the feature tile's ones columns against B2
+      umma_bf16(tmem, umma_desc(sa1, 128, 256), umma_desc(sw + MLP_PK_B2, 128, 256), ID64, 1);
       umma_commit(mbar);
     }
     ok = mbar_wait(mbar, phase) && ok;
@@ -287,9 +450,9 @@ __global__ void __launch_bounds__(128) k_mlp(Dev S, const uint8_t *__restrict__ 
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       float z[16];
-      tmem_ld16(tmem + lane_base + 64 + 16 * c, z);
+      tmem_ld16(tmem + lane_base + 16 * c, z);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) z[j] = silu(z[j] + sm.b2[16 * c + j]);
+      for (int j = 0; j < 16; ++j) z[j] = silu_fast(z[j]);  // (b2 added by the MMA)
       st_row8(sm.a2, tid, 16 * c, 8, z);
       st_row8(sm.a2, tid, 16 * c + 8, 8, z + 8);
     }
@@ -312,9 +475,20 @@ __global__ void __launch_bounds__(128) k_mlp(Dev S, const uint8_t *__restrict__ 
     tmem_ld16(tmem + lane_base, y);
     if (row < n) {
       if (FUSED) {
-        const double g = live ? sc : 0.0;
+        // the start of the line solve: [0] 1 when the proposal is taken,
+        // [1..3] its changes of V_i, V_j, d
+        float take = 0.0f, dVi = 0.0f, dVj = 0.0f, dd = 0.0f;
+        if (live) {
+          const float sf = (float)sc;
+          float dw[MLP_OUT];
 #pragma unroll
-        for (int j = 0; j < MLP_OUT; ++j) out[(long long)j * n + row] = (float)(g * (double)(y[j] + sm.b3[j]));
+          for (int j = 0; j < MLP_OUT; ++j) dw[j] = sf * (y[j] + sm.b3[j]);
+          take = warm_choice(S, S.inst[k], row, lgr, f, sf, af, dw, dVi, dVj, dd) ? 1.0f : 0.0f;
+        }
+        out[row] = take;
+        out[n + row] = dVi;
+        out[2 * n + row] = dVj;
+        out[3 * n + row] = dd;
       } else {
 #pragma unroll
         for (int j = 0; j < MLP_OUT; ++j) out[row * MLP_OUT + j] = y[j] + sm.b3[j];
@@ -338,10 +512,18 @@ __global__ void k_mlp_pack(const float *__restrict__ P, uint8_t *__restrict__ pa
   __nv_bfloat16 *w1 = reinterpret_cast<__nv_bfloat16 *>(pack + MLP_PK_W1);
   __nv_bfloat16 *w2 = reinterpret_cast<__nv_bfloat16 *>(pack + MLP_PK_W2);
   __nv_bfloat16 *w3 = reinterpret_cast<__nv_bfloat16 *>(pack + MLP_PK_W3);
+  __nv_bfloat16 *b2 = reinterpret_cast<__nv_bfloat16 *>(pack + MLP_PK_B2);
   float *b = reinterpret_cast<float *>(pack + MLP_PK_B);
   if (i < 64 * 16) {
     const int o = i / 16, k = i % 16;
-    w1[canon_off(o, k, 2) / 2] = __float2bfloat16_rn(k < MLP_IN ? P[MLP_OW1 + o * MLP_IN + k] : 0.0f);
+    // a bias as a BF16 pair: hi = bf16(b), lo = bf16(b - hi)
+    auto pair = [&](float bias) -> __nv_bfloat16 {
+      const __nv_bfloat16 hi = __float2bfloat16_rn(bias);
+      return k == 12 ? hi : __float2bfloat16_rn(bias - __bfloat162float(hi));
+    };
+    w1[canon_off(o, k, 2) / 2] =
+        k < MLP_IN ? __float2bfloat16_rn(P[MLP_OW1 + o * MLP_IN + k]) : (k < 14 ? pair(P[MLP_OB1 + o]) : __float2bfloat16_rn(0.0f));
+    b2[canon_off(o, k, 2) / 2] = (k == 12 || k == 13) ? pair(P[MLP_OB2 + o]) : __float2bfloat16_rn(0.0f);
   }
   if (i < 64 * 64) {
     const int o = i / 64, k = i % 64;
@@ -495,7 +677,7 @@ __global__ void __launch_bounds__(BS) k_line_features(Dev S, int k, float *__res
   const int t = (int)(loc / I.nl), l = (int)(loc - (long long)t * I.nl);
   float f[MLP_IN];
   double s;
-  line_features(S, I, (long long)I.bpo + loc, t, l, f, s);
+  line_features<true>(S, I, (long long)I.bpo + loc, t, l, f, s);
 #pragma unroll
   for (int j = 0; j < MLP_IN; ++j) feat[loc * MLP_IN + j] = f[j];
   sc[loc] = s;
@@ -515,7 +697,7 @@ __global__ void __launch_bounds__(BS) k_line_features_all(Dev S, float *__restri
   const int loc = (int)(bp - I.bpo), t = loc / I.nl, l = loc - t * I.nl;
   float f[MLP_IN];
   double s;
-  line_features(S, I, bp, t, l, f, s);
+  line_features<true>(S, I, bp, t, l, f, s);
 #pragma unroll
   for (int j = 0; j < MLP_IN; ++j) feat[bp * MLP_IN + j] = f[j];
   sc[bp] = s;

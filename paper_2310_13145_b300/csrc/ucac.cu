@@ -66,6 +66,7 @@ struct ucac_handle {
   int check_every = 50;
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
+  cudaStream_t cap_side = nullptr;  // second capture stream: the MLP branch of the sweep graph
   char *arena = nullptr;
   size_t arena_bytes = 0;
   Dev dev{};
@@ -248,20 +249,38 @@ void launch_mlp(ucac_handle *h, cudaStream_t s) {
   int dev = 0, sms = 148;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long tiles = (h->NBP + 127) / 128;
-  const int grid = (int)std::max(1LL, std::min(tiles, 4LL * sms));
+  const int grid = (int)std::max(1LL, std::min(tiles, (long long)MLP_CTAS_PER_SM * sms));
   k_mlp<true><<<grid, 128, 0, s>>>(h->dev, h->mlp_pack, h->NBP, nullptr, const_cast<float *>(h->dev.prop),
                                    h->mlp_err);
 }
 
-void launch_sweep(ucac_handle *h, cudaStream_t s) {
+// one sweep on stream s.  With the learned start and a side stream, the
+// network runs on the side stream beside the UC dynamic program and the
+// generator kernel (it reads only the line iterates and targets, which
+// neither writes) and joins before the line kernel
+cudaError_t launch_sweep(ucac_handle *h, cudaStream_t s, cudaStream_t side = nullptr, cudaEvent_t fork = nullptr,
+                         cudaEvent_t join = nullptr) {
+  cudaError_t e = cudaSuccess;
+  const bool branch = h->dev.warm && side && fork && join;
+  if (branch) {
+    e = cudaEventRecord(fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
+    if (e == cudaSuccess) launch_mlp(h, side);
+    if (e == cudaSuccess) e = cudaEventRecord(join, side);
+  }
   launch_ucdp(h, s);
   launch_gen(h, s);
-  if (h->dev.warm) launch_mlp(h, s);
+  if (branch) {
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
+  } else if (h->dev.warm) {
+    launch_mlp(h, s);
+  }
   launch_line(h, s);
   launch_bus(h, s);
   launch_ucbar(h, s);
   k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(h->dev);
   if (h->prm.rho_every > 0) launch_prep(h, s, 1);
+  return e;
 }
 
 // (re)captures one sweep into the handle's graph
@@ -270,10 +289,20 @@ cudaError_t capture_graph(ucac_handle *h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   h->exec = nullptr;
   h->graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) return e;
-  launch_sweep(h, h->cap);
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    return e;
+  }
+  const cudaError_t el = launch_sweep(h, h->cap, h->cap_side, fork, join);
   e = cudaStreamEndCapture(h->cap, &h->graph);
+  cudaEventDestroy(fork);
+  cudaEventDestroy(join);
+  if (e == cudaSuccess) e = el;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
   return e;
 }
@@ -748,6 +777,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   if (e == cudaSuccess) e = cudaGetLastError();
   // ---- capture one sweep into a graph (capture needs a non-legacy stream)
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = capture_graph(h);
   if (e != cudaSuccess) {
     std::string m = std::string("setup: ") + cudaGetErrorString(e);
@@ -1154,7 +1184,7 @@ int ucac_mlp_forward(int64_t n, const float *params, const float *x, float *y, v
   k_mlp_pack<<<16, 256, 0, s>>>(params, w.pack);
   CK(cudaMemsetAsync(w.err, 0, sizeof(int), s));
   const long long tiles = (n + 127) / 128;
-  const int grid = (int)std::max(1LL, std::min(tiles, 4LL * sms));
+  const int grid = (int)std::max(1LL, std::min(tiles, (long long)MLP_CTAS_PER_SM * sms));
   Dev none{};
   k_mlp<false><<<grid, 128, 0, s>>>(none, w.pack, n, x, y, w.err);
   CK(cudaGetLastError());
@@ -1428,6 +1458,7 @@ extern "C" void ucac_destroy(ucac_handle *h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->cap_side) cudaStreamDestroy(h->cap_side);
   if (h->arena) {
     cudaStreamSynchronize(h->stream);
     cudaFree(h->arena);
