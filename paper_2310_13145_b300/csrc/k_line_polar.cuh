@@ -491,65 +491,97 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   }
   // 3x3 system in x: H plus c grad g_k grad g_k^T of the slacks held at a
   // bound; a free slack's row gives d_sigma_k = -m_k / c - grad g_k . d_x,
-  // which turns its m_k grad g_k out of the right-hand side
+  // which turns its m_k grad g_k out of the right-hand side.  Second pass: a
+  // free variable that sits at a bound (within 1e-6) and that the Newton step
+  // pushes across it is fixed there, and the system is solved again on the
+  // rest -- the gradient-based active set misses such a variable when the
+  // coupling to the others, not its own gradient, drives it outward, and the
+  // projected step would then not be a descent direction of the model
   const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
-  T Hr[6], rb[3];
-  const bool sheld = act[3] || act[4];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    Hr[q] = H[q];
-    if (sheld) {
-      double add = 0.0;
-#pragma unroll
-      for (int k = 0; k < 2; ++k)
-        if (act[3 + k]) add += c * L.dg[k][pi_[q]] * L.dg[k][pj_[q]];
-      Hr[q] += (T)add;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    double r = -rg[i];
-#pragma unroll
-    for (int k = 0; k < 2; ++k)
-      if (act[3 + k]) r -= c * L.dg[k][i] * d[3 + k];
-    rb[i] = (T)r;
-  }
-  T lm = T(0), y[3];
-  bool ok = false;
-  for (int tries = 0; tries < 40; ++tries) {
-    T A[6];
+  long long bn = 0;
+  T lm = T(0);
+  for (int pass = 0;; ++pass) {
+    T Hr[6], rb[3];
+    const bool sheld = act[3] || act[4];
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      const int i = pi_[q], j = pj_[q];
-      A[q] = (act[i] || act[j]) ? ((i == j) ? T(1) : T(0)) : Hr[q];
-      if (i == j && !act[i]) A[q] += lm;
+      Hr[q] = H[q];
+      if (sheld) {
+        double add = 0.0;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (act[3 + k]) add += c * L.dg[k][pi_[q]] * L.dg[k][pj_[q]];
+        Hr[q] += (T)add;
+      }
     }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      T r = rb[i];
+      double r = -rg[i];
 #pragma unroll
-      for (int j = 0; j < 3; ++j)
-        if (act[j]) r -= hq(Hr, i, j) * (T)d[j];
-      y[i] = act[i] ? (T)d[i] : r;
+      for (int k = 0; k < 2; ++k)
+        if (act[3 + k]) r -= c * L.dg[k][i] * d[3 + k];
+      rb[i] = (T)r;
     }
-    if (chol3p(A, y)) {
-      ok = true;
-      break;
-    }
-    lm = (lm == T(0)) ? T(1e-10) * (hmax > T(0) ? hmax : T(1)) : T(10) * lm;
-  }
-  if (!ok) return NI_STOP;
-  long long bn = 0;
+    T y[3];
+    lm = T(0);
+    bool ok = false;
+    for (int tries = 0; tries < 40; ++tries) {
+      T A[6];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (!act[i]) d[i] = (double)y[i];
-    const long long b = __double_as_longlong(d[i]) & ABS;
-    bn = b > bn ? b : bn;
+      for (int q = 0; q < 6; ++q) {
+        const int i = pi_[q], j = pj_[q];
+        A[q] = (act[i] || act[j]) ? ((i == j) ? T(1) : T(0)) : Hr[q];
+        if (i == j && !act[i]) A[q] += lm;
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        T r = rb[i];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          if (act[j]) r -= hq(Hr, i, j) * (T)d[j];
+        y[i] = act[i] ? (T)d[i] : r;
+      }
+      if (chol3p(A, y)) {
+        ok = true;
+        break;
+      }
+      lm = (lm == T(0)) ? T(1e-10) * (hmax > T(0) ? hmax : T(1)) : T(10) * lm;
+    }
+    if (!ok) return NI_STOP;
+    bn = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (!act[i]) d[i] = (double)y[i];
+      const long long b = __double_as_longlong(d[i]) & ABS;
+      bn = b > bn ? b : bn;
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (!act[3 + k]) d[3 + k] = -L.m[k] * P.ic - (L.dg[k][0] * d[0] + L.dg[k][1] * d[1] + L.dg[k][2] * d[2]);
+    if (pass > 0) break;
+    bool again = false;
+#pragma unroll
+    for (int i = 0; i < POL_NV; ++i) {
+      if (act[i]) continue;
+      const bool lo_at = le_nn(dlo[i], 1e-6) && dkey(d[i]) < dkey(-dlo[i]);
+      const bool hi_at = le_nn(dhi[i], 1e-6) && dkey(d[i]) > dkey(dhi[i]);
+      if (lo_at || hi_at) {
+        act[i] = true;
+        d[i] = lo_at ? -dlo[i] * 1.000001 : dhi[i] * 1.000001;  // onto the bound (clamped below)
+        again = true;
+        if (i >= 3) {  // a held slack keeps its m_k grad g_k in the reduced gradient
+#pragma unroll
+          for (int j = 0; j < 3; ++j) rg[j] = fma(L.m[i - 3], L.dg[i - 3][j], rg[j]);
+        }
+      }
+    }
+    if (!again) break;
+    if (!near) {  // the model of the step now needs the full gradient
+      if (!prox) full_grad();
+      near = true;
+    }
   }
   const double dn = __longlong_as_double(bn);  // max |d_i| over x
-#pragma unroll
-  for (int k = 0; k < 2; ++k)
-    if (!act[3 + k]) d[3 + k] = -L.m[k] * P.ic - (L.dg[k][0] * d[0] + L.dg[k][1] * d[1] + L.dg[k][2] * d[2]);
   counted = 1;
   // model decrease of a step sg: -(gr . sg + 1/2 sg^T H5 sg), where
   // sg^T H5 sg = sx^T H sx + sum_k c (grad g_k . sx + s_sigma_k)^2
