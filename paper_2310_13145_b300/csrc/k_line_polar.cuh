@@ -829,6 +829,10 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
     acc_nw = acc_al = acc_cap = acc_w = 0;
   };
   bool need_full = false, trial = false;
+  // a solve that ends with a non-tiny last step is evaluated once more at its
+  // final point (at the next trip's single call site, with the rest of the
+  // warp) and then finished from that evaluation: 1 converged, 2 stopped
+  int fin_pend = 0;
   PolTrial tr;
   double f = 0.0, Delta = 1.0, hprev = INFINITY, omega = 0.0, cmax = 0.0;
   double v[POL_NV], gx[3], Hd[6];
@@ -978,6 +982,11 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         }
       }
       need_full = !step_now;
+      if (fin_pend) {
+        step_now = false;
+        need_full = false;
+        out = NI_STOP;  // (the finish takes conv from fin_pend)
+      }
       if (step_now) {
         bool accepted;
         int counted;
@@ -995,95 +1004,93 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
       ++itn;
       if (out != NI_CONT || itn >= K_N) {
         trial = false;
-        const bool conv = (out == NI_CONV);
+        const bool conv = fin_pend ? fin_pend == 1 : (out == NI_CONV);
         // flows, cos/sin and h_k at v: first order from the last evaluation
-        // after a converged tiny final step (h_k in FP64 from grad g_k, so
-        // that it matches the slack step taken from the same gradient), a
-        // fresh evaluation otherwise
+        // when the last step is tiny (h_k in FP64 from grad g_k, so that it
+        // matches the slack step taken from the same gradient); otherwise v
+        // is evaluated at the next trip and the solve finishes from there
         // (the flows and cos/sin themselves are formed from the base values
         // ab, cb, sb and the step fx, dxs by the finish ring: with dx <= 1e-8
         // the FP32 product carries ~1e-15 absolute error)
         const double dx0 = v[0] - L.v[0], dx1 = v[1] - L.v[1], dx2 = v[2] - L.v[2];
         const long long b8 = __double_as_longlong(1e-8);
-        const bool tiny = conv && abs_bits(dx0) <= b8 && abs_bits(dx1) <= b8 && abs_bits(dx2) <= b8;
-        double ab[4], cb, sb, dxs, h[2];
-        float fx[3];
-        if (tiny) {
-#pragma unroll
-          for (int r = 0; r < 4; ++r) ab[r] = L.a[r];
-          cb = L.c;
-          sb = L.s;
-          fx[0] = (float)dx0;
-          fx[1] = (float)dx1;
-          fx[2] = (float)dx2;
-          dxs = dx2;
-#pragma unroll
-          for (int q = 0; q < 2; ++q)
-            h[q] = L.h[q] + L.dg[q][0] * dx0 + L.dg[q][1] * dx1 + L.dg[q][2] * dx2 + (v[3 + q] - L.v[3 + q]);
-        } else {
-          const double ht0[2] = {0.0, 0.0};
-          pol_obj(K, P, v, ab, cb, sb, ht0, 0);
-          fx[0] = fx[1] = fx[2] = 0.0f;
-          dxs = 0.0;
-#pragma unroll
-          for (int q = 0; q < 2; ++q)
-            h[q] = ab[2 * q] * ab[2 * q] + ab[2 * q + 1] * ab[2 * q + 1] - K.rate2 + v[3 + q];
-        }
-        // equality multiplier step on h_k = p_k^2 + q_k^2 + sigma_k - rate^2
-        long long bh = 0;
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const long long b = abs_bits(h[q]);
-          bh = b > bh ? b : bh;
-          P.mu[q] += P.c * h[q];
-        }
-        const double hn = __longlong_as_double(bh);  // max |h_k|
-        ++al;
-        const bool done = le_nn(hn, eta) && conv;
-        if (done || al >= K_AL) {
-          S.B[(FB_V0 + 6) * NBP + bp] = v[3];
-          S.B[(FB_V0 + 7) * NBP + bp] = v[4];
-          S.B[(FB_MU0 + 0) * NBP + bp] = 0.0;
-          S.B[(FB_MU0 + 1) * NBP + bp] = 0.0;
-          S.B[(FB_MU0 + 2) * NBP + bp] = P.mu[0];
-          S.B[(FB_MU0 + 3) * NBP + bp] = P.mu[1];
-          S.B[FB_C * NBP + bp] = P.c;
-          {
-            const int sl = atomicAdd(&ftail[wib], 1) & (POL_QF - 1);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) frd[r * POL_QF + sl] = ab[r];
-            frd[4 * POL_QF + sl] = cb;
-            frd[5 * POL_QF + sl] = sb;
-            frd[6 * POL_QF + sl] = v[0];
-            frd[7 * POL_QF + sl] = v[1];
-            frd[8 * POL_QF + sl] = v[2];
-            frd[9 * POL_QF + sl] = dxs;
-            frd[10 * POL_QF + sl] = P.tg[6];
-            frd[11 * POL_QF + sl] = P.tg[7];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-              for (int i = 0; i < 3; ++i) frf[(3 * r + i) * POL_QF + sl] = L.da[r][i];
-            frf[12 * POL_QF + sl] = fx[0];
-            frf[13 * POL_QF + sl] = fx[1];
-            frf[14 * POL_QF + sl] = fx[2];
-            fri[sl] = (int)bp;
-            fri[POL_QF + sl] = (int)lef;
-            fri[2 * POL_QF + sl] = (int)let;
-          }
-          acc_nw += (unsigned long long)newton;
-          acc_al += (unsigned long long)al;
-          acc_cap += done ? 0ull : 1ull;
-          bp = -1;
-        } else {
-          if (hn > 0.25 * hprev) {
-            P.c = fmin(10.0 * P.c, cmax);
-            P.ic = 1.0 / P.c;
-          }
-          hprev = hn;
-          Delta = fmax(Delta, 1e-3);
-          itn = 0;
+        const bool tiny = abs_bits(dx0) <= b8 && abs_bits(dx1) <= b8 && abs_bits(dx2) <= b8;
+        if (!tiny) {
+          fin_pend = conv ? 1 : 2;
           need_full = true;
+        } else {
+          fin_pend = 0;
+          double ab[4], cb, sb, dxs, h[2];
+          float fx[3];
+          {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ab[r] = L.a[r];
+            cb = L.c;
+            sb = L.s;
+            fx[0] = (float)dx0;
+            fx[1] = (float)dx1;
+            fx[2] = (float)dx2;
+            dxs = dx2;
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+              h[q] = L.h[q] + L.dg[q][0] * dx0 + L.dg[q][1] * dx1 + L.dg[q][2] * dx2 + (v[3 + q] - L.v[3 + q]);
+          }
+          // equality multiplier step on h_k = p_k^2 + q_k^2 + sigma_k - rate^2
+          long long bh = 0;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const long long b = abs_bits(h[q]);
+            bh = b > bh ? b : bh;
+            P.mu[q] += P.c * h[q];
+          }
+          const double hn = __longlong_as_double(bh);  // max |h_k|
+          ++al;
+          const bool done = le_nn(hn, eta) && conv;
+          if (done || al >= K_AL) {
+            S.B[(FB_V0 + 6) * NBP + bp] = v[3];
+            S.B[(FB_V0 + 7) * NBP + bp] = v[4];
+            S.B[(FB_MU0 + 0) * NBP + bp] = 0.0;
+            S.B[(FB_MU0 + 1) * NBP + bp] = 0.0;
+            S.B[(FB_MU0 + 2) * NBP + bp] = P.mu[0];
+            S.B[(FB_MU0 + 3) * NBP + bp] = P.mu[1];
+            S.B[FB_C * NBP + bp] = P.c;
+            {
+              const int sl = atomicAdd(&ftail[wib], 1) & (POL_QF - 1);
+#pragma unroll
+              for (int r = 0; r < 4; ++r) frd[r * POL_QF + sl] = ab[r];
+              frd[4 * POL_QF + sl] = cb;
+              frd[5 * POL_QF + sl] = sb;
+              frd[6 * POL_QF + sl] = v[0];
+              frd[7 * POL_QF + sl] = v[1];
+              frd[8 * POL_QF + sl] = v[2];
+              frd[9 * POL_QF + sl] = dxs;
+              frd[10 * POL_QF + sl] = P.tg[6];
+              frd[11 * POL_QF + sl] = P.tg[7];
+#pragma unroll
+              for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) frf[(3 * r + i) * POL_QF + sl] = L.da[r][i];
+              frf[12 * POL_QF + sl] = fx[0];
+              frf[13 * POL_QF + sl] = fx[1];
+              frf[14 * POL_QF + sl] = fx[2];
+              fri[sl] = (int)bp;
+              fri[POL_QF + sl] = (int)lef;
+              fri[2 * POL_QF + sl] = (int)let;
+            }
+            acc_nw += (unsigned long long)newton;
+            acc_al += (unsigned long long)al;
+            acc_cap += done ? 0ull : 1ull;
+            bp = -1;
+          } else {
+            if (hn > 0.25 * hprev) {
+              P.c = fmin(10.0 * P.c, cmax);
+              P.ic = 1.0 / P.c;
+            }
+            hprev = hn;
+            Delta = fmax(Delta, 1e-3);
+            itn = 0;
+            need_full = true;
+          }
         }
       }
     }
