@@ -38,10 +38,12 @@
 // correction before the ratio test: free slacks absorb the O(|dx|^2)
 // remainder of g_k, and a slack held at zero gets a correction in x along
 // grad g_k, so that c/2 h_k^2 sees the linear prediction instead of the
-// remainder magnified by c.  An undamped step of size <= 1e-4 (1 + |x|)
-// inside the radius that leaves every free variable inside its box is
-// accepted without the ratio test (its model error is at the rounding
-// level).
+// remainder magnified by c.  An undamped Newton step (unshifted, so the
+// Hessian is positive definite and the step descends on the model) of size
+// <= 1e-3 (1 + |x|) inside the radius that leaves every free variable inside
+// its box is accepted without the ratio test: its model error, O(|d|^3), is
+// far below the decrease, and the trial evaluation it saves was most of the
+// cost of the late sweeps of a run (1e-2 gains nothing more).
 // Precision split (B300's FP64 pipe is 1/64 of its FP32 pipe): the iterate,
 // flows, residuals, gradient and objective are FP64 -- they fix the converged
 // point -- while the Hessian and the Newton system are FP32 on lanes whose
@@ -626,7 +628,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
       const bool in = b < 0 ? (b & ABS) <= __double_as_longlong(dlo[i]) : b <= __double_as_longlong(dhi[i]);
       inside = inside && (act[i] || in);
     }
-    if (inside && le_nn(dn, 1e-4 * (1.0 + xmax)) && le_nn(dn, Delta)) {
+    if (inside && le_nn(dn, 1e-3 * (1.0 + xmax)) && le_nn(dn, Delta)) {
 #pragma unroll
       for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
       accepted = true;
