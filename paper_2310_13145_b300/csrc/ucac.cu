@@ -66,7 +66,7 @@ struct ucac_handle {
   int check_every = 50;
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr;
-  cudaStream_t cap_side = nullptr;  // second capture stream: the MLP branch of the sweep graph
+  cudaStream_t cap_side = nullptr;  // second capture stream: the generator-side branch of the sweep graph
   char *arena = nullptr;
   size_t arena_bytes = 0;
   Dev dev{};
@@ -254,30 +254,38 @@ void launch_mlp(ucac_handle *h, cudaStream_t s) {
                                    h->mlp_err);
 }
 
-// one sweep on stream s.  With the learned start and a side stream, the
-// network runs on the side stream beside the UC dynamic program and the
-// generator kernel (it reads only the line iterates and targets, which
-// neither writes) and joins before the line kernel
+// one sweep on stream s.  With a side stream (graph capture), the
+// generator side -- UC dynamic program, generator kernel, UC box QPs -- runs
+// beside the line kernel: the line kernel reads only the line iterates and
+// targets, which none of them writes; the bus kernel waits for the
+// generator kernel (it reads the generators' p, q rows) and the finish for
+// the UC box QPs.  The side stream has the higher priority, so its blocks
+// take the SMs the persistent line kernel has not filled yet or has left.
 cudaError_t launch_sweep(ucac_handle *h, cudaStream_t s, cudaStream_t side = nullptr, cudaEvent_t fork = nullptr,
-                         cudaEvent_t join = nullptr) {
+                         cudaEvent_t e_gen = nullptr, cudaEvent_t e_uc = nullptr) {
   cudaError_t e = cudaSuccess;
-  const bool branch = h->dev.warm && side && fork && join;
+  const bool branch = side && fork && e_gen && e_uc;
   if (branch) {
     e = cudaEventRecord(fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(side, fork, 0);
-    if (e == cudaSuccess) launch_mlp(h, side);
-    if (e == cudaSuccess) e = cudaEventRecord(join, side);
+    launch_ucdp(h, side);
+    launch_gen(h, side);
+    if (e == cudaSuccess) e = cudaEventRecord(e_gen, side);
+    launch_ucbar(h, side);
+    if (e == cudaSuccess) e = cudaEventRecord(e_uc, side);
+    if (h->dev.warm) launch_mlp(h, s);
+    launch_line(h, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_gen, 0);
+    launch_bus(h, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e_uc, 0);
+  } else {
+    launch_ucdp(h, s);
+    launch_gen(h, s);
+    if (h->dev.warm) launch_mlp(h, s);
+    launch_line(h, s);
+    launch_bus(h, s);
+    launch_ucbar(h, s);
   }
-  launch_ucdp(h, s);
-  launch_gen(h, s);
-  if (branch) {
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
-  } else if (h->dev.warm) {
-    launch_mlp(h, s);
-  }
-  launch_line(h, s);
-  launch_bus(h, s);
-  launch_ucbar(h, s);
   k_finish<BS_FIN><<<h->K, BS_FIN, 0, s>>>(h->dev);
   if (h->prm.rho_every > 0) launch_prep(h, s, 1);
   return e;
@@ -289,19 +297,19 @@ cudaError_t capture_graph(ucac_handle *h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   h->exec = nullptr;
   h->graph = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // fork, generator kernel done, UC box QPs done
+  cudaError_t e = cudaSuccess;
+  for (auto &x : ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
-    if (fork) cudaEventDestroy(fork);
-    if (join) cudaEventDestroy(join);
+    for (auto &x : ev)
+      if (x) cudaEventDestroy(x);
     return e;
   }
-  const cudaError_t el = launch_sweep(h, h->cap, h->cap_side, fork, join);
+  const cudaError_t el = launch_sweep(h, h->cap, h->cap_side, ev[0], ev[1], ev[2]);
   e = cudaStreamEndCapture(h->cap, &h->graph);
-  cudaEventDestroy(fork);
-  cudaEventDestroy(join);
+  for (auto &x : ev) cudaEventDestroy(x);
   if (e == cudaSuccess) e = el;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->exec, h->graph, 0);
   return e;
@@ -777,7 +785,11 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   if (e == cudaSuccess) e = cudaGetLastError();
   // ---- capture one sweep into a graph (capture needs a non-legacy stream)
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap_side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) {
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->cap_side, cudaStreamNonBlocking, greatest);
+  }
   if (e == cudaSuccess) e = capture_graph(h);
   if (e != cudaSuccess) {
     std::string m = std::string("setup: ") + cudaGetErrorString(e);
