@@ -90,6 +90,25 @@ def test_lockstep_118bus_batch(ucac_mod, line_form):
     _lockstep(ucac_mod, grids, 4, warm=10, line_form=line_form)
 
 
+def test_lockstep_2000bus_late(ucac_mod):
+    """One 2000-bus scenario 700 sweeps into a run to 1e-4, where line limits
+    bind, penalties have grown to 1e8-1e10 and the polar solver's rarer
+    paths run: variables fixed on a bound by the second Newton pass, solves
+    finished from an extra evaluation, FP64-Hessian iterations, several AL
+    rounds.  Two sweeps in lockstep with the oracle."""
+    g = synth.config_instances("c5_2000bus_T24x16")[0]
+    _lockstep(ucac_mod, [g], 2, warm=700, line_form=ucac_mod.UCAC_LINE_POLAR)
+    # the regime is the late one: some solves take several AL rounds and the
+    # Newton steps per solve are above the early runs' ~2
+    h = ucac_mod.Handle([g])
+    h.enqueue(701)
+    r = h.residuals(0)
+    solves = g.T * g.n_branch
+    h.close()
+    assert r["al"] > solves, (r["al"], solves)
+    assert r["newton"] > 2.0 * solves, (r["newton"], solves)
+
+
 def test_lockstep_ragged_small_instances(ucac_mod, line_form):
     # uneven batch: sizes that leave partial blocks in every kernel
     grids = [synth.make_grid(n, nl, max(1, n // 3), T, seed=50 + n, rho=synth.RHO_TABLE["case300"])
