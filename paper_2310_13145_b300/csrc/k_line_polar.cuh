@@ -195,9 +195,9 @@ __device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, double (
 //   sum_r (w_r grad a_r grad a_r^T + u_r hess a_r) + (angle/voltage rows)
 //   + sum_k c grad g_k grad g_k^T,
 // w_r = rho_pq + 2 m_k, u_r = rho_pq (a_r - t_r) + 2 m_k a_r (k = r / 2).
-__device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double (&v)[POL_NV], double (&gx)[3],
-                                           float (&Hf)[6], double (&Hd)[6], PolLast &L, const double (&ht)[2],
-                                           int free_mask) {
+__device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&v)[POL_NV], double (&gx)[3],
+                                         float (&Hf)[6], double (&Hd)[6], PolLast &L, const double (&ht)[2],
+                                         int free_mask) {
   const double Vi = v[0], Vj = v[1], d = v[2];
   double s, c;
   pol_cossin(d, c, s);
@@ -208,7 +208,6 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
   const double Pv = Vi * Vj, Vi2 = Vi * Vi, Vj2 = Vj * Vj;
   const float fVi = (float)Vi, fVj = (float)Vj, fP = fVi * fVj;
   const double Vi2x = 2.0 * Vi, Vj2x = 2.0 * Vj;
-  double f = 0.0;
   double E[4], Ed[4], pe[4];
   float fE[4], fEd[4];
   // FP32 gradient of the flow (for the FP32 Hessian and the first-order
@@ -217,20 +216,16 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
   const float fc = (float)c, fs = (float)s;
   pol_angle_terms(K.ga[0], K.ka[0], K.ga[1], K.ka[1], c, s, E, Ed);
   pol_angle_terms(K.fga(0), K.fka(0), K.fga(1), K.fka(1), fc, fs, fE, fEd);
-  double spe = 0.0;  // sum_r rho_pq (a_r - t_r)^2
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const double a = K.q[r] * (r < 2 ? Vi2 : Vj2) + Pv * E[r];
     L.a[r] = a;
-    const double e = a - P.tg[r];
-    pe[r] = P.rpq * e;
-    spe = fma(pe[r], e, spe);
+    pe[r] = P.rpq * (a - P.tg[r]);
     L.da[r][0] = r < 2 ? 2.0f * K.fq(r) * fVi + fVj * fE[r] : fVj * fE[r];
     L.da[r][1] = r < 2 ? fVi * fE[r] : 2.0f * K.fq(r) * fVj + fVi * fE[r];
     L.da[r][2] = fP * fEd[r];
   }
   const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
-  f = 0.5 * spe + 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
   double mhk[2];
   bool lim = false;
 #pragma unroll
@@ -244,7 +239,6 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
     const double sk = v[3 + k];
     const double h = g + sk;
     const double m = P.mu[k] + P.c * h;
-    f += h * (P.mu[k] + 0.5 * P.c * h);
     L.m[k] = m;
     L.h[k] = h;
     const double AE = fma(L.a[r0], E[r0], L.a[r1] * E[r1]);
@@ -321,6 +315,22 @@ __device__ __forceinline__ double pol_full(const PolK &K, const PolP &P, double 
     Hd[3] += P.rva * (4.0 * Vj * Vj + 2.0 * ewj);
     Hd[5] += 0.5 * P.rva;
   }
+}
+
+// objective at the point of the last evaluation, from its flows and h_k
+// (formed only where a ratio test needs it: a trial step, a held slack's step)
+__device__ __forceinline__ double pol_f(const PolP &P, const PolLast &L) {
+  double spe = 0.0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const double e = L.a[r] - P.tg[r];
+    spe = fma(P.rpq * e, e, spe);
+  }
+  const double ewi = L.v[0] * L.v[0] - P.tg[4], ewj = L.v[1] * L.v[1] - P.tg[5];
+  const double et = L.v[2] - (P.tg[6] - P.tg[7]);
+  double f = 0.5 * spe + 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) f += L.h[k] * (P.mu[k] + 0.5 * P.c * L.h[k]);
   return f;
 }
 
@@ -603,18 +613,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     return -(lin + 0.5 * quad);
   };
   if (lm == T(0)) {
-    // with no bound active d minimises the quadratic model exactly, where
-    // the model decrease is -(1/2) gr . d = -(1/2) (gx . dx - sum_k m_k^2 / c)
-    // (the free slacks' steps d_k = -m_k / c - grad g_k . dx)
-    double predN;
-    if (near) {
-      predN = model(d);
-    } else {
-      const double lin = fma(gx[0], d[0], fma(gx[1], d[1], gx[2] * d[2])) -
-                         P.ic * fma(L.m[0], L.m[0], L.m[1] * L.m[1]);
-      predN = -0.5 * lin;
-    }
-    if (le_nn(dn, 1e-9 * (1.0 + xmax)) || le_nn(predN, 1e-12 * (1.0 + fabs(f)))) {
+    if (le_nn(dn, 1e-9 * (1.0 + xmax))) {
 #pragma unroll
       for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
       return NI_CONV;
@@ -656,6 +655,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     ht[k] = L.h[k] + L.dg[k][0] * sg[0] + L.dg[k][1] * sg[1] + L.dg[k][2] * sg[2] + sg[3 + k];
     if (act[3 + k]) ++nheld; else free_mask |= 1 << k;
   }
+  f = pol_f(P, L);  // the ratio test's baseline: the objective at v
   if (nheld == 0) {
     // the trial point becomes the next trip's evaluation point: every lane
     // of the warp then runs one full evaluation per trip, and the ratio test
@@ -963,9 +963,10 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           for (int i = 0; i < POL_NV; ++i) tr.v[i] = v[i];
           tr.ht[0] = tr.ht[1] = 0.0;
         }
-        const double fe = pol_full(K, P, tr.v, gx, Hf, Hd, L, tr.ht, trial ? 3 : 0);
+        pol_full(K, P, tr.v, gx, Hf, Hd, L, tr.ht, trial ? 3 : 0);
         if (trial) {
           trial = false;
+          const double fe = pol_f(P, L);
           const double ared = f - fe;
           if (tr.pred > 0.0 && ared >= 1e-4 * tr.pred) {
 #pragma unroll
@@ -979,8 +980,6 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
             step_now = false;
             if (Delta <= 1e-15 * (1.0 + fmax(fmax(fabs(v[0]), fabs(v[1])), fabs(v[2])))) out = NI_STOP;
           }
-        } else {
-          f = fe;
         }
       }
       need_full = !step_now;
