@@ -58,7 +58,26 @@ struct Inst {
   int m_rows;
   int gran_gen0, gran_gen1, gran_gp0, gran_gp1, gran_bp0, gran_bp1, gran_up0, gran_up1;
   double rpq, rva, ruc;
+  // constants of the next sweep's x-bar row updates: 1/rho of each family,
+  // and 1/(beta + rho) with the beta its z-updates use (the scheduled
+  // beta_next while an outer update is pending); set by inst_derive whenever
+  // a penalty, beta or the pending flag changes, so that no row-update
+  // thread divides
+  double irpq, irva, iruc, ibpq, ibva, ibuc;
 };
+
+// the derived constants of I from its penalties and control record c (the
+// host at create and the device after each sweep compute the same IEEE
+// quotients, so the bits do not depend on where they were formed)
+__host__ __device__ inline void inst_derive(Inst &I, const double *c) {
+  const double beta = c[C_PEND] != 0.0 ? c[C_BNEXT] : c[C_BETA];
+  I.irpq = 1.0 / I.rpq;
+  I.irva = 1.0 / I.rva;
+  I.iruc = 1.0 / I.ruc;
+  I.ibpq = 1.0 / (beta + I.rpq);
+  I.ibva = 1.0 / (beta + I.rva);
+  I.ibuc = 1.0 / (beta + I.ruc);
+}
 
 struct Params {
   double eps_in, eps_out, tau, theta, beta0, lam_max, eta, omega_rel, c_init_rel, c_max_rel;
@@ -110,7 +129,7 @@ struct Dev {
   const int *blk_off, *blk_w;   // per bus block: slot offset within the period, width
   // buses
   long long NB;
-  const double *Gs, *Bs;
+  const double *Gs, *Bs, *ideg;  // shunt, 1/degree
   const int *inc_ptr;            // CSR row pointers over global buses (degree)
   const int *gen_ptr, *gen_idx;  // CSR over global buses; generator index local
   const int *bus_order;                    // [NB] per instance: local buses sorted by (degree, generators)

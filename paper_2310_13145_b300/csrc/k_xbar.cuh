@@ -34,7 +34,7 @@ namespace ucac {
 constexpr int kBusUnroll = UCAC_BUS_UNROLL;
 
 struct RowCtx {
-  double beta, beta_cur, lam_max;
+  double beta_cur, lam_max;
   bool pend;
 };
 
@@ -43,19 +43,21 @@ __device__ __forceinline__ RowCtx row_ctx(const Dev &S, int k) {
   RowCtx R;
   R.pend = c[C_PEND] != 0.0;
   R.beta_cur = c[C_BETA];
-  R.beta = R.pend ? c[C_BNEXT] : c[C_BETA];
   R.lam_max = S.prm.lam_max;
   return R;
 }
 
-// Per-family constants of the row update: rho, 1/rho and 1/(beta + rho), so
-// that the per-row work has no FP64 division (a division costs the FP64 pipe
-// about as much as ten multiply-adds, and the pipe is the bottleneck).
+// Per-family constants of the row update: rho, 1/rho and 1/(beta + rho),
+// taken from the instance record, so that no row-update thread divides (a
+// division costs the FP64 pipe about as much as ten multiply-adds, and the
+// pipe is the bottleneck).
 struct Fam {
   double rho, irho, ibr;
 };
 
-__device__ __forceinline__ Fam fam(double rho, const RowCtx &R) { return Fam{rho, 1.0 / rho, 1.0 / (R.beta + rho)}; }
+__device__ __forceinline__ Fam fam_pq(const Inst &I) { return Fam{I.rpq, I.irpq, I.ibpq}; }
+__device__ __forceinline__ Fam fam_va(const Inst &I) { return Fam{I.rva, I.irva, I.ibva}; }
+__device__ __forceinline__ Fam fam_uc(const Inst &I) { return Fam{I.ruc, I.iruc, I.ibuc}; }
 
 // x-step target of a UC duplicate row from its x-bar value b: (b - z) - y/rho
 // with each operation rounded separately and a true division -- the UC
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const long long NGP = S.NGP, NEP = S.NEP, NUP = S.NUP;
     const long long e0 = I.eo + (long long)t * I.spp + S.blk_off[I.bo + blk] + lane;  // slot 0 of this bus
     const RowCtx R = row_ctx(S, k);
-    const Fam Fpq = fam(I.rpq, R), Fva = fam(I.rva, R);
+    const Fam Fpq = fam_pq(I), Fva = fam_va(I);
     const double irpq = Fpq.irho;
     const bool last = (t == I.T - 1);
     const int g0 = S.gen_ptr[ig], g1 = S.gen_ptr[ig + 1], deg = S.inc_ptr[ig + 1] - S.inc_ptr[ig];
@@ -179,7 +181,7 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const double fdeg = (double)deg;
     M00 = fma_(fdeg, irpq, M00);
     M11 = fma_(fdeg, irpq, M11);
-    const double ideg = 1.0 / deg;
+    const double ideg = S.ideg[ig];
     mw = mul_(mw, ideg);
     mth = mul_(mth, ideg);
     const double iWw = mul_(Fva.irho, ideg), aPw = -S.Gs[ig], aQw = S.Bs[ig];
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
     const bool has_next = tau < I.T - 1;
     const long long gn = gp + I.ng;
     const RowCtx R = row_ctx(S, k);
-    const Fam Fpq = fam(I.rpq, R), Fuc = fam(I.ruc, R);
+    const Fam Fpq = fam_pq(I), Fuc = fam_uc(I);
     const double rpq = I.rpq, ruc = I.ruc;
     const double Pmin = S.Pmin[gg], Pmax = S.Pmax[gg], Qmin = S.Qmin[gg], Qmax = S.Qmax[gg];
     const double RU = S.RU[gg], RD = S.RD[gg], SU = S.SU[gg], SD = S.SD[gg];
@@ -571,10 +573,12 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
         }
       }
     }
+    inst_derive(*(const_cast<Inst *>(S.inst) + k), c);
   }
 }
 
-// instance penalties from the control record (after a state import)
+// instance penalties and their derived constants from the control record
+// (after a state import)
 __global__ void k_sync_rho(Dev S, int k) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     const double *c = S.ctrl + (long long)k * NCTRL;
@@ -582,6 +586,7 @@ __global__ void k_sync_rho(Dev S, int k) {
     Iw->rpq = c[C_RPQ];
     Iw->rva = c[C_RVA];
     Iw->ruc = c[C_RUC];
+    inst_derive(*Iw, c);
   }
 }
 
@@ -617,7 +622,7 @@ __global__ void __launch_bounds__(BS) k_prep_gen(Dev S, int changed_only) {
   bv[GR_GP] = S.G[F_PBAR * NGP + gp];
   bv[GR_GQ] = S.G[F_QBAR * NGP + gp];
   bv[GR_TC] = (t > 0) ? S.G[F_PBAR * NGP + gp - I.ng] : 0.0;
-  const double irpq = 1.0 / I.rpq;
+  const double irpq = I.irpq;
 #pragma unroll
   for (int r = 0; r < NGR; ++r) {
     S.GT[r * NGP + gp] = (r <= GR_SD) ? row_target_exact(bv[r], S.GZ[r * NGP + gp], S.GY[r * NGP + gp], I.ruc)
@@ -648,7 +653,7 @@ __global__ void __launch_bounds__(BS) k_prep_branch(Dev S, int changed_only) {
   bv[5] = S.U[FU_W * NUP + ut];
   bv[6] = S.U[FU_TH * NUP + uf];
   bv[7] = S.U[FU_TH * NUP + ut];
-  const double irpq = 1.0 / I.rpq, irva = 1.0 / I.rva;
+  const double irpq = I.irpq, irva = I.irva;
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const long long e = erow_u(r) * NEP + (erow_end(r) ? et : ef);

@@ -633,6 +633,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     D.gran_bp0 = q0b[k]; D.gran_bp1 = q1b[k];
     D.gran_up0 = u0b[k]; D.gran_up1 = u1b[k];
     D.rpq = rhos[k].pq; D.rva = rhos[k].va; D.ruc = rhos[k].uc;
+    inst_derive(D, &ctrl[(size_t)k * NCTRL]);
     h->inst_h.push_back(D);
   }
 
@@ -648,7 +649,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_E = A.take<double>((size_t)22 * NEP);
   const size_t o_es = A.take<int>(2 * NL + 2 * blk_off.size());
   const size_t o_stage = A.take<double>((size_t)NSTAGE * max_nbp);
-  const size_t o_bus = A.take<double>(2 * NB);
+  const size_t o_bus = A.take<double>(3 * NB);
   const size_t o_csr = A.take<int>((NB + 1) * 2 + NGEN + NB);
   const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
   const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
@@ -698,7 +699,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.eslot = es; D.blk_off = es + 2 * NL; D.blk_w = D.blk_off + blk_off.size();
   h->stage = (double *)(ar + o_stage);
   D.NB = NB;
-  D.Gs = (const double *)(ar + o_bus); D.Bs = D.Gs + NB;
+  D.Gs = (const double *)(ar + o_bus); D.Bs = D.Gs + NB; D.ideg = D.Gs + 2 * NB;
   const int *csr = (const int *)(ar + o_csr);
   D.inc_ptr = csr; D.gen_ptr = csr + (NB + 1);
   D.gen_idx = D.gen_ptr + (NB + 1);
@@ -743,6 +744,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   bfth.insert(bfth.end(), bt.begin(), bt.end());
   std::vector<double> bush(Gs);
   bush.insert(bush.end(), Bs.begin(), Bs.end());
+  for (long long i = 0; i < NB; ++i) bush.push_back(1.0 / (double)(inc_ptr[i + 1] - inc_ptr[i]));
   std::vector<int> csrh(inc_ptr);
   csrh.insert(csrh.end(), gen_ptr.begin(), gen_ptr.end());
   csrh.insert(csrh.end(), gen_idx.begin(), gen_idx.end());
