@@ -130,6 +130,7 @@ struct Dev {
   // buses
   long long NB;
   const double *Gs, *Bs, *ideg;  // shunt, 1/degree
+  double *bus_nu;  // [2][3][NB]: multiplier-solve coefficients per period kind (k_prep_bus)
   const int *inc_ptr;            // CSR row pointers over global buses (degree)
   const int *gen_ptr, *gen_idx;  // CSR over global buses; generator index local
   const int *bus_order;                    // [NB] per instance: local buses sorted by (degree, generators)

@@ -148,20 +148,17 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const double irpq = Fpq.irho;
     const bool last = (t == I.T - 1);
     const int g0 = S.gen_ptr[ig], g1 = S.gen_ptr[ig + 1], deg = S.inc_ptr[ig + 1] - S.inc_ptr[ig];
-    // pass 1: targets m_v, weights W_v and the 2x2 multiplier system
-    double M00 = 0.0, M01 = 0.0, M11 = 0.0, r0 = 0.0, r1 = 0.0, mw = 0.0, mth = 0.0;
+    // pass 1: targets m_v and the right-hand side of the 2x2 multiplier
+    // system (its matrix is constant between penalty changes: k_prep_bus)
+    double r0 = 0.0, r1 = 0.0, mw = 0.0, mth = 0.0;
     for (int e = g0; e < g1; ++e) {
       const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
       double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GZ[GR_GP * NGP + gp], S.GY[GR_GP * NGP + gp], Fpq);
-      double iW = irpq;
       if (!last) {
         const long long gn = gp + I.ng;
         m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], Fpq)));
-        iW = 0.5 * irpq;
       }
-      M00 = add_(M00, iW);
       r0 = add_(r0, m);
-      M11 = add_(M11, irpq);
       r1 = add_(r1, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq));
     }
     // (the p, q x-bar-step targets are parked in the target slots for pass
@@ -179,26 +176,16 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
       mth = add_(mth, row_mtarget(S.EA[3 * NEP + e], S.EZ[3 * NEP + e], S.EY[3 * NEP + e], Fva));
     }
     const double fdeg = (double)deg;
-    M00 = fma_(fdeg, irpq, M00);
-    M11 = fma_(fdeg, irpq, M11);
     const double ideg = S.ideg[ig];
     mw = mul_(mw, ideg);
     mth = mul_(mth, ideg);
     const double iWw = mul_(Fva.irho, ideg), aPw = -S.Gs[ig], aQw = S.Bs[ig];
-    M00 = fma_(mul_(aPw, aPw), iWw, M00);
-    M01 = fma_(mul_(aPw, aQw), iWw, M01);
-    M11 = fma_(mul_(aQw, aQw), iWw, M11);
     r0 = sub_(fma_(aPw, mw, r0), S.Pd[up]);
     r1 = sub_(fma_(aQw, mw, r1), S.Qd[up]);
-    double nuP, nuQ;
-    if (M01 == 0.0) {
-      nuP = (M00 > 0.0) ? r0 / M00 : 0.0;
-      nuQ = (M11 > 0.0) ? r1 / M11 : 0.0;
-    } else {
-      const double idet = 1.0 / sub_(mul_(M00, M11), mul_(M01, M01));
-      nuP = mul_(sub_(mul_(M11, r0), mul_(M01, r1)), idet);
-      nuQ = mul_(sub_(mul_(M00, r1), mul_(M01, r0)), idet);
-    }
+    const double *cf = S.bus_nu + (last ? 3 * S.NB : 0);
+    const double c0 = cf[ig], c1 = cf[S.NB + ig], c2 = cf[2 * S.NB + ig];
+    const double nuP = fma_(c0, r0, -mul_(c1, r1));
+    const double nuQ = fma_(c2, r1, -mul_(c1, r0));
     // pass 2: new x-bar values, then the rows they own
     for (int e = g0; e < g1; ++e) {
       const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
@@ -658,6 +645,51 @@ __global__ void __launch_bounds__(BS) k_prep_branch(Dev S, int changed_only) {
   for (int r = 0; r < 8; ++r) {
     const long long e = erow_u(r) * NEP + (erow_end(r) ? et : ef);
     S.ET[e] = row_target_fast(bv[r], S.EZ[e], S.EY[e], (r < 4) ? irpq : irva);
+  }
+}
+
+// Coefficients of the bus multiplier solve (R8).  The 2x2 system M nu = r
+// of bus i has
+//   M_PP = sum_g W_g^-1 + deg/rho_pq + Gs^2/(deg rho_va),
+//   M_QQ = n_g/rho_pq + deg/rho_pq + Bs^2/(deg rho_va),
+//   M_PQ = -Gs Bs/(deg rho_va),
+// with W_g = 2 rho_pq for a generator whose p row is averaged with the next
+// period's temporal-copy row (every period but the last) and rho_pq in the
+// last; so M depends on the penalties and the bus alone.  Its inverse is
+// formed here, after create, import and each penalty change, as
+// nu_P = c0 r_P - c1 r_Q, nu_Q = c2 r_Q - c1 r_P: [kind][c0, c1, c2][NB],
+// kind 0 for t < T - 1 and 1 for t = T - 1.  One thread per bus of
+// instance blockIdx.y.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_prep_bus(Dev S, int changed_only) {
+  const int k = blockIdx.y;
+  if (changed_only && S.res[(long long)k * NRES + R_RCHG] == 0.0) return;
+  const Inst I = S.inst[k];
+  const int i = blockIdx.x * BS + threadIdx.x;
+  if (i >= I.nb) return;
+  const int ig = I.uo + i;
+  const double ngen = (double)(S.gen_ptr[ig + 1] - S.gen_ptr[ig]);
+  const double fdeg = (double)(S.inc_ptr[ig + 1] - S.inc_ptr[ig]);
+  const double irpq = I.irpq, iWw = I.irva * S.ideg[ig], aPw = -S.Gs[ig], aQw = S.Bs[ig];
+  for (int kind = 0; kind < 2; ++kind) {
+    const double M00 = (kind ? ngen : 0.5 * ngen) * irpq + fdeg * irpq + aPw * aPw * iWw;
+    const double M11 = ngen * irpq + fdeg * irpq + aQw * aQw * iWw;
+    const double M01 = aPw * aQw * iWw;
+    double c0, c1, c2;
+    if (M01 == 0.0) {
+      c0 = M00 > 0.0 ? 1.0 / M00 : 0.0;
+      c1 = 0.0;
+      c2 = M11 > 0.0 ? 1.0 / M11 : 0.0;
+    } else {
+      const double idet = 1.0 / (M00 * M11 - M01 * M01);
+      c0 = M11 * idet;
+      c1 = M01 * idet;
+      c2 = M00 * idet;
+    }
+    double *cf = S.bus_nu + (long long)kind * 3 * S.NB;
+    cf[ig] = c0;
+    cf[S.NB + ig] = c1;
+    cf[2 * S.NB + ig] = c2;
   }
 }
 
