@@ -220,8 +220,10 @@ const char *ucac_kernel_name(int32_t k);
  * candidate block size of each sweep kernel (32, 64, 128, 256 threads; the
  * persistent line kernel 32, 64, 128) on the handle's own workload --
  * sweeps_per_trial sweeps per candidate after one warm-up sweep, CUDA events
- * on the handle's stream, the iterate restored before every trial -- keeps
- * the fastest per kernel and re-captures the sweep graph.  Block sizes change
+ * on the handle's stream, the iterate restored before every trial -- and
+ * re-captures the sweep graph.  Per kernel the current size is timed first
+ * and a candidate replaces it only when at least 2% faster (on large
+ * batches the sizes differ by about the noise of a trial).  Block sizes change
  * no result (work is split in warp-sized granules of one instance each), only
  * the speed.  cache_path (NULL: none) is a text file of lines
  *   <device name>|<instances>|<gen-periods>|<line-periods>|<bus-periods>|<line form> ucdp gen line bus ucbar

@@ -1079,13 +1079,20 @@ int ucac_autotune(ucac_handle *h, int32_t sweeps_per_trial, const char *cache_pa
   int* fields[5] = {&best.ucdp, &best.gen, &best.line, &best.bus, &best.ucbar};
   const int kidx[5] = {0, 1, 2, 3, 4};  // position of each kernel in ucac_kernel_times
   double ms[UCAC_N_KERNELS];
+  // per kernel: the incumbent block size is timed first, and a candidate
+  // replaces it only when it is at least kWin faster (the kernels' times
+  // differ by about 1% across block sizes on large batches, about the noise
+  // of one trial, so without the margin the pick would follow the noise)
+  constexpr double kWin = 0.02;
   for (int f = 0; f < 5 && e == cudaSuccess; ++f) {
     const bool line = (f == 2);
     const int nc = line ? 3 : 4;
     double best_ms = INFINITY;
-    int best_bs = *fields[f];
-    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-      const int bs = line ? kLineBlockSizes[c] : kBlockSizes[c];
+    const int inc = *fields[f];
+    int best_bs = inc;
+    for (int c = -1; c < nc && e == cudaSuccess; ++c) {
+      const int bs = c < 0 ? inc : (line ? kLineBlockSizes[c] : kBlockSizes[c]);
+      if (c >= 0 && bs == inc) continue;
       h->tune = best;
       int *cur[5] = {&h->tune.ucdp, &h->tune.gen, &h->tune.line, &h->tune.bus, &h->tune.ucbar};
       *cur[f] = bs;
@@ -1094,7 +1101,7 @@ int ucac_autotune(ucac_handle *h, int32_t sweeps_per_trial, const char *cache_pa
       if (e != cudaSuccess) break;
       if (ucac_kernel_times(h, 1, ms) != UCAC_OK) { e = cudaErrorUnknown; break; }
       if (ucac_kernel_times(h, sweeps_per_trial, ms) != UCAC_OK) { e = cudaErrorUnknown; break; }
-      if (ms[kidx[f]] < best_ms) {
+      if (c < 0 || ms[kidx[f]] < (1.0 - kWin) * best_ms) {
         best_ms = ms[kidx[f]];
         best_bs = bs;
       }
