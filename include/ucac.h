@@ -350,8 +350,8 @@ int ucac_warm_start_stats(const ucac_handle *h, int32_t instance, int64_t *taken
 int ucac_probe_fp64(int32_t reps, void *cuda_stream, double *flops);
 
 /*
- * Evaluates the polar line kernel's cos/sin (a table of cos(k/64), sin(k/64)
- * rotated by the Taylor series of the remainder) on the device for n angles
+ * Evaluates the polar line kernel's cos/sin (a table of cos(k/256),
+ * sin(k/256) rotated by the Taylor series of the remainder) on the device for n angles
  * |d[i]| <= pi given in HOST memory; c[i], s[i] (HOST) receive the results.
  * For testing the kernel's trigonometry against a reference.  Synchronises.
  * UCAC_E_ARG for n < 0 or a NULL buffer with n > 0.

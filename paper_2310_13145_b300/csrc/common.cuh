@@ -87,10 +87,11 @@ struct Params {
 
 constexpr int GRAN = 32;  // items per granule (one warp)
 
-// cos(k / 64), sin(k / 64) for k = -TRIG_K..TRIG_K (|k / 64| <= pi + 1/64),
-// filled from the host's libm when a handle is created (the same values on
-// every device and handle)
-constexpr int TRIG_K = 202;
+// cos(k / TRIG_N), sin(k / TRIG_N) for k = -TRIG_K..TRIG_K (|k / TRIG_N| <=
+// pi + 1/TRIG_N, 25.8 KB), filled from the host's libm when a handle is
+// created (the same values on every device and handle)
+constexpr int TRIG_N = 256;
+constexpr int TRIG_K = 805;
 __device__ double2 g_trig[2 * TRIG_K + 1];
 
 struct Granules {

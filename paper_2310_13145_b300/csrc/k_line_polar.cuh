@@ -132,19 +132,20 @@ __device__ __forceinline__ double pol_clamp(const PolK &K, int i, double x) {
   return __double_as_longlong(x) > 0 ? x : 0.0;
 }
 
-// cos d and sin d for |d| <= pi: d = k/64 + r with |r| <= 1/128 (r exact),
-// cos(k/64) and sin(k/64) from the table, cos r and sin r from their Taylor
-// series to r^6 and r^5 (truncation below 4e-19), then the angle-sum
-// formulas.  About 15 FP64 operations against 25 for the library sincos; the
-// table index is clamped on the integer units, so every read is in bounds
+// cos d and sin d for |d| <= pi: d = k/256 + r with |r| <= 1/512 (r exact),
+// cos(k/256) and sin(k/256) from the table, cos r and sin r from their
+// Taylor series to r^4 and r^3 (truncation below 2.4e-16 and 8e-20), then
+// the angle-sum formulas.  About 13 FP64 operations against 25 for the
+// library sincos; the table index is clamped on the integer units, so every
+// read is in bounds
 __device__ __forceinline__ void pol_cossin(double d, double &c, double &s) {
-  const double kd = rint(d * 64.0);
+  const double kd = rint(d * (double)TRIG_N);
   int k = (int)kd;
   k = k < -TRIG_K ? -TRIG_K : (k > TRIG_K ? TRIG_K : k);
-  const double r = fma(-kd, 0.015625, d);
+  const double r = fma(-kd, 1.0 / TRIG_N, d);
   const double r2 = r * r;
-  const double sr = fma(r * r2, fma(r2, 1.0 / 120.0, -1.0 / 6.0), r);
-  const double cr = fma(r2, fma(r2, fma(r2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+  const double sr = fma(r * r2, -1.0 / 6.0, r);
+  const double cr = fma(r2, fma(r2, 1.0 / 24.0, -0.5), 1.0);
   const double2 t = g_trig[k + TRIG_K];
   c = fma(t.x, cr, -(t.y * sr));
   s = fma(t.y, cr, t.x * sr);

@@ -189,8 +189,8 @@ void launch_ucbar(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.ucb
 cudaError_t upload_trig() {
   std::vector<double> t(2 * (2 * TRIG_K + 1));
   for (int k = -TRIG_K; k <= TRIG_K; ++k) {
-    t[2 * (k + TRIG_K)] = std::cos(k / 64.0);
-    t[2 * (k + TRIG_K) + 1] = std::sin(k / 64.0);
+    t[2 * (k + TRIG_K)] = std::cos((double)k / TRIG_N);
+    t[2 * (k + TRIG_K) + 1] = std::sin((double)k / TRIG_N);
   }
   return cudaMemcpyToSymbol(g_trig, t.data(), t.size() * sizeof(double));
 }

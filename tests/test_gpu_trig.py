@@ -1,20 +1,22 @@
-"""The polar line kernel's cos/sin (table of cos(k/64), sin(k/64) rotated by
-the Taylor series of the remainder) against numpy's cos/sin on the device."""
+"""The polar line kernel's cos/sin (table of cos(k/256), sin(k/256) rotated
+by the Taylor series of the remainder) against numpy's cos/sin on the
+device."""
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
 
 PI_BOUND = 3.14159265358979  # the angle bound of the polar line variables
+TRIG_N = 256  # table resolution
 
 
 def _angles():
     rng = np.random.default_rng(7)
-    k = np.arange(-201, 202)
+    k = np.arange(-804, 805)
     pts = [np.array([0.0, -0.0, 1e-300, -1e-300, 1e-9, -1e-9, PI_BOUND, -PI_BOUND, np.pi / 2, -np.pi / 2]),
-           k / 64.0,                                      # table points (remainder 0)
-           (k[:-1] + 0.5) / 64.0,                         # halfway: rint ties
-           np.nextafter((k[:-1] + 0.5) / 64.0, np.inf),   # just past the ties
+           k / TRIG_N,                                      # table points (remainder 0)
+           (k[:-1] + 0.5) / TRIG_N,                         # halfway: rint ties
+           np.nextafter((k[:-1] + 0.5) / TRIG_N, np.inf),   # just past the ties
            rng.uniform(-PI_BOUND, PI_BOUND, 20000),
            rng.normal(0.0, 0.1, 20000).clip(-PI_BOUND, PI_BOUND)]  # line angles are mostly small
     return np.concatenate(pts)
