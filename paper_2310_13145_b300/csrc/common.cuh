@@ -130,7 +130,7 @@ struct Dev {
   const int *blk_off, *blk_w;   // per bus block: slot offset within the period, width
   // buses
   long long NB;
-  const double *Gs, *Bs, *ideg;  // shunt, 1/degree
+  const double *Gs, *Bs, *ideg, *vmid;  // shunt, 1/degree, middle of the voltage band
   double *bus_nu;  // [2][3][NB]: multiplier-solve coefficients per period kind (k_prep_bus)
   const int *inc_ptr;            // CSR row pointers over global buses (degree)
   const int *gen_ptr, *gen_idx;  // CSR over global buses; generator index local

@@ -21,6 +21,7 @@
 #include "../../include/ucac.h"
 #include "common.cuh"
 #include "k_branch.cuh"
+#include "k_cold.cuh"
 #include "k_gen.cuh"
 #include "k_line_polar.cuh"
 #include "k_mlp.cuh"
@@ -402,8 +403,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   std::vector<int> bf(NL), bt(NL);
   std::vector<double> Gs(NB), Bs(NB), Pd(NUP), Qd(NUP);
   std::vector<int> inc_ptr(NB + 1, 0), inc_br(2 * NL), inc_side(2 * NL), gen_ptr(NB + 1, 0), gen_idx(NGEN);
-  std::vector<double> G((size_t)NGF * NGP, 0.0), B((size_t)FB_FB0 * NBP, 0.0), U((size_t)NUF * NUP, 0.0);
-  std::vector<double> fb0((size_t)4 * NBP, 0.0);  // cold-start x-bar of the flow rows, canonical [r][bp]
+  std::vector<double> vmid(NB);  // middle of each bus's voltage band (the cold start, formed on the device)
   std::vector<double> ctrl((size_t)NCTRL * n, 0.0);
   const double twopi = 6.283185307179586476925286766559;
   for (int k = 0; k < n; ++k) {
@@ -454,6 +454,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     for (int i = 0; i < I.nb; ++i) {
       Gs[I.uo + i] = g->Gs[i];
       Bs[I.uo + i] = g->Bs[i];
+      vmid[I.uo + i] = 0.5 * (g->Vmin[i] + g->Vmax[i]);
     }
     for (int t = 0; t < I.T; ++t)
       for (int i = 0; i < I.nb; ++i) {
@@ -466,47 +467,9 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
       inc_ptr[I.uo + g->br_to[l] + 1]++;
     }
     for (int j = 0; j < I.ng; ++j) gen_ptr[I.uo + g->gen_bus[j] + 1]++;
-    // cold start (Sec. IV-A) and all units on
-    for (int t = 0; t < I.T; ++t)
-      for (int j = 0; j < I.ng; ++j) {
-        const long long gp = I.gpo + (long long)t * I.ng + j, gg = I.go + j;
-        const double p = 0.5 * Pmax[gg], q = 0.5 * (qlo[gg] + qhi[gg]);
-        G[F_P * NGP + gp] = p;
-        G[F_Q * NGP + gp] = q;
-        G[F_PH * NGP + gp] = (t > 0) ? 0.5 * Pmax[gg] : p0[gg];
-        G[F_UON * NGP + gp] = 1.0;
-        G[F_PBAR * NGP + gp] = p;
-        G[F_QBAR * NGP + gp] = q;
-        G[F_UBON * NGP + gp] = 1.0;
-      }
-    const double cpen0 = P.c_init_rel * std::max(rhos[k].pq, rhos[k].va);
-    for (int t = 0; t < I.T; ++t) {
-      for (int i = 0; i < I.nb; ++i) {
-        const double V = 0.5 * (g->Vmin[i] + g->Vmax[i]);
-        U[FU_W * NUP + I.upo + (long long)t * I.nb + i] = V * V;
-      }
-      for (int l = 0; l < I.nl; ++l) {
-        const long long bp = I.bpo + (long long)t * I.nl + l, lg = I.lo + l;
-        const int i = g->br_from[l], j = g->br_to[l];
-        const double Vi = 0.5 * (g->Vmin[i] + g->Vmax[i]), Vj = 0.5 * (g->Vmin[j] + g->Vmax[j]);
-        double v[8] = {Vi * Vi, Vj * Vj, Vi * Vj, 0.0, 0.0, 0.0, 0.0, 0.0};
-        const double *Y = &BC[0];
-        auto Yq = [&](int q) { return Y[(BC_Y0 + q) * NL + lg]; };
-        const double a0 = Yq(0) * v[0] + Yq(2) * v[2] + Yq(3) * v[3];
-        const double a1 = -Yq(1) * v[0] - Yq(3) * v[2] + Yq(2) * v[3];
-        const double a2 = Yq(4) * v[1] + Yq(6) * v[2] - Yq(7) * v[3];
-        const double a3 = -Yq(5) * v[1] - Yq(7) * v[2] - Yq(6) * v[3];
-        const double rate2 = BC[BC_RATE2 * NL + lg];
-        v[6] = std::min(std::max(rate2 - a0 * a0 - a1 * a1, 0.0), rate2);
-        v[7] = std::min(std::max(rate2 - a2 * a2 - a3 * a3, 0.0), rate2);
-        for (int q = 0; q < 8; ++q) B[(FB_V0 + q) * NBP + bp] = v[q];
-        B[FB_C * NBP + bp] = cpen0;
-        fb0[0 * NBP + bp] = a0;
-        fb0[1 * NBP + bp] = a1;
-        fb0[2 * NBP + bp] = a2;
-        fb0[3 * NBP + bp] = a3;
-      }
-    }
+    // (the cold start of Sec. IV-A -- flat voltages, all units on at half
+    // capacity, the line variables and flows of that point -- is formed on
+    // the device by the k_cold_* kernels after the upload)
     ctrl[(size_t)k * NCTRL + C_BETA] = P.beta0;
     ctrl[(size_t)k * NCTRL + C_ZPREV] = -1.0;
     ctrl[(size_t)k * NCTRL + C_BNEXT] = P.beta0;
@@ -583,16 +546,6 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   h->NEP = NEP;
   h->max_nbp = max_nbp;
   for (int k = 0; k < n; ++k) h->max_nb = std::max(h->max_nb, (long long)h->hi[k].nb);
-  std::vector<double> efb((size_t)2 * NEP, 0.0);
-  for (int k = 0; k < n; ++k) {
-    const HInst &I = h->hi[k];
-    for (int t = 0; t < I.T; ++t)
-      for (int l = 0; l < I.nl; ++l) {
-        const long long bp = I.bpo + (long long)t * I.nl + l, base = I.eo + (long long)t * I.spp;
-        const long long ee[2] = {base + eslot[I.lo + l], base + eslot[NL + I.lo + l]};
-        for (int r = 0; r < 4; ++r) efb[(size_t)erow_u(r) * NEP + ee[erow_end(r)]] = fb0[(size_t)r * NBP + bp];
-      }
-  }
   // ---- block tables
   std::vector<int> bgi, bgf, bpi, bpf, bbi, bbf, bui, buf_;
   std::vector<int> g0(n), g1(n), p0b(n), p1b(n), q0b(n), q1b(n), u0b(n), u1b(n);
@@ -652,7 +605,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_E = A.take<double>((size_t)22 * NEP);
   const size_t o_es = A.take<int>(2 * NL + 2 * blk_off.size());
   const size_t o_stage = A.take<double>((size_t)NSTAGE * max_nbp);
-  const size_t o_bus = A.take<double>(3 * NB), o_busnu = A.take<double>(6 * NB);
+  const size_t o_bus = A.take<double>(4 * NB), o_busnu = A.take<double>(6 * NB);
   const size_t o_csr = A.take<int>((NB + 1) * 2 + NGEN + NB);
   const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
   const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
@@ -702,7 +655,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.eslot = es; D.blk_off = es + 2 * NL; D.blk_w = D.blk_off + blk_off.size();
   h->stage = (double *)(ar + o_stage);
   D.NB = NB;
-  D.Gs = (const double *)(ar + o_bus); D.Bs = D.Gs + NB; D.ideg = D.Gs + 2 * NB;
+  D.Gs = (const double *)(ar + o_bus); D.Bs = D.Gs + NB; D.ideg = D.Gs + 2 * NB; D.vmid = D.Gs + 3 * NB;
   D.bus_nu = (double *)(ar + o_busnu);
   const int *csr = (const int *)(ar + o_csr);
   D.inc_ptr = csr; D.gen_ptr = csr + (NB + 1);
@@ -749,6 +702,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   std::vector<double> bush(Gs);
   bush.insert(bush.end(), Bs.begin(), Bs.end());
   for (long long i = 0; i < NB; ++i) bush.push_back(1.0 / (double)(inc_ptr[i + 1] - inc_ptr[i]));
+  bush.insert(bush.end(), vmid.begin(), vmid.end());
   std::vector<int> csrh(inc_ptr);
   csrh.insert(csrh.end(), gen_ptr.begin(), gen_ptr.end());
   csrh.insert(csrh.end(), gen_idx.begin(), gen_idx.end());
@@ -767,17 +721,13 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   chain(up(D.inst, h->inst_h.data(), sizeof(Inst) * n));
   chain(up(gd, gdh.data(), gdh.size() * 8));
   chain(up(gi, gih.data(), gih.size() * 4));
-  chain(up(D.G, G.data(), G.size() * 8));
   chain(up(D.BC, BC.data(), BC.size() * 8));
   chain(up(D.BCF, BCF.data(), BCF.size() * 4));
   chain(up(D.bf, bfth.data(), bfth.size() * 4));
-  chain(up(D.B, B.data(), B.size() * 8));
-  chain(up(D.EFB, efb.data(), efb.size() * 8));
   chain(up(D.eslot, esh.data(), esh.size() * 4));
   chain(up(D.Gs, bush.data(), bush.size() * 8));
   chain(up(csr, csrh.data(), csrh.size() * 4));
   chain(up(D.Pd, pqh.data(), pqh.size() * 8));
-  chain(up(D.U, U.data(), U.size() * 8));
   chain(up(D.ctrl, ctrl.data(), ctrl.size() * 8));
   chain(up(D.g_gen.inst, blkh.data(), blkh.size() * 4));
   if (e != cudaSuccess) {
@@ -786,6 +736,15 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     return fail(nullptr, UCAC_E_CUDA, m);
   }
   h->grid_branch = line_grid(h, h->tune.line);
+  {
+    // the cold start, then the x-step targets from it
+    long long max_nup = 0;
+    for (int k = 0; k < n; ++k) max_nup = std::max(max_nup, (long long)h->hi[k].T * h->hi[k].nb);
+    k_cold_gen<BS_PREP><<<blocks_for(h->ngr_gp, BS_PREP), BS_PREP, 0, h->stream>>>(h->dev);
+    k_cold_branch<BS_PREP><<<blocks_for(h->ngr_bp, BS_PREP), BS_PREP, 0, h->stream>>>(h->dev);
+    k_cold_bus<BS_PREP><<<dim3((unsigned)((max_nup + BS_PREP - 1) / BS_PREP), (unsigned)n), BS_PREP, 0, h->stream>>>(
+        h->dev);
+  }
   launch_prep(h, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
