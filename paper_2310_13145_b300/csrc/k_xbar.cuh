@@ -395,27 +395,35 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
     const double Pmin = S.Pmin[gg], Pmax = S.Pmax[gg], Qmin = S.Qmin[gg], Qmax = S.Qmax[gg];
     const double RU = S.RU[gg], RD = S.RD[gg], SU = S.SU[gg], SD = S.SD[gg];
 #define MT(r, idx, F) row_mtarget(S.GA[(r)*NGP + (idx)], S.GZ[(r)*NGP + (idx)], S.GY[(r)*NGP + (idx)], F)
-    double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gv[3] = {0, 0, 0};
-    auto addrow = [&](double w, double m, double e0, double e1, double e2) {
-      const double e[3] = {e0, e1, e2};
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        gv[a] += w * m * e[a];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) H[a][c] += w * e[a] * e[c];
-      }
-    };
-    addrow(ruc, MT(GR_ON, gp, Fuc), 1.0, 0.0, 0.0);
-    addrow(ruc, MT(GR_SD, gp, Fuc), 0.0, 1.0, 0.0);
-    addrow(rpq, MT(GR_PL, gp, Fpq), Pmin, 0.0, 0.0);
-    addrow(rpq, MT(GR_PU, gp, Fpq), Pmax, 0.0, 0.0);
-    addrow(rpq, MT(GR_QL, gp, Fpq), Qmin, 0.0, 0.0);
-    addrow(rpq, MT(GR_QU, gp, Fpq), Qmax, 0.0, 0.0);
-    addrow(rpq, MT(GR_RD, gp, Fpq), -RD, -SD, 0.0);
+    // H and gv of the box QP in (u_on, u_sd, u_su at t+1): row r with weight
+    // w_r, x-bar-step target m_r and coefficients e_r over the three adds
+    // w_r e_r e_r^T to H and w_r m_r e_r to gv.  The rows are
+    //   on (ruc; 1, 0, 0), sd (ruc; 0, 1, 0), pl, pu, ql, qu (rpq; Pmin,
+    //   Pmax, Qmin, Qmax, 0, 0), rd (rpq; -RD, -SD, 0), and with a next
+    //   period su (ruc; 0, 0, 1), ru (rpq; RU, 0, SU);
+    // only the nonzero products are formed (the FP64 pipe bounds the kernel).
+    const double m_on = MT(GR_ON, gp, Fuc), m_sd = MT(GR_SD, gp, Fuc);
+    const double m_pl = MT(GR_PL, gp, Fpq), m_pu = MT(GR_PU, gp, Fpq);
+    const double m_ql = MT(GR_QL, gp, Fpq), m_qu = MT(GR_QU, gp, Fpq), m_rd = MT(GR_RD, gp, Fpq);
+    double H[3][3], gv[3];
+    H[0][0] = ruc + rpq * (Pmin * Pmin + Pmax * Pmax + Qmin * Qmin + Qmax * Qmax + RD * RD);
+    H[0][1] = rpq * (RD * SD);
+    H[1][1] = ruc + rpq * (SD * SD);
+    H[0][2] = H[1][2] = H[2][2] = 0.0;
+    gv[0] = ruc * m_on + rpq * (m_pl * Pmin + m_pu * Pmax + m_ql * Qmin + m_qu * Qmax - m_rd * RD);
+    gv[1] = ruc * m_sd - rpq * (m_rd * SD);
+    gv[2] = 0.0;
     if (has_next) {
-      addrow(ruc, MT(GR_SU, gn, Fuc), 0.0, 0.0, 1.0);
-      addrow(rpq, MT(GR_RU, gn, Fpq), RU, 0.0, SU);
+      const double m_su = MT(GR_SU, gn, Fuc), m_ru = MT(GR_RU, gn, Fpq);
+      H[0][0] += rpq * (RU * RU);
+      H[0][2] = rpq * (RU * SU);
+      H[2][2] = ruc + rpq * (SU * SU);
+      gv[0] += rpq * (m_ru * RU);
+      gv[2] = ruc * m_su + rpq * (m_ru * SU);
     }
+    H[1][0] = H[0][1];
+    H[2][0] = H[0][2];
+    H[2][1] = H[1][2];
     const double on_old = S.G[F_UBON * NGP + gp], sd_old = S.G[F_UBSD * NGP + gp];
     const double su1_old = has_next ? S.G[F_UBSU * NGP + gn] : 0.0;
     const double su0_old = (tau == 0) ? S.G[F_UBSU * NGP + gp] : 0.0;

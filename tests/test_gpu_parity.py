@@ -72,6 +72,18 @@ def test_cold_start_matches(ucac_mod):
     h.close()
 
 
+def test_cold_start_matches_ragged_batch(ucac_mod):
+    # the device forms the cold start of every instance of a batch (uneven
+    # sizes and horizons: the granule and slot indexing of each instance)
+    grids = synth.config_instances("c4_batch64", 4)
+    assert len({(g.n_bus, g.T) for g in grids}) > 1
+    h = ucac_mod.Handle(grids)
+    for k, g in enumerate(grids):
+        bad = compare_states(h.export(k), oracle.Oracle(g).state_vector(), g, rtol=1e-14)
+        assert not bad, (k, bad[:6])
+    h.close()
+
+
 def test_lockstep_9bus(ucac_mod, line_form):
     g = synth.config_instances("c1_9bus_T6")[0]
     _lockstep(ucac_mod, [g], 40, line_form=line_form)
