@@ -701,6 +701,22 @@ __global__ void __launch_bounds__(BS) k_prep_bus(Dev S, int changed_only) {
   }
 }
 
+// The line flows of instance k's solution as one [t * nl + l][4] block
+// (p_ij, q_ij, p_ji, q_ji: the x values of the four flow rows), gathered from
+// the line-end slots for a single copy to the host.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_solution_flows(Dev S, int k, double *pf) {
+  const Inst I = S.inst[k];
+  const long long n = (long long)I.T * I.nl;
+  const long long loc = (long long)blockIdx.x * BS + threadIdx.x;
+  if (loc >= n) return;
+  const int t = (int)(loc / I.nl), l = (int)(loc - (long long)t * I.nl);
+  long long ef, et;
+  line_ends(S, I, t, (long long)I.lo + l, ef, et);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) pf[loc * 4 + r] = S.EA[erow_u(r) * S.NEP + (erow_end(r) ? et : ef)];
+}
+
 // Line-end rows of instance k between the slot layout and the canonical
 // [r][t * nl + l] order of the state vector (dir 0: slots -> canon, 1: back).
 // arr is a [4][NEP] (or [2][NEP] for the x-bar of p, q) slot array; rows r

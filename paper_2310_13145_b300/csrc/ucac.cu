@@ -844,14 +844,12 @@ int ucac_solution(const ucac_handle *hc, int32_t k, double *p, double *q, double
   if (w) CK(cudaMemcpy(w, D.U + FU_W * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost));
   if (theta) CK(cudaMemcpy(theta, D.U + FU_TH * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost));
   if (pf) {
-    edge_stage(h, k, 0, true, h->stream);
+    // gathered into the caller's [t][l][4] order on the device (the staging
+    // rows hold at least 4 nbp doubles), then one copy
+    k_solution_flows<256><<<(unsigned)((nbp + 255) / 256), 256, 0, h->stream>>>(h->dev, k, h->stage);
     CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(pf, h->stage, nbp * 4 * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    std::vector<double> tmp(nbp);
-    for (int r = 0; r < 4; ++r) {
-      CK(cudaMemcpy(tmp.data(), h->stage + (size_t)(4 + 3 * NBR + r) * nbp, nbp * 8, cudaMemcpyDeviceToHost));
-      for (size_t j = 0; j < nbp; ++j) pf[j * 4 + r] = tmp[j];
-    }
   }
   if (u_on) {
     std::vector<double> tmp(ngp);

@@ -226,3 +226,28 @@ def test_adaptive_penalty_resume_bitwise(ucac_mod):
     assert np.array_equal(a.export(0), b.export(0))
     a.close()
     b.close()
+
+
+def test_solution_readback(ucac_mod):
+    # ucac_solution of every instance of a ragged batch: generator p, q, u_on
+    # and bus w, theta are the iterate's own values; the line flows, in
+    # [t][l][p_ij, q_ij, p_ji, q_ji] order, are those of its line variables
+    # (the oracle's flow formula applied to the exported W-form variables)
+    grids = synth.config_instances("c4_batch64", 3)
+    h = ucac_mod.Handle(grids)
+    h.enqueue(12)
+    for k, g in enumerate(grids):
+        sol = ucac_mod.ucac_solution(h.h, k, g.T, g.n_gen, g.n_bus, g.n_branch)
+        buf = h.export(k)
+        st = oracle.unpack_state(buf, g.T, g.n_gen, g.n_branch, g.n_bus)
+        assert np.array_equal(sol["p"], st["p"]) and np.array_equal(sol["q"], st["q"])
+        assert np.array_equal(sol["u_on"], (st["u_on"] != 0).astype(np.uint8))
+        assert np.array_equal(sol["w"], st["wbar"]) and np.array_equal(sol["theta"], st["thbar"])
+        o = oracle.Oracle(g)
+        o.set_state(buf)
+        _, _, BA, _ = o.rows()
+        flows = np.moveaxis(BA[:4], 0, -1)  # [T][nl][4]
+        assert sol["pf"].shape == flows.shape
+        err = np.abs(sol["pf"] - flows).max()
+        assert err <= 1e-9 * max(1.0, np.abs(flows).max()), (k, err)
+    h.close()
