@@ -216,14 +216,15 @@ int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms);
 const char *ucac_kernel_name(int32_t k);
 
 /*
- * Autotuner (batching support; no counterpart in the paper).  Times every
- * candidate block size of each sweep kernel (32, 64, 128, 256 threads; the
- * persistent line kernel 32, 64, 128) on the handle's own workload --
- * sweeps_per_trial sweeps per candidate after one warm-up sweep, CUDA events
- * on the handle's stream, the iterate restored before every trial -- and
- * re-captures the sweep graph.  Per kernel the current size is timed first
- * and a candidate replaces it only when at least 2% faster (on large
- * batches the sizes differ by about the noise of a trial).  Block sizes change
+ * Autotuner (batching support; no counterpart in the paper).  Tries every
+ * candidate block size of each sweep kernel in turn (32, 64, 128, 256
+ * threads; the persistent line kernel 32, 64, 128) on the handle's own
+ * workload: the sweep graph is re-captured with the candidate, the iterate
+ * restored, and sweeps_per_trial replays after one warm-up replay are timed
+ * with CUDA events on the handle's stream.  The objective is the whole
+ * sweep, since the line kernel shares the GPU with the generator-side
+ * branch of the graph.  Per kernel the current size is timed first and a
+ * candidate replaces it only when the sweep is at least 1% faster.  Block sizes change
  * no result (work is split in warp-sized granules of one instance each), only
  * the speed.  cache_path (NULL: none) is a text file of lines
  *   <device name>|<instances>|<gen-periods>|<line-periods>|<bus-periods>|<line form> ucdp gen line bus ucbar
