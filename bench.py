@@ -465,6 +465,9 @@ def time_to_tolerance(ucac, grids, stream, params, max_sweeps, cache=None, warm=
             "newton_total": sum(r["newton_total"] for r in rs), "al_total": sum(r["al_total"] for r in rs),
             "starts_from_network": taken,
             "sweeps": done, "check_every": params.check_every,
+            # (a converged instance takes no further sweep: the last one to
+            # converge fixes the run's length, up to the check interval)
+            "instance_sweeps_max": max(r["sweeps"] for r in rs),
             "objective_mean": statistics.mean(r["objective"] for r in rs),
             "r_p_max": max(r["r_p"] for r in rs), "r_d_max": max(r["r_d"] for r in rs),
             "z_rms_max": max(r["z_rms"] for r in rs), "inf_norm_max": max(r["inf_norm_viol"] for r in rs),

@@ -1192,6 +1192,10 @@ static double mtg_of(double a, double z, double y, double rho) { return (a + z) 
  */
 EXPORT void orc_sweep(void *h) {
   orc_inst *I = (orc_inst *)h;
+  /* Algorithm 1 ends at convergence: an instance whose last sweep met both
+     stopping tests takes no further sweep, so its iterate, residuals and
+     counters stay those of that sweep */
+  if (I->ctrl[C_DONE] != 0.0) return;
   int T = I->T, ng = I->ng, nl = I->nl, nb = I->nb;
   const orc_params *P = &I->P;
   compute_b(I, I->GB, I->BB);

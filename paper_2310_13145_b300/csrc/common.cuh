@@ -178,6 +178,14 @@ __device__ __forceinline__ bool le_nn(double x, double y) { return __double_as_l
 __device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
 
 
+// Algorithm 1 stops an instance once it has converged: after the finish
+// kernel sets its done flag, no kernel of a later sweep touches the
+// instance, so its iterate, residual record and counters stay those of the
+// sweep that converged (the other instances of a batch go on)
+__device__ __forceinline__ bool inst_done(const Dev &S, int k) {
+  return S.ctrl[(long long)k * NCTRL + C_DONE] != 0.0;
+}
+
 // slots of the from / to end of line lg at period t of instance I
 __device__ __forceinline__ void line_ends(const Dev &S, const Inst &I, int t, long long lg, long long &ef,
                                           long long &et) {

@@ -399,6 +399,10 @@ __global__ void __launch_bounds__(BS) k_branch(Dev S) {
         } else {
           bp = item;
           k = find_instance(S, bp);
+        }
+        if (active && inst_done(S, k)) {
+          bp = -1;  // a converged instance's line: skipped (the lane fetches again)
+        } else if (active) {
           const Inst &I = S.inst[k];
           const int loc = (int)(bp - I.bpo);
           const int t = loc / I.nl, l = loc - t * I.nl;
@@ -438,7 +442,7 @@ __global__ void __launch_bounds__(BS) k_branch(Dev S) {
       }
     }
     if (__ballot_sync(FULL, active) == 0) break;
-    if (active) {
+    if (active && bp >= 0) {
       // ---- one Newton iteration
       if (need_f) f = br_phi(K, P, v);
       if (need_gH) br_derivs(K, P, v, g, H);

@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(BS) k_gen(Dev S) {
   const int gr = warp_granule<BS>(S.g_gp.n);
   if (gr < 0) return;
   const int k = S.g_gp.inst[gr];
+  if (inst_done(S, k)) return;
   const Inst I = S.inst[k];
   const long long gp = (long long)S.g_gp.first[gr] + (threadIdx.x & 31);
   if (gp >= (long long)I.gpo + (long long)I.T * I.ng) return;

@@ -864,27 +864,38 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         const long long left = NBP - (long long)base;
         const int got = left <= 0 ? 0 : (left < nb ? (int)left : nb);
         if (left <= nb) drained = true;
+        // the lines of a converged instance are skipped: the fetched items
+        // that remain are packed into the ring
+        long long it = -1;
+        int ki = 0;
         if (lane < got) {
-          const long long it = (long long)base + lane;
-          const int ki = find_instance(S, it);
+          it = (long long)base + lane;
+          ki = find_instance(S, it);
+          if (inst_done(S, ki)) it = -1;
+        }
+        const unsigned vm = __ballot_sync(FULL, it >= 0);
+        if (it >= 0) {
           double vs[POL_NV], ic;
           pol_start(S, ki, it, vs, ic);
-          const int sl = (qhead + qcount + lane) & (QN - 1);
+          const int sl = (qhead + qcount + __popc(vm & ((1u << lane) - 1u))) & (QN - 1);
           qit[wib][sl] = it;
           qk[wib][sl] = ki;
 #pragma unroll
           for (int i = 0; i < POL_NV; ++i) qv[wib][i][sl] = vs[i];
           qv[wib][POL_NV][sl] = ic;
         }
-        qcount += got;
+        qcount += __popc(vm);
         __syncwarp();
       }
       if (want) {
         const int r = __popc(m & ((1u << lane) - 1u));
         if (r >= qcount) {
-          // the ring is empty and the counter has passed NBP
-          active = false;
-          flush();
+          // the ring is empty: retire once the counter has passed NBP, else
+          // wait for the next fetch (skipped items can leave a fetch short)
+          if (drained) {
+            active = false;
+            flush();
+          }
         } else {
           const int sl = (qhead + r) & (QN - 1);
           bp = qit[wib][sl];
@@ -951,7 +962,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
       if (lane < ftail[wib] - fhead) pol_finish_out(S, frd, frf, fri, (fhead + lane) & (POL_QF - 1));
       break;
     }
-    if (active) {
+    if (active && bp >= 0) {
       // one full evaluation per trip: at a pending trial point (then the
       // ratio test), else at the current point when it moved
       int out = NI_CONT;

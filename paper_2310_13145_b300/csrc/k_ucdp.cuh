@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(BS) k_ucdp(Dev S) {
   const int gr = warp_granule<BS>(S.g_gen.n);
   if (gr < 0) return;
   const int k = S.g_gen.inst[gr];
+  if (inst_done(S, k)) return;
   const Inst I = S.inst[k];
   const int gg = S.g_gen.first[gr] + (threadIdx.x & 31);
   if (gg >= I.go + I.ng) return;

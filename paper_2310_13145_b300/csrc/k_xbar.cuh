@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
   const int gr = warp_granule<BS>(S.g_up.n);
   if (gr < 0) return;
   const int k = S.g_up.inst[gr];
+  if (inst_done(S, k)) return;  // (warp-uniform: a granule is one instance)
   const Inst I = S.inst[k];
   const int tb = S.g_up.first[gr];  // t * nblk + block
   const int t = tb / I.nblk, blk = tb - t * I.nblk;
@@ -380,6 +381,7 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
   const int gr = warp_granule<BS>(S.g_gp.n);
   if (gr < 0) return;
   const int k = S.g_gp.inst[gr];
+  if (inst_done(S, k)) return;  // (warp-uniform)
   const Inst I = S.inst[k];
   const long long gp = (long long)S.g_gp.first[gr] + (threadIdx.x & 31);
   double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -479,6 +481,7 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
 template <int BS>
 __global__ void __launch_bounds__(BS) k_finish(Dev S) {
   const int k = blockIdx.x;
+  if (inst_done(S, k)) return;  // converged earlier: the record stays
   const Inst I = S.inst[k];
   double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int bb = I.gran_up0 + threadIdx.x; bb < I.gran_up1; bb += BS) {

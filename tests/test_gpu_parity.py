@@ -251,3 +251,27 @@ def test_solution_readback(ucac_mod):
         err = np.abs(sol["pf"] - flows).max()
         assert err <= 1e-9 * max(1.0, np.abs(flows).max()), (k, err)
     h.close()
+
+
+def test_converged_instance_is_frozen_in_a_batch(ucac_mod):
+    # an instance that converges stops (Algorithm 1) while the rest of the
+    # batch goes on; the oracle agrees that a converged state takes no sweep
+    small = synth.config_instances("c1_9bus_T6")[0]
+    big = synth.config_instances("c2_118bus_T24x3", 1)[0]
+    h = ucac_mod.Handle([small, big])
+    for _ in range(80):
+        h.enqueue(25)
+        if h.residuals(0)["status"] == 1:
+            break
+    r0 = h.residuals(0)
+    assert r0["status"] == 1 and h.residuals(1)["status"] == 0
+    s0, s1 = h.export(0), h.export(1)
+    h.enqueue(10)
+    assert np.array_equal(h.export(0), s0)
+    assert h.residuals(0) == r0
+    assert not np.array_equal(h.export(1), s1)
+    o = oracle.Oracle(small)
+    o.set_state(s0)
+    o.sweep(3)
+    assert np.array_equal(o.state_vector(), s0)
+    h.close()

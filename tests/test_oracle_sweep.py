@@ -212,3 +212,23 @@ def test_adaptive_penalty_rule_and_state():
     o.sweep()
     o2.sweep()
     assert np.array_equal(o.state_vector(), o2.state_vector())
+
+
+def test_converged_instance_takes_no_further_sweep():
+    """Algorithm 1 ends at convergence: once a sweep has met both stopping
+    tests (r_p, r_d <= eps_in and z_rms <= eps_out), further sweep calls
+    leave the iterate and the residual record as they were."""
+    g = synth.config_instances("c1_9bus_T6")[0]
+    o = oracle.Oracle(g)
+    for _ in range(60):
+        o.sweep(50)
+        if oracle.unpack_state(o.state_vector(), g.T, g.n_gen, g.n_branch, g.n_bus)["done"]:
+            break
+    st = oracle.unpack_state(o.state_vector(), g.T, g.n_gen, g.n_branch, g.n_bus)
+    assert st["done"] == 1.0
+    r = o.residuals()
+    assert r["r_p"] <= 1e-4 and r["r_d"] <= 1e-4 and r["z_rms"] <= 1e-4
+    vec = o.state_vector()
+    o.sweep(5)
+    assert np.array_equal(o.state_vector(), vec)
+    assert o.residuals() == r
