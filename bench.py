@@ -82,6 +82,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start arm")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batching comparison")
     ap.add_argument("--no-uc-warm", action="store_true", help="skip the UC warm-start time-to-1e-4 run")
     ap.add_argument("--uc-warm-sweeps", type=int, default=300, help="relaxed sweeps of the UC warm start")
     return ap.parse_args()
@@ -373,6 +374,9 @@ def main():
     learned = None
     if not a.no_learned:
         learned = learned_arm(ucac, grids, stream, params, a, cache)
+    batch = None
+    if not a.no_batch:
+        batch = batch_arm(ucac, stream, params, cache)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         v, sample = oracle_sweep_rate(grids, budget_s=15.0)
@@ -388,7 +392,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single",
                            "l2": "state larger than L2 (no flush needed)", "r_p_inst0": r["r_p"]},
                 "gpu_launches": 6 * a.steps, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "time_to_1e-4": ttc, "variants_118bus": ucw, "learned": learned,
+                "time_to_1e-4": ttc, "variants_118bus": ucw, "learned": learned, "batch64": batch,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -428,6 +432,42 @@ def learned_arm(ucac, grids, stream, params, a, cache):
     if not a.no_ttc:
         out["time_to_1e-4"] = time_to_tolerance(ucac, grids, stream, params, a.ttc_max_sweeps, cache, warm=wp)
     return out
+
+
+def batch_arm(ucac, stream, params, cache, warmup=5, sweeps=50):
+    """The batching pattern on 64 instances of uneven size and horizon
+    (buses 30..500, T in {12, 18, 24}): sweeps/s of one handle holding all
+    of them (one graph replay per sweep, autotuned block sizes) against one
+    handle per instance (64 graph replays per sweep), the same sweeps from
+    the cold start on the same stream, CUDA events around the timed sweeps."""
+    import torch
+    grids = synth.config_instances("c4_batch64")
+
+    def timed(handles):
+        with torch.cuda.stream(stream):
+            for hh in handles:
+                hh.enqueue(warmup)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(sweeps):
+                for hh in handles:
+                    hh.enqueue(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        return sweeps / (e0.elapsed_time(e1) * 1e-3)
+
+    hb = ucac.Handle(grids, params=params, stream=stream.cuda_stream)
+    tuning = hb.autotune(3, cache) if cache is not None else None
+    batched = timed([hb])
+    hb.close()
+    singles = [ucac.Handle([g], params=params, stream=stream.cuda_stream) for g in grids]
+    separate = timed(singles)
+    for hh in singles:
+        hh.close()
+    return {"workload": "c4_batch64", "instances": len(grids), "sweeps": sweeps,
+            "batched_sweeps_per_s": batched, "one_handle_per_instance_sweeps_per_s": separate,
+            "speedup": batched / separate, "block_sizes": tuning}
 
 
 def time_to_tolerance(ucac, grids, stream, params, max_sweeps, cache=None, warm=None, uc_warm=0):
