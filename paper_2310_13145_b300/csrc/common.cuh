@@ -122,6 +122,11 @@ struct Dev {
   // live with the line-end rows)
   long long NBP;
   double *B;
+  // the polar line kernel's own copy of V_i, V_j and 1/c of each
+  // line-period [3][NBP] (not part of the state: formed from B by the target
+  // preparation after create and import, then written by each solve, so
+  // that a solve starts without two square roots and a division)
+  double *LV;
   // line-end rows in the slot layout: [4][NEP] (p, q, w, theta of the end)
   // for x values, y, z, lambda and x-step targets; x-bar of p, q [2][NEP]
   long long NEP;

@@ -723,20 +723,18 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   return NI_CONT;
 }
 
-// starting point of line-period `it` (instance k): V = sqrt(w) and
-// d = theta_i - theta_j of the stored iterate, clamped to their bounds, the
-// slacks, and 1 / c
-__device__ __forceinline__ void pol_start(const Dev &S, int k, long long it, double (&v)[POL_NV], double &ic) {
-  const Inst &I = S.inst[k];
-  const long long NBP = S.NBP, NL = S.NL;
-  const int loc = (int)(it - I.bpo);
-  const long long lg = (long long)I.lo + (loc - (loc / I.nl) * I.nl);
-  v[0] = clampd(sqrt(fmax(S.B[(FB_V0 + 0) * NBP + it], 0.0)), S.BC[(BC_VB + 0) * NL + lg], S.BC[(BC_VB + 1) * NL + lg]);
-  v[1] = clampd(sqrt(fmax(S.B[(FB_V0 + 1) * NBP + it], 0.0)), S.BC[(BC_VB + 2) * NL + lg], S.BC[(BC_VB + 3) * NL + lg]);
+// starting point of line-period `it`: V_i, V_j and 1 / c from the kernel's
+// own copy (the last solve's values, or sqrt(w) clamped to the voltage band
+// after create or import), d = theta_i - theta_j of the stored iterate
+// clamped to [-pi, pi], and the slacks
+__device__ __forceinline__ void pol_start(const Dev &S, long long it, double (&v)[POL_NV], double &ic) {
+  const long long NBP = S.NBP;
+  v[0] = S.LV[it];
+  v[1] = S.LV[NBP + it];
+  ic = S.LV[2 * NBP + it];
   v[2] = clampd(S.B[(FB_V0 + 4) * NBP + it] - S.B[(FB_V0 + 5) * NBP + it], -3.14159265358979, 3.14159265358979);
   v[3] = fmax(S.B[(FB_V0 + 6) * NBP + it], 0.0);
   v[4] = fmax(S.B[(FB_V0 + 7) * NBP + it], 0.0);
-  ic = 1.0 / S.B[FB_C * NBP + it];
 }
 
 // Finish ring: a lane whose solve is done records what the outputs need
@@ -750,7 +748,7 @@ __device__ __forceinline__ void pol_start(const Dev &S, int k, long long it, dou
 //   floats 0-11 grad a_r (FP32, r * 3 + i), 12-14 the step in x (FP32)
 //   ints 0 item, 1-2 slots of the from / to end
 constexpr int POL_QF = 64;
-constexpr int POL_FD = 12, POL_FF = 15, POL_FI = 3;
+constexpr int POL_FD = 13, POL_FF = 15, POL_FI = 3;
 __host__ __device__ constexpr size_t pol_dyn_smem(int bs) {
   return (size_t)(bs / 32) * POL_QF * (POL_FD * sizeof(double) + POL_FF * sizeof(float) + POL_FI * sizeof(int));
 }
@@ -775,6 +773,9 @@ __device__ __forceinline__ void pol_finish_out(const Dev &S, const double *fd, c
   const double v6[6] = {Vi * Vi, Vj * Vj, Pv * c, Pv * sn, tm + 0.5 * d, tm - 0.5 * d};
 #pragma unroll
   for (int i = 0; i < 6; ++i) S.B[(FB_V0 + i) * NBP + bp] = v6[i];
+  S.LV[bp] = Vi;
+  S.LV[NBP + bp] = Vj;
+  S.LV[2 * NBP + bp] = fd[12 * POL_QF + sl];
 #pragma unroll
   for (int r = 0; r < 4; ++r) S.EA[erow_u(r) * NEP + (erow_end(r) ? let : lef)] = a[r];
   S.EA[2 * NEP + lef] = v6[0];
@@ -876,7 +877,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         const unsigned vm = __ballot_sync(FULL, it >= 0);
         if (it >= 0) {
           double vs[POL_NV], ic;
-          pol_start(S, ki, it, vs, ic);
+          pol_start(S, it, vs, ic);
           const int sl = (qhead + qcount + __popc(vm & ((1u << lane) - 1u))) & (QN - 1);
           qit[wib][sl] = it;
           qk[wib][sl] = ki;
@@ -1079,6 +1080,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
               frd[9 * POL_QF + sl] = dxs;
               frd[10 * POL_QF + sl] = P.tg[6];
               frd[11 * POL_QF + sl] = P.tg[7];
+              frd[12 * POL_QF + sl] = P.ic;
 #pragma unroll
               for (int r = 0; r < 4; ++r)
 #pragma unroll

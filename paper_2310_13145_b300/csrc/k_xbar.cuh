@@ -657,6 +657,16 @@ __global__ void __launch_bounds__(BS) k_prep_branch(Dev S, int changed_only) {
     const long long e = erow_u(r) * NEP + (erow_end(r) ? et : ef);
     S.ET[e] = row_target_fast(bv[r], S.EZ[e], S.EY[e], (r < 4) ? irpq : irva);
   }
+  if (!changed_only) {
+    // the polar line kernel's V_i, V_j and 1/c from the state: sqrt(w)
+    // clamped to the voltage band
+    const long long NBP = S.NBP, NL = S.NL;
+    S.LV[bp] = clampd(sqrt(fmax(S.B[(FB_V0 + 0) * NBP + bp], 0.0)), S.BC[(BC_VB + 0) * NL + lg],
+                      S.BC[(BC_VB + 1) * NL + lg]);
+    S.LV[NBP + bp] = clampd(sqrt(fmax(S.B[(FB_V0 + 1) * NBP + bp], 0.0)), S.BC[(BC_VB + 2) * NL + lg],
+                            S.BC[(BC_VB + 3) * NL + lg]);
+    S.LV[2 * NBP + bp] = 1.0 / S.B[FB_C * NBP + bp];
+  }
 }
 
 // Coefficients of the bus multiplier solve (R8).  The 2x2 system M nu = r

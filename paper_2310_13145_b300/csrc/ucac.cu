@@ -620,7 +620,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_GR = A.take<double>((size_t)5 * NGR * NGP);
   const size_t o_BC = A.take<double>((size_t)BC_N * NL), o_bft = A.take<int>(2 * NL);
   const size_t o_BCF = A.take<float>((size_t)8 * NL);
-  const size_t o_B = A.take<double>((size_t)FB_FB0 * NBP);
+  const size_t o_B = A.take<double>((size_t)FB_FB0 * NBP), o_LV = A.take<double>((size_t)3 * NBP);
   const size_t o_E = A.take<double>((size_t)22 * NEP);
   const size_t o_es = A.take<int>(2 * NL + 2 * blk_off.size());
   const size_t o_stage = A.take<double>((size_t)NSTAGE * max_nbp);
@@ -666,6 +666,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.bf = (const int *)(ar + o_bft); D.bt = D.bf + NL;
   D.NBP = NBP;
   D.B = (double *)(ar + o_B);
+  D.LV = (double *)(ar + o_LV);
   D.NEP = NEP;
   double *er = (double *)(ar + o_E);
   D.EA = er; D.EY = er + (size_t)4 * NEP; D.EZ = er + (size_t)8 * NEP; D.EL = er + (size_t)12 * NEP;
