@@ -64,12 +64,21 @@ struct Inst {
   // a penalty, beta or the pending flag changes, so that no row-update
   // thread divides
   double irpq, irva, iruc, ibpq, ibva, ibuc;
+  // the line solves' stationarity tolerance omega_rel max(rho) and penalty
+  // cap c_max_rel max(rho), and FP32 copies of rho_pq, rho_va (Hessian)
+  double omega, cmax;
+  float frpq, frva;
 };
 
 // the derived constants of I from its penalties and control record c (the
 // host at create and the device after each sweep compute the same IEEE
 // quotients, so the bits do not depend on where they were formed)
-__host__ __device__ inline void inst_derive(Inst &I, const double *c) {
+__host__ __device__ inline void inst_derive(Inst &I, const double *c, double omega_rel, double c_max_rel) {
+  const double rmax = fmax(I.rpq, I.rva);
+  I.omega = omega_rel * rmax;
+  I.cmax = c_max_rel * rmax;
+  I.frpq = (float)I.rpq;
+  I.frva = (float)I.rva;
   const double beta = c[C_PEND] != 0.0 ? c[C_BNEXT] : c[C_BETA];
   I.irpq = 1.0 / I.rpq;
   I.irva = 1.0 / I.rva;

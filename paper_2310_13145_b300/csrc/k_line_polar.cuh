@@ -930,8 +930,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           for (int r8 = 0; r8 < 8; ++r8) P.tg[r8] = S.ET[erow_u(r8) * NEP + (erow_end(r8) ? let : lef)];
           P.rpq = I.rpq;
           P.rva = I.rva;
-          P.frpq = (float)I.rpq;
-          P.frva = (float)I.rva;
+          P.frpq = I.frpq;
+          P.frva = I.frva;
           P.mu[0] = S.B[(FB_MU0 + 2) * NBP + bp];
           P.mu[1] = S.B[(FB_MU0 + 3) * NBP + bp];
           P.c = S.B[FB_C * NBP + bp];
@@ -944,9 +944,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
             v[2] = pol_clamp(K, 2, v[2] + (double)S.prop[3 * NBP + bp]);
             ++acc_w;
           }
-          const double rmax = fmax(I.rpq, I.rva);
-          omega = S.prm.omega_rel * rmax;
-          cmax = S.prm.c_max_rel * rmax;
+          omega = I.omega;
+          cmax = I.cmax;
           hprev = INFINITY;
           Delta = 1.0;
           itn = al = newton = 0;

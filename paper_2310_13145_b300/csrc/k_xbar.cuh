@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
         }
       }
     }
-    inst_derive(*(const_cast<Inst *>(S.inst) + k), c);
+    inst_derive(*(const_cast<Inst *>(S.inst) + k), c, S.prm.omega_rel, S.prm.c_max_rel);
   }
 }
 
@@ -584,7 +584,7 @@ __global__ void k_sync_rho(Dev S, int k) {
     Iw->rpq = c[C_RPQ];
     Iw->rva = c[C_RVA];
     Iw->ruc = c[C_RUC];
-    inst_derive(*Iw, c);
+    inst_derive(*Iw, c, S.prm.omega_rel, S.prm.c_max_rel);
   }
 }
 

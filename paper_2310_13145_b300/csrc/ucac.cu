@@ -608,7 +608,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     D.gran_bp0 = q0b[k]; D.gran_bp1 = q1b[k];
     D.gran_up0 = u0b[k]; D.gran_up1 = u1b[k];
     D.rpq = rhos[k].pq; D.rva = rhos[k].va; D.ruc = rhos[k].uc;
-    inst_derive(D, &ctrl[(size_t)k * NCTRL]);
+    inst_derive(D, &ctrl[(size_t)k * NCTRL], P.omega_rel, P.c_max_rel);
     h->inst_h.push_back(D);
   }
 
