@@ -732,9 +732,16 @@ __device__ __forceinline__ void pol_start(const Dev &S, long long it, double (&v
   v[0] = S.LV[it];
   v[1] = S.LV[NBP + it];
   ic = S.LV[2 * NBP + it];
-  v[2] = clampd(S.B[(FB_V0 + 4) * NBP + it] - S.B[(FB_V0 + 5) * NBP + it], -3.14159265358979, 3.14159265358979);
-  v[3] = fmax(S.B[(FB_V0 + 6) * NBP + it], 0.0);
-  v[4] = fmax(S.B[(FB_V0 + 7) * NBP + it], 0.0);
+  // (the clamps on the integer units: dkey order, as in pol_clamp)
+  long long kd = dkey(S.B[(FB_V0 + 4) * NBP + it] - S.B[(FB_V0 + 5) * NBP + it]);
+  const long long kl = dkey(-3.14159265358979), kh = dkey(3.14159265358979);
+  kd = kd < kl ? kl : (kd > kh ? kh : kd);
+  v[2] = dunkey(kd);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double sk = S.B[(FB_V0 + 6 + k) * NBP + it];
+    v[3 + k] = __double_as_longlong(sk) > 0 ? sk : 0.0;
+  }
 }
 
 // Finish ring: a lane whose solve is done records what the outputs need
