@@ -62,7 +62,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one launch of the polar line kernel on the
 # 16 x 2000-bus workload, from an ncu capture of sweep 31 (the summary under
 # profiles/ gives the command); None for a form or workload not captured
-LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 372.8e6}
+LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 373.9e6}
 
 
 def parse():
