@@ -121,6 +121,15 @@ def test_lockstep_2000bus_late(ucac_mod):
     assert r["newton"] > 2.0 * solves, (r["newton"], solves)
 
 
+def test_lockstep_uneven_batch(ucac_mod):
+    # instances of the 64-instance batching workload (buses 93..416,
+    # T in {12, 18, 24}) in one handle, 25 sweeps in, then 3 lockstep sweeps
+    # of every instance against the oracle
+    grids = synth.config_instances("c4_batch64", 4)
+    assert len({g.T for g in grids}) > 1
+    _lockstep(ucac_mod, grids, 3, warm=25)
+
+
 def test_lockstep_ragged_small_instances(ucac_mod, line_form):
     # uneven batch: sizes that leave partial blocks in every kernel
     grids = [synth.make_grid(n, nl, max(1, n // 3), T, seed=50 + n, rho=synth.RHO_TABLE["case300"])
