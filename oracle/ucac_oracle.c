@@ -1078,7 +1078,10 @@ EXPORT void *orc_create(const orc_grid *g, const orc_params *prm) {
   I->BBold = (double *)calloc(NBR * BN + 1, sizeof(double));
   I->U = (double *)calloc(NU_FIELDS * UN + 1, sizeof(double));
   /* cold start (Sec. IV-A): p, q, |V| at the middle of their bounds, angles 0,
-     flows from the initial voltages; UC all on (reading R13). */
+     flows from the initial voltages; UC all on (reading R13).
+     Parity pinned: rebuilt from the text with complex phasors of the pi
+     model, per-bus voltage bands, charging and a positive reactive floor
+     (tests). */
   double cpen0 = I->P.c_init_rel * ((I->P.rho_pq > I->P.rho_va) ? I->P.rho_pq : I->P.rho_va);
   for (int t = 0; t < T; ++t)
     for (int k = 0; k < ng; ++k) {
@@ -1282,7 +1285,10 @@ EXPORT void orc_sweep(void *h) {
       }
   }
   compute_a(I, I->GA, I->BA);
-  /* ---- pending outer update (Eq. step:outer) */
+  /* ---- pending outer update (Eq. step:outer), decided when the inner level
+     terminated in the previous sweep: lambda <- clip(lambda + beta z), then
+     beta <- beta_next.  Parity pinned: lambda and beta followed by hand over a
+     run, both sides of the strict beta comparison (tests). */
   if (I->ctrl[C_PEND] != 0.0) {
     double beta = I->ctrl[C_BETA], lm = P->lam_max;
     for (size_t k = 0; k < (size_t)NGR * T * ng; ++k) I->GL[k] = clampd(I->GL[k] + beta * I->GZ[k], -lm, lm);
