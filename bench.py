@@ -37,32 +37,33 @@ from paper_2310_13145_b300 import synth  # noqa: E402
 METRIC = "ADMM sweeps/s (one sweep = all instances of the workload)"
 UNIT = "sweeps/s"
 
-# Algorithmic FP64 operation counts of the line kernel, counted from its
-# source (a multiply-add counts 2; divisions, square roots, sin and cos count
-# one each; FP32 work -- the Hessian and the 3x3 Newton system of lanes
-# without a slack held at zero -- is not counted: the FP64 pipe is the
-# bound and FP32 runs at 64x its rate).
-# Polar form (default), per counted Newton iteration 425: evaluation at the
-# point 242 (sincos 2, four flows with their x-gradients 112, voltage/angle
-# rows 27, two line-limit rows with slack, multiplier estimate and gradient
-# 76, x-gradient 24, product 1), the iteration 100 (bound distances 10,
-# reduced gradient and stationarity 22, exact slack steps 4, slack steps of
-# the Newton direction 14, model decrease 31, step and rules 19), and a trial
-# point on half the iterations (measured: the rest take the final-step or
-# the small-step rule) 0.5 x 166 (step and projection 16, model 31, predicted
-# h 16, objective at the trial point 101, ratio 2); per multiplier round 200
-# (the stationarity check that ends half of the solves without a counted
-# step, 0.5 x 274; first-order finish, multiplier step and outputs 63).
-# W-form: one damped-Newton iteration 1229 (projected-gradient and active-set
-# scan 64, masked Cholesky build 64 + factor 168 + 2 triangular solves 112,
-# Newton-decrement and model terms 288, trial step 24, objective at the trial
-# point 85, gradient and Hessian at the accepted point 280); one AL round 60.
-FLOPS = {"polar": (425, 200), "w": (1229, 60)}
+# FP64 work of the line kernel per line-period solve (the unit a launch
+# processes), counted by the hardware: (DADD + DMUL + 2 DFMA) thread
+# instructions of one launch (ncu smsp__sass_thread_inst_executed_op_d*_pred_on)
+# divided by the launch's line-period solves.  16 x 2000-bus scenarios:
+# 810.5 M FLOP over 1,228,800 solves at sweep 31 (660 per solve; 290 per
+# counted Newton iteration) and 804.8 M at sweep 701 (655 per solve): the
+# work per solve hardly moves over a run, while the Newton count does.  The
+# capture and its command are summarised under profiles/.
+LINE_FLOP_PER_SOLVE = {"polar": 659.6}
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one launch of the polar line kernel on the
-# 16 x 2000-bus workload, from an ncu capture of sweep 31 (the summary under
-# profiles/ gives the command); None for a form or workload not captured
-LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 373.9e6}
+# 16 x 2000-bus workload, from the same ncu capture of sweep 31; None for a
+# form or workload not captured
+LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 372.2e6}
+# Algorithmic bytes (FP64 reads + writes each kernel must make) per unit of
+# the streaming x-bar and generator kernels, from their data layout:
+#  k_bus per line-period: 4 flow-end rows x (a, y, z, lambda, old copy read;
+#    z, y, next target, copy written) 72 B + 4 w/theta-end rows x (a, y, z,
+#    lambda read; z, y, next target written) 56 B = 512 B; per gen-period the
+#    rows gp, gq, tc 3 x 56 B + pbar, qbar read and written 32 B = 200 B; per
+#    bus-period loads Pd, Qd and w, theta read and written 48 B;
+#  k_ucbar per gen-period: 9 rows (on, sd, pl, pu, ql, qu, rd; su, ru of the
+#    next period) x 56 B + ubar_on, ubar_sd, ubar_su read and written 48 B +
+#    the objective's p, u_on, u_su, u_sd 32 B = 584 B;
+#  k_gen per gen-period: 9 targets and p, phat read 88 B; p, q, phat and six
+#    slacks 72 B and 9 row values 72 B written = 232 B.
+STREAM_BYTES = {"k_bus": (512, 200, 48), "k_ucbar": (0, 584, 0), "k_gen": (0, 232, 0)}
 
 
 def parse():
@@ -167,13 +168,27 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sweep_rate(grids, budget_s, warm=1):
-    """Times the oracle (plain C, one thread) on one instance of the workload;
-    returns (workload sweeps/s, sample description)."""
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_sweep_rate(grids, budget_s, warm=1, threads=1):
+    """Times the oracle (plain C; one thread, or `threads` threads of its
+    OpenMP build) on one instance of the workload; returns (workload
+    sweeps/s, sample description)."""
     import oracle
-    oracle.build()
+    omp = threads > 1
+    oracle.build(omp=omp)
+    if omp:
+        oracle.threads(threads)
     g = grids[0]
-    o = oracle.Oracle(g)
+    o = oracle.Oracle(g, omp=omp)
     o.sweep(warm)
     n, t0 = 0, time.perf_counter()
     while True:
@@ -184,7 +199,8 @@ def oracle_sweep_rate(grids, budget_s, warm=1):
             break
     per_instance = el / n
     rate = 1.0 / (per_instance * len(grids))
-    return rate, f"{n} oracle sweep(s) of instance 0 of {len(grids)} (after {warm} warm-up), scaled to the batch"
+    return rate, (f"{n} oracle sweep(s) of instance 0 of {len(grids)} (after {warm} warm-up) on {threads} "
+                  f"thread(s), scaled to the batch")
 
 
 def reference_arm(a, grids):
@@ -192,11 +208,15 @@ def reference_arm(a, grids):
     if rank != 0:
         return
     import oracle
-    oracle.build()
+    # the oracle on every host core (its OpenMP build: the x-step subproblems
+    # in parallel, the same bits as the single-thread build)
+    ncores = os.cpu_count() or 1
+    oracle.build(omp=True)
+    oracle.threads(ncores)
     # bounded sample: every step is one oracle sweep over one instance restricted
     # to its first T_s periods, T_s chosen so that the whole run takes ~2 min.
     g0 = grids[0]
-    probe = oracle.Oracle(g0)
+    probe = oracle.Oracle(g0, omp=True)
     probe.sweep(2)
     t0 = time.perf_counter()
     probe.sweep()
@@ -208,7 +228,7 @@ def reference_arm(a, grids):
     gs.T = Ts
     gs.Pd = np.ascontiguousarray(g0.Pd[:Ts])
     gs.Qd = np.ascontiguousarray(g0.Qd[:Ts])
-    o = oracle.Oracle(gs)
+    o = oracle.Oracle(gs, omp=True)
     for _ in range(a.warmup):
         o.sweep()
     times = []
@@ -223,7 +243,8 @@ def reference_arm(a, grids):
             "warmup": a.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded grids shaped like the paper's workloads)",
             "config": {"workload": a.workload, "instances": len(grids)},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": ncores, "kind": "oracle (OpenMP build)",
+                             "sample": sample, "cpu": cpu_model()},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -342,14 +363,33 @@ def main():
     fp64 = ucac.ucac_probe_fp64(5, stream.cuda_stream)
     torch.cuda.synchronize()
     t_br = kt["k_branch"] * 1e-3
-    f_newton, f_al = FLOPS[a.line_form]
-    flops = newton * f_newton + al * f_al
-    achieved = flops / t_br / 1e12
-    roofline = {"bound": "alu", "kernel": "k_branch (line subproblems, %s form)" % a.line_form, "achieved": achieved, "peak": fp64 / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / (fp64 / 1e12), "traffic": LINE_TRAFFIC.get((a.line_form, a.workload)) if a.instances is None else None,
+    sz = synth.stack_sizes(grids)
+    fps = LINE_FLOP_PER_SOLVE.get(a.line_form)
+    achieved = fps * sz["branch_periods"] / t_br / 1e12 if fps else None
+    peaks = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    roofline = {"bound": "alu", "kernel": "k_branch (line subproblems, %s form)" % a.line_form,
+                "achieved": achieved, "peak": fp64 / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / (fp64 / 1e12) if achieved else None,
+                "traffic": LINE_TRAFFIC.get((a.line_form, a.workload)) if a.instances is None else None,
                 "traffic_unit": "bytes per launch (ncu, sweep 31)",
-                "peak_source": "measured FP64 FMA probe on this GPU (nominal %.2f)" % FP64_NOMINAL_TFLOPS,
+                "flop_per_unit": fps, "units_per_launch": sz["branch_periods"],
+                "flop_source": "ncu DADD + DMUL + 2 DFMA per line-period solve (sweep 31)",
+                "peak_source": "measured FP64 FMA probe on this GPU, events (nominal %.2f)" % FP64_NOMINAL_TFLOPS,
+                # the FP64 pipe's own rate at the maximum SM clock: 2 FMA lanes per SM per clock
+                "peak_pipe_at_max_clock": 2 * 2 * n_sm * sm_mhz * 1e6 / 1e12,
+                "frac_of_pipe_at_max_clock": (achieved / (4 * n_sm * sm_mhz * 1e6 / 1e12)) if achieved else None,
                 "newton_per_sweep": newton, "al_per_sweep": al, "kernel_ms": kt}
+    # streaming kernels: algorithmic bytes per launch / event time / measured HBM copy rate
+    hbm = float(peaks.get("hbm_gbs", 6314.0))
+    streaming = {}
+    for kname, (per_bp, per_gp, per_up) in STREAM_BYTES.items():
+        nbytes = per_bp * sz["branch_periods"] + per_gp * sz["gen_periods"] + per_up * sz["bus_periods"]
+        gbs = nbytes / (kt[kname] * 1e-3) / 1e9
+        streaming[kname] = {"bytes_per_launch": nbytes, "ms": kt[kname], "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+    roofline["streaming"] = streaming
+    roofline["hbm_peak_gbs"] = hbm
     # end to end through the public API: create from pinned host arrays, sweeps,
     # read back the solution and the residual record
     e2e = None
@@ -379,8 +419,13 @@ def main():
         batch = batch_arm(ucac, stream, params, cache)
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        v, sample = oracle_sweep_rate(grids, budget_s=15.0)
+        v, sample = oracle_sweep_rate(grids, budget_s=12.0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        # the same oracle with its x-step subproblems on every host core
+        ncores = os.cpu_count() or 1
+        v2, sample2 = oracle_sweep_rate(grids, budget_s=8.0, threads=ncores)
+        cpu["all_cores"] = {"value": v2, "unit": UNIT, "cores": ncores, "kind": "oracle (OpenMP build)",
+                            "sample": sample2, "cpu": cpu_model()}
     h.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -535,14 +580,22 @@ def e2e_run(ucac, grids, steps, stream, params, cache=None):
     h = ucac.Handle(pinned, params=params, stream=stream.cuda_stream)
     if cache:
         h.autotune(3, cache)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     ucac.ucac_iterate(h.h, steps)
+    t2 = time.perf_counter()
     for k, g in enumerate(grids):
         ucac.ucac_solution(h.h, k, g.T, g.n_gen, g.n_bus, g.n_branch)
         h.residuals(k)
-    el = time.perf_counter() - t0
+    t3 = time.perf_counter()
     h.close()
+    el = t3 - t0
     return {"value": steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
-            "note": "create from pinned host arrays + ucac_iterate + ucac_solution + ucac_residuals, amortised"}
+            "create_s": t1 - t0, "sweeps_s": t2 - t1, "readback_s": t3 - t2,
+            "sweeps_per_s_without_create_and_readback": steps / (t2 - t1),
+            "note": "create from pinned host arrays + ucac_iterate (host checks every check_every sweeps) + "
+                    "ucac_solution + ucac_residuals of every instance, amortised over the steps; create, sweeps "
+                    "and readback are also given separately"}
 
 
 if __name__ == "__main__":

@@ -41,9 +41,9 @@ extern "C" {
 #define UCAC_E_ARG (-1)          /* bad argument (NULL pointer, size, index) */
 #define UCAC_E_GRID (-2)         /* invalid grid data (disconnected, r=x=0, bounds out of order, ...) */
 #define UCAC_E_CUDA (-3)         /* a CUDA runtime call failed */
-#define UCAC_E_NEWTON_MAXIT (-4) /* reported in ucac_residuals.status only */
+#define UCAC_E_NEWTON_MAXIT (-4) /* a line subproblem stopped on an iteration cap (params.stop_on_cap = 1) */
 #define UCAC_E_NAN (-5)          /* a residual became NaN or Inf */
-#define UCAC_E_DIVERGED (-6)     /* reported in ucac_residuals.status only */
+#define UCAC_E_DIVERGED (-6)     /* r_p or r_d grew past params.div_bound */
 
 /*
  * Instance data (Sec. II: variables, Eq. acopf, Eq. set:UC, Eq. coupling).
@@ -98,6 +98,15 @@ typedef struct ucac_rho {
  * multiplied by rho_tau (2) when r_p > rho_mu r_d (rho_mu = 10) and divided
  * by it when r_d > rho_mu r_p, at most 6 net steps either way from the
  * penalties of create; the current penalties are part of the state.
+ * Failure detection (the library's, not the paper's): after each sweep an
+ * instance whose residuals are not finite takes status UCAC_E_NAN; one whose
+ * r_p or r_d exceeds div_bound (default 1e6, in the RMS units of the rows)
+ * takes UCAC_E_DIVERGED; with stop_on_cap = 1 (default 0) one whose sweep
+ * had a line subproblem stopped by K_N / K_AL before meeting its tolerances
+ * takes UCAC_E_NEWTON_MAXIT (with 0 such solves are only counted, in
+ * ucac_report.n_newton_maxit).  An instance with an error status takes no
+ * further sweep (its iterate and record stay those of that sweep) while the
+ * rest of a batch goes on; ucac_iterate returns the code.
  */
 #define UCAC_LINE_W 0
 #define UCAC_LINE_POLAR 1
@@ -105,7 +114,8 @@ typedef struct ucac_params {
   double eps_in, eps_out, tau, theta, beta0, lambda_max;
   double eta, omega_rel, c_init_rel, c_max_rel;
   double rho_mu, rho_tau;
-  int32_t K_AL, K_N, L_max, check_every, line_form, uc_relax, rho_every, reserved;
+  int32_t K_AL, K_N, L_max, check_every, line_form, uc_relax, rho_every, stop_on_cap;
+  double div_bound;
 } ucac_params;
 
 /*
@@ -117,7 +127,8 @@ typedef struct ucac_params {
  * current x.  newton / al = line-subproblem Newton / multiplier iterations in
  * the last sweep; n_newton_maxit = line subproblems that stopped on a cap;
  * newton_total / al_total = the same counts summed over every sweep since
- * create.  status: 0 running, 1 converged, or a negative UCAC_E_* code.
+ * create.  status: 0 running, 1 converged, or a negative UCAC_E_* code
+ * (UCAC_E_NAN, UCAC_E_DIVERGED, UCAC_E_NEWTON_MAXIT; see ucac_params).
  */
 typedef struct ucac_report {
   double r_p, r_d, z_norm, z_rms, inf_norm_viol, objective, beta;
@@ -157,7 +168,9 @@ int32_t ucac_instances(const ucac_handle *h);
  * updates applied when an instance's inner loop stops), checking on the host
  * every params.check_every sweeps whether every instance has converged
  * (inner residuals <= eps_in and z_rms <= eps_out).  Synchronises the
- * stream.  Returns 1 when all instances have converged, 0 otherwise.
+ * stream.  Returns 1 when all instances have converged, 0 otherwise, or the
+ * negative status of the first instance that stopped on an error (UCAC_E_NAN,
+ * UCAC_E_DIVERGED, UCAC_E_NEWTON_MAXIT; ucac_last_error names the instance).
  */
 int ucac_iterate(ucac_handle *h, int32_t n_sweeps);
 
@@ -172,16 +185,23 @@ int ucac_enqueue_sweeps(ucac_handle *h, int32_t n_sweeps);
 int ucac_residuals(const ucac_handle *h, int32_t instance, ucac_report *out);
 
 /*
- * Copies the solution of one instance into caller host buffers (any may be
- * NULL): p, q [T][n_gen] (generator x-side), w, theta [T][n_bus] (bus copies),
- * pf [T][n_branch][4] (p_ij, q_ij, p_ji, q_ji from the line subproblems),
- * u_on [T][n_gen] (0/1 from the UC dynamic program).
+ * Copies the solution of one instance -- the iterate Algorithm 1 returns,
+ * in the variables of Sec. II (generator outputs, Eq. acopf voltages and
+ * flows, the commitment of Eq. set:UC) -- into caller host buffers (any may
+ * be NULL): p, q [T][n_gen] (generator x-side), w, theta [T][n_bus] (bus
+ * copies: |V|^2 and the voltage angle), pf [T][n_branch][4] (p_ij, q_ij,
+ * p_ji, q_ji from the line subproblems), u_on [T][n_gen] (0/1 from the UC
+ * dynamic program).  Synchronises the handle's stream.  UCAC_E_ARG for a bad
+ * handle or instance, UCAC_E_CUDA if a copy fails.
  */
 int ucac_solution(const ucac_handle *h, int32_t instance, double *p, double *q, double *w, double *theta,
                   double *pf, uint8_t *u_on);
 
 /*
- * Full iterate of one instance in a fixed canonical order of FP64 arrays
+ * Full iterate of one instance of the two-level ADMM of Sec. III-A (x, x-bar,
+ * z, y, lambda, beta and the inner/outer counters of Algorithm 1; each
+ * inner level starts from the previous one's iterate), in a fixed canonical
+ * order of FP64 arrays
  * (all [T][n] with n the component count):
  *   17 generator fields  p q phat s_pl s_pu s_ql s_qu s_rd s_ru u_on u_su u_sd
  *                        pbar qbar ubar_on ubar_su ubar_sd
@@ -190,11 +210,15 @@ int ucac_solution(const ucac_handle *h, int32_t instance, double *p, double *q, 
  *                        sigma_ji) mu0..mu3 c fbar0..fbar3
  *   y, z, lambda of the 8 line rows  p_ij q_ij p_ji q_ji w_i w_j th_i th_j
  *   2 bus fields         wbar thetabar
- *   7 scalars            beta, |z| at the last outer update (-1 if none),
+ *   12 scalars           beta, |z| at the last outer update (-1 if none),
  *                        inner sweep count, outer count, pending-outer flag,
- *                        next beta, converged flag.
+ *                        next beta, stop flag (1 converged, 2 stopped on an
+ *                        error status), the three current penalties, the
+ *                        adaptive-penalty sweep counter and net step count.
  * ucac_state_size gives the number of doubles.  Export then import restores
- * the iterate bit for bit (resume / checkpoint).
+ * the iterate bit for bit (resume / checkpoint).  buf is a caller host array
+ * of n_doubles = ucac_state_size(h, instance) doubles (UCAC_E_ARG otherwise);
+ * both calls synchronise the handle's stream.
  */
 size_t ucac_state_size(const ucac_handle *h, int32_t instance);
 int ucac_state_export(const ucac_handle *h, int32_t instance, double *buf, size_t n_doubles);
@@ -341,6 +365,15 @@ int ucac_line_features(const ucac_handle *h, int32_t instance, float *feat, doub
  * line), into HOST buffers; any of the three may be NULL.  Synchronises. */
 int ucac_line_samples(const ucac_handle *h, float *feat, double *scale, double *iterate);
 int ucac_set_warm_start(ucac_handle *h, const float *params);
+/*
+ * The same switch with the network given as a BF16 blob (no counterpart in
+ * the paper): mlp_weights_bf16 holds the ucac_mlp_param_count() parameters
+ * in the order above as IEEE bfloat16 bit patterns (uint16, host byte
+ * order), bytes = 2 * ucac_mlp_param_count(); the library widens them to
+ * FP32 exactly and proceeds as ucac_set_warm_start.  NULL with bytes = 0
+ * disables the learned start.  UCAC_E_ARG for any other size.
+ */
+int ucac_set_warmstart(ucac_handle *h, const void *mlp_weights_bf16, size_t bytes);
 int ucac_warm_start_stats(const ucac_handle *h, int32_t instance, int64_t *taken, int32_t *mma_error);
 
 /*

@@ -21,20 +21,26 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ucac_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (FP contraction off: every op rounded separately)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc (FP contraction off: every op rounded
+    separately); omp=True builds the OpenMP variant (the x-step subproblems
+    on all host cores, the same bits)."""
+    out = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared"] + (["-fopenmp"] if omp else [])
+                              + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class OrcGrid(C.Structure):
@@ -56,11 +62,12 @@ class OrcParams(C.Structure):
         [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "uc_relax", "rho_every", "pad")]
 
 
-def lib():
-    global _lib
+def lib(omp: bool = False):
+    """The plain build (default) or the OpenMP build; the same entry points."""
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if (_lib_omp if omp else _lib) is None:
+            L = C.CDLL(build(omp=omp))
             L.orc_create.restype = C.c_void_p
             L.orc_create.argtypes = [C.POINTER(OrcGrid), C.POINTER(OrcParams)]
             L.orc_destroy.argtypes = [C.c_void_p]
@@ -82,8 +89,18 @@ def lib():
             L.orc_boxqp.argtypes = [C.c_int, _dp, _dp, _dp]
             L.orc_ucdp_batch.argtypes = [C.c_int, C.c_int, C.c_double] + [_dp] * 6 + [_ip] * 4 + \
                 [C.POINTER(C.c_int8), _dp]
-            _lib = L
-    return _lib
+            L.orc_threads.argtypes = [C.c_int]
+            L.orc_threads.restype = C.c_int
+            if omp:
+                _lib_omp = L
+            else:
+                _lib = L
+    return _lib_omp if omp else _lib
+
+
+def threads(n: int = 0) -> int:
+    """Sets (n > 0) and returns the thread count of the OpenMP build."""
+    return lib(omp=True).orc_threads(int(n))
 
 
 def _d(a):
@@ -147,10 +164,11 @@ def pack_state(st, T, ng, nl, nb):
 
 # ---------------------------------------------------------------- instances
 class Oracle:
-    """One instance of the sweep on the CPU (plain FP64)."""
+    """One instance of the sweep on the CPU (plain FP64).  omp=True runs it on
+    the OpenMP build (x-step subproblems on all host cores, the same bits)."""
 
-    def __init__(self, grid, params: OrcParams | None = None, **kw):
-        L = lib()
+    def __init__(self, grid, params: OrcParams | None = None, omp: bool = False, **kw):
+        L = self._L = lib(omp)
         self.grid = grid
         self.params = params if params is not None else default_params(rho=grid.rho, **kw)
         self._keep = []
@@ -183,12 +201,12 @@ class Oracle:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and _lib is not None:
-            _lib.orc_destroy(h)
+        if h is not None and getattr(self, "_L", None) is not None:
+            self._L.orc_destroy(h)
             self._h = None
 
     def state_vector(self):
-        L = lib()
+        L = self._L
         buf = np.empty(L.orc_state_size(self._h), np.float64)
         L.orc_state_get(self._h, _d(buf))
         return buf
@@ -199,17 +217,17 @@ class Oracle:
     def set_state(self, st):
         buf = st if isinstance(st, np.ndarray) else pack_state(st, *self.dims)
         buf = np.ascontiguousarray(buf, dtype=np.float64)
-        assert buf.size == lib().orc_state_size(self._h)
-        lib().orc_state_set(self._h, _d(buf))
+        assert buf.size == self._L.orc_state_size(self._h)
+        self._L.orc_state_set(self._h, _d(buf))
 
     def sweep(self, n: int = 1):
         for _ in range(n):
-            lib().orc_sweep(self._h)
+            self._L.orc_sweep(self._h)
 
     def residuals(self):
         out = np.zeros(6)
         st = (C.c_long * 4)()
-        lib().orc_residuals(self._h, _d(out), st)
+        self._L.orc_residuals(self._h, _d(out), st)
         keys = ("r_p", "r_d", "z_norm", "inf_norm", "objective", "z_rms")
         d = {k: float(v) for k, v in zip(keys, out)}
         d.update(sweeps=st[0], newton=st[1], al=st[2], branch_fail=st[3])
@@ -219,7 +237,7 @@ class Oracle:
         T, ng, nl, nb = self.dims
         GA = np.zeros((12, T, ng)); GB = np.zeros((12, T, ng))
         BA = np.zeros((8, T, nl)); BB = np.zeros((8, T, nl))
-        lib().orc_rows(self._h, _d(GA), _d(GB), _d(BA), _d(BB))
+        self._L.orc_rows(self._h, _d(GA), _d(GB), _d(BA), _d(BB))
         return GA, GB, BA, BB
 
 

@@ -22,6 +22,10 @@
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared -o liboracle.so ucac_oracle.c -lm
  * (-ffp-contract=off keeps every product and sum separately rounded, so the
  * UC stage costs reproduce bit for bit the evaluation order stated below).
+ * Built a second time with -fopenmp (liboracle_omp.so), the independent
+ * per-(period, generator) and per-(period, line) subproblems of the x-step
+ * run on all host cores (OpenMP over components); every other step, and
+ * every sum, stays sequential, so both builds give the same bits.
  *
  * Parity status of each function is given in its header comment.
  */
@@ -31,6 +35,9 @@
 #include <string.h>
 
 #define EXPORT __attribute__((visibility("default")))
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---------------------------------------------------------------- input -- */
 typedef struct orc_grid {
@@ -1241,6 +1248,7 @@ EXPORT void orc_sweep(void *h) {
     free(ton); free(tsu); free(tsd); free(L); free(u);
   }
   /* ---- x^OPF generators (Eq. step:opf, R5) */
+#pragma omp parallel for collapse(2) schedule(static)
   for (int t = 0; t < T; ++t)
     for (int g = 0; g < ng; ++g) {
       double prm[7] = {I->c2p[g], I->c1p[g], P->rho_pq, I->Pmax[g], I->qlo[g], I->qhi[g], I->p0[g]};
@@ -1260,6 +1268,8 @@ EXPORT void orc_sweep(void *h) {
   {
     double rmax = (P->rho_pq > P->rho_va) ? P->rho_pq : P->rho_va;
     double omega = P->omega_rel * rmax, cmax = P->c_max_rel * rmax;
+    long nw = 0, na = 0, nf = 0;
+#pragma omp parallel for collapse(2) schedule(dynamic, 16) reduction(+ : nw, na, nf)
     for (int t = 0; t < T; ++t)
       for (int l = 0; l < nl; ++l) {
         double cst[25], tg[8], v[8], mu[4], c, a[8];
@@ -1279,10 +1289,13 @@ EXPORT void orc_sweep(void *h) {
         for (int k = 0; k < 8; ++k) I->B[BIX(I, FB_V0 + k, t, l)] = v[k];
         for (int k = 0; k < 4; ++k) I->B[BIX(I, FB_MU0 + k, t, l)] = mu[k];
         I->B[BIX(I, FB_C, t, l)] = c;
-        I->newton_total += info[0];
-        I->al_total += info[1];
-        if (info[2] != 0) I->br_fail++;
+        nw += info[0];
+        na += info[1];
+        if (info[2] != 0) nf++;
       }
+    I->newton_total += nw;
+    I->al_total += na;
+    I->br_fail += nf;
   }
   compute_a(I, I->GA, I->BA);
   /* ---- pending outer update (Eq. step:outer), decided when the inner level
@@ -1485,6 +1498,18 @@ EXPORT void orc_sweep(void *h) {
       }
     }
   }
+}
+
+/* Threads of the x-step subproblem loops: n > 0 sets them (OpenMP build
+   only); returns the number in use (1 for the plain build). */
+EXPORT int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* out = {r_p, r_d, z_norm, inf_norm, objective, z_rms}; stats = {sweeps, newton, al, branch_fail} */

@@ -91,7 +91,8 @@ __host__ __device__ inline void inst_derive(Inst &I, const double *c, double ome
 struct Params {
   double eps_in, eps_out, tau, theta, beta0, lam_max, eta, omega_rel, c_init_rel, c_max_rel;
   double rho_mu, rho_tau;
-  int K_AL, K_N, L_max, line_form, uc_relax, rho_every;
+  int K_AL, K_N, L_max, line_form, uc_relax, rho_every, stop_on_cap;
+  double div_bound;
 };
 
 constexpr int GRAN = 32;  // items per granule (one warp)

@@ -726,21 +726,26 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
 // starting point of line-period `it`: V_i, V_j and 1 / c from the kernel's
 // own copy (the last solve's values, or sqrt(w) clamped to the voltage band
 // after create or import), d = theta_i - theta_j of the stored iterate
-// clamped to [-pi, pi], and the slacks
+// clamped to [-pi, pi], and the slacks projected onto sigma >= 0
 __device__ __forceinline__ void pol_start(const Dev &S, long long it, double (&v)[POL_NV], double &ic) {
   const long long NBP = S.NBP;
   v[0] = S.LV[it];
   v[1] = S.LV[NBP + it];
   ic = S.LV[2 * NBP + it];
-  // (the clamps on the integer units: dkey order, as in pol_clamp)
+  // (the clamps on the integer units: dkey order, as in pol_clamp; a NaN's
+  // key lies beyond both infinities, so a NaN angle difference starts at
+  // -pi or pi by the sign of its pattern)
   long long kd = dkey(S.B[(FB_V0 + 4) * NBP + it] - S.B[(FB_V0 + 5) * NBP + it]);
   const long long kl = dkey(-3.14159265358979), kh = dkey(3.14159265358979);
   kd = kd < kl ? kl : (kd > kh ? kh : kd);
   v[2] = dunkey(kd);
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
+    // positive patterns up to +inf pass, everything else (negative values,
+    // -0, any NaN) starts at 0: the same values as fmax(sigma, 0)
     const double sk = S.B[(FB_V0 + 6 + k) * NBP + it];
-    v[3 + k] = __double_as_longlong(sk) > 0 ? sk : 0.0;
+    const long long b = __double_as_longlong(sk);
+    v[3 + k] = (b > 0 && b <= 0x7ff0000000000000LL) ? sk : 0.0;
   }
 }
 

@@ -527,14 +527,29 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
       c[C_BETA] = c[C_BNEXT];
       c[C_PEND] = 0.0;
     }
+    // failure detection: a non-finite residual, a residual past the
+    // divergence bound, or (when asked for) a line solve stopped on a cap;
+    // the instance then takes no further sweep (stop flag 2)
     const bool finite = isfinite(rp) && isfinite(rd) && isfinite(zn);
-    r[R_STATUS] = finite ? (c[C_DONE] != 0.0 ? 1.0 : 0.0) : -5.0;
+    double st = 0.0;
+    if (!finite)
+      st = (double)UCAC_E_NAN;
+    else if (rp > P.div_bound || rd > P.div_bound)
+      st = (double)UCAC_E_DIVERGED;
+    else if (P.stop_on_cap && nc > 0)
+      st = (double)UCAC_E_NEWTON_MAXIT;
+    r[R_STATUS] = st;
+    r[R_RCHG] = 0.0;
+    if (st < 0.0) {
+      c[C_DONE] = 2.0;
+      return;
+    }
     c[C_LIN] += 1.0;
     const bool inner_ok = (rp <= P.eps_in) && (rd <= P.eps_in);
     if (inner_ok || c[C_LIN] >= (double)P.L_max) {
       if (inner_ok && zr <= P.eps_out) {
         c[C_DONE] = 1.0;
-        if (finite) r[R_STATUS] = 1.0;
+        r[R_STATUS] = 1.0;
       } else {
         const double bnext = (c[C_ZPREV] >= 0.0 && zn > P.theta * c[C_ZPREV]) ? P.tau * c[C_BETA] : c[C_BETA];
         c[C_PEND] = 1.0;
@@ -551,7 +566,6 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
     // penalties of create (unbounded, the rule can run away: r_d shrinks as
     // the penalty grows); the sweep's target preparation then rewrites the
     // x-step targets with the new penalties
-    r[R_RCHG] = 0.0;
     if (P.rho_every > 0 && c[C_DONE] == 0.0) {
       c[C_RCNT] += 1.0;
       if (c[C_RCNT] >= (double)P.rho_every) {

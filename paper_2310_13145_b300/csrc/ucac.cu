@@ -364,6 +364,8 @@ void ucac_default_params(ucac_params *p) {
   p->rho_every = 0;
   p->rho_mu = 10.0;
   p->rho_tau = 2.0;
+  p->stop_on_cap = 0;
+  p->div_bound = 1e6;
 }
 
 int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, const ucac_rho *rhos, int32_t n,
@@ -382,7 +384,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   if (params) P = *params;
   if (P.K_AL < 1 || P.K_N < 1 || P.L_max < 1 || P.check_every < 1 || !(P.beta0 > 0) ||
       (P.line_form != UCAC_LINE_W && P.line_form != UCAC_LINE_POLAR) || (P.uc_relax != 0 && P.uc_relax != 1) ||
-      P.rho_every < 0 || (P.rho_every > 0 && !(P.rho_mu > 1.0 && P.rho_tau > 1.0)))
+      P.rho_every < 0 || (P.rho_every > 0 && !(P.rho_mu > 1.0 && P.rho_tau > 1.0)) ||
+      (P.stop_on_cap != 0 && P.stop_on_cap != 1) || !(P.div_bound > 0.0))
     return fail(nullptr, UCAC_E_ARG, "bad parameters");
 
   h = new ucac_handle();
@@ -391,7 +394,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   h->check_every = P.check_every;
   h->prm = Params{P.eps_in, P.eps_out, P.tau, P.theta, P.beta0, P.lambda_max, P.eta, P.omega_rel, P.c_init_rel,
                   P.c_max_rel, P.rho_mu, P.rho_tau, P.K_AL, P.K_N, P.L_max, P.line_form, P.uc_relax,
-                  P.rho_every};
+                  P.rho_every, P.stop_on_cap, P.div_bound};
   // ---- sizes and offsets
   long long go = 0, gpo = 0, lo = 0, bpo = 0, uo = 0, upo = 0;
   for (int k = 0; k < n; ++k) {
@@ -812,7 +815,13 @@ int ucac_iterate(ucac_handle *h, int32_t n_sweeps) {
     CK(cudaStreamSynchronize(h->stream));
     bool all = true;
     for (int k = 0; k < h->K; ++k) {
-      if (r[(size_t)k * NRES + R_STATUS] < 0) return fail(h, UCAC_E_NAN, "residual became NaN/Inf");
+      const int st = (int)r[(size_t)k * NRES + R_STATUS];
+      if (st < 0) {
+        const char *why = st == UCAC_E_NAN        ? "a residual became NaN/Inf"
+                          : st == UCAC_E_DIVERGED ? "a residual grew past div_bound"
+                                                  : "a line subproblem stopped on an iteration cap";
+        return fail(h, st, "instance " + std::to_string(k) + ": " + why);
+      }
       all = all && c[(size_t)k * NCTRL + C_DONE] != 0.0;
     }
     if (all) return UCAC_CONVERGED;
@@ -1289,6 +1298,25 @@ int ucac_set_warm_start(ucac_handle *h, const float *params) {
   CK(cudaMemset(h->dev.wstat, 0, sizeof(unsigned long long) * h->K));
   CK(capture_graph(h));
   return UCAC_OK;
+}
+
+int ucac_set_warmstart(ucac_handle *h, const void *mlp_weights_bf16, size_t bytes) {
+  if (!h) return fail(h, UCAC_E_ARG, "bad arguments");
+  if (!mlp_weights_bf16) {
+    if (bytes != 0) return fail(h, UCAC_E_ARG, "NULL weights with a nonzero size");
+    return ucac_set_warm_start(h, nullptr);
+  }
+  if (bytes != (size_t)MLP_NPARAM * 2)
+    return fail(h, UCAC_E_ARG, "expected " + std::to_string(MLP_NPARAM) + " BF16 values (" +
+                                   std::to_string(2 * MLP_NPARAM) + " bytes)");
+  // a BF16 value is the upper half of the FP32 value with the same bits
+  std::vector<float> f(MLP_NPARAM);
+  const uint16_t *b = (const uint16_t *)mlp_weights_bf16;
+  for (int i = 0; i < MLP_NPARAM; ++i) {
+    const uint32_t u = (uint32_t)b[i] << 16;
+    std::memcpy(&f[i], &u, 4);
+  }
+  return ucac_set_warm_start(h, f.data());
 }
 
 int ucac_warm_start_stats(const ucac_handle *hc, int32_t k, int64_t *taken, int32_t *mma_error) {

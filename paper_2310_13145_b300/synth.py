@@ -148,12 +148,18 @@ def _load_shape(T: int) -> np.ndarray:
 def make_grid(n_bus: int, n_branch: int, n_gen: int, T: int, seed: int = 0,
               load_seed: int | None = None, load_scale: float = 1.0,
               rho=(5e3, 1e4, 1e4), name: str = "", loading: float | None = None,
-              q_ratio: float = 0.5) -> Grid:
+              q_ratio: float = 0.5, shunts: bool = False) -> Grid:
     """Draw one instance.
 
     `seed` fixes the network, generator fleet and base loads; `load_seed`, when
     given, multiplies every (t, bus) load by (1 + 0.05 N(0,1)) from its own
-    stream (a load-profile scenario on the same network).
+    stream (a load-profile scenario on the same network).  `shunts` adds, from
+    a stream of its own (everything else is unchanged), bus shunts G^s, B^s
+    (Eq. acopf balance equations) at about a third of the buses -- G^s ~
+    U(0.005, 0.05), B^s ~ U(-0.1, 0.3) p.u., both nonzero, so that the bus
+    projection's two balance multipliers are coupled -- and total line
+    charging b ~ U(0.02, 0.3) p.u. (the pi model of Eq. acopf's flow
+    equations) on about half of the lines.
     """
     if n_bus < 2 or n_branch < n_bus - 1 or n_gen < 1 or n_gen > n_bus or T < 1:
         raise ValueError("bad instance sizes")
@@ -184,11 +190,22 @@ def make_grid(n_bus: int, n_branch: int, n_gen: int, T: int, seed: int = 0,
     c_su = rc.uniform(200.0, 1000.0, n_gen)
     ref_bus = int(gen_bus[int(np.argmax(Pmax))])
     ones = np.ones(n_bus)
+    Gs, Bs, br_b = np.zeros(n_bus), np.zeros(n_bus), np.zeros(n_branch)
+    if shunts:
+        rsh = _rng(seed, 6)
+        on = rsh.random(n_bus) < 1.0 / 3.0
+        on[int(rsh.integers(n_bus))] = True  # at least one shunt bus
+        Gs = np.where(on, rsh.uniform(0.005, 0.05, n_bus), 0.0)
+        Bs = np.where(on, rsh.uniform(-0.1, 0.3, n_bus), 0.0)
+        Bs = np.where(on & (Bs == 0.0), 0.1, Bs)
+        ch = rsh.random(n_branch) < 0.5
+        ch[int(rsh.integers(n_branch))] = True
+        br_b = np.where(ch, rsh.uniform(0.02, 0.3, n_branch), 0.0)
     return Grid(
         n_bus=n_bus, n_branch=n_branch, n_gen=n_gen, T=T, ref_bus=ref_bus,
         Pd=np.ascontiguousarray(Pd), Qd=np.ascontiguousarray(Qd),
-        Gs=np.zeros(n_bus), Bs=np.zeros(n_bus), Vmin=0.9 * ones, Vmax=1.1 * ones,
-        br_from=frm, br_to=to, br_r=r, br_x=x, br_b=np.zeros(n_branch), br_rate=rate,
+        Gs=Gs, Bs=Bs, Vmin=0.9 * ones, Vmax=1.1 * ones,
+        br_from=frm, br_to=to, br_r=r, br_x=x, br_b=br_b, br_rate=rate,
         gen_bus=gen_bus, Pmin=0.2 * Pmax, Pmax=Pmax, Qmin=-0.3 * Pmax, Qmax=q_ratio * Pmax,
         c2=c2, c1=c1, c0=c0, c_su=c_su, c_sd=np.zeros(n_gen),
         RU=0.5 * Pmax, RD=0.5 * Pmax, SU=0.5 * Pmax, SD=0.5 * Pmax,
@@ -208,13 +225,14 @@ CONFIGS = {
 }
 
 
-def config_instances(name: str, n_instances: int | None = None) -> List[Grid]:
-    """Instances of a named workload; `n_instances` truncates batched ones."""
+def config_instances(name: str, n_instances: int | None = None, shunts: bool = False) -> List[Grid]:
+    """Instances of a named workload; `n_instances` truncates batched ones;
+    `shunts` adds bus shunts and line charging (see make_grid) to each."""
     if name == "c1_9bus_T6":
-        out = [make_grid(9, 9, 3, 6, seed=0, rho=RHO_TABLE["case9"], name=name)]
+        out = [make_grid(9, 9, 3, 6, seed=0, rho=RHO_TABLE["case9"], name=name, shunts=shunts)]
     elif name == "c2_118bus_T24x3":
         out = [make_grid(118, 186, 54, 24, seed=0, load_seed=s, rho=RHO_TABLE["case118"],
-                         name=f"{name}[{s}]") for s in range(3)]
+                         name=f"{name}[{s}]", shunts=shunts) for s in range(3)]
     elif name == "c4_batch64":
         r = _rng(0, 77)
         out = []
@@ -223,13 +241,10 @@ def config_instances(name: str, n_instances: int | None = None) -> List[Grid]:
             T = int(r.choice([12, 18, 24]))
             sc = float(r.uniform(0.8, 1.1))
             out.append(make_grid(n, int(round(1.5 * n)), max(1, int(round(0.3 * n))), T, seed=100 + k,
-                                 load_scale=sc, rho=RHO_TABLE["case300"], name=f"{name}[{k}]"))
+                                 load_scale=sc, rho=RHO_TABLE["case300"], name=f"{name}[{k}]", shunts=shunts))
     elif name == "c5_2000bus_T24x16":
-        g0 = make_grid(2000, 3200, 500, 24, seed=0, load_seed=0, rho=RHO_TABLE["case300"], name=f"{name}[0]")
-        out = [g0]
-        for s in range(1, 16):
-            out.append(make_grid(2000, 3200, 500, 24, seed=0, load_seed=s, rho=RHO_TABLE["case300"],
-                                 name=f"{name}[{s}]"))
+        out = [make_grid(2000, 3200, 500, 24, seed=0, load_seed=s, rho=RHO_TABLE["case300"],
+                         name=f"{name}[{s}]", shunts=shunts) for s in range(16 if n_instances is None else n_instances)]
     else:
         raise KeyError(name)
     if n_instances is not None:

@@ -28,7 +28,8 @@ EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_inst
            "ucac_enqueue_sweeps", "ucac_residuals", "ucac_solution", "ucac_state_size", "ucac_state_export",
            "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp", "ucac_ucdp_noalloc",
            "ucac_probe_fp64", "ucac_probe_cossin", "ucac_autotune", "ucac_uc_warm_start", "ucac_mlp_param_count", "ucac_mlp_workspace_bytes", "ucac_mlp_forward",
-           "ucac_mlp_grad", "ucac_mlp_adam", "ucac_line_features", "ucac_line_samples", "ucac_set_warm_start", "ucac_warm_start_stats",
+           "ucac_mlp_grad", "ucac_mlp_adam", "ucac_line_features", "ucac_line_samples", "ucac_set_warm_start", "ucac_set_warmstart",
+           "ucac_warm_start_stats",
            "ucac_destroy", "ucac_last_error"]
 
 
@@ -52,7 +53,8 @@ class ucac_params(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("eps_in", "eps_out", "tau", "theta", "beta0", "lambda_max", "eta",
                                           "omega_rel", "c_init_rel", "c_max_rel", "rho_mu", "rho_tau")] + \
         [(n, C.c_int32) for n in ("K_AL", "K_N", "L_max", "check_every", "line_form", "uc_relax", "rho_every",
-                                  "reserved")]
+                                  "stop_on_cap")] + \
+        [("div_bound", C.c_double)]
 
 
 class ucac_report(C.Structure):
@@ -111,6 +113,7 @@ def lib():
         L.ucac_line_features.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), _dp]
         L.ucac_line_samples.argtypes = [vp, C.POINTER(C.c_float), _dp, _dp]
         L.ucac_set_warm_start.argtypes = [vp, C.POINTER(C.c_float)]
+        L.ucac_set_warmstart.argtypes = [vp, vp, C.c_size_t]
         L.ucac_warm_start_stats.argtypes = [vp, C.c_int32, C.POINTER(C.c_int64), _ip]
         L.ucac_destroy.argtypes = [vp]
         L.ucac_destroy.restype = None
@@ -330,6 +333,16 @@ def ucac_set_warm_start(h, params) -> None:
     if p.size != ucac_mlp_param_count():
         raise UcacError(f"warm-start parameters: expected {ucac_mlp_param_count()} values, got {p.size}")
     _check(lib().ucac_set_warm_start(h, p.ctypes.data_as(C.POINTER(C.c_float))), h)
+
+
+def ucac_set_warmstart(h, blob_bf16) -> None:
+    """The network as BF16 bit patterns (uint16 array of ucac_mlp_param_count()
+    values), or None to disable the learned start."""
+    if blob_bf16 is None:
+        _check(lib().ucac_set_warmstart(h, None, 0), h)
+        return
+    b = np.ascontiguousarray(blob_bf16, dtype=np.uint16)
+    _check(lib().ucac_set_warmstart(h, C.c_void_p(b.ctypes.data), b.nbytes), h)
 
 
 def ucac_warm_start_stats(h, instance: int = 0):

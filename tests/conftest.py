@@ -41,3 +41,9 @@ def ucac_mod():
     from paper_2310_13145_b300 import build, ucac
     build.build()
     return ucac
+
+
+def pytest_sessionfinish(session, exitstatus):
+    # achieved per-field errors of the parity tests, when UCAC_PARITY_LOG is set
+    from tests import _helpers
+    _helpers.dump_stats()

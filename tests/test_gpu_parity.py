@@ -84,6 +84,47 @@ def test_cold_start_matches_ragged_batch(ucac_mod):
     h.close()
 
 
+def _coupled_buses(g):
+    # buses whose P and Q balance multipliers are coupled in the x-bar
+    # projection (Eq. step:opf_bar): the off-diagonal -G^s B^s / (deg rho_va)
+    # of the 2x2 multiplier system is nonzero
+    return np.flatnonzero((g.Gs != 0.0) & (g.Bs != 0.0))
+
+
+def test_cold_start_matches_shunts(ucac_mod):
+    # line charging enters the flows of the cold start (Eq. acopf, pi model)
+    grids = synth.config_instances("c4_batch64", 4, shunts=True)
+    assert all(np.any(g.br_b != 0.0) for g in grids)
+    h = ucac_mod.Handle(grids)
+    for k, g in enumerate(grids):
+        bad = compare_states(h.export(k), oracle.Oracle(g).state_vector(), g, rtol=1e-14)
+        assert not bad, (k, bad[:6])
+    h.close()
+
+
+def test_lockstep_9bus_shunts(ucac_mod, line_form):
+    """Bus shunts and line charging (Eq. acopf, Sec. II-A): the bus
+    kernel's coupled 2x2 multiplier solve and the charging terms of both
+    line solvers, 40 sweeps in lockstep."""
+    g = synth.config_instances("c1_9bus_T6", shunts=True)[0]
+    assert _coupled_buses(g).size > 0 and np.count_nonzero(g.br_b) > 0
+    _lockstep(ucac_mod, [g], 40, line_form=line_form)
+
+
+def test_lockstep_9bus_shunts_with_outer_updates(ucac_mod, line_form):
+    g = synth.config_instances("c1_9bus_T6", shunts=True)[0]
+    p = ucac_mod.ucac_default_params(L_max=4)
+    _lockstep(ucac_mod, [g], 20, params=p, oparams=lambda gg: oracle.default_params(rho=gg.rho, L_max=4), warm=60,
+              line_form=line_form)
+
+
+def test_lockstep_uneven_batch_shunts(ucac_mod, line_form):
+    # four instances of the uneven batching workload with shunts and charging
+    grids = synth.config_instances("c4_batch64", 4, shunts=True)
+    assert all(_coupled_buses(g).size > 0 for g in grids)
+    _lockstep(ucac_mod, grids, 3, warm=25, line_form=line_form)
+
+
 def test_lockstep_9bus(ucac_mod, line_form):
     g = synth.config_instances("c1_9bus_T6")[0]
     _lockstep(ucac_mod, [g], 40, line_form=line_form)

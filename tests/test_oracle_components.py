@@ -170,42 +170,45 @@ def test_bus_matches_dense_kkt(seed):
 # ------------------------------------------------------------------ line
 
 
-def _line(rng, r=None, x=None, rate=None):
+def _line(rng, r=None, x=None, rate=None, bc=0.0):
     r = rng.uniform(0.005, 0.05) if r is None else r
     x = rng.uniform(0.05, 0.3) if x is None else x
     rate = rng.uniform(1, 3) if rate is None else rate
     z2 = r * r + x * x
     gs, bs = r / z2, -x / z2
-    Y = [gs, bs, -gs, -bs, gs, bs, -gs, -bs]
+    # (Gii, Bii, Gij, Bij, Gjj, Bjj, Gji, Bji) of the pi model with total charging bc
+    Y = [gs, bs + 0.5 * bc, -gs, -bs, gs, bs + 0.5 * bc, -gs, -bs]
     lo = [0.81, 0.81, -1.21, -1.21, -2 * np.pi, -2 * np.pi, 0, 0]
     hi = [1.21, 1.21, 1.21, 1.21, 2 * np.pi, 2 * np.pi, rate * rate, rate * rate]
     return np.array(Y + [rate * rate] + lo + hi), (gs, bs, rate)
 
 
-def polar_flows(gs, bs, Vi, Vj, ti, tj):
-    """Line flows from polar voltages (series admittance gs + j bs, no shunt)."""
-    d = ti - tj
-    pij = gs * Vi * Vi - Vi * Vj * (gs * np.cos(d) + bs * np.sin(d))
-    qij = -bs * Vi * Vi - Vi * Vj * (gs * np.sin(d) - bs * np.cos(d))
-    pji = gs * Vj * Vj - Vi * Vj * (gs * np.cos(d) - bs * np.sin(d))
-    qji = -bs * Vj * Vj + Vi * Vj * (gs * np.sin(d) + bs * np.cos(d))
-    return pij, qij, pji, qji
+def polar_flows(gs, bs, Vi, Vj, ti, tj, bc=0.0):
+    """Line flows from polar voltages: complex power V conj(I) of the pi
+    model with series admittance gs + j bs and half the charging bc at each
+    end."""
+    Ui, Uj = Vi * np.exp(1j * ti), Vj * np.exp(1j * tj)
+    y = gs + 1j * bs
+    Sij = Ui * np.conj((y + 0.5j * bc) * Ui - y * Uj)
+    Sji = Uj * np.conj((y + 0.5j * bc) * Uj - y * Ui)
+    return Sij.real, Sij.imag, Sji.real, Sji.imag
 
 
-def consensus(v_polar, gs, bs, tg, rpq, rva):
+def consensus(v_polar, gs, bs, tg, rpq, rva, bc=0.0):
     Vi, Vj, ti, tj = v_polar
-    fl = polar_flows(gs, bs, Vi, Vj, ti, tj)
+    fl = polar_flows(gs, bs, Vi, Vj, ti, tj, bc)
     a = list(fl) + [Vi * Vi, Vj * Vj, ti, tj]
     return sum((rpq if k < 4 else rva) * 0.5 * (a[k] - tg[k]) ** 2 for k in range(8))
 
 
+@pytest.mark.parametrize("bc", [0.0, 0.25])
 @pytest.mark.parametrize("seed", range(8))
-def test_line_exact_ac_point_is_returned(seed):
+def test_line_exact_ac_point_is_returned(seed, bc):
     rng = np.random.default_rng(300 + seed)
-    cst, (gs, bs, rate) = _line(rng, rate=5.0)
+    cst, (gs, bs, rate) = _line(rng, rate=5.0, bc=bc)
     Vi, Vj = rng.uniform(0.95, 1.05, 2)
     ti, tj = rng.uniform(-0.1, 0.1, 2)
-    fl = polar_flows(gs, bs, Vi, Vj, ti, tj)
+    fl = polar_flows(gs, bs, Vi, Vj, ti, tj, bc)
     tgt = np.array(list(fl) + [Vi * Vi, Vj * Vj, ti, tj])
     d = ti - tj
     truth = np.array([Vi * Vi, Vj * Vj, Vi * Vj * np.cos(d), Vi * Vj * np.sin(d), ti, tj,
@@ -218,14 +221,15 @@ def test_line_exact_ac_point_is_returned(seed):
     assert np.allclose(a, tgt, atol=1e-9)
 
 
+@pytest.mark.parametrize("bc", [0.0, 0.25])
 @pytest.mark.parametrize("seed", range(10))
-def test_line_kkt_second_order_and_polar_grid(seed):
+def test_line_kkt_second_order_and_polar_grid(seed, bc):
     rng = np.random.default_rng(400 + seed)
-    cst, (gs, bs, rate) = _line(rng)
+    cst, (gs, bs, rate) = _line(rng, bc=bc)
     rpq, rva = 5e3, 1e4
     Vi, Vj = rng.uniform(0.95, 1.05, 2)
     ti, tj = rng.uniform(-0.2, 0.2, 2)
-    fl = np.array(polar_flows(gs, bs, Vi, Vj, ti, tj))
+    fl = np.array(polar_flows(gs, bs, Vi, Vj, ti, tj, bc))
     # inconsistent targets: perturbed flows, voltages and angles
     tgt = np.concatenate([fl * rng.uniform(0.8, 1.2, 4) + rng.normal(0, 0.05, 4),
                           [Vi * Vi + rng.normal(0, 0.02), Vj * Vj + rng.normal(0, 0.02), ti + rng.normal(0, 0.02),
@@ -266,7 +270,7 @@ def test_line_kkt_second_order_and_polar_grid(seed):
     # polar voltages, on a dense grid in a small box around the solution
     Vi_s, Vj_s = np.sqrt(v[0]), np.sqrt(v[1])
     th_i, th_j = v[4], v[5]
-    base = consensus((Vi_s, Vj_s, th_i, th_j), gs, bs, tgt, rpq, rva)
+    base = consensus((Vi_s, Vj_s, th_i, th_j), gs, bs, tgt, rpq, rva, bc)
     f_or, _ = f_of(v)
     assert abs(base - f_or) <= 1e-9 * max(1, f_or)
     g7 = np.linspace(-1e-3, 1e-3, 7)
@@ -278,10 +282,10 @@ def test_line_kkt_second_order_and_polar_grid(seed):
                     Vi2, Vj2 = Vi_s + a1, Vj_s + a2
                     if not (0.9 <= Vi2 <= 1.1 and 0.9 <= Vj2 <= 1.1):
                         continue
-                    fl2 = polar_flows(gs, bs, Vi2, Vj2, th_i + a3, th_j + a4)
+                    fl2 = polar_flows(gs, bs, Vi2, Vj2, th_i + a3, th_j + a4, bc)
                     if fl2[0] ** 2 + fl2[1] ** 2 > cst[8] or fl2[2] ** 2 + fl2[3] ** 2 > cst[8]:
                         continue
-                    best = min(best, consensus((Vi2, Vj2, th_i + a3, th_j + a4), gs, bs, tgt, rpq, rva))
+                    best = min(best, consensus((Vi2, Vj2, th_i + a3, th_j + a4), gs, bs, tgt, rpq, rva, bc))
     assert best >= f_or - 1e-9 * max(1.0, f_or)
 
 

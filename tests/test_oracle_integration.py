@@ -15,9 +15,11 @@ from oracle import bruteforce as bf
 from paper_2310_13145_b300 import synth
 
 
-@pytest.fixture(scope="module")
-def converged():
-    g = synth.config_instances("c1_9bus_T6")[0]
+@pytest.fixture(scope="module", params=[False, True], ids=["plain", "shunts"])
+def converged(request):
+    # the second grid has bus shunts (one with both G^s and B^s) and line
+    # charging on most lines
+    g = synth.config_instances("c1_9bus_T6", shunts=request.param)[0]
     o = oracle.Oracle(g)
     for k in range(6000):
         o.sweep()
@@ -26,11 +28,12 @@ def converged():
     return g, o, o.state(), o.residuals(), k + 1
 
 
-def _polar(gs, bs, Vi, Vj, d):
+def _polar(gs, bs, Vi, Vj, d, bc=0.0):
+    # pi model: series admittance gs + j bs, half the charging bc at each end
     pij = gs * Vi * Vi - Vi * Vj * (gs * np.cos(d) + bs * np.sin(d))
-    qij = -bs * Vi * Vi - Vi * Vj * (gs * np.sin(d) - bs * np.cos(d))
+    qij = -(bs + 0.5 * bc) * Vi * Vi - Vi * Vj * (gs * np.sin(d) - bs * np.cos(d))
     pji = gs * Vj * Vj - Vi * Vj * (gs * np.cos(d) - bs * np.sin(d))
-    qji = -bs * Vj * Vj + Vi * Vj * (gs * np.sin(d) + bs * np.cos(d))
+    qji = -(bs + 0.5 * bc) * Vj * Vj + Vi * Vj * (gs * np.sin(d) + bs * np.cos(d))
     return np.stack([pij, qij, pji, qji])
 
 
@@ -48,7 +51,8 @@ def test_ac_power_flow_in_polar_form(converged):
     for l in range(g.n_branch):
         i, j = g.br_from[l], g.br_to[l]
         z2 = g.br_r[l] ** 2 + g.br_x[l] ** 2
-        fl = _polar(g.br_r[l] / z2, -g.br_x[l] / z2, V[:, i], V[:, j], st["thbar"][:, i] - st["thbar"][:, j])
+        fl = _polar(g.br_r[l] / z2, -g.br_x[l] / z2, V[:, i], V[:, j], st["thbar"][:, i] - st["thbar"][:, j],
+                    g.br_b[l])
         assert np.abs(fl - BA[:4, :, l]).max() <= tol, l
         assert np.abs(fl - np.stack([st["fb%d" % k][:, l] for k in range(4)])).max() <= tol, l
 

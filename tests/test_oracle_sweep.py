@@ -22,9 +22,11 @@ GR = {r: i for i, r in enumerate(oracle.GEN_ROWS)}
 BR = {r: i for i, r in enumerate(oracle.BR_ROWS)}
 
 
-@pytest.fixture(scope="module")
-def swept():
-    g = synth.config_instances("c1_9bus_T6")[0]
+@pytest.fixture(scope="module", params=[False, True], ids=["plain", "shunts"])
+def swept(request):
+    # the second grid adds bus shunts (coupled P/Q balance multipliers) and
+    # line charging
+    g = synth.config_instances("c1_9bus_T6", shunts=request.param)[0]
     o = oracle.Oracle(g, oracle.default_params(rho=g.rho, L_max=5))
     o.sweep(27)
     pre = o.state()
