@@ -44,8 +44,9 @@ UNIT = "sweeps/s"
 # 810.5 M FLOP over 1,228,800 solves at sweep 31 (660 per solve; 290 per
 # counted Newton iteration) and 804.8 M at sweep 701 (655 per solve): the
 # work per solve hardly moves over a run, while the Newton count does.  The
-# capture and its command are summarised under profiles/.
-LINE_FLOP_PER_SOLVE = {"polar": 659.6}
+# W-form kernel: 10,340.8 M FLOP at sweep 31 (8,415 per solve).  The
+# captures and their commands are summarised under profiles/.
+LINE_FLOP_PER_SOLVE = {"polar": 659.6, "w": 8415.3}
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one launch of the polar line kernel on the
 # 16 x 2000-bus workload, from the same ncu capture of sweep 31; None for a

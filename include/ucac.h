@@ -122,7 +122,7 @@ typedef struct ucac_params {
  * Residual record of one instance after the last sweep.
  * r_p = |Ax + Bxbar + z|_2 / sqrt(m), r_d = |B(xbar_new - xbar_old)|_2 / sqrt(m)
  * (m = number of coupling rows), z_norm = |z|_2, z_rms = z_norm / sqrt(m),
- * inf_norm_viol = |Ax + Bxbar|_inf (the primal infeasibility of Sec. IV-C),
+ * inf_norm_viol = |Ax + Bxbar|_inf (the primal infeasibility of Sec. IV-D),
  * objective = sum of generation, no-load, start-up and shut-down costs at the
  * current x.  newton / al = line-subproblem Newton / multiplier iterations in
  * the last sweep; n_newton_maxit = line subproblems that stopped on a cap;
@@ -290,7 +290,10 @@ int ucac_ucdp(int32_t n_gen, int32_t T, double rho_uc, const double *tau_on, con
  * The call never allocates or frees device memory.  Its first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, once per
  * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array and overwrites it; every scratch
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset (or anything else that destroys the device's primary
+ * context) it is stale, and the entry point must not be called again on that
+ * device.  Every call shares the one array and overwrites it; every scratch
  * entry is written before it is read within a call, so nothing needs to start
  * at zero, but two calls that overlap on the GPU (different streams, or
  * different host threads without ordering) race on the array and must be

@@ -58,6 +58,12 @@
 #pragma once
 #include "common.cuh"
 
+// 1: the Hessian and the 3x3 Newton system in FP64 on every lane (default
+// 0: FP32 on lanes without a held slack, see the precision split above)
+#ifndef UCAC_POL_FP64_NEWTON
+#define UCAC_POL_FP64_NEWTON 0
+#endif
+
 namespace ucac {
 
 // a_r = q_r V'^2 + V_i V_j E_r with E_r = ga_r cos d + ka_r sin d and V' =
@@ -273,6 +279,9 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
     gx[1] = fma(Vj2x, Sq1, Vi * SE) + 2.0 * P.rva * ewj * Vj;
     gx[2] = Pv * SEd + 0.5 * P.rva * et;
   }
+  // (UCAC_POL_FP64_NEWTON = 1 builds the all-FP64 Hessian and Newton system
+  // on every lane, the same model: the A/B reference of the precision split)
+  lim = lim || UCAC_POL_FP64_NEWTON;
   L.lim = lim;
   // packed symmetric index: 0:(0,0) 1:(0,1) 2:(0,2) 3:(1,1) 4:(1,2) 5:(2,2)
   const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};

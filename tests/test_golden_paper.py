@@ -1,5 +1,5 @@
 """The only derived numbers the paper prints: Table 3's gaps follow from
-Tables 1 and 2 with the definition of Sec. IV-D, (upper - lower)/upper."""
+Tables 1 and 2 with the definition of Sec. IV-E, (upper - lower)/upper."""
 import json
 import os
 
