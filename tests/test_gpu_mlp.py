@@ -121,8 +121,10 @@ def test_trained_warm_start_gain(ucac_mod):
     """Trains the network on line solves logged from 9-bus runs (seeds
     100..), evaluates on a held-out 118-bus instance: the trained network
     predicts the change of the line iterates better than the plain start
-    (which predicts no change), and the solver with it on reports how many
-    solves started from its proposal and how many Newton iterations it took."""
+    (which predicts no change); over 200 sweeps with it on the line solves
+    take fewer Newton iterations than without it, and the run ends at the
+    same residuals and objective (the Newton solve polishes either start to
+    the same tolerance)."""
     X, Y = [], []
     for seed in range(100, 106):
         g = synth.make_grid(9, 9, 3, 6, seed=seed, load_seed=seed, name="c1_9bus_T6_train%d" % seed)
@@ -156,7 +158,11 @@ def test_trained_warm_start_gain(ucac_mod):
             h.enqueue(1)
             newton += h.residuals(0)["newton"]
         taken, err = h.warm_start_stats(0)
-        runs[mode] = (newton, taken, err, h.residuals(0)["r_p"])
+        r = h.residuals(0)
+        runs[mode] = (newton, taken, err, r["r_p"], r["objective"])
         h.close()
     print("Newton iterations over 200 sweeps:", runs)
-    assert runs["learned"][2] == 0
+    assert runs["learned"][2] == 0 and runs["learned"][1] > 0
+    assert runs["learned"][0] < runs["plain"][0], runs
+    assert abs(runs["learned"][3] - runs["plain"][3]) <= 1e-6 * runs["plain"][3]
+    assert abs(runs["learned"][4] - runs["plain"][4]) <= 1e-6 * abs(runs["plain"][4])
