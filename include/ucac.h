@@ -266,7 +266,10 @@ int ucac_autotune(ucac_handle *h, int32_t sweeps_per_trial, const char *cache_pa
  * K0 [n_gen] (K0 = forced initial periods).  Writes u_on [T][n_gen] (int8
  * 0/1) and cost [n_gen] (the optimal DP cost c_{1,u0}).  workspace is a device
  * buffer of at least ucac_ucdp_workspace_bytes(n_gen, T) bytes owned by the
- * caller.  Enqueued on cuda_stream; returns without synchronising.
+ * caller (for up to 2,048 generators the kernel runs a warp per generator
+ * with its scratch in shared memory and leaves the workspace untouched; the
+ * results are the same bits either way).  Enqueued on cuda_stream; returns
+ * without synchronising.
  */
 size_t ucac_ucdp_workspace_bytes(int32_t n_gen, int32_t T);
 int ucac_ucdp(int32_t n_gen, int32_t T, double rho_uc, const double *tau_on, const double *tau_su,

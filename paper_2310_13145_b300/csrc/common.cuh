@@ -192,6 +192,27 @@ __device__ __forceinline__ bool le_nn(double x, double y) { return __double_as_l
 // max |x_i| of non-negative magnitudes, by bit pattern
 __device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
 
+// FP64 <-> FP32 conversions on the integer units (the FP64 pipe also runs
+// the hardware conversions, at the FP64 rate).  d2f_trunc keeps the top 24
+// significant bits of a magnitude in [2^-126, 2^128) (truncation, within one
+// FP32 ulp of the rounded value), returns a signed zero below that range and
+// a NaN above it (infinities and NaNs included).  f2d_exact widens a normal
+// float exactly; a subnormal float becomes a signed zero.
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7ffu, sg = hi & 0x80000000u;
+  const unsigned f = sg | (((e - 896u) << 23) + (((hi & 0xfffffu) << 3) | (lo >> 29)));
+  return __uint_as_float(e <= 896u ? sg : (e < 1151u ? f : (sg | 0x7fc00000u)));
+}
+__device__ __forceinline__ double f2d_exact(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu, sg = u & 0x80000000u;
+  const unsigned hi = sg | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  const unsigned lo = u << 29;
+  return __hiloint2double((int)(e != 0u ? hi : sg), (int)(e != 0u ? lo : 0u));
+}
+
 
 // Algorithm 1 stops an instance once it has converged: after the finish
 // kernel sets its done flag, no kernel of a later sweep touches the

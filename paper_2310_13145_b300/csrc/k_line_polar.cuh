@@ -44,7 +44,9 @@
 // its box is accepted without the ratio test: its model error, O(|d|^3), is
 // far below the decrease, and the trial evaluation it saves was most of the
 // cost of the late sweeps of a run (1e-2 gains nothing more).
-// Precision split (B300's FP64 pipe is 1/64 of its FP32 pipe): the iterate,
+// Precision split (B300's FP64 pipe is 1/64 of its FP32 pipe; it also runs
+// the FP32 <-> FP64 conversions, so the FP32 copies are made on the integer
+// units: d2f_trunc, f2d_exact): the iterate,
 // flows, residuals, gradient and objective are FP64 -- they fix the converged
 // point -- while the Hessian and the Newton system are FP32 on lanes whose
 // slacks are off zero (condition number ~1e3-1e4, so the direction is
@@ -65,6 +67,23 @@
 #endif
 
 namespace ucac {
+
+// FP64 <-> T (float or double) for the Newton system of type T; the FP32
+// conversions run on the integer units (see d2f_trunc, f2d_exact)
+template <typename T>
+__device__ __forceinline__ T to_t(double x) {
+  if constexpr (sizeof(T) == 4)
+    return d2f_trunc(x);
+  else
+    return x;
+}
+template <typename T>
+__device__ __forceinline__ double to_d(T x) {
+  if constexpr (sizeof(T) == 4)
+    return f2d_exact(x);
+  else
+    return x;
+}
 
 // a_r = q_r V'^2 + V_i V_j E_r with E_r = ga_r cos d + ka_r sin d and V' =
 // V_i for the from-end rows r = 0, 1 and V_j for the to-end rows r = 2, 3.
@@ -213,14 +232,15 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) L.v[i] = v[i];
   const double Pv = Vi * Vj, Vi2 = Vi * Vi, Vj2 = Vj * Vj;
-  const float fVi = (float)Vi, fVj = (float)Vj, fP = fVi * fVj;
+  // (the FP32 copies are truncated on the integer units: d2f_trunc)
+  const float fVi = d2f_trunc(Vi), fVj = d2f_trunc(Vj), fP = fVi * fVj;
   const double Vi2x = 2.0 * Vi, Vj2x = 2.0 * Vj;
   double E[4], Ed[4], pe[4];
   float fE[4], fEd[4];
   // FP32 gradient of the flow (for the FP32 Hessian and the first-order
   // finish) from FP32 cos/sin and constants: two conversions per
   // evaluation, the products on the FP32 pipe
-  const float fc = (float)c, fs = (float)s;
+  const float fc = d2f_trunc(c), fs = d2f_trunc(s);
   pol_angle_terms(K.ga[0], K.ka[0], K.ga[1], K.ka[1], c, s, E, Ed);
   pol_angle_terms(K.fga(0), K.fka(0), K.fga(1), K.fka(1), fc, fs, fE, fEd);
 #pragma unroll
@@ -292,14 +312,14 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
     for (int q = 0; q < 6; ++q) Hf[q] = 0.0f;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const float fu = (float)pe[r];
+      const float fu = d2f_trunc(pe[r]);
       const float d2[6] = {r < 2 ? 2.0f * K.fq(r) : 0.0f, fE[r], fVj * fEd[r], r < 2 ? 0.0f : 2.0f * K.fq(r),
                            fVi * fEd[r], -fP * fE[r]};
 #pragma unroll
       for (int q = 0; q < 6; ++q) Hf[q] += fw * L.da[r][pi_[q]] * L.da[r][pj_[q]] + fu * d2[q];
     }
-    Hf[0] += rva * (4.0f * fVi * fVi + 2.0f * (float)ewi);
-    Hf[3] += rva * (4.0f * fVj * fVj + 2.0f * (float)ewj);
+    Hf[0] += rva * (4.0f * fVi * fVi + 2.0f * d2f_trunc(ewi));
+    Hf[3] += rva * (4.0f * fVj * fVj + 2.0f * d2f_trunc(ewj));
     Hf[5] += 0.5f * rva;
   } else {
     double w[4], u[4], da[4][3];
@@ -542,7 +562,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
 #pragma unroll
       for (int k = 0; k < 2; ++k)
         if (act[3 + k]) r -= c * L.dg[k][i] * d[3 + k];
-      rb[i] = (T)r;
+      rb[i] = to_t<T>(r);
     }
     T y[3];
     lm = T(0);
@@ -573,7 +593,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     bn = 0;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      if (!act[i]) d[i] = (double)y[i];
+      if (!act[i]) d[i] = to_d<T>(y[i]);
       const long long b = __double_as_longlong(d[i]) & ABS;
       bn = b > bn ? b : bn;
     }
@@ -1061,9 +1081,9 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
             for (int r = 0; r < 4; ++r) ab[r] = L.a[r];
             cb = L.c;
             sb = L.s;
-            fx[0] = (float)dx0;
-            fx[1] = (float)dx1;
-            fx[2] = (float)dx2;
+            fx[0] = d2f_trunc(dx0);
+            fx[1] = d2f_trunc(dx1);
+            fx[2] = d2f_trunc(dx2);
             dxs = dx2;
 #pragma unroll
             for (int q = 0; q < 2; ++q)

@@ -32,22 +32,21 @@ __device__ __forceinline__ double uc_stage(double b, double su, double sd, doubl
   return __dadd_rn(lin, __dmul_rn(hr, q));
 }
 
-// DP for one generator.  tau_* point at period 0 of the generator's column
-// (element stride `st` between periods); L/C/D are scratch columns with the
-// same stride.  Writes u^on_t (0/1) through `uon` and returns c_{1,u0}.
+// The four stage costs of period t, entry ab = a*2+b at L[(ab*T + t)*st].
+__device__ __forceinline__ void uc_stage4(int T, int t, long long st, double ton, double tsu, double tsd, double c0,
+                                          double csu, double csd, double hr, double *L) {
+  L[(0 * T + t) * st] = uc_stage(0.0, 0.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
+  L[(1 * T + t) * st] = uc_stage(1.0, 1.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
+  L[(2 * T + t) * st] = uc_stage(0.0, 0.0, 1.0, ton, tsu, tsd, c0, csu, csd, hr);
+  L[(3 * T + t) * st] = uc_stage(1.0, 0.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
+}
+
+// Backward pass and forward reconstruction of Algorithm 2 from the
+// stage-cost table L (element stride `st` between periods; C, D scratch with
+// the same stride).  Writes u^on_t (0/1) through `uon` and returns c_{1,u0}.
 template <typename WriteU>
-__device__ __forceinline__ double uc_dp(int T, int TU, int TD, int u0, int K0, double c0, double csu, double csd,
-                                        double hr, const double *tau_on, const double *tau_su,
-                                        const double *tau_sd, long long st, double *L, double *C,
-                                        unsigned char *D, WriteU uon) {
-  // stage costs, entry ab = a*2+b at L[(ab*T + t)*st]
-  for (int t = 0; t < T; ++t) {
-    const double ton = tau_on[t * st], tsu = tau_su[t * st], tsd = tau_sd[t * st];
-    L[(0 * T + t) * st] = uc_stage(0.0, 0.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
-    L[(1 * T + t) * st] = uc_stage(1.0, 1.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
-    L[(2 * T + t) * st] = uc_stage(0.0, 0.0, 1.0, ton, tsu, tsd, c0, csu, csd, hr);
-    L[(3 * T + t) * st] = uc_stage(1.0, 0.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
-  }
+__device__ __forceinline__ double uc_dp_tab(int T, int TU, int TD, int u0, int K0, long long st, const double *L,
+                                            double *C, unsigned char *D, WriteU uon) {
 #define LTAB(t1, a, b) L[(((a)*2 + (b)) * T + ((t1)-1)) * st]
 #define CTAB(t1, s) C[((s) * (T + 1) + ((t1)-1)) * st]
 #define DTAB(t1, s) D[((s)*T + ((t1)-1)) * st]
@@ -94,6 +93,19 @@ __device__ __forceinline__ double uc_dp(int T, int TU, int TD, int u0, int K0, d
 #undef CTAB
 #undef DTAB
   return cost;
+}
+
+// DP for one generator on one thread.  tau_* point at period 0 of the
+// generator's column (element stride `st` between periods); L/C/D are
+// scratch columns with the same stride.
+template <typename WriteU>
+__device__ __forceinline__ double uc_dp(int T, int TU, int TD, int u0, int K0, double c0, double csu, double csd,
+                                        double hr, const double *tau_on, const double *tau_su,
+                                        const double *tau_sd, long long st, double *L, double *C,
+                                        unsigned char *D, WriteU uon) {
+  for (int t = 0; t < T; ++t)
+    uc_stage4(T, t, st, tau_on[t * st], tau_su[t * st], tau_sd[t * st], c0, csu, csd, hr, L);
+  return uc_dp_tab(T, TU, TD, u0, K0, st, L, C, D, uon);
 }
 
 // In-sweep x^UC step: reads the duplicate-row targets tau = ubar - z - y/rho
@@ -191,6 +203,42 @@ __global__ void __launch_bounds__(BS) k_uc_round(Dev S, double p_frac) {
     S.G[F_USD * NGP + i] = (prev > u) ? 1.0 : 0.0;
     prev = u;
   }
+}
+
+// Standalone DP over [T][n_gen] device arrays, one warp per generator, for
+// fleets too small to fill the GPU with one thread each: the lanes form the
+// 4T stage costs in parallel into shared memory (per warp L [4][T], C
+// [2][T+1] doubles, then D [2][T] bytes after the four warps' doubles) and
+// lane 0 runs the serial backward pass and the reconstruction on them (the
+// same operations in the same order as the thread-per-generator kernel, so
+// the same bits).  Blocks of 4 warps; dynamic shared memory
+// ucdp_warp_smem(T).
+__host__ __device__ constexpr size_t ucdp_warp_smem(int T) {
+  return 4 * (6 * (size_t)T + 2) * sizeof(double) + 4 * 2 * (size_t)T;
+}
+
+__global__ void __launch_bounds__(128) k_ucdp_warp(int ng, int T, double rho, const double *tau_on,
+                                                   const double *tau_su, const double *tau_sd, const double *c0,
+                                                   const double *csu, const double *csd, const int *TU,
+                                                   const int *TD, const int *u0, const int *K0, int8_t *u_on,
+                                                   double *cost) {
+  extern __shared__ double dp_sm[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = blockIdx.x * 4 + w;
+  if (g >= ng) return;  // (warp-uniform)
+  double *L = dp_sm + (size_t)w * (6 * T + 2);
+  double *C = L + 4 * T;
+  unsigned char *D = (unsigned char *)(dp_sm + 4 * (6 * (size_t)T + 2)) + (size_t)w * 2 * T;
+  const double hr = __dmul_rn(0.5, rho);
+  for (int t = lane; t < T; t += 32) {
+    const long long i = (long long)t * ng + g;
+    uc_stage4(T, t, 1, tau_on[i], tau_su[i], tau_sd[i], c0[g], csu[g], csd[g], hr, L);
+  }
+  __syncwarp();
+  if (lane != 0) return;
+  int8_t *uo = u_on + g;
+  cost[g] = uc_dp_tab(T, max(TU[g], 1), max(TD[g], 1), u0[g] ? 1 : 0, min(max(K0[g], 0), T), 1, L, C, D,
+                      [&](int t, int u) { uo[(long long)t * ng] = (int8_t)u; });
 }
 
 // Standalone DP over [T][n_gen] device arrays (one thread per generator).

@@ -27,7 +27,11 @@ def _run_gpu(ucac, tau_on, tau_su, tau_sd, c0, csu, csd, TU, TD, u0, K0, rho):
     return u.cpu().numpy(), cost.cpu().numpy()
 
 
-@pytest.mark.parametrize("T,ng,seed", [(24, 1000, 0), (1, 7, 1), (2, 33, 2), (168, 257, 3), (48, 10000, 4)])
+# (ucac_ucdp runs a warp per generator up to 2,048 generators, with its
+# tables in shared memory -- more than 48 KB of it from T ~ 190 on -- and a
+# thread per generator beyond: cases on both sides of each threshold)
+@pytest.mark.parametrize("T,ng,seed", [(24, 1000, 0), (1, 7, 1), (2, 33, 2), (168, 257, 3), (48, 10000, 4),
+                                       (24, 2048, 5), (24, 2049, 6), (600, 64, 7)])
 def test_ucdp_bit_exact(ucac_mod, T, ng, seed):
     rng = np.random.default_rng(seed)
     rho = 1e4
