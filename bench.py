@@ -53,18 +53,20 @@ FP64_NOMINAL_TFLOPS = 1.25
 # form or workload not captured
 LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 372.2e6}
 # Algorithmic bytes (FP64 reads + writes each kernel must make) per unit of
-# the streaming x-bar and generator kernels, from their data layout:
-#  k_bus per line-period: 4 flow-end rows x (a, y, z, lambda, old copy read;
-#    z, y, next target, copy written) 72 B + 4 w/theta-end rows x (a, y, z,
-#    lambda read; z, y, next target written) 56 B = 512 B; per gen-period the
-#    rows gp, gq, tc 3 x 56 B + pbar, qbar read and written 32 B = 200 B; per
-#    bus-period loads Pd, Qd and w, theta read and written 48 B;
+# the streaming x-bar and generator kernels, from their data layout (a row
+# keeps w = z + y/rho beside its next x-step target):
+#  k_bus per line-period: 4 flow-end rows x (a, w, y, lambda, old copy read;
+#    z, y, next target, w, copy written) 80 B + 4 w/theta-end rows x (a, w,
+#    y, lambda read; z, y, next target, w written) 64 B = 576 B; per
+#    gen-period the rows gp, gq, tc 3 x 64 B + pbar, qbar read and written
+#    32 B = 224 B; per bus-period loads Pd, Qd and w, theta read and written
+#    48 B;
 #  k_ucbar per gen-period: 9 rows (on, sd, pl, pu, ql, qu, rd; su, ru of the
-#    next period) x 56 B + ubar_on, ubar_sd, ubar_su read and written 48 B +
-#    the objective's p, u_on, u_su, u_sd 32 B = 584 B;
+#    next period) x 64 B + ubar_on, ubar_sd, ubar_su read and written 48 B +
+#    the objective's p, u_on, u_su, u_sd 32 B = 656 B;
 #  k_gen per gen-period: 9 targets and p, phat read 88 B; p, q, phat and six
 #    slacks 72 B and 9 row values 72 B written = 232 B.
-STREAM_BYTES = {"k_bus": (512, 200, 48), "k_ucbar": (0, 584, 0), "k_gen": (0, 232, 0)}
+STREAM_BYTES = {"k_bus": (576, 224, 48), "k_ucbar": (0, 656, 0), "k_gen": (0, 232, 0)}
 
 
 def parse():

@@ -119,7 +119,7 @@ struct Dev {
   const int *TU, *TD, *u0, *K0;
   // generator-period state [NGF][NGP], rows [NGR][NGP]
   long long NGP;
-  double *G, *GA, *GY, *GZ, *GL, *GT;
+  double *G, *GA, *GY, *GZ, *GL, *GT, *GW;
   // branch constants [BC_N][NL]
   long long NL;
   const double *BC;
@@ -140,7 +140,7 @@ struct Dev {
   // line-end rows in the slot layout: [4][NEP] (p, q, w, theta of the end)
   // for x values, y, z, lambda and x-step targets; x-bar of p, q [2][NEP]
   long long NEP;
-  double *EA, *EY, *EZ, *EL, *ET, *EFB;
+  double *EA, *EY, *EZ, *EL, *ET, *EFB, *EW;
   const int *eslot;             // [2][NL]: slot of the from / to end within its period
   const int *blk_off, *blk_w;   // per bus block: slot offset within the period, width
   // buses

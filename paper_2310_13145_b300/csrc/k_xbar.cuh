@@ -66,12 +66,13 @@ __device__ __forceinline__ double row_target_exact(double b, double z, double y,
   return __dsub_rn(__dsub_rn(b, z), __ddiv_rn(y, rho));
 }
 
-// x-step target of every other row: (b - z) - y * (1/rho) as one
-// multiply-add, with explicit rounding so that the sweep kernels and the
+// The sum w = z + y * (1/rho) of a row, kept beside its targets: the x-step
+// target of a row other than the UC duplicates is b - w, the x-bar-step
+// target m = a + w (one addition each instead of an addition and a
+// multiply-add).  Explicitly rounded, so that the sweep kernels and the
 // target preparation after an import produce the same bits.
-__device__ __forceinline__ double row_target_fast(double b, double z, double y, double irho) {
-  return __fma_rn(-y, irho, __dsub_rn(b, z));
-}
+__device__ __forceinline__ double row_w(double z, double y, double irho) { return __fma_rn(y, irho, z); }
+__device__ __forceinline__ double row_target_w(double b, double w) { return __dsub_rn(b, w); }
 
 // Explicitly rounded operations: the x-bar kernels spell out every multiply,
 // add and fused multiply-add, so that no template instantiation (block size)
@@ -82,10 +83,8 @@ __device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
 
-// x-bar-step target of a row from its x value a: (a + z) + y/rho
-__device__ __forceinline__ double row_mtarget(double a, double z, double y, const Fam &F) {
-  return fma_(y, F.irho, add_(a, z));
-}
+// x-bar-step target of a row from its x value a and its w = z + y/rho
+__device__ __forceinline__ double row_mtarget(double a, double w) { return add_(a, w); }
 
 // max(q, |c|) for q >= 0 on the bit patterns (order-preserving for
 // non-negative doubles): integer work instead of an FP64 min/max
@@ -98,9 +97,9 @@ __device__ __forceinline__ double max_abs_bits(double q, double c) {
 // SD: accumulate this row's (b_new - b_old)^2 here (false when the caller
 // adds it once for rows that share b, as a bus's w and theta rows do)
 template <bool EXACT, bool SD = true>
-__device__ __forceinline__ void row_update(double *A, double *Y, double *Z, double *L, double *Tg, long long idx,
-                                           double b_new, double b_old, const Fam &F, const RowCtx &R,
-                                           double (&q)[NQ]) {
+__device__ __forceinline__ void row_update(double *A, double *Y, double *Z, double *L, double *Tg, double *W,
+                                           long long idx, double b_new, double b_old, const Fam &F,
+                                           const RowCtx &R, double (&q)[NQ]) {
   const double a = A[idx], y = Y[idx], z = Z[idx];
   double lam = L[idx];
   if (R.pend) {
@@ -113,7 +112,9 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
   const double yn = fma_(F.rho, cz, y);
   Z[idx] = zn;
   Y[idx] = yn;
-  Tg[idx] = EXACT ? row_target_exact(b_new, zn, yn, F.rho) : row_target_fast(b_new, zn, yn, F.irho);
+  const double w = row_w(zn, yn, F.irho);
+  W[idx] = w;
+  Tg[idx] = EXACT ? row_target_exact(b_new, zn, yn, F.rho) : row_target_w(b_new, w);
   q[Q_SP] = fma_(cz, cz, q[Q_SP]);
   if (SD) {
     const double db = sub_(b_new, b_old);
@@ -154,27 +155,27 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     double r0 = 0.0, r1 = 0.0, mw = 0.0, mth = 0.0;
     for (int e = g0; e < g1; ++e) {
       const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
-      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GZ[GR_GP * NGP + gp], S.GY[GR_GP * NGP + gp], Fpq);
+      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
       if (!last) {
         const long long gn = gp + I.ng;
-        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], Fpq)));
+        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])));
       }
       r0 = add_(r0, m);
-      r1 = add_(r1, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq));
+      r1 = add_(r1, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
     }
     // (the p, q x-bar-step targets are parked in the target slots for pass
     // 2, which overwrites them with the next x-step targets)
 #pragma unroll kBusUnroll
     for (int j = 0; j < deg; ++j) {
       const long long e = e0 + 32LL * j;
-      const double mp = row_mtarget(S.EA[e], S.EZ[e], S.EY[e], Fpq);
-      const double mq = row_mtarget(S.EA[NEP + e], S.EZ[NEP + e], S.EY[NEP + e], Fpq);
+      const double mp = row_mtarget(S.EA[e], S.EW[e]);
+      const double mq = row_mtarget(S.EA[NEP + e], S.EW[NEP + e]);
       S.ET[e] = mp;
       S.ET[NEP + e] = mq;
       r0 = sub_(r0, mp);
       r1 = sub_(r1, mq);
-      mw = add_(mw, row_mtarget(S.EA[2 * NEP + e], S.EZ[2 * NEP + e], S.EY[2 * NEP + e], Fva));
-      mth = add_(mth, row_mtarget(S.EA[3 * NEP + e], S.EZ[3 * NEP + e], S.EY[3 * NEP + e], Fva));
+      mw = add_(mw, row_mtarget(S.EA[2 * NEP + e], S.EW[2 * NEP + e]));
+      mth = add_(mth, row_mtarget(S.EA[3 * NEP + e], S.EW[3 * NEP + e]));
     }
     const double fdeg = (double)deg;
     const double ideg = S.ideg[ig];
@@ -191,25 +192,24 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     for (int e = g0; e < g1; ++e) {
       const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
       const long long gn = gp + I.ng;
-      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GZ[GR_GP * NGP + gp], S.GY[GR_GP * NGP + gp], Fpq);
+      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
       double iW = irpq;
       if (!last) {
-        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GZ[GR_TC * NGP + gn], S.GY[GR_TC * NGP + gn], Fpq)));
+        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])));
         iW = 0.5 * irpq;
       }
       const double pnew = fma_(-nuP, iW, m);
-      const double qnew =
-          fma_(-nuQ, irpq, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GZ[GR_GQ * NGP + gp], S.GY[GR_GQ * NGP + gp], Fpq));
+      const double qnew = fma_(-nuQ, irpq, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
       const double pold = S.G[F_PBAR * NGP + gp], qold = S.G[F_QBAR * NGP + gp];
       S.G[F_PBAR * NGP + gp] = pnew;
       S.G[F_QBAR * NGP + gp] = qnew;
       row_update<false>(S.GA + GR_GP * NGP, S.GY + GR_GP * NGP, S.GZ + GR_GP * NGP, S.GL + GR_GP * NGP,
-                        S.GT + GR_GP * NGP, gp, pnew, pold, Fpq, R, q);
+                        S.GT + GR_GP * NGP, S.GW + GR_GP * NGP, gp, pnew, pold, Fpq, R, q);
       if (!last)
         row_update<false>(S.GA + GR_TC * NGP, S.GY + GR_TC * NGP, S.GZ + GR_TC * NGP, S.GL + GR_TC * NGP,
-                          S.GT + GR_TC * NGP, gn, pnew, pold, Fpq, R, q);
+                          S.GT + GR_TC * NGP, S.GW + GR_TC * NGP, gn, pnew, pold, Fpq, R, q);
       row_update<false>(S.GA + GR_GQ * NGP, S.GY + GR_GQ * NGP, S.GZ + GR_GQ * NGP, S.GL + GR_GQ * NGP,
-                        S.GT + GR_GQ * NGP, gp, qnew, qold, Fpq, R, q);
+                        S.GT + GR_GQ * NGP, S.GW + GR_GQ * NGP, gp, qnew, qold, Fpq, R, q);
     }
     const double wold = S.U[FU_W * NUP + up], thold = S.U[FU_TH * NUP + up];
     const double wnew = sub_(mw, mul_(fma_(nuP, aPw, mul_(nuQ, aQw)), iWw));
@@ -229,10 +229,10 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
         const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, S.ET[eu]);
         const double vold = S.EFB[eu];
         S.EFB[eu] = vnew;
-        row_update<false>(S.EA, S.EY, S.EZ, S.EL, S.ET, eu, vnew, vold, Fpq, R, q);
+        row_update<false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, eu, vnew, vold, Fpq, R, q);
       }
-      row_update<false, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, 2 * NEP + e, wnew, wold, Fva, R, q);
-      row_update<false, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, 3 * NEP + e, thnew, thold, Fva, R, q);
+      row_update<false, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, 2 * NEP + e, wnew, wold, Fva, R, q);
+      row_update<false, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, 3 * NEP + e, thnew, thold, Fva, R, q);
     }
   }
   warp_reduce_q(q, S.part_up + (long long)gr * NQ);
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
     const double rpq = I.rpq, ruc = I.ruc;
     const double Pmin = S.Pmin[gg], Pmax = S.Pmax[gg], Qmin = S.Qmin[gg], Qmax = S.Qmax[gg];
     const double RU = S.RU[gg], RD = S.RD[gg], SU = S.SU[gg], SD = S.SD[gg];
-#define MT(r, idx, F) row_mtarget(S.GA[(r)*NGP + (idx)], S.GZ[(r)*NGP + (idx)], S.GY[(r)*NGP + (idx)], F)
+#define MT(r, idx, F) row_mtarget(S.GA[(r)*NGP + (idx)], S.GW[(r)*NGP + (idx)])
     // H and gv of the box QP in (u_on, u_sd, u_su at t+1): row r with weight
     // w_r, x-bar-step target m_r and coefficients e_r over the three adds
     // w_r e_r e_r^T to H and w_r m_r e_r to gv.  The rows are
@@ -447,8 +447,8 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
     if (has_next) S.G[F_UBSU * NGP + gn] = su1;
     if (tau == 0) S.G[F_UBSU * NGP + gp] = su0;
 #define RU_(E, r, idx, bn, bo, F)                                                                            \
-  row_update<E>(S.GA + (r)*NGP, S.GY + (r)*NGP, S.GZ + (r)*NGP, S.GL + (r)*NGP, S.GT + (r)*NGP, idx, bn, bo, \
-                F, R, q)
+  row_update<E>(S.GA + (r)*NGP, S.GY + (r)*NGP, S.GZ + (r)*NGP, S.GL + (r)*NGP, S.GT + (r)*NGP,  \
+                S.GW + (r)*NGP, idx, bn, bo, F, R, q)
     RU_(true, GR_ON, gp, on, on_old, Fuc);
     RU_(true, GR_SD, gp, sdv, sd_old, Fuc);
     RU_(false, GR_PL, gp, Pmin * on, Pmin * on_old, Fpq);
@@ -634,11 +634,13 @@ __global__ void __launch_bounds__(BS) k_prep_gen(Dev S, int changed_only) {
   bv[GR_GP] = S.G[F_PBAR * NGP + gp];
   bv[GR_GQ] = S.G[F_QBAR * NGP + gp];
   bv[GR_TC] = (t > 0) ? S.G[F_PBAR * NGP + gp - I.ng] : 0.0;
-  const double irpq = I.irpq;
+  const double irpq = I.irpq, iruc = I.iruc;
 #pragma unroll
   for (int r = 0; r < NGR; ++r) {
-    S.GT[r * NGP + gp] = (r <= GR_SD) ? row_target_exact(bv[r], S.GZ[r * NGP + gp], S.GY[r * NGP + gp], I.ruc)
-                                      : row_target_fast(bv[r], S.GZ[r * NGP + gp], S.GY[r * NGP + gp], irpq);
+    const double z = S.GZ[r * NGP + gp], y = S.GY[r * NGP + gp];
+    const double w = row_w(z, y, (r <= GR_SD) ? iruc : irpq);
+    S.GW[r * NGP + gp] = w;
+    S.GT[r * NGP + gp] = (r <= GR_SD) ? row_target_exact(bv[r], z, y, I.ruc) : row_target_w(bv[r], w);
   }
 }
 
@@ -669,7 +671,9 @@ __global__ void __launch_bounds__(BS) k_prep_branch(Dev S, int changed_only) {
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const long long e = erow_u(r) * NEP + (erow_end(r) ? et : ef);
-    S.ET[e] = row_target_fast(bv[r], S.EZ[e], S.EY[e], (r < 4) ? irpq : irva);
+    const double w = row_w(S.EZ[e], S.EY[e], (r < 4) ? irpq : irva);
+    S.EW[e] = w;
+    S.ET[e] = row_target_w(bv[r], w);
   }
   if (!changed_only) {
     // the polar line kernel's V_i, V_j and 1/c from the state: sqrt(w)

@@ -624,11 +624,11 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_inst = A.take<Inst>(n);
   const size_t o_gd = A.take<double>(16 * NGEN), o_gi = A.take<int>(4 * NGEN);
   const size_t o_G = A.take<double>((size_t)NGF * NGP);
-  const size_t o_GR = A.take<double>((size_t)5 * NGR * NGP);
+  const size_t o_GR = A.take<double>((size_t)6 * NGR * NGP);
   const size_t o_BC = A.take<double>((size_t)BC_N * NL), o_bft = A.take<int>(2 * NL);
   const size_t o_BCF = A.take<float>((size_t)8 * NL);
   const size_t o_B = A.take<double>((size_t)FB_FB0 * NBP), o_LV = A.take<double>((size_t)3 * NBP);
-  const size_t o_E = A.take<double>((size_t)22 * NEP);
+  const size_t o_E = A.take<double>((size_t)26 * NEP);
   const size_t o_es = A.take<int>(2 * NL + 2 * blk_off.size());
   const size_t o_stage = A.take<double>((size_t)NSTAGE * max_nbp);
   const size_t o_bus = A.take<double>(4 * NB), o_busnu = A.take<double>(6 * NB);
@@ -667,6 +667,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   double *gr = (double *)(ar + o_GR);
   D.GA = gr; D.GY = gr + (size_t)NGR * NGP; D.GZ = gr + (size_t)2 * NGR * NGP; D.GL = gr + (size_t)3 * NGR * NGP;
   D.GT = gr + (size_t)4 * NGR * NGP;
+  D.GW = gr + (size_t)5 * NGR * NGP;
   D.NL = NL;
   D.BC = (const double *)(ar + o_BC);
   D.BCF = (const float *)(ar + o_BCF);
@@ -677,7 +678,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.NEP = NEP;
   double *er = (double *)(ar + o_E);
   D.EA = er; D.EY = er + (size_t)4 * NEP; D.EZ = er + (size_t)8 * NEP; D.EL = er + (size_t)12 * NEP;
-  D.ET = er + (size_t)16 * NEP; D.EFB = er + (size_t)20 * NEP;
+  D.ET = er + (size_t)16 * NEP; D.EFB = er + (size_t)20 * NEP; D.EW = er + (size_t)22 * NEP;
   const int *es = (const int *)(ar + o_es);
   D.eslot = es; D.blk_off = es + 2 * NL; D.blk_w = D.blk_off + blk_off.size();
   h->stage = (double *)(ar + o_stage);
