@@ -168,6 +168,15 @@ struct Dev {
   int warm;
   unsigned long long *wstat;
   unsigned long long *bp_counter;  // work counter of the persistent line kernel
+  // order of the polar line kernel's work: pctl[0] counter of the listed
+  // items, [1 + b] count of list b, [3] the sweep generation G (sweeps of
+  // the line kernel since create or import), [4] warps retired; the lists
+  // plist[b][NBP] of the line-periods a sweep flagged (sweep G writes list
+  // (G + 1) & 1, reads list G & 1), and per line-period the generation mark
+  // pgen = G + 2 of the last sweep G that flagged it
+  unsigned long long *pctl;
+  unsigned *pgen;
+  int *plist;
   // UC dynamic-program scratch: stage costs, cost-to-go, decisions
   double *dpL;        // [4][T][ng] per instance, instance slice at 4*gpo
   double *dpC;        // [2][T+1][ng] per instance, slice at 2*(gpo+go)

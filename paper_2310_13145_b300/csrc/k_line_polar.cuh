@@ -405,7 +405,8 @@ enum { NI_TRIAL = 3 };
 template <typename T>
 __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v)[POL_NV], double &f,
                                         const double (&gx)[3], const PolLast &L, const T (&H)[6], double &Delta,
-                                        double omega, bool &accepted, int &counted, PolTrial &tr) {
+                                        double omega, bool &accepted, int &counted, PolTrial &tr,
+                                        bool &nearb) {
   accepted = false;
   counted = 0;
   const double c = P.c;
@@ -444,6 +445,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     }
   }
   xmax = __longlong_as_double(bx);  // max |x_i| (order of non-negative doubles = order of their bits)
+  nearb = prox || near;
   if (prox) {
     full_grad();
 #pragma unroll
@@ -798,9 +800,26 @@ __host__ __device__ constexpr size_t pol_dyn_smem(int bs) {
 // the W-form iterate (w_i, w_j, wR, wI, theta_i, theta_j) and the line-end
 // rows (the slacks, multipliers and penalty are written by the lane itself)
 __device__ __forceinline__ void pol_finish_out(const Dev &S, const double *fd, const float *ff, const int *fi,
-                                               int sl) {
+                                               int sl, unsigned G) {
   const long long NBP = S.NBP, NEP = S.NEP;
-  const long long bp = fi[sl], lef = fi[POL_QF + sl], let = fi[2 * POL_QF + sl];
+  const unsigned fw = (unsigned)fi[sl];
+  const long long bp = fw & 0x7fffffffu, lef = fi[POL_QF + sl], let = fi[2 * POL_QF + sl];
+  // a flagged solve (see k_line_polar) gets this sweep's mark and joins the
+  // next sweep's list (one atomic per warp and flush)
+  const bool hard = (fw >> 31) != 0u;
+  {
+    const unsigned am = __activemask(), hm = __ballot_sync(am, hard);
+    if (hm) {
+      const int lane = threadIdx.x & 31, leader = __ffs(hm) - 1, nxt = (int)((G + 1u) & 1u);
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(&S.pctl[1 + nxt], (unsigned long long)__popc(hm));
+      base = __shfl_sync(am, base, leader);
+      if (hard) {
+        S.pgen[bp] = G + 2u;
+        S.plist[(long long)nxt * NBP + (long long)base + __popc(hm & ((1u << lane) - 1u))] = (int)bp;
+      }
+    }
+  }
   const float fx0 = ff[12 * POL_QF + sl], fx1 = ff[13 * POL_QF + sl], fx2 = ff[14 * POL_QF + sl];
   double a[4];
 #pragma unroll
@@ -854,6 +873,19 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   __syncwarp();
   const long long NBP = S.NBP, NL = S.NL, NEP = S.NEP;
   const long long tail = 2LL * gridDim.x * BS;
+  // Order of the work: first the line-periods the previous sweep flagged
+  // (a solve that had a variable near a bound or a slack held at zero: the
+  // rarer, divergent paths of the solver), from its list, so that they
+  // share warps with each other; then every other line-period in index
+  // order.  Each solve is independent, so the order changes no result.
+  // The list is the one the previous sweep wrote; a line-period is on it
+  // exactly when its mark pgen is G + 1, and one that this sweep has already
+  // taken from the list and flagged again carries G + 2: the second phase
+  // skips both (G changes only when the last warp retires).
+  const unsigned G = (unsigned)S.pctl[3];
+  // warp-uniform: 0 the listed items, then 1 the rest; 2 the rest when the
+  // list is empty (no mark can then equal G + 1 or G + 2, and none is read)
+  int phase = S.pctl[1 + (G & 1u)] > 0ull ? 0 : 2;
   const double eta = S.prm.eta;
   const int K_N = S.prm.K_N, K_AL = S.prm.K_AL;
   bool active = true;
@@ -874,6 +906,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
     acc_nw = acc_al = acc_cap = acc_w = 0;
   };
   bool need_full = false, trial = false;
+  bool hard = false;  // the current solve met a bound or held a slack: flagged for the next sweep
   // a solve that ends with a non-tiny last step is evaluated once more at its
   // final point (at the next trip's single call site, with the rest of the
   // warp) and then finished from that evaluation: 1 converged, 2 stopped
@@ -892,26 +925,44 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
     const unsigned m = __ballot_sync(FULL, want);
     if (m) {
       const int nw = __popc(m);
-      if (qcount < nw && !drained) {
+      for (int fetch = 0; fetch < 2 && qcount < nw && !drained; ++fetch) {
         __syncwarp();
         unsigned long long base = 0;
         int nb = 0;
-        if (lane == 0) {
-          const unsigned long long cur = *(volatile unsigned long long *)S.bp_counter;
-          nb = ((long long)cur + tail < NBP) ? 32 : nw - qcount;
-          base = atomicAdd(S.bp_counter, (unsigned long long)nb);
-        }
-        base = __shfl_sync(FULL, base, 0);
-        nb = __shfl_sync(FULL, nb, 0);
-        const long long left = NBP - (long long)base;
-        const int got = left <= 0 ? 0 : (left < nb ? (int)left : nb);
-        if (left <= nb) drained = true;
-        // the lines of a converged instance are skipped: the fetched items
-        // that remain are packed into the ring
         long long it = -1;
         int ki = 0;
-        if (lane < got) {
-          it = (long long)base + lane;
+        if (phase == 0) {
+          const int par = (int)(G & 1u);
+          // the flagged line-periods of the previous sweep, from its list
+          if (lane == 0) base = atomicAdd(&S.pctl[0], 32ull);
+          base = __shfl_sync(FULL, base, 0);
+          const long long left = (long long)S.pctl[1 + par] - (long long)base;
+          const int got = left <= 0 ? 0 : (left < 32 ? (int)left : 32);
+          if (left <= 32) phase = 1;
+          if (lane < got) it = S.plist[(long long)par * NBP + (long long)base + lane];
+        } else {
+          if (lane == 0) {
+            const unsigned long long cur = *(volatile unsigned long long *)S.bp_counter;
+            nb = ((long long)cur + tail < NBP) ? 32 : nw - qcount;
+            base = atomicAdd(S.bp_counter, (unsigned long long)nb);
+          }
+          base = __shfl_sync(FULL, base, 0);
+          nb = __shfl_sync(FULL, nb, 0);
+          const long long left = NBP - (long long)base;
+          const int got = left <= 0 ? 0 : (left < nb ? (int)left : nb);
+          if (left <= nb) drained = true;
+          // (a line-period on the list was taken in the first phase)
+          if (lane < got) {
+            it = (long long)base + lane;
+            if (phase == 1) {
+              const unsigned mk = S.pgen[it];
+              if (mk == G + 1u || mk == G + 2u) it = -1;
+            }
+          }
+        }
+        // the lines of a converged instance are skipped: the fetched items
+        // that remain are packed into the ring
+        if (it >= 0) {
           ki = find_instance(S, it);
           if (inst_done(S, ki)) it = -1;
         }
@@ -992,6 +1043,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           itn = al = newton = 0;
           need_full = true;
           trial = false;
+          hard = false;
         }
       }
       const int used = nw < qcount ? nw : qcount;
@@ -1000,7 +1052,18 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
     }
     if (__ballot_sync(FULL, active) == 0) {
       __syncwarp();
-      if (lane < ftail[wib] - fhead) pol_finish_out(S, frd, frf, fri, (fhead + lane) & (POL_QF - 1));
+      if (lane < ftail[wib] - fhead) pol_finish_out(S, frd, frf, fri, (fhead + lane) & (POL_QF - 1), G);
+      __syncwarp();
+      // the last warp to retire makes this sweep's flags and list the next
+      // sweep's, and clears the count of the buffer it will write
+      if (lane == 0) {
+        const unsigned long long nwarps = (unsigned long long)gridDim.x * (BS / 32);
+        if (atomicAdd(&S.pctl[4], 1ull) == nwarps - 1ull) {
+          S.pctl[1 + (G & 1u)] = 0ull;
+          S.pctl[3] = (unsigned long long)(G + 1u);
+          S.pctl[4] = 0ull;
+        }
+      }
       break;
     }
     if (active && bp >= 0) {
@@ -1044,8 +1107,10 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
       if (step_now) {
         bool accepted;
         int counted;
-        out = L.lim ? pol_iter<double>(K, P, v, f, gx, L, Hd, Delta, omega, accepted, counted, tr)
-                    : pol_iter<float>(K, P, v, f, gx, L, Hf, Delta, omega, accepted, counted, tr);
+        bool nearb;
+        out = L.lim ? pol_iter<double>(K, P, v, f, gx, L, Hd, Delta, omega, accepted, counted, tr, nearb)
+                    : pol_iter<float>(K, P, v, f, gx, L, Hf, Delta, omega, accepted, counted, tr, nearb);
+        hard = hard || nearb || L.lim;
         newton += counted;
         if (out == NI_TRIAL) {
           trial = true;
@@ -1128,7 +1193,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
               frf[12 * POL_QF + sl] = fx[0];
               frf[13 * POL_QF + sl] = fx[1];
               frf[14 * POL_QF + sl] = fx[2];
-              fri[sl] = (int)bp;
+              fri[sl] = (int)((unsigned)bp | (hard ? 0x80000000u : 0u));
               fri[POL_QF + sl] = (int)lef;
               fri[2 * POL_QF + sl] = (int)let;
             }
@@ -1152,7 +1217,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
     // the outputs of 32 finish records, with every lane active
     __syncwarp();
     if (ftail[wib] - fhead >= 32) {
-      pol_finish_out(S, frd, frf, fri, (fhead + lane) & (POL_QF - 1));
+      pol_finish_out(S, frd, frf, fri, (fhead + lane) & (POL_QF - 1), G);
       fhead += 32;
       __syncwarp();
     }

@@ -171,8 +171,18 @@ void build_granules(const std::vector<long long> &off, const std::vector<long lo
 }
 
 void reset_branch_work(ucac_handle *h, cudaStream_t s) {
-  cudaMemsetAsync(h->dev.bp_counter, 0, sizeof(unsigned long long), s);
+  // the two work counters of the line kernel (bp_counter and pctl[0] are adjacent)
+  cudaMemsetAsync(h->dev.bp_counter, 0, 2 * sizeof(unsigned long long), s);
   cudaMemsetAsync(h->dev.bstat, 0, sizeof(long long) * 3 * h->K, s);
+}
+
+// forget the line kernel's work order (flags and lists of the last sweep):
+// needed whenever an instance that was stopped may run again (state import,
+// UC warm start), since a stopped instance's items keep stale flags
+cudaError_t reset_line_order(ucac_handle *h) {
+  cudaError_t e = cudaMemsetAsync(h->dev.pgen, 0, sizeof(unsigned) * (size_t)h->NBP, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->dev.pctl + 1, 0, 4 * sizeof(unsigned long long), h->stream);
+  return e;
 }
 
 inline int blocks_for(int granules, int bs) { return std::max(1, (granules + bs / 32 - 1) / (bs / 32)); }
@@ -642,6 +652,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_dpD = A.take<unsigned char>(2 * NGP);
   const size_t o_prop = A.take<float>((size_t)MLP_OUT * NBP), o_pack = A.take<uint8_t>(MLP_PACK_BYTES);
   const size_t o_wst = A.take<unsigned long long>(n), o_merr = A.take<int>(1);
+  const size_t o_pfl = A.take<unsigned>((size_t)NBP), o_pli = A.take<int>(2 * (size_t)NBP);
   const size_t o_blk = A.take<int>(2 * ((size_t)h->ngr_gen + h->ngr_gp + h->ngr_bp + h->ngr_up));
   h->arena_bytes = A.off;
   cudaError_t ce = cudaMalloc((void **)&h->arena, h->arena_bytes);
@@ -699,6 +710,9 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.part_gp = (double *)(ar + o_pgp);
   D.bstat = (long long *)(ar + o_pbp);
   D.bp_counter = (unsigned long long *)(D.bstat + 3 * (size_t)n);
+  D.pctl = D.bp_counter + 1;
+  D.pgen = (unsigned *)(ar + o_pfl);
+  D.plist = (int *)(ar + o_pli);
   D.dpL = (double *)(ar + o_dpL);
   D.dpC = (double *)(ar + o_dpC);
   D.dpD = (unsigned char *)(ar + o_dpD);
@@ -964,6 +978,7 @@ int ucac_state_import(ucac_handle *h, int32_t k, const double *buf, size_t n) {
   k_sync_rho<<<1, 32, 0, h->stream>>>(h->dev, k);
   launch_prep(h, h->stream);
   CK(cudaGetLastError());
+  CK(reset_line_order(h));
   CK(cudaStreamSynchronize(h->stream));
   return UCAC_OK;
 }
