@@ -325,3 +325,26 @@ def test_converged_instance_is_frozen_in_a_batch(ucac_mod):
     o.sweep(3)
     assert np.array_equal(o.state_vector(), s0)
     h.close()
+
+
+def test_work_order_changes_no_result(ucac_mod):
+    """The polar line kernel takes the line-periods that met a bound or held
+    a slack in the previous sweep first (their marks and list are cleared by
+    a state import).  300 sweeps into the 118-bus batch -- voltage bounds
+    and line limits bind by then -- a run that keeps its marks and a run
+    that restarts from the exported state without them reach the same bits
+    30 sweeps later."""
+    grids = synth.config_instances("c2_118bus_T24x3")
+    a = ucac_mod.Handle(grids)
+    a.enqueue(300)
+    snaps = [a.export(k) for k in range(len(grids))]
+    a.enqueue(30)
+    b = ucac_mod.Handle(grids)
+    for k, s in enumerate(snaps):
+        b.import_(k, s)
+    b.enqueue(30)
+    for k in range(len(grids)):
+        assert np.array_equal(a.export(k), b.export(k)), k
+        assert a.residuals(k)["newton"] == b.residuals(k)["newton"]
+    a.close()
+    b.close()
