@@ -7,6 +7,7 @@
 // ucac_iterate / ucac_enqueue_sweeps replay.  No device work ever runs on
 // the host: after create, a sweep is six kernel launches and nothing else.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -31,6 +32,15 @@
 using namespace ucac;
 
 namespace {
+
+// NVTX range over one entry point (a profiler shows where host time goes;
+// without a tool attached the calls return at once)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int BS_FIN = 256;   // finish kernel
 // standalone DP: a warp per generator up to this many generators, with at
@@ -384,6 +394,7 @@ void ucac_default_params(ucac_params *p) {
 
 int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, const ucac_rho *rhos, int32_t n,
                       const ucac_params *params, void *cuda_stream, ucac_handle **out) {
+  NvtxRange nvtx_("ucac_create");
   ucac_handle *h = nullptr;
   if (out) *out = nullptr;
   if (!grids || !horizons || !rhos || n < 1 || !out) return fail(nullptr, UCAC_E_ARG, "bad arguments");
@@ -816,12 +827,14 @@ int ucac_create(const ucac_grid *grid, int32_t horizon, ucac_rho rho, const ucac
 int32_t ucac_instances(const ucac_handle *h) { return h ? h->K : 0; }
 
 int ucac_enqueue_sweeps(ucac_handle *h, int32_t n_sweeps) {
+  NvtxRange nvtx_("ucac_enqueue_sweeps");
   if (!h || n_sweeps < 0) return fail(h, UCAC_E_ARG, "bad arguments");
   for (int i = 0; i < n_sweeps; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
   return UCAC_OK;
 }
 
 int ucac_iterate(ucac_handle *h, int32_t n_sweeps) {
+  NvtxRange nvtx_("ucac_iterate");
   if (!h || n_sweeps < 0) return fail(h, UCAC_E_ARG, "bad arguments");
   std::vector<double> c((size_t)NCTRL * h->K), r((size_t)NRES * h->K);
   int done = 0;
@@ -881,6 +894,7 @@ void edge_stage(ucac_handle *h, int k, int dir, bool with_x, cudaStream_t s);
 
 int ucac_solution(const ucac_handle *hc, int32_t k, double *p, double *q, double *w, double *theta, double *pf,
                   uint8_t *u_on) {
+  NvtxRange nvtx_("ucac_solution");
   ucac_handle *h = const_cast<ucac_handle *>(hc);
   if (!h || k < 0 || k >= h->K) return fail(h, UCAC_E_ARG, "bad arguments");
   const HInst &I = h->hi[k];
@@ -952,6 +966,7 @@ void edge_stage(ucac_handle *h, int k, int dir, bool with_x, cudaStream_t s) {
 }  // namespace
 
 int ucac_state_export(const ucac_handle *hc, int32_t k, double *buf, size_t n) {
+  NvtxRange nvtx_("ucac_state_export");
   ucac_handle *h = const_cast<ucac_handle *>(hc);
   if (!h || !buf || k < 0 || k >= h->K || n < ucac_state_size(h, k)) return fail(h, UCAC_E_ARG, "bad arguments");
   CK(cudaStreamSynchronize(h->stream));
@@ -967,6 +982,7 @@ int ucac_state_export(const ucac_handle *hc, int32_t k, double *buf, size_t n) {
 }
 
 int ucac_state_import(ucac_handle *h, int32_t k, const double *buf, size_t n) {
+  NvtxRange nvtx_("ucac_state_import");
   if (!h || !buf || k < 0 || k >= h->K || n < ucac_state_size(h, k)) return fail(h, UCAC_E_ARG, "bad arguments");
   CK(cudaStreamSynchronize(h->stream));
   size_t o = 0;
@@ -995,6 +1011,7 @@ __global__ void k_delay(long long cycles) {
 }  // namespace
 
 int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
+  NvtxRange nvtx_("ucac_kernel_times");
   if (!h || !ms || n_sweeps < 1) return fail(h, UCAC_E_ARG, "bad arguments");
   // events around each launch of one sweep, in launch order:
   // ucdp, gen, mlp (warm start only), line, bus, ucbar, finish
@@ -1037,6 +1054,7 @@ int ucac_kernel_times(ucac_handle *h, int32_t n_sweeps, double *ms) {
 }
 
 int ucac_autotune(ucac_handle *h, int32_t sweeps_per_trial, const char *cache_path, int32_t *out5) {
+  NvtxRange nvtx_("ucac_autotune");
   if (!h || sweeps_per_trial < 1) return fail(h, UCAC_E_ARG, "bad arguments");
   int dev = 0;
   CK(cudaGetDevice(&dev));
@@ -1128,6 +1146,7 @@ int ucac_autotune(ucac_handle *h, int32_t sweeps_per_trial, const char *cache_pa
 
 // ------------------------------------------------------- UC warm start
 int ucac_uc_warm_start(ucac_handle *h, int32_t relax_sweeps, double p_frac) {
+  NvtxRange nvtx_("ucac_uc_warm_start");
   if (!h || relax_sweeps < 0 || !(p_frac >= 0.0)) return fail(h, UCAC_E_ARG, "bad arguments");
   CK(cudaStreamSynchronize(h->stream));
   // the cold start of every instance (the state right after create)
