@@ -47,17 +47,25 @@ __device__ __forceinline__ RowCtx row_ctx(const Dev &S, int k) {
   return R;
 }
 
-// Per-family constants of the row update: rho, 1/rho and 1/(beta + rho),
+// Per-family constants of the row update: rho, 1/rho and -1/(beta + rho),
 // taken from the instance record, so that no row-update thread divides (a
 // division costs the FP64 pipe about as much as ten multiply-adds, and the
 // pipe is the bottleneck).
 struct Fam {
-  double rho, irho, ibr;
+  double rho, irho, nbr;
 };
 
-__device__ __forceinline__ Fam fam_pq(const Inst &I) { return Fam{I.rpq, I.irpq, I.ibpq}; }
-__device__ __forceinline__ Fam fam_va(const Inst &I) { return Fam{I.rva, I.irva, I.ibva}; }
-__device__ __forceinline__ Fam fam_uc(const Inst &I) { return Fam{I.ruc, I.iruc, I.ibuc}; }
+__device__ __forceinline__ Fam fam_pq(const Inst &I) { return Fam{I.rpq, I.irpq, I.nbpq}; }
+__device__ __forceinline__ Fam fam_va(const Inst &I) { return Fam{I.rva, I.irva, I.nbva}; }
+__device__ __forceinline__ Fam fam_uc(const Inst &I) { return Fam{I.ruc, I.iruc, I.nbuc}; }
+
+// a compile-time flag: the x-bar kernels take the pending outer update as a
+// template choice made once per warp, so the rows of a sweep without one
+// carry no (predicated-off) multiplier-clip instructions
+template <bool B>
+struct Flag {
+  static constexpr bool value = B;
+};
 
 // x-step target of a UC duplicate row from its x-bar value b: (b - z) - y/rho
 // with each operation rounded separately and a true division -- the UC
@@ -95,19 +103,20 @@ __device__ __forceinline__ double max_abs_bits(double q, double c) {
 }
 
 // SD: accumulate this row's (b_new - b_old)^2 here (false when the caller
-// adds it once for rows that share b, as a bus's w and theta rows do)
-template <bool EXACT, bool SD = true>
+// adds it once for rows that share b, as a bus's w and theta rows do);
+// PEND: an outer update is pending (R.pend, warp-uniform)
+template <bool EXACT, bool PEND, bool SD = true>
 __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, double *L, double *Tg, double *W,
                                            long long idx, double b_new, double b_old, const Fam &F,
                                            const RowCtx &R, double (&q)[NQ]) {
   const double a = A[idx], y = Y[idx], z = Z[idx];
   double lam = L[idx];
-  if (R.pend) {
+  if (PEND) {
     lam = clampd(fma_(R.beta_cur, z, lam), -R.lam_max, R.lam_max);
     L[idx] = lam;
   }
   const double c = sub_(a, b_new);
-  const double zn = -mul_(fma_(F.rho, c, add_(lam, y)), F.ibr);
+  const double zn = mul_(fma_(F.rho, c, add_(lam, y)), F.nbr);
   const double cz = add_(c, zn);
   const double yn = fma_(F.rho, cz, y);
   Z[idx] = zn;
@@ -188,52 +197,60 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const double c0 = cf[ig], c1 = cf[S.NB + ig], c2 = cf[2 * S.NB + ig];
     const double nuP = fma_(c0, r0, -mul_(c1, r1));
     const double nuQ = fma_(c2, r1, -mul_(c1, r0));
-    // pass 2: new x-bar values, then the rows they own
-    for (int e = g0; e < g1; ++e) {
-      const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
-      const long long gn = gp + I.ng;
-      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
-      double iW = irpq;
-      if (!last) {
-        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])));
-        iW = 0.5 * irpq;
+    // pass 2: new x-bar values, then the rows they own (instantiated with and
+    // without the pending outer update, chosen once per warp)
+    auto pass2 = [&](auto pend) {
+      constexpr bool PEND = decltype(pend)::value;
+      for (int e = g0; e < g1; ++e) {
+        const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
+        const long long gn = gp + I.ng;
+        double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
+        double iW = irpq;
+        if (!last) {
+          m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])));
+          iW = 0.5 * irpq;
+        }
+        const double pnew = fma_(-nuP, iW, m);
+        const double qnew = fma_(-nuQ, irpq, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
+        const double pold = S.G[F_PBAR * NGP + gp], qold = S.G[F_QBAR * NGP + gp];
+        S.G[F_PBAR * NGP + gp] = pnew;
+        S.G[F_QBAR * NGP + gp] = qnew;
+        row_update<false, PEND>(S.GA + GR_GP * NGP, S.GY + GR_GP * NGP, S.GZ + GR_GP * NGP, S.GL + GR_GP * NGP,
+                          S.GT + GR_GP * NGP, S.GW + GR_GP * NGP, gp, pnew, pold, Fpq, R, q);
+        if (!last)
+          row_update<false, PEND>(S.GA + GR_TC * NGP, S.GY + GR_TC * NGP, S.GZ + GR_TC * NGP, S.GL + GR_TC * NGP,
+                            S.GT + GR_TC * NGP, S.GW + GR_TC * NGP, gn, pnew, pold, Fpq, R, q);
+        row_update<false, PEND>(S.GA + GR_GQ * NGP, S.GY + GR_GQ * NGP, S.GZ + GR_GQ * NGP, S.GL + GR_GQ * NGP,
+                          S.GT + GR_GQ * NGP, S.GW + GR_GQ * NGP, gp, qnew, qold, Fpq, R, q);
       }
-      const double pnew = fma_(-nuP, iW, m);
-      const double qnew = fma_(-nuQ, irpq, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
-      const double pold = S.G[F_PBAR * NGP + gp], qold = S.G[F_QBAR * NGP + gp];
-      S.G[F_PBAR * NGP + gp] = pnew;
-      S.G[F_QBAR * NGP + gp] = qnew;
-      row_update<false>(S.GA + GR_GP * NGP, S.GY + GR_GP * NGP, S.GZ + GR_GP * NGP, S.GL + GR_GP * NGP,
-                        S.GT + GR_GP * NGP, S.GW + GR_GP * NGP, gp, pnew, pold, Fpq, R, q);
-      if (!last)
-        row_update<false>(S.GA + GR_TC * NGP, S.GY + GR_TC * NGP, S.GZ + GR_TC * NGP, S.GL + GR_TC * NGP,
-                          S.GT + GR_TC * NGP, S.GW + GR_TC * NGP, gn, pnew, pold, Fpq, R, q);
-      row_update<false>(S.GA + GR_GQ * NGP, S.GY + GR_GQ * NGP, S.GZ + GR_GQ * NGP, S.GL + GR_GQ * NGP,
-                        S.GT + GR_GQ * NGP, S.GW + GR_GQ * NGP, gp, qnew, qold, Fpq, R, q);
-    }
-    const double wold = S.U[FU_W * NUP + up], thold = S.U[FU_TH * NUP + up];
-    const double wnew = sub_(mw, mul_(fma_(nuP, aPw, mul_(nuQ, aQw)), iWw));
-    const double thnew = (i == I.ref) ? 0.0 : mth;
-    S.U[FU_W * NUP + up] = wnew;
-    S.U[FU_TH * NUP + up] = thnew;
-    // every incident w (theta) row has the bus's w (theta) as its x-bar:
-    // their x-bar changes enter the dual residual as deg times one square
-    const double dw = sub_(wnew, wold), dth = sub_(thnew, thold);
-    q[Q_SD] = fma_(mul_(fdeg, dw), dw, q[Q_SD]);
-    q[Q_SD] = fma_(mul_(fdeg, dth), dth, q[Q_SD]);
-    for (int j = 0; j < deg; ++j) {
-      const long long e = e0 + 32LL * j;
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const long long eu = u * NEP + e;
-        const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, S.ET[eu]);
-        const double vold = S.EFB[eu];
-        S.EFB[eu] = vnew;
-        row_update<false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, eu, vnew, vold, Fpq, R, q);
+      const double wold = S.U[FU_W * NUP + up], thold = S.U[FU_TH * NUP + up];
+      const double wnew = sub_(mw, mul_(fma_(nuP, aPw, mul_(nuQ, aQw)), iWw));
+      const double thnew = (i == I.ref) ? 0.0 : mth;
+      S.U[FU_W * NUP + up] = wnew;
+      S.U[FU_TH * NUP + up] = thnew;
+      // every incident w (theta) row has the bus's w (theta) as its x-bar:
+      // their x-bar changes enter the dual residual as deg times one square
+      const double dw = sub_(wnew, wold), dth = sub_(thnew, thold);
+      q[Q_SD] = fma_(mul_(fdeg, dw), dw, q[Q_SD]);
+      q[Q_SD] = fma_(mul_(fdeg, dth), dth, q[Q_SD]);
+      for (int j = 0; j < deg; ++j) {
+        const long long e = e0 + 32LL * j;
+  #pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const long long eu = u * NEP + e;
+          const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, S.ET[eu]);
+          const double vold = S.EFB[eu];
+          S.EFB[eu] = vnew;
+          row_update<false, PEND>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, eu, vnew, vold, Fpq, R, q);
+        }
+        row_update<false, PEND, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, 2 * NEP + e, wnew, wold, Fva, R, q);
+        row_update<false, PEND, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, 3 * NEP + e, thnew, thold, Fva, R, q);
       }
-      row_update<false, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, 2 * NEP + e, wnew, wold, Fva, R, q);
-      row_update<false, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, 3 * NEP + e, thnew, thold, Fva, R, q);
-    }
+    };
+    if (R.pend)
+      pass2(Flag<true>{});
+    else
+      pass2(Flag<false>{});
   }
   warp_reduce_q(q, S.part_up + (long long)gr * NQ);
 }
@@ -446,25 +463,33 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
     S.G[F_UBSD * NGP + gp] = sdv;
     if (has_next) S.G[F_UBSU * NGP + gn] = su1;
     if (tau == 0) S.G[F_UBSU * NGP + gp] = su0;
-#define RU_(E, r, idx, bn, bo, F)                                                                            \
-  row_update<E>(S.GA + (r)*NGP, S.GY + (r)*NGP, S.GZ + (r)*NGP, S.GL + (r)*NGP, S.GT + (r)*NGP,  \
-                S.GW + (r)*NGP, idx, bn, bo, F, R, q)
-    RU_(true, GR_ON, gp, on, on_old, Fuc);
-    RU_(true, GR_SD, gp, sdv, sd_old, Fuc);
-    RU_(false, GR_PL, gp, Pmin * on, Pmin * on_old, Fpq);
-    RU_(false, GR_PU, gp, Pmax * on, Pmax * on_old, Fpq);
-    RU_(false, GR_QL, gp, Qmin * on, Qmin * on_old, Fpq);
-    RU_(false, GR_QU, gp, Qmax * on, Qmax * on_old, Fpq);
-    RU_(false, GR_RD, gp, (-RD * on) - SD * sdv, (-RD * on_old) - SD * sd_old, Fpq);
-    if (has_next) {
-      RU_(true, GR_SU, gn, su1, su1_old, Fuc);
-      RU_(false, GR_RU, gn, RU * on + SU * su1, RU * on_old + SU * su1_old, Fpq);
-    }
-    if (tau == 0) {
-      RU_(true, GR_SU, gp, su0, su0_old, Fuc);
-      RU_(false, GR_RU, gp, RU * u0 + SU * su0, RU * u0 + SU * su0_old, Fpq);
-    }
+    // the rows, with and without the pending outer update (chosen per warp)
+    auto rows = [&](auto pend) {
+      constexpr bool PEND = decltype(pend)::value;
+#define RU_(E, r, idx, bn, bo, F)                                                                         \
+  row_update<E, PEND>(S.GA + (r)*NGP, S.GY + (r)*NGP, S.GZ + (r)*NGP, S.GL + (r)*NGP, S.GT + (r)*NGP, \
+                      S.GW + (r)*NGP, idx, bn, bo, F, R, q)
+      RU_(true, GR_ON, gp, on, on_old, Fuc);
+      RU_(true, GR_SD, gp, sdv, sd_old, Fuc);
+      RU_(false, GR_PL, gp, Pmin * on, Pmin * on_old, Fpq);
+      RU_(false, GR_PU, gp, Pmax * on, Pmax * on_old, Fpq);
+      RU_(false, GR_QL, gp, Qmin * on, Qmin * on_old, Fpq);
+      RU_(false, GR_QU, gp, Qmax * on, Qmax * on_old, Fpq);
+      RU_(false, GR_RD, gp, (-RD * on) - SD * sdv, (-RD * on_old) - SD * sd_old, Fpq);
+      if (has_next) {
+        RU_(true, GR_SU, gn, su1, su1_old, Fuc);
+        RU_(false, GR_RU, gn, RU * on + SU * su1, RU * on_old + SU * su1_old, Fpq);
+      }
+      if (tau == 0) {
+        RU_(true, GR_SU, gp, su0, su0_old, Fuc);
+        RU_(false, GR_RU, gp, RU * u0 + SU * su0, RU * u0 + SU * su0_old, Fpq);
+      }
 #undef RU_
+    };
+    if (R.pend)
+      rows(Flag<true>{});
+    else
+      rows(Flag<false>{});
     const double p = S.G[F_P * NGP + gp];
     q[Q_OBJ] = S.c2p[gg] * p * p + S.c1p[gg] * p + S.c0[gg] * S.G[F_UON * NGP + gp] +
                S.csu[gg] * S.G[F_USU * NGP + gp] + S.csd[gg] * S.G[F_USD * NGP + gp];
