@@ -102,35 +102,59 @@ __device__ __forceinline__ double max_abs_bits(double q, double c) {
   return __longlong_as_double((long long)(bc > bq ? bc : bq));
 }
 
-// SD: accumulate this row's (b_new - b_old)^2 here (false when the caller
-// adds it once for rows that share b, as a bus's w and theta rows do);
-// PEND: an outer update is pending (R.pend, warp-uniform)
-template <bool EXACT, bool PEND, bool SD = true>
-__device__ __forceinline__ void row_update(double *A, double *Y, double *Z, double *L, double *Tg, double *W,
-                                           long long idx, double b_new, double b_old, const Fam &F,
-                                           const RowCtx &R, double (&q)[NQ]) {
-  const double a = A[idx], y = Y[idx], z = Z[idx];
-  double lam = L[idx];
-  if (PEND) {
-    lam = clampd(fma_(R.beta_cur, z, lam), -R.lam_max, R.lam_max);
-    L[idx] = lam;
-  }
+// The row update from its loaded inputs a, y, lambda: the new z, y, w and
+// next target, and the row's residual terms into q.  SD: accumulate its
+// (b_new - b_old)^2 here (false when the caller adds it once for rows that
+// share b, as a bus's w and theta rows do).
+struct RowNew {
+  double z, y, w, t;
+};
+
+template <bool EXACT, bool SD = true>
+__device__ __forceinline__ RowNew row_step(double a, double y, double lam, double b_new, double b_old, const Fam &F,
+                                           double (&q)[NQ]) {
+  RowNew r;
   const double c = sub_(a, b_new);
-  const double zn = mul_(fma_(F.rho, c, add_(lam, y)), F.nbr);
-  const double cz = add_(c, zn);
-  const double yn = fma_(F.rho, cz, y);
-  Z[idx] = zn;
-  Y[idx] = yn;
-  const double w = row_w(zn, yn, F.irho);
-  W[idx] = w;
-  Tg[idx] = EXACT ? row_target_exact(b_new, zn, yn, F.rho) : row_target_w(b_new, w);
+  r.z = mul_(fma_(F.rho, c, add_(lam, y)), F.nbr);
+  const double cz = add_(c, r.z);
+  r.y = fma_(F.rho, cz, y);
+  r.w = row_w(r.z, r.y, F.irho);
+  r.t = EXACT ? row_target_exact(b_new, r.z, r.y, F.rho) : row_target_w(b_new, r.w);
   q[Q_SP] = fma_(cz, cz, q[Q_SP]);
   if (SD) {
     const double db = sub_(b_new, b_old);
     q[Q_SD] = fma_(db, db, q[Q_SD]);
   }
-  q[Q_SZ] = fma_(zn, zn, q[Q_SZ]);
+  q[Q_SZ] = fma_(r.z, r.z, q[Q_SZ]);
   q[Q_INF] = max_abs_bits(q[Q_INF], c);
+  return r;
+}
+
+__device__ __forceinline__ void row_store(double *Y, double *Z, double *Tg, double *W, long long idx, const RowNew &r) {
+  Z[idx] = r.z;
+  Y[idx] = r.y;
+  W[idx] = r.w;
+  Tg[idx] = r.t;
+}
+
+// the outer update of one row, lambda <- clip(lambda + beta z) (Eq. step:outer)
+__device__ __forceinline__ double outer_lambda(double lam, double z, const RowCtx &R) {
+  return clampd(fma_(R.beta_cur, z, lam), -R.lam_max, R.lam_max);
+}
+
+// load, update and store one row; PEND: an outer update is pending (R.pend,
+// warp-uniform) and is applied to the row's lambda first
+template <bool EXACT, bool PEND, bool SD = true>
+__device__ __forceinline__ void row_update(double *A, double *Y, double *Z, double *L, double *Tg, double *W,
+                                           long long idx, double b_new, double b_old, const Fam &F,
+                                           const RowCtx &R, double (&q)[NQ]) {
+  const double a = A[idx], y = Y[idx];
+  double lam = L[idx];
+  if (PEND) {
+    lam = outer_lambda(lam, Z[idx], R);
+    L[idx] = lam;
+  }
+  row_store(Y, Z, Tg, W, idx, row_step<EXACT, SD>(a, y, lam, b_new, b_old, F, q));
 }
 
 // ------------------------------------------------------------ bus (R8) ----
@@ -197,60 +221,85 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const double c0 = cf[ig], c1 = cf[S.NB + ig], c2 = cf[2 * S.NB + ig];
     const double nuP = fma_(c0, r0, -mul_(c1, r1));
     const double nuQ = fma_(c2, r1, -mul_(c1, r0));
-    // pass 2: new x-bar values, then the rows they own (instantiated with and
-    // without the pending outer update, chosen once per warp)
-    auto pass2 = [&](auto pend) {
-      constexpr bool PEND = decltype(pend)::value;
+    // a pending outer update first, over every row this thread owns: a
+    // separate pass in the few sweeps that carry one, so that the row
+    // updates below hold no multiplier clip
+    if (R.pend) {
       for (int e = g0; e < g1; ++e) {
         const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
-        const long long gn = gp + I.ng;
-        double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
-        double iW = irpq;
-        if (!last) {
-          m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])));
-          iW = 0.5 * irpq;
-        }
-        const double pnew = fma_(-nuP, iW, m);
-        const double qnew = fma_(-nuQ, irpq, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
-        const double pold = S.G[F_PBAR * NGP + gp], qold = S.G[F_QBAR * NGP + gp];
-        S.G[F_PBAR * NGP + gp] = pnew;
-        S.G[F_QBAR * NGP + gp] = qnew;
-        row_update<false, PEND>(S.GA + GR_GP * NGP, S.GY + GR_GP * NGP, S.GZ + GR_GP * NGP, S.GL + GR_GP * NGP,
-                          S.GT + GR_GP * NGP, S.GW + GR_GP * NGP, gp, pnew, pold, Fpq, R, q);
-        if (!last)
-          row_update<false, PEND>(S.GA + GR_TC * NGP, S.GY + GR_TC * NGP, S.GZ + GR_TC * NGP, S.GL + GR_TC * NGP,
-                            S.GT + GR_TC * NGP, S.GW + GR_TC * NGP, gn, pnew, pold, Fpq, R, q);
-        row_update<false, PEND>(S.GA + GR_GQ * NGP, S.GY + GR_GQ * NGP, S.GZ + GR_GQ * NGP, S.GL + GR_GQ * NGP,
-                          S.GT + GR_GQ * NGP, S.GW + GR_GQ * NGP, gp, qnew, qold, Fpq, R, q);
+        const long long r0i = GR_GP * NGP + gp, r1i = GR_TC * NGP + gp + I.ng, r2i = GR_GQ * NGP + gp;
+        S.GL[r0i] = outer_lambda(S.GL[r0i], S.GZ[r0i], R);
+        if (!last) S.GL[r1i] = outer_lambda(S.GL[r1i], S.GZ[r1i], R);
+        S.GL[r2i] = outer_lambda(S.GL[r2i], S.GZ[r2i], R);
       }
-      const double wold = S.U[FU_W * NUP + up], thold = S.U[FU_TH * NUP + up];
-      const double wnew = sub_(mw, mul_(fma_(nuP, aPw, mul_(nuQ, aQw)), iWw));
-      const double thnew = (i == I.ref) ? 0.0 : mth;
-      S.U[FU_W * NUP + up] = wnew;
-      S.U[FU_TH * NUP + up] = thnew;
-      // every incident w (theta) row has the bus's w (theta) as its x-bar:
-      // their x-bar changes enter the dual residual as deg times one square
-      const double dw = sub_(wnew, wold), dth = sub_(thnew, thold);
-      q[Q_SD] = fma_(mul_(fdeg, dw), dw, q[Q_SD]);
-      q[Q_SD] = fma_(mul_(fdeg, dth), dth, q[Q_SD]);
-      for (int j = 0; j < deg; ++j) {
-        const long long e = e0 + 32LL * j;
-  #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const long long eu = u * NEP + e;
-          const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, S.ET[eu]);
-          const double vold = S.EFB[eu];
-          S.EFB[eu] = vnew;
-          row_update<false, PEND>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, eu, vnew, vold, Fpq, R, q);
+      for (int j = 0; j < deg; ++j)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const long long eu = u * NEP + e0 + 32LL * j;
+          S.EL[eu] = outer_lambda(S.EL[eu], S.EZ[eu], R);
         }
-        row_update<false, PEND, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, 2 * NEP + e, wnew, wold, Fva, R, q);
-        row_update<false, PEND, false>(S.EA, S.EY, S.EZ, S.EL, S.ET, S.EW, 3 * NEP + e, thnew, thold, Fva, R, q);
+    }
+    // pass 2: new x-bar values, then the rows they own
+    for (int e = g0; e < g1; ++e) {
+      const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
+      const long long gn = gp + I.ng;
+      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
+      double iW = irpq;
+      if (!last) {
+        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])));
+        iW = 0.5 * irpq;
       }
-    };
-    if (R.pend)
-      pass2(Flag<true>{});
-    else
-      pass2(Flag<false>{});
+      const double pnew = fma_(-nuP, iW, m);
+      const double qnew = fma_(-nuQ, irpq, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
+      const double pold = S.G[F_PBAR * NGP + gp], qold = S.G[F_QBAR * NGP + gp];
+      S.G[F_PBAR * NGP + gp] = pnew;
+      S.G[F_QBAR * NGP + gp] = qnew;
+      row_update<false, false>(S.GA + GR_GP * NGP, S.GY + GR_GP * NGP, S.GZ + GR_GP * NGP, S.GL + GR_GP * NGP,
+                               S.GT + GR_GP * NGP, S.GW + GR_GP * NGP, gp, pnew, pold, Fpq, R, q);
+      if (!last)
+        row_update<false, false>(S.GA + GR_TC * NGP, S.GY + GR_TC * NGP, S.GZ + GR_TC * NGP, S.GL + GR_TC * NGP,
+                                 S.GT + GR_TC * NGP, S.GW + GR_TC * NGP, gn, pnew, pold, Fpq, R, q);
+      row_update<false, false>(S.GA + GR_GQ * NGP, S.GY + GR_GQ * NGP, S.GZ + GR_GQ * NGP, S.GL + GR_GQ * NGP,
+                               S.GT + GR_GQ * NGP, S.GW + GR_GQ * NGP, gp, qnew, qold, Fpq, R, q);
+    }
+    const double wold = S.U[FU_W * NUP + up], thold = S.U[FU_TH * NUP + up];
+    const double wnew = sub_(mw, mul_(fma_(nuP, aPw, mul_(nuQ, aQw)), iWw));
+    const double thnew = (i == I.ref) ? 0.0 : mth;
+    S.U[FU_W * NUP + up] = wnew;
+    S.U[FU_TH * NUP + up] = thnew;
+    // every incident w (theta) row has the bus's w (theta) as its x-bar:
+    // their x-bar changes enter the dual residual as deg times one square
+    const double dw = sub_(wnew, wold), dth = sub_(thnew, thold);
+    q[Q_SD] = fma_(mul_(fdeg, dw), dw, q[Q_SD]);
+    q[Q_SD] = fma_(mul_(fdeg, dth), dth, q[Q_SD]);
+    for (int j = 0; j < deg; ++j) {
+      const long long e = e0 + 32LL * j;
+      // every input of the line end's four rows is loaded before any of
+      // its stores (for all the compiler knows a store may alias a later
+      // load, so a load placed after a store would cost a round trip of
+      // its own): one memory round trip per line end instead of six
+      double a[4], y[4], lam[4], mt[2], bo[2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = S.EA[u * NEP + e];
+        y[u] = S.EY[u * NEP + e];
+        lam[u] = S.EL[u * NEP + e];
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        mt[u] = S.ET[u * NEP + e];  // (the x-bar-step target parked by pass 1)
+        bo[u] = S.EFB[u * NEP + e];
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const long long eu = u * NEP + e;
+        const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, mt[u]);
+        S.EFB[eu] = vnew;
+        row_store(S.EY, S.EZ, S.ET, S.EW, eu, row_step<false>(a[u], y[u], lam[u], vnew, bo[u], Fpq, q));
+      }
+      row_store(S.EY, S.EZ, S.ET, S.EW, 2 * NEP + e, row_step<false, false>(a[2], y[2], lam[2], wnew, wold, Fva, q));
+      row_store(S.EY, S.EZ, S.ET, S.EW, 3 * NEP + e, row_step<false, false>(a[3], y[3], lam[3], thnew, thold, Fva, q));
+    }
   }
   warp_reduce_q(q, S.part_up + (long long)gr * NQ);
 }
