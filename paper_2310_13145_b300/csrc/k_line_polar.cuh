@@ -128,10 +128,18 @@ struct PolP {
 
 // last full evaluation: flows, their gradients (FP32: used only for the
 // first-order update after a tiny step), cos/sin, the point, the limit
-// gradients grad(g_k) and the multiplier estimates m_k = mu_k + c h_k
+// gradients grad(g_k) in FP32 and the multiplier estimates m_k = mu_k + c h_k.
+// A free slack is eliminated from the Newton system exactly, so grad g_k
+// reaches the x iterates only where a slack is held at zero, a variable is
+// near a bound or a trust-region step is modelled: there pol_iter forms it
+// in FP64 from the point (pol_dg64).  Elsewhere it enters only the free
+// slacks' step and the first-order h_k of a finish after a tiny step, where
+// the FP32 copy's ~1e-7 relative error times the step is far below the
+// tolerances.
 struct PolLast {
   double a[4], c, s, v[5];
-  double dg[2][3], m[2], h[2];
+  double m[2], h[2];
+  float fdg[2][3];
   float da[4][3];
   bool lim;  // a slack is held at zero: the FP64 Hessian is in use
 };
@@ -268,17 +276,11 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
     const double m = P.mu[k] + P.c * h;
     L.m[k] = m;
     L.h[k] = h;
-    const double AE = fma(L.a[r0], E[r0], L.a[r1] * E[r1]);
-    const double AEd = fma(L.a[r0], Ed[r0], L.a[r1] * Ed[r1]);
-    const double Aq = fma(L.a[r0], K.q[r0], L.a[r1] * K.q[r1]);
-    if (k == 0) {
-      L.dg[0][0] = fma(2.0 * Vi2x, Aq, Vj2x * AE);
-      L.dg[0][1] = Vi2x * AE;
-    } else {
-      L.dg[1][0] = Vj2x * AE;
-      L.dg[1][1] = fma(2.0 * Vj2x, Aq, Vi2x * AE);
-    }
-    L.dg[k][2] = 2.0 * Pv * AEd;
+    // grad g_k = 2 sum_r a_r grad a_r over the end's two rows, in FP32 from
+    // the FP32 flow gradients
+    const float fa0 = d2f_trunc(L.a[r0]), fa1 = d2f_trunc(L.a[r1]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) L.fdg[k][i] = 2.0f * (fa0 * L.da[r0][i] + fa1 * L.da[r1][i]);
     // a free slack's optimum has m_k = 0, so the Newton model takes the
     // reduced x-Hessian there; m_k hess g_k stays only for a slack that may
     // be held at zero
@@ -347,6 +349,32 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
   }
 }
 
+// FP64 gradients of the limit functions at the last evaluation point:
+//   grad g_0 = (4 V_i A_q + 2 V_j A_E, 2 V_i A_E, 2 V_i V_j A_Ed),
+//   grad g_1 = (2 V_j A_E, 4 V_j A_q + 2 V_i A_E, 2 V_i V_j A_Ed),
+// with the end's sums A_E = sum a_r E_r, A_Ed = sum a_r Ed_r, A_q = sum a_r q_r
+__device__ __forceinline__ void pol_dg64(const PolK &K, const PolLast &L, double (&dg)[2][3]) {
+  const double Vi = L.v[0], Vj = L.v[1];
+  const double Pv = Vi * Vj, Vi2x = 2.0 * Vi, Vj2x = 2.0 * Vj;
+  double E[4], Ed[4];
+  pol_angle_terms(K.ga[0], K.ka[0], K.ga[1], K.ka[1], L.c, L.s, E, Ed);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int r0 = 2 * k, r1 = 2 * k + 1;
+    const double AE = fma(L.a[r0], E[r0], L.a[r1] * E[r1]);
+    const double AEd = fma(L.a[r0], Ed[r0], L.a[r1] * Ed[r1]);
+    const double Aq = fma(L.a[r0], K.q[r0], L.a[r1] * K.q[r1]);
+    if (k == 0) {
+      dg[0][0] = fma(2.0 * Vi2x, Aq, Vj2x * AE);
+      dg[0][1] = Vi2x * AE;
+    } else {
+      dg[1][0] = Vj2x * AE;
+      dg[1][1] = fma(2.0 * Vj2x, Aq, Vi2x * AE);
+    }
+    dg[k][2] = 2.0 * Pv * AEd;
+  }
+}
+
 // objective at the point of the last evaluation, from its flows and h_k
 // (formed only where a ratio test needs it: a trial step, a held slack's step)
 __device__ __forceinline__ double pol_f(const PolP &P, const PolLast &L) {
@@ -397,7 +425,107 @@ __device__ __forceinline__ T hq(const T (&H)[6], int i, int j) {
 struct PolTrial {
   double v[POL_NV], ht[2], pred, scale, smax;
 };
-enum { NI_TRIAL = 3 };
+enum { NI_TRIAL = 3, NI_FULL = 4 };
+
+// The common Newton iteration of a lane with no slack held at zero (FP32
+// Hessian H): no variable within 1e-6 of a bound, the unshifted system
+// factorises, no variable is pushed across a bound it sits at, and the step
+// is the stop step or lies in the box and the trust region.  Its arithmetic
+// is that of pol_iter in this case, except that the free slacks' step takes
+// grad g_k . d_x from the FP32 gradients (the slacks do not enter the
+// reduced x-system, so the x iterates are the same).  Any other case
+// returns NI_FULL with nothing written, and the caller runs pol_iter, which
+// forms grad g_k in FP64.
+__device__ __forceinline__ int pol_fast(const PolK &K, const PolP &P, double (&v)[POL_NV], const double (&gx)[3],
+                                        const PolLast &L, const float (&H)[6], double Delta, double omega,
+                                        bool &accepted, int &counted) {
+  const long long b6 = __double_as_longlong(1e-6), ABS = 0x7fffffffffffffffLL;
+  double dlo[POL_NV], dhi[POL_NV];
+  long long bx = 0;
+  bool edge = false;  // a variable within 1e-6 of a bound
+#pragma unroll
+  for (int i = 0; i < POL_NV; ++i) {
+    dlo[i] = v[i] - pol_lo(K, i);
+    dhi[i] = i < 3 ? pol_hi(K, i) - v[i] : INFINITY;
+    if (i < 3) {
+      const long long b = __double_as_longlong(v[i]) & ABS;
+      bx = b > bx ? b : bx;
+      edge = edge || __double_as_longlong(dlo[i]) <= b6 || __double_as_longlong(dhi[i]) <= b6;
+    } else {
+      edge = edge || (__double_as_longlong(dlo[i]) <= b6 && __double_as_longlong(L.m[i - 3]) > 0);
+    }
+  }
+  if (edge) return NI_FULL;
+  const double xmax = __longlong_as_double(bx);
+  // stationarity on the reduced gradient, the free slacks' exact step
+  bool stat = true;
+  const long long bom = __double_as_longlong(omega);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const long long br = __double_as_longlong(gx[i]);
+    const long long bd = __double_as_longlong(br > 0 ? dlo[i] : dhi[i]);
+    stat = stat && ((br & ABS) <= bom || bd <= bom);
+  }
+  double sn[2];
+  bool sok = true;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    sn[k] = v[3 + k] - L.m[k] * P.ic;
+    const long long b = __double_as_longlong(sn[k]);
+    sok = sok && (b >= 0 || b == (long long)0x8000000000000000ULL);
+  }
+  accepted = false;
+  counted = 0;
+  if (stat && sok) {
+    v[3] = sn[0];
+    v[4] = sn[1];
+    return NI_CONV;
+  }
+  float y[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[i] = to_t<float>(-gx[i]);
+  if (!chol3p(H, y)) return NI_FULL;
+  double d[POL_NV];
+  long long bn = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    d[i] = to_d<float>(y[i]);
+    const long long b = __double_as_longlong(d[i]) & ABS;
+    bn = b > bn ? b : bn;
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float gd = L.fdg[k][0] * y[0] + L.fdg[k][1] * y[1] + L.fdg[k][2] * y[2];
+    d[3 + k] = -L.m[k] * P.ic - f2d_exact(gd);
+  }
+  // the second pass of pol_iter: no x variable sits within 1e-6 of a bound
+  // here, but a slack may (with m_k <= 0); one that the step pushes below
+  // zero is fixed there by pol_iter
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    if (le_nn(dlo[3 + k], 1e-6) && dkey(d[3 + k]) < dkey(-dlo[3 + k])) return NI_FULL;
+  const double dn = __longlong_as_double(bn);
+  if (le_nn(dn, 1e-9 * (1.0 + xmax))) {
+#pragma unroll
+    for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
+    counted = 1;
+    return NI_CONV;
+  }
+  bool inside = true;
+#pragma unroll
+  for (int i = 0; i < POL_NV; ++i) {
+    const long long b = __double_as_longlong(d[i]);
+    inside = inside && (b < 0 ? (b & ABS) <= __double_as_longlong(dlo[i]) : b <= __double_as_longlong(dhi[i]));
+  }
+  if (inside && le_nn(dn, 1e-3 * (1.0 + xmax)) && le_nn(dn, Delta)) {
+#pragma unroll
+    for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
+    counted = 1;
+    accepted = true;
+    return NI_CONT;
+  }
+  return NI_FULL;
+}
 
 // one projected Newton iteration over v = (V_i, V_j, d, sigma_ij, sigma_ji)
 // with the x-Hessian H of type T (see newton_iter of the W-form kernel for
@@ -416,9 +544,14 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   double gr[POL_NV];
   gr[3] = L.m[0];
   gr[4] = L.m[1];
+  // FP64 grad g_k (this is the path of the solves pol_fast hands over: a
+  // variable near a bound, a held slack, a shifted or second-pass system,
+  // a trust-region step)
+  double dg[2][3];
+  pol_dg64(K, L, dg);
   auto full_grad = [&]() {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) gr[i] = fma(L.m[0], L.dg[0][i], fma(L.m[1], L.dg[1][i], gx[i]));
+    for (int i = 0; i < 3; ++i) gr[i] = fma(L.m[0], dg[0][i], fma(L.m[1], dg[1][i], gx[i]));
   };
   double xmax = 0.0, dlo[POL_NV], dhi[POL_NV];
   T hmax = T(0);
@@ -507,7 +640,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int k = 0; k < 2; ++k)
-        if (act[3 + k]) rg[i] = fma(L.m[k], L.dg[k][i], rg[i]);
+        if (act[3 + k]) rg[i] = fma(L.m[k], dg[k][i], rg[i]);
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -554,7 +687,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
         double add = 0.0;
 #pragma unroll
         for (int k = 0; k < 2; ++k)
-          if (act[3 + k]) add += c * L.dg[k][pi_[q]] * L.dg[k][pj_[q]];
+          if (act[3 + k]) add += c * dg[k][pi_[q]] * dg[k][pj_[q]];
         Hr[q] += (T)add;
       }
     }
@@ -563,7 +696,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
       double r = -rg[i];
 #pragma unroll
       for (int k = 0; k < 2; ++k)
-        if (act[3 + k]) r -= c * L.dg[k][i] * d[3 + k];
+        if (act[3 + k]) r -= c * dg[k][i] * d[3 + k];
       rb[i] = to_t<T>(r);
     }
     T y[3];
@@ -601,7 +734,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     }
 #pragma unroll
     for (int k = 0; k < 2; ++k)
-      if (!act[3 + k]) d[3 + k] = -L.m[k] * P.ic - (L.dg[k][0] * d[0] + L.dg[k][1] * d[1] + L.dg[k][2] * d[2]);
+      if (!act[3 + k]) d[3 + k] = -L.m[k] * P.ic - (dg[k][0] * d[0] + dg[k][1] * d[1] + dg[k][2] * d[2]);
     if (pass > 0) break;
     bool again = false;
 #pragma unroll
@@ -615,7 +748,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
         again = true;
         if (i >= 3) {  // a held slack keeps its m_k grad g_k in the reduced gradient
 #pragma unroll
-          for (int j = 0; j < 3; ++j) rg[j] = fma(L.m[i - 3], L.dg[i - 3][j], rg[j]);
+          for (int j = 0; j < 3; ++j) rg[j] = fma(L.m[i - 3], dg[i - 3][j], rg[j]);
         }
       }
     }
@@ -639,7 +772,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     double quad = (double)sHs;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const double e = L.dg[k][0] * sg[0] + L.dg[k][1] * sg[1] + L.dg[k][2] * sg[2] + sg[3 + k];
+      const double e = dg[k][0] * sg[0] + dg[k][1] * sg[1] + dg[k][2] * sg[2] + sg[3 + k];
       quad += c * e * e;
     }
     return -(lin + 0.5 * quad);
@@ -684,7 +817,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   int free_mask = 0, nheld = 0;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    ht[k] = L.h[k] + L.dg[k][0] * sg[0] + L.dg[k][1] * sg[1] + L.dg[k][2] * sg[2] + sg[3 + k];
+    ht[k] = L.h[k] + dg[k][0] * sg[0] + dg[k][1] * sg[1] + dg[k][2] * sg[2] + sg[3 + k];
     if (act[3 + k]) ++nheld; else free_mask |= 1 << k;
   }
   f = pol_f(P, L);  // the ratio test's baseline: the objective at v
@@ -708,9 +841,9 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
 #pragma unroll
     for (int k = 0; k < 2; ++k)
       r[k] = act[3 + k] ? (at[2 * k] * at[2 * k] + at[2 * k + 1] * at[2 * k + 1] - K.rate2 + vt[3 + k]) - ht[k] : 0.0;
-    G[0] = L.dg[0][0] * L.dg[0][0] + L.dg[0][1] * L.dg[0][1] + L.dg[0][2] * L.dg[0][2];
-    G[1] = L.dg[0][0] * L.dg[1][0] + L.dg[0][1] * L.dg[1][1] + L.dg[0][2] * L.dg[1][2];
-    G[2] = L.dg[1][0] * L.dg[1][0] + L.dg[1][1] * L.dg[1][1] + L.dg[1][2] * L.dg[1][2];
+    G[0] = dg[0][0] * dg[0][0] + dg[0][1] * dg[0][1] + dg[0][2] * dg[0][2];
+    G[1] = dg[0][0] * dg[1][0] + dg[0][1] * dg[1][1] + dg[0][2] * dg[1][2];
+    G[2] = dg[1][0] * dg[1][0] + dg[1][1] * dg[1][1] + dg[1][2] * dg[1][2];
     double al0 = 0.0, al1 = 0.0;
     if (nheld == 2) {
       const double det = G[0] * G[2] - G[1] * G[1];
@@ -726,7 +859,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     double vc[POL_NV];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      vc[i] = clampd(vt[i] - al0 * L.dg[0][i] - al1 * L.dg[1][i], pol_lo(K, i), pol_hi(K, i));
+      vc[i] = clampd(vt[i] - al0 * dg[0][i] - al1 * dg[1][i], pol_lo(K, i), pol_hi(K, i));
     vc[3] = vt[3];
     vc[4] = vt[4];
     double ac[4], cc, sc;
@@ -1108,8 +1241,13 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         bool accepted;
         int counted;
         bool nearb;
-        out = L.lim ? pol_iter<double>(K, P, v, f, gx, L, Hd, Delta, omega, accepted, counted, tr, nearb)
-                    : pol_iter<float>(K, P, v, f, gx, L, Hf, Delta, omega, accepted, counted, tr, nearb);
+        if (L.lim) {
+          out = pol_iter<double>(K, P, v, f, gx, L, Hd, Delta, omega, accepted, counted, tr, nearb);
+        } else {
+          out = pol_fast(K, P, v, gx, L, Hf, Delta, omega, accepted, counted);
+          nearb = false;
+          if (out == NI_FULL) out = pol_iter<float>(K, P, v, f, gx, L, Hf, Delta, omega, accepted, counted, tr, nearb);
+        }
         hard = hard || nearb || L.lim;
         newton += counted;
         if (out == NI_TRIAL) {
@@ -1152,7 +1290,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
             dxs = dx2;
 #pragma unroll
             for (int q = 0; q < 2; ++q)
-              h[q] = L.h[q] + L.dg[q][0] * dx0 + L.dg[q][1] * dx1 + L.dg[q][2] * dx2 + (v[3 + q] - L.v[3 + q]);
+              h[q] = L.h[q] + f2d_exact(L.fdg[q][0] * fx[0] + L.fdg[q][1] * fx[1] + L.fdg[q][2] * fx[2]) +
+                     (v[3 + q] - L.v[3 + q]);
           }
           // equality multiplier step on h_k = p_k^2 + q_k^2 + sigma_k - rate^2
           long long bh = 0;
