@@ -41,17 +41,17 @@ UNIT = "sweeps/s"
 # processes), counted by the hardware: (DADD + DMUL + 2 DFMA) thread
 # instructions of one launch (ncu smsp__sass_thread_inst_executed_op_d*_pred_on)
 # divided by the launch's line-period solves.  16 x 2000-bus scenarios:
-# 812.0 M FLOP over 1,228,800 solves at sweep 31 (660.8 per solve; 291 per
-# counted Newton iteration) and 806.1 M at sweep 701 (656.0 per solve): the
+# 576.6 M FLOP over 1,228,800 solves at sweep 31 (469.2 per solve; 207 per
+# counted Newton iteration) and 580.0 M at sweep 701 (472.0 per solve): the
 # work per solve hardly moves over a run, while the Newton count does.  The
 # W-form kernel: 10,340.8 M FLOP at sweep 31 (8,415 per solve).  The
 # captures and their commands are summarised under profiles/.
-LINE_FLOP_PER_SOLVE = {"polar": 660.8, "w": 8415.3}
+LINE_FLOP_PER_SOLVE = {"polar": 469.2, "w": 8415.3}
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one launch of the polar line kernel on the
 # 16 x 2000-bus workload, from the same ncu capture of sweep 31; None for a
 # form or workload not captured
-LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 375.0e6}
+LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 376.1e6}
 # Algorithmic bytes (FP64 reads + writes each kernel must make) per unit of
 # the streaming x-bar and generator kernels, from their data layout (a row
 # keeps w = z + y/rho beside its next x-step target):
