@@ -148,6 +148,11 @@ struct Dev {
   long long NB;
   const double *Gs, *Bs, *ideg, *vmid;  // shunt, 1/degree, middle of the voltage band
   double *bus_nu;  // [2][3][NB]: multiplier-solve coefficients per period kind (k_prep_bus)
+  // UC box QPs: the inverse of the free block of H for each free-coordinate
+  // mask, [variant (0: a next period, 1: the last)][mask][6 packed][NGEN]
+  // (k_prep_ucbar)
+  double *uc_hinv;
+  long long NGEN;
   const int *inc_ptr;            // CSR row pointers over global buses (degree)
   const int *gen_ptr, *gen_idx;  // CSR over global buses; generator index local
   const int *bus_order;                    // [NB] per instance: local buses sorted by (degree, generators)

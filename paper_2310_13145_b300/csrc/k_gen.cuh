@@ -52,32 +52,21 @@ __device__ __forceinline__ GenOut gen_solve(double c2p, double c1p, double rho, 
   const double t_pl = tg[0], t_pu = tg[1], t_ql = tg[2], t_qu = tg[3], t_rd = tg[4], t_ru = tg[5];
   const double t_gp = tg[6], t_gq = tg[7], t_tc = tg[8];
   GenOut o;
-  // ---- q: root of rho[(q - t_gq) + min(0, q - t_ql) + max(0, q - t_qu)] on [qlo, qhi]
+  // ---- q: root of rho[(q - t_gq) + min(0, q - t_ql) + max(0, q - t_qu)] on
+  // [qlo, qhi].  D is increasing and linear between its breakpoints t_ql,
+  // t_qu, so its sign at the two breakpoints picks the piece that holds the
+  // unconstrained root, and that root clamped to [qlo, qhi] is the root on
+  // the interval.  The piece's root divides by its slope k = 1, 2 or 3
+  // (k = 3 only when the targets cross, t_ql > t_qu)
   {
     auto D = [&](double q) { return (q - t_gq) + fmin(q - t_ql, 0.0) + fmax(q - t_qu, 0.0); };
-    double q;
-    if (D(qlo) >= 0.0) {
-      q = qlo;
-    } else if (D(qhi) <= 0.0) {
-      q = qhi;
-    } else {
-      double best = INFINITY;
-      q = qlo;
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        int al, ah;
-        double ilo, ihi;
-        regime(r, t_ql, t_qu, al, ah, ilo, ihi);
-        const double k = 1.0 + al + ah;
-        const double qc = clampd((t_gq + (al ? t_ql : 0.0) + (ah ? t_qu : 0.0)) / k, qlo, qhi);
-        const double viol = dist_interval(qc, ilo, ihi);
-        if (viol < best) {
-          best = viol;
-          q = qc;
-        }
-      }
-    }
-    o.q = q;
+    const int r = D(fmin(t_ql, t_qu)) >= 0.0 ? 0 : (D(fmax(t_ql, t_qu)) >= 0.0 ? 1 : 2);
+    int al, ah;
+    double ilo, ihi;
+    regime(r, t_ql, t_qu, al, ah, ilo, ihi);
+    const double num = t_gq + (al ? t_ql : 0.0) + (ah ? t_qu : 0.0);
+    const int k = 1 + al + ah;
+    o.q = clampd(k == 1 ? num : (k == 2 ? 0.5 * num : num / 3.0), qlo, qhi);
   }
   // ---- (p, phat): candidate of piece (i, j) and its distance from its cell
   auto piece = [&](int i, int j, double &pc, double &phc) -> double {

@@ -314,43 +314,62 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
 // so one face is solved instead of 27; otherwise every face is enumerated and
 // the KKT-consistent candidate of least objective is kept (fallback: least
 // objective among in-box candidates).
+// H of the box QP of generator gg, the same for every period but the last
+// (has_next: the su, ru rows of the next period); constant between penalty
+// changes.  Rows and weights as listed in k_ucbar.
+__device__ __forceinline__ void uc_box_h(const Dev &S, int gg, double rpq, double ruc, bool has_next,
+                                         double (&H)[3][3]) {
+  const double Pmin = S.Pmin[gg], Pmax = S.Pmax[gg], Qmin = S.Qmin[gg], Qmax = S.Qmax[gg];
+  const double RU = S.RU[gg], RD = S.RD[gg], SU = S.SU[gg], SD = S.SD[gg];
+  H[0][0] = ruc + rpq * (Pmin * Pmin + Pmax * Pmax + Qmin * Qmin + Qmax * Qmax + RD * RD);
+  H[0][1] = rpq * (RD * SD);
+  H[1][1] = ruc + rpq * (SD * SD);
+  H[0][2] = H[1][2] = H[2][2] = 0.0;
+  if (has_next) {
+    H[0][0] += rpq * (RU * RU);
+    H[0][2] = rpq * (RU * SU);
+    H[2][2] = ruc + rpq * (SU * SU);
+  }
+  H[1][0] = H[0][1];
+  H[2][0] = H[0][2];
+  H[2][1] = H[1][2];
+}
+
+// entries of the inverse table: [variant][free mask][packed (0,0) (0,1)
+// (0,2) (1,1) (1,2) (2,2)], each a [NGEN] array
+constexpr int UC_HINV_N = 2 * 8 * 6;
+
 struct FaceRes {
   double x[3], f;
   bool inbox, kkt;
   int next[3];  // block principal pivoting: the face to try next
 };
 
+// Hv: the generator's inverse table for its variant (k_prep_ucbar), entry
+// (mask, q) at Hv[(6 mask + q) NGEN]
 __device__ __forceinline__ FaceRes solve_face(int n, const int (&st)[3], const double (&H)[3][3],
-                                              const double (&gv)[3], double tolx, double tolg) {
+                                              const double (&gv)[3], double tolx, double tolg, const double *Hv,
+                                              long long NGEN) {
   FaceRes R;
-  double A[3][3], rhs[3];
+  // free rows: r_i = g_i - sum over the fixed j of H_ij x_j; the free block's
+  // inverse (zero outside the block) maps them to the free coordinates
+  double rhs[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const bool fi = (st[i] == 0);
     double r = gv[i];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const bool fj = (st[j] == 0);
-      const double xj = (st[j] == 2) ? 1.0 : 0.0;
-      if (!fj) r -= H[i][j] * xj;
-      A[i][j] = (fi && fj) ? H[i][j] : ((i == j) ? 1.0 : 0.0);
-    }
-    rhs[i] = fi ? r : ((st[i] == 2) ? 1.0 : 0.0);
+    for (int j = 0; j < 3; ++j)
+      if (st[j] != 0) r -= H[i][j] * ((st[j] == 2) ? 1.0 : 0.0);
+    rhs[i] = (st[i] == 0) ? r : 0.0;
   }
-  // A = L D L^T (no square roots: three reciprocals instead of three square
-  // roots and three reciprocals of the Cholesky factor)
-  const double iD0 = 1.0 / A[0][0];
-  const double L10 = A[1][0] * iD0, L20 = A[2][0] * iD0;
-  const double iD1 = 1.0 / (A[1][1] - L10 * A[1][0]);
-  const double A21r = A[2][1] - L20 * A[1][0];
-  const double L21 = A21r * iD1;
-  const double iD2 = 1.0 / (A[2][2] - L20 * A[2][0] - L21 * A21r);
-  const double y0 = rhs[0];
-  const double y1 = rhs[1] - L10 * y0;
-  const double y2 = rhs[2] - L20 * y0 - L21 * y1;
-  R.x[2] = y2 * iD2;
-  R.x[1] = y1 * iD1 - L21 * R.x[2];
-  R.x[0] = y0 * iD0 - L10 * R.x[1] - L20 * R.x[2];
+  const int mask = (st[0] == 0 ? 1 : 0) | (st[1] == 0 ? 2 : 0) | (st[2] == 0 ? 4 : 0);
+  const double *hv = Hv + (long long)mask * 6 * NGEN;
+  double Hi[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) Hi[q] = hv[q * NGEN];
+  R.x[0] = Hi[0] * rhs[0] + Hi[1] * rhs[1] + Hi[2] * rhs[2];
+  R.x[1] = Hi[1] * rhs[0] + Hi[3] * rhs[1] + Hi[4] * rhs[2];
+  R.x[2] = Hi[2] * rhs[0] + Hi[4] * rhs[1] + Hi[5] * rhs[2];
   R.inbox = true;
   R.kkt = true;
   R.f = 0.0;
@@ -389,7 +408,7 @@ __device__ __forceinline__ FaceRes solve_face(int n, const int (&st)[3], const d
 }
 
 __device__ __forceinline__ void boxqp3(int n, const double (&H)[3][3], const double (&gv)[3], const double (&x0)[3],
-                                       double (&x)[3]) {
+                                       double (&x)[3], const double *Hv, long long NGEN) {
   long long bs = 0;  // max |gv_i|, |H_ij| by bit pattern
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -408,7 +427,7 @@ __device__ __forceinline__ void boxqp3(int n, const double (&H)[3][3], const dou
 #pragma unroll
     for (int i = 0; i < 3; ++i) st[i] = (i >= n) ? 1 : (dkey(x0[i]) <= k0 ? 1 : (dkey(x0[i]) >= k1 ? 2 : 0));
     for (int it = 0; it < 4; ++it) {
-      const FaceRes R = solve_face(n, st, H, gv, tolx, tolg);
+      const FaceRes R = solve_face(n, st, H, gv, tolx, tolg, Hv, NGEN);
       if (R.inbox && R.kkt) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) x[i] = clampd(R.x[i], 0.0, 1.0);
@@ -425,7 +444,7 @@ __device__ __forceinline__ void boxqp3(int n, const double (&H)[3][3], const dou
     int st[3] = {face % 3, (face / 3) % 3, face / 9};
     if (n == 2 && st[2] != 0) continue;
     if (n == 2) st[2] = 1;  // absent coordinate pinned at 0
-    const FaceRes R = solve_face(n, st, H, gv, tolx, tolg);
+    const FaceRes R = solve_face(n, st, H, gv, tolx, tolg, Hv, NGEN);
     if (!R.inbox) continue;
     if (R.f < bestf) {
       bestf = R.f;
@@ -474,30 +493,21 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
     const double m_pl = MT(GR_PL, gp, Fpq), m_pu = MT(GR_PU, gp, Fpq);
     const double m_ql = MT(GR_QL, gp, Fpq), m_qu = MT(GR_QU, gp, Fpq), m_rd = MT(GR_RD, gp, Fpq);
     double H[3][3], gv[3];
-    H[0][0] = ruc + rpq * (Pmin * Pmin + Pmax * Pmax + Qmin * Qmin + Qmax * Qmax + RD * RD);
-    H[0][1] = rpq * (RD * SD);
-    H[1][1] = ruc + rpq * (SD * SD);
-    H[0][2] = H[1][2] = H[2][2] = 0.0;
+    uc_box_h(S, gg, rpq, ruc, has_next, H);
     gv[0] = ruc * m_on + rpq * (m_pl * Pmin + m_pu * Pmax + m_ql * Qmin + m_qu * Qmax - m_rd * RD);
     gv[1] = ruc * m_sd - rpq * (m_rd * SD);
     gv[2] = 0.0;
     if (has_next) {
       const double m_su = MT(GR_SU, gn, Fuc), m_ru = MT(GR_RU, gn, Fpq);
-      H[0][0] += rpq * (RU * RU);
-      H[0][2] = rpq * (RU * SU);
-      H[2][2] = ruc + rpq * (SU * SU);
       gv[0] += rpq * (m_ru * RU);
       gv[2] = ruc * m_su + rpq * (m_ru * SU);
     }
-    H[1][0] = H[0][1];
-    H[2][0] = H[0][2];
-    H[2][1] = H[1][2];
     const double on_old = S.G[F_UBON * NGP + gp], sd_old = S.G[F_UBSD * NGP + gp];
     const double su1_old = has_next ? S.G[F_UBSU * NGP + gn] : 0.0;
     const double su0_old = (tau == 0) ? S.G[F_UBSU * NGP + gp] : 0.0;
     const double x0[3] = {on_old, sd_old, su1_old};
     double x[3];
-    boxqp3(has_next ? 3 : 2, H, gv, x0, x);
+    boxqp3(has_next ? 3 : 2, H, gv, x0, x, S.uc_hinv + (has_next ? 0LL : 48LL * S.NGEN) + gg, S.NGEN);
     // lone block: ubar_su at t = 0 (ubar_on before period 1 is the data u0)
     double su0 = 0.0;
     const double u0 = (double)S.u0[gg];
@@ -803,6 +813,63 @@ __global__ void __launch_bounds__(BS) k_prep_bus(Dev S, int changed_only) {
     cf[ig] = c0;
     cf[S.NB + ig] = c1;
     cf[2 * S.NB + ig] = c2;
+  }
+}
+
+// The UC box QPs' free-block inverses: for each generator of instance
+// blockIdx.y, each variant (0: a next period, coordinates on, sd, su; 1: the
+// last period, on and sd only) and each mask of free coordinates, the
+// inverse of H restricted to the free coordinates (zero outside the block;
+// masks that free the absent coordinate of variant 1 stay zero).  H is
+// positive definite, so every principal block is invertible.  Formed after
+// create, import and each penalty change; one thread per generator.
+template <int BS>
+__global__ void __launch_bounds__(BS) k_prep_ucbar(Dev S, int changed_only) {
+  const int k = blockIdx.y;
+  if (changed_only && S.res[(long long)k * NRES + R_RCHG] == 0.0) return;
+  const Inst I = S.inst[k];
+  const int g = blockIdx.x * BS + threadIdx.x;
+  if (g >= I.ng) return;
+  const int gg = I.go + g;
+  const long long NG = S.NGEN;
+  const int pi_[6] = {0, 0, 0, 1, 1, 2}, pj_[6] = {0, 1, 2, 1, 2, 2};
+  for (int var = 0; var < 2; ++var) {
+    double H[3][3];
+    uc_box_h(S, gg, I.rpq, I.ruc, var == 0, H);
+    for (int mask = 0; mask < 8; ++mask) {
+      double Hi[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+      int f[3], m = 0;
+      for (int i = 0; i < 3; ++i)
+        if ((mask >> i) & 1) f[m++] = i;
+      if (!(var == 1 && (mask & 4))) {
+        if (m == 1) {
+          Hi[f[0]][f[0]] = 1.0 / H[f[0]][f[0]];
+        } else if (m == 2) {
+          const double a = H[f[0]][f[0]], b = H[f[0]][f[1]], c = H[f[1]][f[1]];
+          const double id = 1.0 / (a * c - b * b);
+          Hi[f[0]][f[0]] = c * id;
+          Hi[f[0]][f[1]] = Hi[f[1]][f[0]] = -b * id;
+          Hi[f[1]][f[1]] = a * id;
+        } else if (m == 3) {
+          // cofactors of the symmetric 3x3 block
+          const double C00 = H[1][1] * H[2][2] - H[1][2] * H[1][2];
+          const double C01 = H[0][2] * H[1][2] - H[0][1] * H[2][2];
+          const double C02 = H[0][1] * H[1][2] - H[1][1] * H[0][2];
+          const double C11 = H[0][0] * H[2][2] - H[0][2] * H[0][2];
+          const double C12 = H[0][1] * H[0][2] - H[0][0] * H[1][2];
+          const double C22 = H[0][0] * H[1][1] - H[0][1] * H[0][1];
+          const double id = 1.0 / (H[0][0] * C00 + H[0][1] * C01 + H[0][2] * C02);
+          Hi[0][0] = C00 * id;
+          Hi[0][1] = Hi[1][0] = C01 * id;
+          Hi[0][2] = Hi[2][0] = C02 * id;
+          Hi[1][1] = C11 * id;
+          Hi[1][2] = Hi[2][1] = C12 * id;
+          Hi[2][2] = C22 * id;
+        }
+      }
+      double *out = S.uc_hinv + ((long long)var * 8 + mask) * 6 * NG + gg;
+      for (int q = 0; q < 6; ++q) out[q * NG] = Hi[pi_[q]][pj_[q]];
+    }
   }
 }
 

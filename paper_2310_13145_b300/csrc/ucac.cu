@@ -85,7 +85,7 @@ struct ucac_handle {
   char *arena = nullptr;
   size_t arena_bytes = 0;
   Dev dev{};
-  long long NGEN = 0, NGP = 0, NL = 0, NBP = 0, NB = 0, NUP = 0, NEP = 0, max_nbp = 0, max_nb = 0;
+  long long NGEN = 0, NGP = 0, NL = 0, NBP = 0, NB = 0, NUP = 0, NEP = 0, max_nbp = 0, max_nb = 0, max_ng = 0;
   double *stage = nullptr;  // [NSTAGE][max_nbp]: line-end rows of one instance in canonical order
   uint8_t *mlp_pack = nullptr;  // packed warm-start network (BF16 operands, FP32 biases)
   int *mlp_err = nullptr;       // set by the MLP kernel on a timed-out wait
@@ -269,6 +269,8 @@ void launch_prep(ucac_handle *h, cudaStream_t s, int changed_only = 0) {
   k_prep_branch<BS_PREP><<<blocks_for(h->ngr_bp, BS_PREP), BS_PREP, 0, s>>>(h->dev, changed_only);
   const unsigned nbx = (unsigned)std::max(1LL, (h->max_nb + BS_PREP - 1) / BS_PREP);
   k_prep_bus<BS_PREP><<<dim3(nbx, (unsigned)h->K), BS_PREP, 0, s>>>(h->dev, changed_only);
+  const unsigned ngx = (unsigned)std::max(1LL, (h->max_ng + BS_PREP - 1) / BS_PREP);
+  k_prep_ucbar<BS_PREP><<<dim3(ngx, (unsigned)h->K), BS_PREP, 0, s>>>(h->dev, changed_only);
 }
 
 // persistent tensor-core MLP over all line-periods (learned warm start)
@@ -593,6 +595,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   h->NEP = NEP;
   h->max_nbp = max_nbp;
   for (int k = 0; k < n; ++k) h->max_nb = std::max(h->max_nb, (long long)h->hi[k].nb);
+  for (int k = 0; k < n; ++k) h->max_ng = std::max(h->max_ng, (long long)h->hi[k].ng);
   // ---- block tables
   std::vector<int> bgi, bgf, bpi, bpf, bbi, bbf, bui, buf_;
   std::vector<int> g0(n), g1(n), p0b(n), p1b(n), q0b(n), q1b(n), u0b(n), u1b(n);
@@ -653,6 +656,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_es = A.take<int>(2 * NL + 2 * blk_off.size());
   const size_t o_stage = A.take<double>((size_t)NSTAGE * max_nbp);
   const size_t o_bus = A.take<double>(4 * NB), o_busnu = A.take<double>(6 * NB);
+  const size_t o_uchinv = A.take<double>((size_t)UC_HINV_N * NGEN);
   const size_t o_csr = A.take<int>((NB + 1) * 2 + NGEN + NB);
   const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
   const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
@@ -707,6 +711,8 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.NB = NB;
   D.Gs = (const double *)(ar + o_bus); D.Bs = D.Gs + NB; D.ideg = D.Gs + 2 * NB; D.vmid = D.Gs + 3 * NB;
   D.bus_nu = (double *)(ar + o_busnu);
+  D.uc_hinv = (double *)(ar + o_uchinv);
+  D.NGEN = NGEN;
   const int *csr = (const int *)(ar + o_csr);
   D.inc_ptr = csr; D.gen_ptr = csr + (NB + 1);
   D.gen_idx = D.gen_ptr + (NB + 1);
