@@ -22,23 +22,33 @@
 
 namespace ucac {
 
-__device__ __forceinline__ double uc_stage(double b, double su, double sd, double tau_on, double tau_su,
-                                           double tau_sd, double c0, double csu, double csd, double hr) {
-  double e_on = __dsub_rn(b, tau_on);
-  double e_su = __dsub_rn(su, tau_su);
-  double e_sd = __dsub_rn(sd, tau_sd);
-  double q = __dadd_rn(__dadd_rn(__dmul_rn(e_on, e_on), __dmul_rn(e_su, e_su)), __dmul_rn(e_sd, e_sd));
-  double lin = __dadd_rn(__dadd_rn(__dmul_rn(c0, b), __dmul_rn(csu, su)), __dmul_rn(csd, sd));
-  return __dadd_rn(lin, __dmul_rn(hr, q));
+// The linear parts c0*b + csu*su + csd*sd of the four stage costs, entry
+// ab = a*2+b ((b, su, sd) = (0,0,0), (1,1,0), (0,0,1), (1,0,0)); they
+// depend on the generator only, so they are formed once, in the order the
+// rule at the top of this file fixes.
+__device__ __forceinline__ void uc_lin4(double c0, double csu, double csd, double (&lin)[4]) {
+  const double b[4] = {0.0, 1.0, 0.0, 1.0}, su[4] = {0.0, 1.0, 0.0, 0.0}, sd[4] = {0.0, 0.0, 1.0, 0.0};
+#pragma unroll
+  for (int ab = 0; ab < 4; ++ab)
+    lin[ab] = __dadd_rn(__dadd_rn(__dmul_rn(c0, b[ab]), __dmul_rn(csu, su[ab])), __dmul_rn(csd, sd[ab]));
 }
 
-// The four stage costs of period t, entry ab = a*2+b at L[(ab*T + t)*st].
-__device__ __forceinline__ void uc_stage4(int T, int t, long long st, double ton, double tsu, double tsd, double c0,
-                                          double csu, double csd, double hr, double *L) {
-  L[(0 * T + t) * st] = uc_stage(0.0, 0.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
-  L[(1 * T + t) * st] = uc_stage(1.0, 1.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
-  L[(2 * T + t) * st] = uc_stage(0.0, 0.0, 1.0, ton, tsu, tsd, c0, csu, csd, hr);
-  L[(3 * T + t) * st] = uc_stage(1.0, 0.0, 0.0, ton, tsu, tsd, c0, csu, csd, hr);
+// The four stage costs of period t, entry ab = a*2+b at L[(ab*T + t)*st],
+// the values of the rule at the top of this file: with b, su, sd in {0, 1}
+// each e = b - tau is
+// -tau (0 - tau is exact) or 1 - tau, and e*e does not depend on e's sign,
+// so the six squares are formed once and shared; each q keeps the rule's
+// summation order.
+__device__ __forceinline__ void uc_stage4(int T, int t, long long st, double ton, double tsu, double tsd,
+                                          const double (&lin)[4], double hr, double *L) {
+  const double on0 = __dmul_rn(ton, ton), su0 = __dmul_rn(tsu, tsu), sd0 = __dmul_rn(tsd, tsd);
+  const double eon = __dsub_rn(1.0, ton), esu = __dsub_rn(1.0, tsu), esd = __dsub_rn(1.0, tsd);
+  const double on1 = __dmul_rn(eon, eon), su1 = __dmul_rn(esu, esu), sd1 = __dmul_rn(esd, esd);
+  const double a00 = __dadd_rn(on0, su0);
+  const double q[4] = {__dadd_rn(a00, sd0), __dadd_rn(__dadd_rn(on1, su1), sd0), __dadd_rn(a00, sd1),
+                       __dadd_rn(__dadd_rn(on1, su0), sd0)};
+#pragma unroll
+  for (int ab = 0; ab < 4; ++ab) L[(ab * T + t) * st] = __dadd_rn(lin[ab], __dmul_rn(hr, q[ab]));
 }
 
 // Backward pass and forward reconstruction of Algorithm 2 from the
@@ -103,8 +113,9 @@ __device__ __forceinline__ double uc_dp(int T, int TU, int TD, int u0, int K0, d
                                         double hr, const double *tau_on, const double *tau_su,
                                         const double *tau_sd, long long st, double *L, double *C,
                                         unsigned char *D, WriteU uon) {
-  for (int t = 0; t < T; ++t)
-    uc_stage4(T, t, st, tau_on[t * st], tau_su[t * st], tau_sd[t * st], c0, csu, csd, hr, L);
+  double lin[4];
+  uc_lin4(c0, csu, csd, lin);
+  for (int t = 0; t < T; ++t) uc_stage4(T, t, st, tau_on[t * st], tau_su[t * st], tau_sd[t * st], lin, hr, L);
   return uc_dp_tab(T, TU, TD, u0, K0, st, L, C, D, uon);
 }
 
@@ -230,9 +241,11 @@ __global__ void __launch_bounds__(128) k_ucdp_warp(int ng, int T, double rho, co
   double *C = L + 4 * T;
   unsigned char *D = (unsigned char *)(dp_sm + 4 * (6 * (size_t)T + 2)) + (size_t)w * 2 * T;
   const double hr = __dmul_rn(0.5, rho);
+  double lin[4];
+  uc_lin4(c0[g], csu[g], csd[g], lin);
   for (int t = lane; t < T; t += 32) {
     const long long i = (long long)t * ng + g;
-    uc_stage4(T, t, 1, tau_on[i], tau_su[i], tau_sd[i], c0[g], csu[g], csd[g], hr, L);
+    uc_stage4(T, t, 1, tau_on[i], tau_su[i], tau_sd[i], lin, hr, L);
   }
   __syncwarp();
   if (lane != 0) return;
