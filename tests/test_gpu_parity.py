@@ -348,3 +348,69 @@ def test_work_order_changes_no_result(ucac_mod):
         assert a.residuals(k)["newton"] == b.residuals(k)["newton"]
     a.close()
     b.close()
+
+
+def test_lockstep_generator_q_pieces(ucac_mod):
+    """The generator kernel takes q from the piece of its piecewise linear
+    optimality condition that the condition's signs at the two breakpoints
+    (the q-bound rows' targets) pick.  Multipliers of the q-bound and
+    q-consensus rows are drawn so that the targets fall in every order --
+    crossed ones (the slope-3 piece) included -- and one sweep from that
+    state is compared with the oracle's."""
+    g = synth.config_instances("c2_118bus_T24x3")[0]
+    dims = _dims(g)
+    h = ucac_mod.Handle([g])
+    h.enqueue(20)
+    st = oracle.unpack_state(h.export(0), *dims)
+    rng = np.random.default_rng(11)
+    rho = st["rho_pq"]
+    span = np.maximum(g.Qmax - g.Qmin, 0.1)[None, :]
+    for row in ("ql", "qu", "gq"):
+        st["gy_" + row] = st["gy_" + row] + rho * span * rng.uniform(-1.5, 1.5, st["gy_" + row].shape)
+    # targets t = b - z - y/rho of the q-bound rows (their x-bar values are
+    # Qmin u_on and Qmax u_on): some must cross
+    t_ql = g.Qmin[None, :] * st["ub_on"] - st["gz_ql"] - st["gy_ql"] / rho
+    t_qu = g.Qmax[None, :] * st["ub_on"] - st["gz_qu"] - st["gy_qu"] / rho
+    assert np.count_nonzero(t_ql > t_qu) > 100
+    h.import_(0, oracle.pack_state(st, *dims))
+    pre = h.export(0)
+    h.enqueue(1)
+    o = oracle.Oracle(g)
+    o.set_state(pre)
+    o.sweep()
+    bad = compare_states(h.export(0), o.state_vector(), g, skip=POLAR_SKIP,
+                         mu_eta=ucac_mod.ucac_default_params().eta)
+    assert not bad, bad[:6]
+    h.close()
+
+
+def test_lockstep_uc_box_faces(ucac_mod):
+    """The duplicate-UC box QPs solve each face from the free block's
+    inverse, formed once per generator and penalty (k_prep_ucbar).
+    Multipliers of every row of the box QPs drawn at the scale of the
+    penalties move their minimisers onto every kind of face -- interior,
+    edges, corners, through the pivots and the full enumeration -- and one
+    sweep from that state is compared with the oracle's."""
+    g = synth.config_instances("c2_118bus_T24x3")[1]
+    dims = _dims(g)
+    h = ucac_mod.Handle([g])
+    h.enqueue(20)
+    st = oracle.unpack_state(h.export(0), *dims)
+    rng = np.random.default_rng(12)
+    for row, rho in (("on", st["rho_uc"]), ("su", st["rho_uc"]), ("sd", st["rho_uc"]), ("pl", st["rho_pq"]),
+                     ("pu", st["rho_pq"]), ("rd", st["rho_pq"]), ("ru", st["rho_pq"])):
+        st["gy_" + row] = st["gy_" + row] + rho * rng.uniform(-2.0, 2.0, st["gy_" + row].shape)
+    h.import_(0, oracle.pack_state(st, *dims))
+    pre = h.export(0)
+    h.enqueue(1)
+    o = oracle.Oracle(g)
+    o.set_state(pre)
+    o.sweep()
+    out = oracle.unpack_state(h.export(0), *dims)
+    # the minimisers spread over the box: interior and bound values both occur
+    ub = np.concatenate([out["ub_on"].ravel(), out["ub_sd"].ravel()])
+    assert np.count_nonzero((ub > 1e-9) & (ub < 1 - 1e-9)) > 50 and np.count_nonzero(ub <= 0.0) > 50
+    bad = compare_states(h.export(0), o.state_vector(), g, skip=POLAR_SKIP,
+                         mu_eta=ucac_mod.ucac_default_params().eta)
+    assert not bad, bad[:6]
+    h.close()
