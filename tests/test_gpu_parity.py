@@ -414,3 +414,37 @@ def test_lockstep_uc_box_faces(ucac_mod):
                          mu_eta=ucac_mod.ucac_default_params().eta)
     assert not bad, bad[:6]
     h.close()
+
+
+def test_lockstep_line_solves_pushed_to_bounds(ucac_mod):
+    """The polar line kernel takes the common Newton step with FP32 limit
+    gradients and hands every other case -- a variable near a bound, a
+    held slack, a shifted system, a trust-region step -- to the full step.
+    Multipliers of the flow and voltage rows drawn at half the penalty's
+    scale push many solves onto line limits and voltage bounds, so both
+    paths run in one sweep; the sweep is compared with the oracle's.  (At
+    twice the penalty's scale the targets sit ~2 p.u. from any feasible
+    flow; the nonconvex line subproblems then have several KKT points and
+    the two solvers, on their different routes, stop at different ones.)"""
+    g = synth.config_instances("c2_118bus_T24x3")[2]
+    dims = _dims(g)
+    h = ucac_mod.Handle([g])
+    h.enqueue(20)
+    st = oracle.unpack_state(h.export(0), *dims)
+    rng = np.random.default_rng(13)
+    for row, rho, sc in (("pij", st["rho_pq"], 0.5), ("qij", st["rho_pq"], 0.5), ("pji", st["rho_pq"], 0.5),
+                         ("qji", st["rho_pq"], 0.5), ("wi", st["rho_va"], 0.05), ("wj", st["rho_va"], 0.05)):
+        st["by_" + row] = st["by_" + row] + rho * sc * rng.uniform(-1.0, 1.0, st["by_" + row].shape)
+    h.import_(0, oracle.pack_state(st, *dims))
+    pre = h.export(0)
+    h.enqueue(1)
+    o = oracle.Oracle(g)
+    o.set_state(pre)
+    o.sweep()
+    out = oracle.unpack_state(h.export(0), *dims)
+    # line limits bind (positive limit multipliers) on a good share of solves
+    assert np.count_nonzero(out["mu2"] > 0) + np.count_nonzero(out["mu3"] > 0) > 100
+    bad = compare_states(h.export(0), o.state_vector(), g, skip=POLAR_SKIP,
+                         mu_eta=ucac_mod.ucac_default_params().eta)
+    assert not bad, bad[:6]
+    h.close()
