@@ -52,6 +52,9 @@ FP64_NOMINAL_TFLOPS = 1.25
 # 16 x 2000-bus workload, from the same ncu capture of sweep 31; None for a
 # form or workload not captured
 LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 376.1e6}
+# FP64 pipe cycles active over the line kernel's active cycles, from the same
+# capture (sm__pipe_fp64_cycles_active, sweep 31)
+LINE_FP64_BUSY = {"polar": 0.675, "w": 0.876}
 # Algorithmic bytes (FP64 reads + writes each kernel must make) per unit of
 # the streaming x-bar and generator kernels, from their data layout (a row
 # keeps w = z + y/rho beside its next x-step target):
@@ -383,6 +386,11 @@ def main():
                 # the FP64 pipe's own rate at the maximum SM clock: 2 FMA lanes per SM per clock
                 "peak_pipe_at_max_clock": 2 * 2 * n_sm * sm_mhz * 1e6 / 1e12,
                 "frac_of_pipe_at_max_clock": (achieved / (4 * n_sm * sm_mhz * 1e6 / 1e12)) if achieved else None,
+                "fp64_pipe_busy": LINE_FP64_BUSY.get(a.line_form),
+                "note": "FLOP are the FP64 instructions the kernel executes; the common Newton step takes the "
+                        "line-limit gradients in FP32 (660.8 FLOP per solve before it, 469.2 after, with 22% less "
+                        "time), and the FP64 pipe is busy 68% of the active cycles beside the per-lane solves' "
+                        "dependency and memory waits",
                 "newton_per_sweep": newton, "al_per_sweep": al, "kernel_ms": kt}
     # streaming kernels: algorithmic bytes per launch / event time / measured HBM copy rate
     hbm = float(peaks.get("hbm_gbs", 6314.0))
