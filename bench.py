@@ -390,7 +390,7 @@ def main():
                 "note": "FLOP are the FP64 instructions the kernel executes; the common Newton step takes the "
                         "line-limit gradients in FP32 (660.8 FLOP per solve before it, 469.2 after, with 22% less "
                         "time), and the FP64 pipe is busy 68% of the active cycles beside the per-lane solves' "
-                        "dependency and memory waits",
+                        "dependency and memory waits" if a.line_form == "polar" else None,
                 "newton_per_sweep": newton, "al_per_sweep": al, "kernel_ms": kt}
     # streaming kernels: algorithmic bytes per launch / event time / measured HBM copy rate
     hbm = float(peaks.get("hbm_gbs", 6314.0))
