@@ -366,6 +366,13 @@ def main():
     kt = h.kernel_times(4)
     newton = sum(h.residuals(k)["newton"] for k in range(len(grids)))
     al = sum(h.residuals(k)["al"] for k in range(len(grids)))
+    # per-solve device counters of the last sweep: histograms over all instances
+    nhist, ahist = None, None
+    for k in range(len(grids)):
+        nw, na = h.line_counts(k)
+        hn, ha = ucac.count_histogram(nw), ucac.count_histogram(na, top=4)
+        nhist = hn if nhist is None else [x + y for x, y in zip(nhist, hn)]
+        ahist = ha if ahist is None else [x + y for x, y in zip(ahist, ha)]
     fp64 = ucac.ucac_probe_fp64(5, stream.cuda_stream)
     torch.cuda.synchronize()
     t_br = kt["k_branch"] * 1e-3
@@ -391,7 +398,10 @@ def main():
                         "line-limit gradients in FP32 (660.8 FLOP per solve before it, 469.2 after, with 22% less "
                         "time), and the FP64 pipe is busy 68% of the active cycles beside the per-lane solves' "
                         "dependency and memory waits" if a.line_form == "polar" else None,
-                "newton_per_sweep": newton, "al_per_sweep": al, "kernel_ms": kt}
+                "newton_per_sweep": newton, "al_per_sweep": al,
+                "solves_by_newton_iterations": {"bins": "0..7, 8 or more", "counts": nhist},
+                "solves_by_multiplier_rounds": {"bins": "0..3, 4 or more", "counts": ahist},
+                "kernel_ms": kt}
     # streaming kernels: algorithmic bytes per launch / event time / measured HBM copy rate
     hbm = float(peaks.get("hbm_gbs", 6314.0))
     streaming = {}

@@ -185,6 +185,18 @@ int ucac_enqueue_sweeps(ucac_handle *h, int32_t n_sweeps);
 int ucac_residuals(const ucac_handle *h, int32_t instance, ucac_report *out);
 
 /*
+ * The device counters of the line subproblems (Eq. acopf; the trust-region
+ * Newton inside the augmented-Lagrangian loop that Sec. IV-A names): for
+ * every line-period of instance `instance`, the Newton iterations (newton)
+ * and multiplier rounds (al) of its solve in the last sweep the instance
+ * ran, [T][n_branch] each, into caller HOST buffers (either may be NULL).
+ * Counts saturate at 65535.  Their sums equal the record's newton and al.
+ * Synchronises.  UCAC_E_ARG for a bad handle or instance, UCAC_E_CUDA if a
+ * copy fails.
+ */
+int ucac_line_counts(const ucac_handle *h, int32_t instance, uint16_t *newton, uint16_t *al);
+
+/*
  * Copies the solution of one instance -- the iterate Algorithm 1 returns,
  * in the variables of Sec. II (generator outputs, Eq. acopf voltages and
  * flows, the commitment of Eq. set:UC) -- into caller host buffers (any may

@@ -153,6 +153,9 @@ struct Dev {
   // (k_prep_ucbar)
   double *uc_hinv;
   long long NGEN;
+  // per line-period, its last solve's Newton iterations [0][NBP] and
+  // multiplier rounds [1][NBP] (the device counters behind the histograms)
+  unsigned short *lcount;
   const int *inc_ptr;            // CSR row pointers over global buses (degree)
   const int *gen_ptr, *gen_idx;  // CSR over global buses; generator index local
   const int *bus_order;                    // [NB] per instance: local buses sorted by (degree, generators)

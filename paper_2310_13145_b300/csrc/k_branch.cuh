@@ -483,6 +483,8 @@ __global__ void __launch_bounds__(BS) k_branch(Dev S) {
           atomicAdd((unsigned long long *)&st[0], (unsigned long long)newton);
           atomicAdd((unsigned long long *)&st[1], (unsigned long long)al);
           if (!done) atomicAdd((unsigned long long *)&st[2], 1ull);
+          S.lcount[bp] = (unsigned short)min(newton, 65535);  // (saturated)
+          S.lcount[NBP + bp] = (unsigned short)min(al, 65535);
           bp = -1;
         } else {
           if (hn > 0.25 * hprev) P.c = fmin(10.0 * P.c, cmax);

@@ -1339,6 +1339,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
             acc_nw += (unsigned long long)newton;
             acc_al += (unsigned long long)al;
             acc_cap += done ? 0ull : 1ull;
+            S.lcount[bp] = (unsigned short)min(newton, 65535);  // (saturated)
+            S.lcount[NBP + bp] = (unsigned short)min(al, 65535);
             bp = -1;
           } else {
             if (hn > 0.25 * hprev) {

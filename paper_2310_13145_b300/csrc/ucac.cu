@@ -657,6 +657,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_stage = A.take<double>((size_t)NSTAGE * max_nbp);
   const size_t o_bus = A.take<double>(4 * NB), o_busnu = A.take<double>(6 * NB);
   const size_t o_uchinv = A.take<double>((size_t)UC_HINV_N * NGEN);
+  const size_t o_lcount = A.take<unsigned short>((size_t)2 * NBP);
   const size_t o_csr = A.take<int>((NB + 1) * 2 + NGEN + NB);
   const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
   const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
@@ -712,6 +713,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.Gs = (const double *)(ar + o_bus); D.Bs = D.Gs + NB; D.ideg = D.Gs + 2 * NB; D.vmid = D.Gs + 3 * NB;
   D.bus_nu = (double *)(ar + o_busnu);
   D.uc_hinv = (double *)(ar + o_uchinv);
+  D.lcount = (unsigned short *)(ar + o_lcount);
   D.NGEN = NGEN;
   const int *csr = (const int *)(ar + o_csr);
   D.inc_ptr = csr; D.gen_ptr = csr + (NB + 1);
@@ -897,6 +899,18 @@ int ucac_residuals(const ucac_handle *hc, int32_t instance, ucac_report *out) {
 namespace {
 void edge_stage(ucac_handle *h, int k, int dir, bool with_x, cudaStream_t s);
 }  // namespace
+
+int ucac_line_counts(const ucac_handle *hc, int32_t instance, uint16_t *newton, uint16_t *al) {
+  ucac_handle *h = const_cast<ucac_handle *>(hc);
+  if (!h || instance < 0 || instance >= h->K) return fail(h, UCAC_E_ARG, "bad arguments");
+  NvtxRange nvtx_("ucac_line_counts");
+  const HInst &I = h->hi[instance];
+  const size_t n = (size_t)I.T * I.nl;
+  CK(cudaStreamSynchronize(h->stream));
+  if (newton && n) CK(cudaMemcpy(newton, h->dev.lcount + I.bpo, n * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+  if (al && n) CK(cudaMemcpy(al, h->dev.lcount + h->NBP + I.bpo, n * sizeof(uint16_t), cudaMemcpyDeviceToHost));
+  return UCAC_OK;
+}
 
 int ucac_solution(const ucac_handle *hc, int32_t k, double *p, double *q, double *w, double *theta, double *pf,
                   uint8_t *u_on) {

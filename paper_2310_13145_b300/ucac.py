@@ -29,7 +29,7 @@ EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_inst
            "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp", "ucac_ucdp_noalloc",
            "ucac_probe_fp64", "ucac_probe_cossin", "ucac_autotune", "ucac_uc_warm_start", "ucac_mlp_param_count", "ucac_mlp_workspace_bytes", "ucac_mlp_forward",
            "ucac_mlp_grad", "ucac_mlp_adam", "ucac_line_features", "ucac_line_samples", "ucac_set_warm_start", "ucac_set_warmstart",
-           "ucac_warm_start_stats",
+           "ucac_warm_start_stats", "ucac_line_counts",
            "ucac_destroy", "ucac_last_error"]
 
 
@@ -88,6 +88,7 @@ def lib():
         L.ucac_enqueue_sweeps.argtypes = [vp, C.c_int32]
         L.ucac_residuals.argtypes = [vp, C.c_int32, C.POINTER(ucac_report)]
         L.ucac_solution.argtypes = [vp, C.c_int32, _dp, _dp, _dp, _dp, _dp, C.POINTER(C.c_uint8)]
+        L.ucac_line_counts.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint16), C.POINTER(C.c_uint16)]
         L.ucac_state_size.argtypes = [vp, C.c_int32]
         L.ucac_state_size.restype = C.c_size_t
         L.ucac_state_export.argtypes = [vp, C.c_int32, _dp, C.c_size_t]
@@ -204,6 +205,23 @@ def ucac_solution(h, instance: int, T: int, ng: int, nb: int, nl: int) -> dict:
                                th.ctypes.data_as(_dp), pf.ctypes.data_as(_dp),
                                u.ctypes.data_as(C.POINTER(C.c_uint8))), h)
     return {"p": p, "q": q, "w": w, "theta": th, "pf": pf, "u_on": u}
+
+
+def ucac_line_counts(h, instance: int, T: int, nl: int) -> tuple:
+    """Newton iterations and multiplier rounds of each line-period's solve in
+    the last sweep the instance ran, two [T][n_branch] uint16 arrays."""
+    nw = np.zeros((T, nl), np.uint16)
+    na = np.zeros((T, nl), np.uint16)
+    _check(lib().ucac_line_counts(h, int(instance), nw.ctypes.data_as(C.POINTER(C.c_uint16)),
+                                  na.ctypes.data_as(C.POINTER(C.c_uint16))), h)
+    return nw, na
+
+
+def count_histogram(counts: np.ndarray, top: int = 8) -> list:
+    """Histogram of per-solve counts: bins 0 .. top - 1 and a last bin for
+    top or more."""
+    c = np.minimum(np.asarray(counts).ravel().astype(np.int64), top)
+    return np.bincount(c, minlength=top + 1).tolist()
 
 
 def ucac_state_size(h, instance: int = 0) -> int:
@@ -389,6 +407,10 @@ class Handle:
 
     def residuals(self, k=0):
         return ucac_residuals(self.h, k)
+
+    def line_counts(self, k=0):
+        T = self.horizons[k] if self.horizons is not None else self.grids[k].T
+        return ucac_line_counts(self.h, k, T, self.grids[k].n_branch)
 
     def export(self, k=0):
         return ucac_state_export(self.h, k)

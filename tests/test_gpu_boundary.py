@@ -52,6 +52,14 @@ def test_boundary_entry_points_through_ctypes(ucac_mod):
     assert L.ucac_solution(h, 0, _ptr(p), _ptr(q), _ptr(w), _ptr(th), _ptr(pf), _ptr(uon, C.POINTER(C.c_uint8))) == 0
     assert np.all(w > 0.5) and np.all(uon <= 1) and np.all(np.isfinite(pf))
     assert L.ucac_solution(h, 0, None, None, None, None, None, None) == 0
+    # ucac_line_counts: per line-period Newton iterations and multiplier
+    # rounds of the last sweep, summing to the record's counts
+    nw, na = np.zeros((T, nl), np.uint16), np.zeros((T, nl), np.uint16)
+    u16 = C.POINTER(C.c_uint16)
+    assert L.ucac_line_counts(h, 0, _ptr(nw, u16), _ptr(na, u16)) == 0
+    assert int(nw.sum()) == rep.newton and int(na.sum()) == rep.al and na.min() >= 1
+    assert L.ucac_line_counts(h, 0, None, None) == 0
+    assert L.ucac_line_counts(h, 5, None, None) == u.UCAC_E_ARG
     # ucac_state_export / ucac_state_import: resume instance 0 of the batch
     # from the single handle's iterate
     n = L.ucac_state_size(h, 0)

@@ -448,3 +448,24 @@ def test_lockstep_line_solves_pushed_to_bounds(ucac_mod):
                          mu_eta=ucac_mod.ucac_default_params().eta)
     assert not bad, bad[:6]
     h.close()
+
+
+def test_line_counts_sum_to_the_record(ucac_mod, line_form):
+    """The per-solve device counters behind the Newton-iteration histograms:
+    for every instance of a batch and both line forms, the Newton iterations
+    and multiplier rounds stored per line-period sum to the instance's
+    record of the same sweep, and every solve ran at least one multiplier
+    round."""
+    grids = synth.config_instances("c2_118bus_T24x3")
+    h = ucac_mod.Handle(grids, params=ucac_mod.ucac_default_params(line_form=line_form))
+    for sweeps in (1, 14):
+        h.enqueue(sweeps)
+        for k, g in enumerate(grids):
+            nw, na = h.line_counts(k)
+            r = h.residuals(k)
+            assert nw.shape == (g.T, g.n_branch)
+            assert int(nw.sum()) == r["newton"] and int(na.sum()) == r["al"], (k, sweeps)
+            assert na.min() >= 1
+            hist = ucac_mod.count_histogram(nw)
+            assert sum(hist) == g.T * g.n_branch
+    h.close()
