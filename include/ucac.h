@@ -197,6 +197,19 @@ int ucac_residuals(const ucac_handle *h, int32_t instance, ucac_report *out);
 int ucac_line_counts(const ucac_handle *h, int32_t instance, uint16_t *newton, uint16_t *al);
 
 /*
+ * Index-checked builds (compiled with UCAC_CHECK=1, libucac_check.so; no
+ * counterpart in the paper): the sweep kernels test every index they take
+ * from a table against the extent of the buffer it addresses; a failed test
+ * records its site on the device and skips the access, and the next host
+ * check of ucac_iterate returns UCAC_E_CUDA with "index check failed at
+ * site N" (the record stays: every later call fails the same way).
+ * ucac_check_inject records site (> 0) as a failed check from a device
+ * thread, as a kernel's failed test would, to exercise that path; it
+ * synchronises.  In a default build it returns UCAC_E_ARG.
+ */
+int ucac_check_inject(ucac_handle *h, int32_t site);
+
+/*
  * Copies the solution of one instance -- the iterate Algorithm 1 returns,
  * in the variables of Sec. II (generator outputs, Eq. acopf voltages and
  * flows, the commitment of Eq. set:UC) -- into caller host buffers (any may

@@ -156,6 +156,7 @@ struct Dev {
   // per line-period, its last solve's Newton iterations [0][NBP] and
   // multiplier rounds [1][NBP] (the device counters behind the histograms)
   unsigned short *lcount;
+  int *chk;  // first failed index check (UCAC_CHECK builds; 0 = none)
   const int *inc_ptr;            // CSR row pointers over global buses (degree)
   const int *gen_ptr, *gen_idx;  // CSR over global buses; generator index local
   const int *bus_order;                    // [NB] per instance: local buses sorted by (degree, generators)
@@ -231,6 +232,29 @@ __device__ __forceinline__ double f2d_exact(float x) {
   return __hiloint2double((int)(e != 0u ? hi : sg), (int)(e != 0u ? lo : 0u));
 }
 
+
+// Index checks.  A UCAC_CHECK=1 build tests every index that the sweep
+// kernels take from a table (line-end slots, generator and bus orders, work
+// lists, instance lookups) against the extent of the buffer it addresses,
+// before the access it guards.  A failed test records its site in S.chk
+// (the first one wins) and the guarded access is skipped -- no trap, no
+// early exit past a warp-collective -- so the host reads the site after the
+// sweep (ucac_iterate fails with UCAC_E_CUDA naming it).  In the default
+// build chk_ is the constant true and the tests compile away.
+#ifndef UCAC_CHECK
+#define UCAC_CHECK 0
+#endif
+__device__ __forceinline__ bool chk_(const Dev &S, bool ok, int site) {
+#if UCAC_CHECK
+  if (!ok) atomicCAS(S.chk, 0, site);
+  return ok;
+#else
+  (void)S;
+  (void)ok;
+  (void)site;
+  return true;
+#endif
+}
 
 // Algorithm 1 stops an instance once it has converged: after the finish
 // kernel sets its done flag, no kernel of a later sweep touches the

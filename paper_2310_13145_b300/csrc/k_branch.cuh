@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(BS) k_branch(Dev S) {
         } else {
           bp = item;
           k = find_instance(S, bp);
+          if (!chk_(S, k >= 0 && k < S.K && bp >= (long long)S.inst[k].bpo, 6)) k = 0;
         }
         if (active && inst_done(S, k)) {
           bp = -1;  // a converged instance's line: skipped (the lane fetches again)
@@ -422,6 +423,7 @@ __global__ void __launch_bounds__(BS) k_branch(Dev S) {
             K.hi[i] = S.BC[(BC_HI + i) * NL + lg];
           }
           line_ends(S, I, t, lg, lef, let);
+          if (!chk_(S, lef >= 0 && lef < NEP && let >= 0 && let < NEP, 5)) lef = let = 0;
 #pragma unroll
           for (int r = 0; r < 8; ++r) P.tg[r] = S.ET[erow_u(r) * NEP + (erow_end(r) ? let : lef)];
           P.rpq = I.rpq;

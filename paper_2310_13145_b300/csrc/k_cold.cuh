@@ -79,6 +79,7 @@ __global__ void __launch_bounds__(BS) k_cold_branch(Dev S) {
   S.B[FB_C * NBP + bp] = __dmul_rn(S.prm.c_init_rel, fmax(I.rpq, I.rva));
   long long ef, et;
   line_ends(S, I, t, lg, ef, et);
+  if (!chk_(S, ef >= 0 && ef < S.NEP && et >= 0 && et < S.NEP, 51)) ef = et = 0;
   const double a[4] = {a0, a1, a2, a3};
 #pragma unroll
   for (int r = 0; r < 4; ++r) S.EFB[erow_u(r) * NEP + (erow_end(r) ? et : ef)] = a[r];

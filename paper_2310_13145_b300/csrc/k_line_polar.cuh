@@ -1072,7 +1072,10 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           const long long left = (long long)S.pctl[1 + par] - (long long)base;
           const int got = left <= 0 ? 0 : (left < 32 ? (int)left : 32);
           if (left <= 32) phase = 1;
-          if (lane < got) it = S.plist[(long long)par * NBP + (long long)base + lane];
+          if (lane < got && chk_(S, (long long)base + lane < NBP, 1)) {
+            it = S.plist[(long long)par * NBP + (long long)base + lane];
+            if (!chk_(S, it >= 0 && it < NBP, 2)) it = -1;
+          }
         } else {
           if (lane == 0) {
             const unsigned long long cur = *(volatile unsigned long long *)S.bp_counter;
@@ -1097,7 +1100,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         // that remain are packed into the ring
         if (it >= 0) {
           ki = find_instance(S, it);
-          if (inst_done(S, ki)) it = -1;
+          if (!chk_(S, ki >= 0 && ki < S.K && it >= (long long)S.inst[ki].bpo, 3)) it = -1;
+          else if (inst_done(S, ki)) it = -1;
         }
         const unsigned vm = __ballot_sync(FULL, it >= 0);
         if (it >= 0) {
@@ -1151,6 +1155,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           K.lo1 = S.BC[(BC_VB + 2) * NL + lg];
           K.hi1 = S.BC[(BC_VB + 3) * NL + lg];
           line_ends(S, I, t, lg, lef, let);
+          if (!chk_(S, lef >= 0 && lef < NEP && let >= 0 && let < NEP, 4)) lef = let = 0;
 #pragma unroll
           for (int r8 = 0; r8 < 8; ++r8) P.tg[r8] = S.ET[erow_u(r8) * NEP + (erow_end(r8) ? let : lef)];
           P.rpq = I.rpq;

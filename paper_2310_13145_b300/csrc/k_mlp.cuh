@@ -72,6 +72,7 @@ __device__ __forceinline__ bool line_features(const Dev &S, const Inst &I, long 
                          Y[4] * wj + Y[6] * wR - Y[7] * wI, -Y[5] * wj - Y[7] * wR - Y[6] * wI};
     long long ef, et;
     line_ends(S, I, t, lg, ef, et);
+    if (!chk_(S, ef >= 0 && ef < S.NEP && et >= 0 && et < S.NEP, 30)) ef = et = 0;
     double tg[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) tg[r] = S.ET[erow_u(r) * NEP + (erow_end(r) ? et : ef)];
@@ -122,6 +123,7 @@ __device__ __forceinline__ bool line_features(const Dev &S, const Inst &I, long 
                        Y[4] * wj + Y[6] * wR - Y[7] * wI, -Y[5] * wj - Y[7] * wR - Y[6] * wI};
   long long ef, et;
   line_ends(S, I, t, lg, ef, et);
+  if (!chk_(S, ef >= 0 && ef < S.NEP && et >= 0 && et < S.NEP, 31)) ef = et = 0;
   double tg[8];
 #pragma unroll
   for (int r = 0; r < 8; ++r) tg[r] = S.ET[erow_u(r) * NEP + (erow_end(r) ? et : ef)];

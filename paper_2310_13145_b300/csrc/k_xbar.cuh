@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
   const int lane = threadIdx.x & 31, pos = blk * 32 + lane;
   double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (pos < I.nb) {
-    const int i = S.bus_order[I.uo + pos], ig = I.uo + i;
+    const int i0 = S.bus_order[I.uo + pos];
+    const int i = chk_(S, i0 >= 0 && i0 < I.nb, 10) ? i0 : 0, ig = I.uo + i;
     const long long up = (long long)I.upo + (long long)t * I.nb + i;
     const long long NGP = S.NGP, NEP = S.NEP, NUP = S.NUP;
     const long long e0 = I.eo + (long long)t * I.spp + S.blk_off[I.bo + blk] + lane;  // slot 0 of this bus
@@ -182,12 +183,17 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const Fam Fpq = fam_pq(I), Fva = fam_va(I);
     const double irpq = Fpq.irho;
     const bool last = (t == I.T - 1);
-    const int g0 = S.gen_ptr[ig], g1 = S.gen_ptr[ig + 1], deg = S.inc_ptr[ig + 1] - S.inc_ptr[ig];
+    const int d0 = S.inc_ptr[ig + 1] - S.inc_ptr[ig];
+    const int deg = chk_(S, e0 >= 0 && (d0 == 0 || e0 + 32LL * (d0 - 1) < NEP), 11) ? d0 : 0;
+    const int g0 = S.gen_ptr[ig], g1r = S.gen_ptr[ig + 1];
+    const int g1 = chk_(S, g0 >= 0 && g1r >= g0 && g1r <= S.NGEN, 12) ? g1r : g0;
     // pass 1: targets m_v and the right-hand side of the 2x2 multiplier
     // system (its matrix is constant between penalty changes: k_prep_bus)
     double r0 = 0.0, r1 = 0.0, mw = 0.0, mth = 0.0;
     for (int e = g0; e < g1; ++e) {
-      const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
+      const int gl = S.gen_idx[e];
+      if (!chk_(S, gl >= 0 && gl < I.ng, 13)) continue;
+      const long long gp = (long long)I.gpo + (long long)t * I.ng + gl;
       double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
       if (!last) {
         const long long gn = gp + I.ng;
@@ -226,7 +232,9 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     // updates below hold no multiplier clip
     if (R.pend) {
       for (int e = g0; e < g1; ++e) {
-        const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
+        const int gl = S.gen_idx[e];
+        if (!chk_(S, gl >= 0 && gl < I.ng, 13)) continue;
+        const long long gp = (long long)I.gpo + (long long)t * I.ng + gl;
         const long long r0i = GR_GP * NGP + gp, r1i = GR_TC * NGP + gp + I.ng, r2i = GR_GQ * NGP + gp;
         S.GL[r0i] = outer_lambda(S.GL[r0i], S.GZ[r0i], R);
         if (!last) S.GL[r1i] = outer_lambda(S.GL[r1i], S.GZ[r1i], R);
@@ -241,7 +249,9 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     }
     // pass 2: new x-bar values, then the rows they own
     for (int e = g0; e < g1; ++e) {
-      const long long gp = (long long)I.gpo + (long long)t * I.ng + S.gen_idx[e];
+      const int gl = S.gen_idx[e];
+      if (!chk_(S, gl >= 0 && gl < I.ng, 13)) continue;
+      const long long gp = (long long)I.gpo + (long long)t * I.ng + gl;
       const long long gn = gp + I.ng;
       double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
       double iW = irpq;
@@ -568,14 +578,16 @@ __global__ void __launch_bounds__(BS) k_finish(Dev S) {
   if (inst_done(S, k)) return;  // converged earlier: the record stays
   const Inst I = S.inst[k];
   double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int bb = I.gran_up0 + threadIdx.x; bb < I.gran_up1; bb += BS) {
+  const int up1 = chk_(S, I.gran_up0 >= 0 && I.gran_up1 <= S.g_up.n, 40) ? I.gran_up1 : I.gran_up0;
+  const int gp1 = chk_(S, I.gran_gp0 >= 0 && I.gran_gp1 <= S.g_gp.n, 41) ? I.gran_gp1 : I.gran_gp0;
+  for (int bb = I.gran_up0 + threadIdx.x; bb < up1; bb += BS) {
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
       const double v = S.part_up[(long long)bb * NQ + j];
       q[j] = (j == Q_INF) ? fmax(q[j], v) : q[j] + v;
     }
   }
-  for (int bb = I.gran_gp0 + threadIdx.x; bb < I.gran_gp1; bb += BS) {
+  for (int bb = I.gran_gp0 + threadIdx.x; bb < gp1; bb += BS) {
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
       const double v = S.part_gp[(long long)bb * NQ + j];
@@ -744,6 +756,7 @@ __global__ void __launch_bounds__(BS) k_prep_branch(Dev S, int changed_only) {
   const long long ut = (long long)I.upo + (long long)t * I.nb + S.bt[lg];
   long long ef, et;
   line_ends(S, I, t, lg, ef, et);
+  if (!chk_(S, ef >= 0 && ef < S.NEP && et >= 0 && et < S.NEP, 50)) ef = et = 0;
   double bv[8];
 #pragma unroll
   for (int r = 0; r < 4; ++r) bv[r] = S.EFB[erow_u(r) * NEP + (erow_end(r) ? et : ef)];
@@ -885,6 +898,7 @@ __global__ void __launch_bounds__(BS) k_solution_flows(Dev S, int k, double *pf)
   const int t = (int)(loc / I.nl), l = (int)(loc - (long long)t * I.nl);
   long long ef, et;
   line_ends(S, I, t, (long long)I.lo + l, ef, et);
+  if (!chk_(S, ef >= 0 && ef < S.NEP && et >= 0 && et < S.NEP, 52)) ef = et = 0;
 #pragma unroll
   for (int r = 0; r < 4; ++r) pf[loc * 4 + r] = S.EA[erow_u(r) * S.NEP + (erow_end(r) ? et : ef)];
 }
@@ -902,6 +916,7 @@ __global__ void __launch_bounds__(BS) k_edge_canon(Dev S, int k, int dir, double
   const int t = (int)(loc / I.nl), l = (int)(loc - (long long)t * I.nl);
   long long ef, et;
   line_ends(S, I, t, (long long)I.lo + l, ef, et);
+  if (!chk_(S, ef >= 0 && ef < S.NEP && et >= 0 && et < S.NEP, 53)) ef = et = 0;
   for (int r = 0; r < nrows; ++r) {
     const long long e = erow_u(r) * S.NEP + (erow_end(r) ? et : ef);
     if (dir == 0)

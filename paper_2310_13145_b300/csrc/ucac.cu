@@ -658,6 +658,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   const size_t o_bus = A.take<double>(4 * NB), o_busnu = A.take<double>(6 * NB);
   const size_t o_uchinv = A.take<double>((size_t)UC_HINV_N * NGEN);
   const size_t o_lcount = A.take<unsigned short>((size_t)2 * NBP);
+  const size_t o_chk = A.take<int>(1);
   const size_t o_csr = A.take<int>((NB + 1) * 2 + NGEN + NB);
   const size_t o_pq = A.take<double>(2 * NUP), o_U = A.take<double>((size_t)NUF * NUP);
   const size_t o_ctrl = A.take<double>((size_t)NCTRL * n), o_res = A.take<double>((size_t)NRES * n);
@@ -714,6 +715,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
   D.bus_nu = (double *)(ar + o_busnu);
   D.uc_hinv = (double *)(ar + o_uchinv);
   D.lcount = (unsigned short *)(ar + o_lcount);
+  D.chk = (int *)(ar + o_chk);
   D.NGEN = NGEN;
   const int *csr = (const int *)(ar + o_csr);
   D.inc_ptr = csr; D.gen_ptr = csr + (NB + 1);
@@ -850,9 +852,12 @@ int ucac_iterate(ucac_handle *h, int32_t n_sweeps) {
     const int m = std::min(h->check_every, n_sweeps - done);
     for (int i = 0; i < m; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
     done += m;
+    int chk = 0;
     CK(cudaMemcpyAsync(c.data(), h->dev.ctrl, c.size() * 8, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(r.data(), h->dev.res, r.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&chk, h->dev.chk, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    if (chk != 0) return fail(h, UCAC_E_CUDA, "index check failed at site " + std::to_string(chk));
     bool all = true;
     for (int k = 0; k < h->K; ++k) {
       const int st = (int)r[(size_t)k * NRES + R_STATUS];
@@ -899,6 +904,25 @@ int ucac_residuals(const ucac_handle *hc, int32_t instance, ucac_report *out) {
 namespace {
 void edge_stage(ucac_handle *h, int k, int dir, bool with_x, cudaStream_t s);
 }  // namespace
+
+namespace {
+// records `site` as a failed index check, as a kernel's failed test would
+__global__ void k_check_inject(Dev S, int site) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) chk_(S, false, site);
+}
+}  // namespace
+
+int ucac_check_inject(ucac_handle *h, int32_t site) {
+  if (!h || site <= 0) return fail(h, UCAC_E_ARG, "bad arguments");
+#if UCAC_CHECK
+  k_check_inject<<<1, 32, 0, h->stream>>>(h->dev, site);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  return UCAC_OK;
+#else
+  return fail(h, UCAC_E_ARG, "not an index-checked build (UCAC_CHECK=1)");
+#endif
+}
 
 int ucac_line_counts(const ucac_handle *hc, int32_t instance, uint16_t *newton, uint16_t *al) {
   ucac_handle *h = const_cast<ucac_handle *>(hc);

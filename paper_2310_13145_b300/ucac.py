@@ -29,7 +29,7 @@ EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_inst
            "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp", "ucac_ucdp_noalloc",
            "ucac_probe_fp64", "ucac_probe_cossin", "ucac_autotune", "ucac_uc_warm_start", "ucac_mlp_param_count", "ucac_mlp_workspace_bytes", "ucac_mlp_forward",
            "ucac_mlp_grad", "ucac_mlp_adam", "ucac_line_features", "ucac_line_samples", "ucac_set_warm_start", "ucac_set_warmstart",
-           "ucac_warm_start_stats", "ucac_line_counts",
+           "ucac_warm_start_stats", "ucac_line_counts", "ucac_check_inject",
            "ucac_destroy", "ucac_last_error"]
 
 
@@ -89,6 +89,7 @@ def lib():
         L.ucac_residuals.argtypes = [vp, C.c_int32, C.POINTER(ucac_report)]
         L.ucac_solution.argtypes = [vp, C.c_int32, _dp, _dp, _dp, _dp, _dp, C.POINTER(C.c_uint8)]
         L.ucac_line_counts.argtypes = [vp, C.c_int32, C.POINTER(C.c_uint16), C.POINTER(C.c_uint16)]
+        L.ucac_check_inject.argtypes = [vp, C.c_int32]
         L.ucac_state_size.argtypes = [vp, C.c_int32]
         L.ucac_state_size.restype = C.c_size_t
         L.ucac_state_export.argtypes = [vp, C.c_int32, _dp, C.c_size_t]
