@@ -392,20 +392,35 @@ __device__ __forceinline__ double pol_f(const PolP &P, const PolLast &L) {
   return f;
 }
 
+// a pivot's square root L = sqrt(s) and its reciprocal 1/L; in FP32 both
+// from the hardware reciprocal square root (2 ulp: far below the FP32
+// Newton system's own error), in FP64 exact
+__device__ __forceinline__ void piv_root(float s, float &L, float &iL) {
+  iL = rsqrtf(s);
+  L = s * iL;
+}
+__device__ __forceinline__ void piv_root(double s, double &L, double &iL) {
+  L = sqrt(s);
+  iL = 1.0 / L;
+}
+
 // masked 3x3 Cholesky solve (packed symmetric A), T = float or double
 template <typename T>
 __device__ __forceinline__ bool chol3p(const T (&A)[6], T (&b)[3]) {
   const T s0 = A[0];
   if (!(s0 > T(0))) return false;
-  const T L00 = sqrt(s0), i0 = T(1) / L00;
+  T L00, i0;
+  piv_root(s0, L00, i0);
   const T L10 = A[1] * i0, L20 = A[2] * i0;
   const T s1 = A[3] - L10 * L10;
   if (!(s1 > T(0))) return false;
-  const T L11 = sqrt(s1), i1 = T(1) / L11;
+  T L11, i1;
+  piv_root(s1, L11, i1);
   const T L21 = (A[4] - L20 * L10) * i1;
   const T s2 = A[5] - L20 * L20 - L21 * L21;
   if (!(s2 > T(0))) return false;
-  const T L22 = sqrt(s2), i2 = T(1) / L22;
+  T L22, i2;
+  piv_root(s2, L22, i2);
   const T y0 = b[0] * i0, y1 = (b[1] - L10 * y0) * i1, y2 = (b[2] - L20 * y0 - L21 * y1) * i2;
   b[2] = y2 * i2;
   b[1] = (y1 - L21 * b[2]) * i1;
