@@ -415,13 +415,27 @@ int ucac_warm_start_stats(const ucac_handle *h, int32_t instance, int64_t *taken
 int ucac_probe_fp64(int32_t reps, void *cuda_stream, double *flops);
 
 /*
- * Evaluates the polar line kernel's cos/sin (a table of cos(k/256),
- * sin(k/256) rotated by the Taylor series of the remainder) on the device for n angles
- * |d[i]| <= pi given in HOST memory; c[i], s[i] (HOST) receive the results.
- * For testing the kernel's trigonometry against a reference.  Synchronises.
- * UCAC_E_ARG for n < 0 or a NULL buffer with n > 0.
+ * Evaluates the polar line kernel's cos/sin (double-word arithmetic: a table
+ * of cos(k/256), sin(k/256) rotated by the Taylor series of the remainder) on
+ * the device for n angles |d[i]| <= pi given in HOST memory (each truncated to
+ * a double-word as the kernel does); c[i], s[i] (HOST) receive the results
+ * widened to FP64.  For testing the kernel's trigonometry against a
+ * reference.  Synchronises.  UCAC_E_ARG for n < 0 or a NULL buffer with n > 0.
  */
 int ucac_probe_cossin(int32_t n, const double *d, double *c, double *s);
+
+/*
+ * Applies one double-word operation of the bus kernel (the FP32-pair
+ * arithmetic that stands in for FP64 in its row updates) on the device to n
+ * operand triples x[i], y[i], z[i] given in HOST memory, each first truncated
+ * to a double-word: op 0 the conversion itself, 1 x + y, 2 x - y,
+ * 3 x + (float)y, 4 x * y, 5 x * (float)y, 6 x^2, 7 x * y + z.  out (HOST,
+ * 4 n doubles) receives per operand the result's high and low parts (op 0:
+ * also their FP64 sum).  For testing the device arithmetic bit for bit
+ * against the same code built for the host.  Synchronises.  UCAC_E_ARG for
+ * an unknown op, n < 0 or a NULL buffer with n > 0.
+ */
+int ucac_probe_dw(int32_t op, int32_t n, const double *x, const double *y, const double *z, double *out);
 
 /* Destroys the handle and frees its device memory (NULL is ignored). */
 void ucac_destroy(ucac_handle *h);

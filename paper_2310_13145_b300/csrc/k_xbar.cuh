@@ -19,19 +19,15 @@
 // finish kernel is applied to each row right before its z-update.
 #pragma once
 #include "common.cuh"
+#include "dword.cuh"
 
-// resident blocks per SM requested for the bus kernel (register cap), and the
-// unroll factor of its gather loop (memory-level parallelism)
+// resident blocks of 128 threads per SM requested for the bus kernel (its
+// register cap: 5 gives 96 registers, the fastest of 5, 6 and 8 measured)
 #ifndef UCAC_BUS_MINB
-#define UCAC_BUS_MINB 6
-#endif
-#ifndef UCAC_BUS_UNROLL
-#define UCAC_BUS_UNROLL 4
+#define UCAC_BUS_MINB 5
 #endif
 
 namespace ucac {
-
-constexpr int kBusUnroll = UCAC_BUS_UNROLL;
 
 struct RowCtx {
   double beta_cur, lam_max;
@@ -158,6 +154,68 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
 }
 
 // ------------------------------------------------------------ bus (R8) ----
+// The bus kernel's row algebra runs in double-word arithmetic on the FP32
+// pipe (dword.cuh).  B300's FP64 unit takes 16 cycles per warp instruction,
+// and in FP64 each coupling row cost ~17 such instructions, which held the
+// kernel at a quarter of the HBM bandwidth.  The loads enter as double-words
+// truncated on the integer units; the row's z and y are rounded once to FP64
+// for the state, and its w = z + y/rho and next x-step target b - w are then
+// formed from those FP64 values by the explicitly rounded FP64 operations of
+// the target preparation (row_w, row_target_w), so that a run resumed from an
+// exported state reproduces them bit for bit.  Everything else (the x-bar
+// step's targets and sums, the 2x2 multiplier solve, the new x-bar values,
+// z, y and the residual sums) is accurate to ~2^-46 relative per operation.
+__device__ __forceinline__ dw W_(double x) { return dw_from_d(x); }
+
+struct FamW {
+  dw rho, nbr;
+  double irho;
+};
+__device__ __forceinline__ FamW fam_w(const Fam &F) { return FamW{W_(F.rho), W_(F.nbr), F.irho}; }
+
+// residual partials of one bus thread: sums of squares of the primal
+// residual, of the x-bar change and of z, and the largest |c| (as a
+// magnitude ih + il)
+struct QAcc {
+  dw sp, sd, sz;
+  float ih, il;
+};
+__device__ __forceinline__ void qacc_inf(QAcc &Q, dw c) {
+  const float ah = fabsf(c.h), al = c.h < 0.0f ? -c.l : c.l;
+  if (ah > Q.ih || (ah == Q.ih && al > Q.il)) {
+    Q.ih = ah;
+    Q.il = al;
+  }
+}
+
+// the row update from its loaded inputs a, y, lambda and the new x-bar value
+// b (double-word; bd its stored FP64 value), stored: z, y, w and the next
+// target (R9, R10: c = a - b; z = -(lambda + y + rho c)/(beta + rho);
+// y += rho (c + z)); SD: accumulate (b - b_old)^2 here
+__device__ __forceinline__ void row_dw(double *Y, double *Z, double *Tg, double *Wr, long long idx, dw a, dw y,
+                                       dw lam, dw b, double bd, dw bold, const FamW &F, QAcc &Q, bool sd) {
+  const dw c = dw_sub(a, b);
+  const dw z = dw_mul(dw_fma(F.rho, c, dw_add(lam, y)), F.nbr);
+  const dw cz = dw_add(c, z);
+  const dw yn = dw_fma(F.rho, cz, y);
+  Q.sp = dw_fma(cz, cz, Q.sp);
+  // (b - b_old = 0 leaves Q.sd unchanged: rows whose square the caller adds
+  // once pass their own b as b_old)
+  const dw db = sd ? dw_sub(b, bold) : dw_make(0.0f);
+  Q.sd = dw_fma(db, db, Q.sd);
+  Q.sz = dw_fma(z, z, Q.sz);
+  qacc_inf(Q, c);
+  const double zd = dw_to_d(z), yd = dw_to_d(yn);
+  const double w = row_w(zd, yd, F.irho);
+  Z[idx] = zd;
+  Y[idx] = yd;
+  Wr[idx] = w;
+  Tg[idx] = row_target_w(bd, w);
+}
+
+// x-bar-step target a + w of a row, from its FP64 x value and w
+__device__ __forceinline__ dw row_mtarget_dw(double a, double w) { return dw_add(W_(a), W_(w)); }
+
 // One warp per (period, block of 32 buses in the instance's degree order):
 // the lanes' j-th incident line ends are adjacent slots, so every load and
 // store of a line-end row is one coalesced 256-byte access; the lanes of a
@@ -172,7 +230,7 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
   const int tb = S.g_up.first[gr];  // t * nblk + block
   const int t = tb / I.nblk, blk = tb - t * I.nblk;
   const int lane = threadIdx.x & 31, pos = blk * 32 + lane;
-  double q[NQ] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  QAcc Q{dw_make(0.0f), dw_make(0.0f), dw_make(0.0f), 0.0f, 0.0f};
   if (pos < I.nb) {
     const int i0 = S.bus_order[I.uo + pos];
     const int i = chk_(S, i0 >= 0 && i0 < I.nb, 10) ? i0 : 0, ig = I.uo + i;
@@ -180,8 +238,8 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const long long NGP = S.NGP, NEP = S.NEP, NUP = S.NUP;
     const long long e0 = I.eo + (long long)t * I.spp + S.blk_off[I.bo + blk] + lane;  // slot 0 of this bus
     const RowCtx R = row_ctx(S, k);
-    const Fam Fpq = fam_pq(I), Fva = fam_va(I);
-    const double irpq = Fpq.irho;
+    const FamW Fpq = fam_w(fam_pq(I)), Fva = fam_w(fam_va(I));
+    const dw irpq = W_(I.irpq);
     const bool last = (t == I.T - 1);
     const int d0 = S.inc_ptr[ig + 1] - S.inc_ptr[ig];
     const int deg = chk_(S, e0 >= 0 && (d0 == 0 || e0 + 32LL * (d0 - 1) < NEP), 11) ? d0 : 0;
@@ -189,44 +247,46 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const int g1 = chk_(S, g0 >= 0 && g1r >= g0 && g1r <= S.NGEN, 12) ? g1r : g0;
     // pass 1: targets m_v and the right-hand side of the 2x2 multiplier
     // system (its matrix is constant between penalty changes: k_prep_bus)
-    double r0 = 0.0, r1 = 0.0, mw = 0.0, mth = 0.0;
+    dw r0 = dw_make(0.0f), r1 = dw_make(0.0f), mw = dw_make(0.0f), mth = dw_make(0.0f);
     for (int e = g0; e < g1; ++e) {
       const int gl = S.gen_idx[e];
       if (!chk_(S, gl >= 0 && gl < I.ng, 13)) continue;
       const long long gp = (long long)I.gpo + (long long)t * I.ng + gl;
-      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
+      dw m = row_mtarget_dw(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
       if (!last) {
         const long long gn = gp + I.ng;
-        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])));
+        m = dw_pow2(dw_add(m, row_mtarget_dw(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])), 0.5f);
       }
-      r0 = add_(r0, m);
-      r1 = add_(r1, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
+      r0 = dw_add(r0, m);
+      r1 = dw_add(r1, row_mtarget_dw(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
     }
-    // (the p, q x-bar-step targets are parked in the target slots for pass
-    // 2, which overwrites them with the next x-step targets)
-#pragma unroll kBusUnroll
+    // (the p, q x-bar-step targets are parked, as double-words, in the
+    // target slots for pass 2, which overwrites them with the next x-step
+    // targets)
+    float2 *park = reinterpret_cast<float2 *>(S.ET);
+#pragma unroll 1
     for (int j = 0; j < deg; ++j) {
       const long long e = e0 + 32LL * j;
-      const double mp = row_mtarget(S.EA[e], S.EW[e]);
-      const double mq = row_mtarget(S.EA[NEP + e], S.EW[NEP + e]);
-      S.ET[e] = mp;
-      S.ET[NEP + e] = mq;
-      r0 = sub_(r0, mp);
-      r1 = sub_(r1, mq);
-      mw = add_(mw, row_mtarget(S.EA[2 * NEP + e], S.EW[2 * NEP + e]));
-      mth = add_(mth, row_mtarget(S.EA[3 * NEP + e], S.EW[3 * NEP + e]));
+      const dw mp = row_mtarget_dw(S.EA[e], S.EW[e]);
+      const dw mq = row_mtarget_dw(S.EA[NEP + e], S.EW[NEP + e]);
+      park[e] = make_float2(mp.h, mp.l);
+      park[NEP + e] = make_float2(mq.h, mq.l);
+      r0 = dw_sub(r0, mp);
+      r1 = dw_sub(r1, mq);
+      mw = dw_add(mw, row_mtarget_dw(S.EA[2 * NEP + e], S.EW[2 * NEP + e]));
+      mth = dw_add(mth, row_mtarget_dw(S.EA[3 * NEP + e], S.EW[3 * NEP + e]));
     }
-    const double fdeg = (double)deg;
-    const double ideg = S.ideg[ig];
-    mw = mul_(mw, ideg);
-    mth = mul_(mth, ideg);
-    const double iWw = mul_(Fva.irho, ideg), aPw = -S.Gs[ig], aQw = S.Bs[ig];
-    r0 = sub_(fma_(aPw, mw, r0), S.Pd[up]);
-    r1 = sub_(fma_(aQw, mw, r1), S.Qd[up]);
+    const float fdeg = (float)deg;
+    const dw ideg = W_(S.ideg[ig]);
+    mw = dw_mul(mw, ideg);
+    mth = dw_mul(mth, ideg);
+    const dw iWw = dw_mul(W_(Fva.irho), ideg), aPw = W_(-S.Gs[ig]), aQw = W_(S.Bs[ig]);
+    r0 = dw_sub(dw_fma(aPw, mw, r0), W_(S.Pd[up]));
+    r1 = dw_sub(dw_fma(aQw, mw, r1), W_(S.Qd[up]));
     const double *cf = S.bus_nu + (last ? 3 * S.NB : 0);
-    const double c0 = cf[ig], c1 = cf[S.NB + ig], c2 = cf[2 * S.NB + ig];
-    const double nuP = fma_(c0, r0, -mul_(c1, r1));
-    const double nuQ = fma_(c2, r1, -mul_(c1, r0));
+    const dw c0 = W_(cf[ig]), c1 = W_(cf[S.NB + ig]), c2 = W_(cf[2 * S.NB + ig]);
+    const dw nuP = dw_fma(c0, r0, dw_neg(dw_mul(c1, r1)));
+    const dw nuQ = dw_fma(c2, r1, dw_neg(dw_mul(c1, r0)));
     // a pending outer update first, over every row this thread owns: a
     // separate pass in the few sweeps that carry one, so that the row
     // updates below hold no multiplier clip
@@ -253,42 +313,47 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
       if (!chk_(S, gl >= 0 && gl < I.ng, 13)) continue;
       const long long gp = (long long)I.gpo + (long long)t * I.ng + gl;
       const long long gn = gp + I.ng;
-      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
-      double iW = irpq;
+      dw m = row_mtarget_dw(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
+      dw iW = irpq;
       if (!last) {
-        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])));
-        iW = 0.5 * irpq;
+        m = dw_pow2(dw_add(m, row_mtarget_dw(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])), 0.5f);
+        iW = dw_pow2(irpq, 0.5f);
       }
-      const double pnew = fma_(-nuP, iW, m);
-      const double qnew = fma_(-nuQ, irpq, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
-      const double pold = S.G[F_PBAR * NGP + gp], qold = S.G[F_QBAR * NGP + gp];
-      S.G[F_PBAR * NGP + gp] = pnew;
-      S.G[F_QBAR * NGP + gp] = qnew;
-      row_update<false, false>(S.GA + GR_GP * NGP, S.GY + GR_GP * NGP, S.GZ + GR_GP * NGP, S.GL + GR_GP * NGP,
-                               S.GT + GR_GP * NGP, S.GW + GR_GP * NGP, gp, pnew, pold, Fpq, R, q);
-      if (!last)
-        row_update<false, false>(S.GA + GR_TC * NGP, S.GY + GR_TC * NGP, S.GZ + GR_TC * NGP, S.GL + GR_TC * NGP,
-                                 S.GT + GR_TC * NGP, S.GW + GR_TC * NGP, gn, pnew, pold, Fpq, R, q);
-      row_update<false, false>(S.GA + GR_GQ * NGP, S.GY + GR_GQ * NGP, S.GZ + GR_GQ * NGP, S.GL + GR_GQ * NGP,
-                               S.GT + GR_GQ * NGP, S.GW + GR_GQ * NGP, gp, qnew, qold, Fpq, R, q);
+      const dw pnew = dw_fma(dw_neg(nuP), iW, m);
+      const dw qnew = dw_fma(dw_neg(nuQ), irpq, row_mtarget_dw(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
+      const dw pold = W_(S.G[F_PBAR * NGP + gp]), qold = W_(S.G[F_QBAR * NGP + gp]);
+      const double pnd = dw_to_d(pnew), qnd = dw_to_d(qnew);
+      S.G[F_PBAR * NGP + gp] = pnd;
+      S.G[F_QBAR * NGP + gp] = qnd;
+      // rows gp (t), tc (t + 1, absent in the last period) and gq (t)
+#pragma unroll 1
+      for (int u = 0; u < 3; ++u) {
+        if (u == 1 && last) continue;
+        const long long ri = (u == 0 ? GR_GP * NGP + gp : (u == 1 ? GR_TC * NGP + gn : GR_GQ * NGP + gp));
+        const bool isq = u == 2;
+        row_dw(S.GY, S.GZ, S.GT, S.GW, ri, W_(S.GA[ri]), W_(S.GY[ri]), W_(S.GL[ri]), isq ? qnew : pnew,
+               isq ? qnd : pnd, isq ? qold : pold, Fpq, Q, true);
+      }
     }
-    const double wold = S.U[FU_W * NUP + up], thold = S.U[FU_TH * NUP + up];
-    const double wnew = sub_(mw, mul_(fma_(nuP, aPw, mul_(nuQ, aQw)), iWw));
-    const double thnew = (i == I.ref) ? 0.0 : mth;
-    S.U[FU_W * NUP + up] = wnew;
-    S.U[FU_TH * NUP + up] = thnew;
+    const dw wold = W_(S.U[FU_W * NUP + up]), thold = W_(S.U[FU_TH * NUP + up]);
+    const dw wnew = dw_sub(mw, dw_mul(dw_fma(nuP, aPw, dw_mul(nuQ, aQw)), iWw));
+    const dw thnew = (i == I.ref) ? dw_make(0.0f) : mth;
+    const double wnd = dw_to_d(wnew), thnd = dw_to_d(thnew);
+    S.U[FU_W * NUP + up] = wnd;
+    S.U[FU_TH * NUP + up] = thnd;
     // every incident w (theta) row has the bus's w (theta) as its x-bar:
     // their x-bar changes enter the dual residual as deg times one square
-    const double dw = sub_(wnew, wold), dth = sub_(thnew, thold);
-    q[Q_SD] = fma_(mul_(fdeg, dw), dw, q[Q_SD]);
-    q[Q_SD] = fma_(mul_(fdeg, dth), dth, q[Q_SD]);
+    const dw dwv = dw_sub(wnew, wold), dth = dw_sub(thnew, thold);
+    Q.sd = dw_fma(dw_mul_f(dwv, fdeg), dwv, Q.sd);
+    Q.sd = dw_fma(dw_mul_f(dth, fdeg), dth, Q.sd);
     for (int j = 0; j < deg; ++j) {
       const long long e = e0 + 32LL * j;
       // every input of the line end's four rows is loaded before any of
       // its stores (for all the compiler knows a store may alias a later
       // load, so a load placed after a store would cost a round trip of
       // its own): one memory round trip per line end instead of six
-      double a[4], y[4], lam[4], mt[2], bo[2];
+      double a[4], y[4], lam[4], bo[2];
+      float2 mt[2];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         a[u] = S.EA[u * NEP + e];
@@ -297,20 +362,29 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        mt[u] = S.ET[u * NEP + e];  // (the x-bar-step target parked by pass 1)
+        mt[u] = park[u * NEP + e];  // (the x-bar-step target parked by pass 1)
         bo[u] = S.EFB[u * NEP + e];
       }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const long long eu = u * NEP + e;
-        const double vnew = fma_(u == 0 ? nuP : nuQ, irpq, mt[u]);
-        S.EFB[eu] = vnew;
-        row_store(S.EY, S.EZ, S.ET, S.EW, eu, row_step<false>(a[u], y[u], lam[u], vnew, bo[u], Fpq, q));
+      const dw vp = dw_fma(nuP, irpq, dw{mt[0].x, mt[0].y}), vq = dw_fma(nuQ, irpq, dw{mt[1].x, mt[1].y});
+      const double vpd = dw_to_d(vp), vqd = dw_to_d(vq);
+      S.EFB[e] = vpd;
+      S.EFB[NEP + e] = vqd;
+      // the rows p, q (x-bar: the line end's new flow copies) and w, theta
+      // (x-bar: the bus's w and theta), one body for the four
+#pragma unroll 1
+      for (int u = 0; u < 4; ++u) {
+        const double au = u == 0 ? a[0] : (u == 1 ? a[1] : (u == 2 ? a[2] : a[3]));
+        const double yu = u == 0 ? y[0] : (u == 1 ? y[1] : (u == 2 ? y[2] : y[3]));
+        const double lu = u == 0 ? lam[0] : (u == 1 ? lam[1] : (u == 2 ? lam[2] : lam[3]));
+        const dw bu = u == 0 ? vp : (u == 1 ? vq : (u == 2 ? wnew : thnew));
+        const double bud = u == 0 ? vpd : (u == 1 ? vqd : (u == 2 ? wnd : thnd));
+        const dw bold = u == 0 ? W_(bo[0]) : (u == 1 ? W_(bo[1]) : bu);
+        row_dw(S.EY, S.EZ, S.ET, S.EW, u * NEP + e, W_(au), W_(yu), W_(lu), bu, bud, bold, u < 2 ? Fpq : Fva, Q,
+               u < 2);
       }
-      row_store(S.EY, S.EZ, S.ET, S.EW, 2 * NEP + e, row_step<false, false>(a[2], y[2], lam[2], wnew, wold, Fva, q));
-      row_store(S.EY, S.EZ, S.ET, S.EW, 3 * NEP + e, row_step<false, false>(a[3], y[3], lam[3], thnew, thold, Fva, q));
     }
   }
+  double q[NQ] = {dw_to_d(Q.sp), dw_to_d(Q.sd), dw_to_d(Q.sz), dw_to_d(dw{Q.ih, Q.il}), 0.0};
   warp_reduce_q(q, S.part_up + (long long)gr * NQ);
 }
 

@@ -1561,6 +1561,35 @@ __global__ void k_cossin_probe(const double *d, double *c, double *s, int n) {
 }
 }  // namespace
 
+namespace {
+__global__ void k_dw_probe(int op, const double *x, const double *y, const double *z, double *out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dw_probe_op(op, x[i], y[i], z[i], out + 4 * (size_t)i);
+}
+}  // namespace
+
+extern "C" int ucac_probe_dw(int32_t op, int32_t n, const double *x, const double *y, const double *z,
+                             double *out) {
+  ucac_handle *h = nullptr;
+  if (n < 0 || op < 0 || op > 7 || (n > 0 && (!x || !y || !z || !out)))
+    return fail(nullptr, UCAC_E_ARG, "bad arguments");
+  if (n == 0) return UCAC_OK;
+  double *buf = nullptr;
+  CK(cudaMalloc(&buf, 7 * (size_t)n * sizeof(double)));
+  const size_t nb = (size_t)n * sizeof(double);
+  cudaError_t e = cudaMemcpy(buf, x, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(buf + n, y, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(buf + 2 * (size_t)n, z, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_dw_probe<<<(n + 255) / 256, 256>>>(op, buf, buf + n, buf + 2 * (size_t)n, buf + 3 * (size_t)n, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, buf + 3 * (size_t)n, 4 * nb, cudaMemcpyDeviceToHost);
+  cudaFree(buf);
+  if (e != cudaSuccess) return fail(nullptr, UCAC_E_CUDA, std::string("probe_dw: ") + cudaGetErrorString(e));
+  return UCAC_OK;
+}
+
 extern "C" int ucac_probe_cossin(int32_t n, const double *d, double *c, double *s) {
   ucac_handle *h = nullptr;
   if (n < 0 || (n > 0 && (!d || !c || !s))) return fail(nullptr, UCAC_E_ARG, "bad arguments");

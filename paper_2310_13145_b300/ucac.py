@@ -27,7 +27,7 @@ UCAC_LINE_W, UCAC_LINE_POLAR = 0, 1
 EXPORTS = ["ucac_default_params", "ucac_create", "ucac_create_batch", "ucac_instances", "ucac_iterate",
            "ucac_enqueue_sweeps", "ucac_residuals", "ucac_solution", "ucac_state_size", "ucac_state_export",
            "ucac_state_import", "ucac_kernel_times", "ucac_kernel_name", "ucac_ucdp_workspace_bytes", "ucac_ucdp", "ucac_ucdp_noalloc",
-           "ucac_probe_fp64", "ucac_probe_cossin", "ucac_autotune", "ucac_uc_warm_start", "ucac_mlp_param_count", "ucac_mlp_workspace_bytes", "ucac_mlp_forward",
+           "ucac_probe_fp64", "ucac_probe_cossin", "ucac_probe_dw", "ucac_autotune", "ucac_uc_warm_start", "ucac_mlp_param_count", "ucac_mlp_workspace_bytes", "ucac_mlp_forward",
            "ucac_mlp_grad", "ucac_mlp_adam", "ucac_line_features", "ucac_line_samples", "ucac_set_warm_start", "ucac_set_warmstart",
            "ucac_warm_start_stats", "ucac_line_counts", "ucac_check_inject",
            "ucac_destroy", "ucac_last_error"]
@@ -103,6 +103,7 @@ def lib():
         L.ucac_ucdp_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_double] + [vp] * 12 + [vp]
         L.ucac_probe_fp64.argtypes = [C.c_int32, vp, _dp]
         L.ucac_probe_cossin.argtypes = [C.c_int32, _dp, _dp, _dp]
+        L.ucac_probe_dw.argtypes = [C.c_int32, C.c_int32, _dp, _dp, _dp, _dp]
         L.ucac_autotune.argtypes = [vp, C.c_int32, C.c_char_p, _ip]
         L.ucac_uc_warm_start.argtypes = [vp, C.c_int32, C.c_double]
         L.ucac_mlp_param_count.argtypes = []
@@ -287,6 +288,18 @@ def ucac_probe_cossin(d) -> tuple:
     c, s = np.empty_like(d), np.empty_like(d)
     _check(lib().ucac_probe_cossin(int(d.size), d.ctypes.data_as(_dp), c.ctypes.data_as(_dp), s.ctypes.data_as(_dp)))
     return c, s
+
+
+def ucac_probe_dw(op: int, x, y=None, z=None):
+    """One double-word operation of the line kernel's evaluation on the
+    device (see include/ucac.h): an (n, 4) array of result parts."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros_like(x) if y is None else np.ascontiguousarray(y, dtype=np.float64)
+    z = np.zeros_like(x) if z is None else np.ascontiguousarray(z, dtype=np.float64)
+    out = np.zeros((x.size, 4))
+    _check(lib().ucac_probe_dw(int(op), int(x.size), x.ctypes.data_as(_dp), y.ctypes.data_as(_dp),
+                               z.ctypes.data_as(_dp), out.ctypes.data_as(_dp)))
+    return out
 
 
 def ucac_autotune(h, sweeps_per_trial: int = 3, cache_path: str | None = None) -> dict:
