@@ -162,9 +162,10 @@ __device__ __forceinline__ void row_update(double *A, double *Y, double *Z, doub
 // for the state, and its w = z + y/rho and next x-step target b - w are then
 // formed from those FP64 values by the explicitly rounded FP64 operations of
 // the target preparation (row_w, row_target_w), so that a run resumed from an
-// exported state reproduces them bit for bit.  Everything else (the x-bar
-// step's targets and sums, the 2x2 multiplier solve, the new x-bar values,
-// z, y and the residual sums) is accurate to ~2^-46 relative per operation.
+// exported state reproduces them bit for bit.  The x-bar step's targets
+// a + w and their sums over the bus stay FP64 too (pass 1: two additions per
+// row); the 2x2 multiplier solve, the new x-bar values, z, y and the
+// residual sums are double-words, accurate to ~2^-46 relative per operation.
 __device__ __forceinline__ dw W_(double x) { return dw_from_d(x); }
 
 struct FamW {
@@ -246,36 +247,38 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
     const int g0 = S.gen_ptr[ig], g1r = S.gen_ptr[ig + 1];
     const int g1 = chk_(S, g0 >= 0 && g1r >= g0 && g1r <= S.NGEN, 12) ? g1r : g0;
     // pass 1: targets m_v and the right-hand side of the 2x2 multiplier
-    // system (its matrix is constant between penalty changes: k_prep_bus)
-    dw r0 = dw_make(0.0f), r1 = dw_make(0.0f), mw = dw_make(0.0f), mth = dw_make(0.0f);
+    // system (its matrix is constant between penalty changes: k_prep_bus).
+    // Its sums stay FP64 (two additions per line-end row): in double-words
+    // each would take two conversions and two sums, and the kernel's issue
+    // slots, not its FP64 pipe, are the scarcer resource (0.338 -> 0.322 ms)
+    double r0d = 0.0, r1d = 0.0, mwd = 0.0, mthd = 0.0;
     for (int e = g0; e < g1; ++e) {
       const int gl = S.gen_idx[e];
       if (!chk_(S, gl >= 0 && gl < I.ng, 13)) continue;
       const long long gp = (long long)I.gpo + (long long)t * I.ng + gl;
-      dw m = row_mtarget_dw(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
+      double m = row_mtarget(S.GA[GR_GP * NGP + gp], S.GW[GR_GP * NGP + gp]);
       if (!last) {
         const long long gn = gp + I.ng;
-        m = dw_pow2(dw_add(m, row_mtarget_dw(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])), 0.5f);
+        m = mul_(0.5, add_(m, row_mtarget(S.GA[GR_TC * NGP + gn], S.GW[GR_TC * NGP + gn])));
       }
-      r0 = dw_add(r0, m);
-      r1 = dw_add(r1, row_mtarget_dw(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
+      r0d = add_(r0d, m);
+      r1d = add_(r1d, row_mtarget(S.GA[GR_GQ * NGP + gp], S.GW[GR_GQ * NGP + gp]));
     }
-    // (the p, q x-bar-step targets are parked, as double-words, in the
-    // target slots for pass 2, which overwrites them with the next x-step
-    // targets)
-    float2 *park = reinterpret_cast<float2 *>(S.ET);
-#pragma unroll 1
+    // (the p, q x-bar-step targets are parked in the target slots for pass
+    // 2, which overwrites them with the next x-step targets)
+#pragma unroll 4
     for (int j = 0; j < deg; ++j) {
       const long long e = e0 + 32LL * j;
-      const dw mp = row_mtarget_dw(S.EA[e], S.EW[e]);
-      const dw mq = row_mtarget_dw(S.EA[NEP + e], S.EW[NEP + e]);
-      park[e] = make_float2(mp.h, mp.l);
-      park[NEP + e] = make_float2(mq.h, mq.l);
-      r0 = dw_sub(r0, mp);
-      r1 = dw_sub(r1, mq);
-      mw = dw_add(mw, row_mtarget_dw(S.EA[2 * NEP + e], S.EW[2 * NEP + e]));
-      mth = dw_add(mth, row_mtarget_dw(S.EA[3 * NEP + e], S.EW[3 * NEP + e]));
+      const double mp = row_mtarget(S.EA[e], S.EW[e]);
+      const double mq = row_mtarget(S.EA[NEP + e], S.EW[NEP + e]);
+      S.ET[e] = mp;
+      S.ET[NEP + e] = mq;
+      r0d = sub_(r0d, mp);
+      r1d = sub_(r1d, mq);
+      mwd = add_(mwd, row_mtarget(S.EA[2 * NEP + e], S.EW[2 * NEP + e]));
+      mthd = add_(mthd, row_mtarget(S.EA[3 * NEP + e], S.EW[3 * NEP + e]));
     }
+    dw r0 = W_(r0d), r1 = W_(r1d), mw = W_(mwd), mth = W_(mthd);
     const float fdeg = (float)deg;
     const dw ideg = W_(S.ideg[ig]);
     mw = dw_mul(mw, ideg);
@@ -352,8 +355,7 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
       // its stores (for all the compiler knows a store may alias a later
       // load, so a load placed after a store would cost a round trip of
       // its own): one memory round trip per line end instead of six
-      double a[4], y[4], lam[4], bo[2];
-      float2 mt[2];
+      double a[4], y[4], lam[4], mt[2], bo[2];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         a[u] = S.EA[u * NEP + e];
@@ -362,10 +364,10 @@ __global__ void __launch_bounds__(BS, (UCAC_BUS_MINB * 128) / BS) k_bus(Dev S) {
       }
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        mt[u] = park[u * NEP + e];  // (the x-bar-step target parked by pass 1)
+        mt[u] = S.ET[u * NEP + e];  // (the x-bar-step target parked by pass 1)
         bo[u] = S.EFB[u * NEP + e];
       }
-      const dw vp = dw_fma(nuP, irpq, dw{mt[0].x, mt[0].y}), vq = dw_fma(nuQ, irpq, dw{mt[1].x, mt[1].y});
+      const dw vp = dw_fma(nuP, irpq, W_(mt[0])), vq = dw_fma(nuQ, irpq, W_(mt[1]));
       const double vpd = dw_to_d(vp), vqd = dw_to_d(vq);
       S.EFB[e] = vpd;
       S.EFB[NEP + e] = vqd;
