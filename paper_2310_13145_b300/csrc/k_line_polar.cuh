@@ -102,6 +102,10 @@ struct PolK {
   __device__ __forceinline__ float fq(int r) const { return f[r * fs]; }
   __device__ __forceinline__ float fga(int e) const { return f[(4 + e) * fs]; }
   __device__ __forceinline__ float fka(int e) const { return f[(6 + e) * fs]; }
+  // FP32 copies of the voltage bounds (truncated; f[(8 + j) * fs]: lo0, hi0,
+  // lo1, hi1), for the common step's near-bound prefilter
+  __device__ __forceinline__ float flo(int i) const { return f[(8 + 2 * i) * fs]; }
+  __device__ __forceinline__ float fhi(int i) const { return f[(9 + 2 * i) * fs]; }
 };
 
 // E_r and Ed_r of the four flow rows from those of rows 0 and 2 (T = double
@@ -455,32 +459,33 @@ __device__ __forceinline__ int pol_fast(const PolK &K, const PolP &P, double (&v
                                         const PolLast &L, const float (&H)[6], double Delta, double omega,
                                         bool &accepted, int &counted) {
   const long long b6 = __double_as_longlong(1e-6), ABS = 0x7fffffffffffffffLL;
-  double dlo[POL_NV], dhi[POL_NV];
   long long bx = 0;
-  bool edge = false;  // a variable within 1e-6 of a bound
+  // near-bound prefilter (a variable within 1e-6 of a bound hands the step
+  // to pol_iter): for V_i, V_j and d in FP32 from truncated copies, whose
+  // difference is within two FP32 ulps (< 5e-7 for |x| < 4) of the exact
+  // distance, so the 1.5e-6 test is conservative; for a slack its value is
+  // its distance (compared on the bit patterns).  With omega < 1e-6 a
+  // variable beyond that margin cannot meet the stationarity test through
+  // its bound distance, so no FP64 bound distance is formed here
+  bool edge = __double_as_longlong(omega) >= b6;
 #pragma unroll
-  for (int i = 0; i < POL_NV; ++i) {
-    dlo[i] = v[i] - pol_lo(K, i);
-    dhi[i] = i < 3 ? pol_hi(K, i) - v[i] : INFINITY;
-    if (i < 3) {
-      const long long b = __double_as_longlong(v[i]) & ABS;
-      bx = b > bx ? b : bx;
-      edge = edge || __double_as_longlong(dlo[i]) <= b6 || __double_as_longlong(dhi[i]) <= b6;
-    } else {
-      edge = edge || (__double_as_longlong(dlo[i]) <= b6 && __double_as_longlong(L.m[i - 3]) > 0);
-    }
+  for (int i = 0; i < 3; ++i) {
+    const long long b = __double_as_longlong(v[i]) & ABS;
+    bx = b > bx ? b : bx;
+    const float fv = d2f_trunc(v[i]);
+    const float flo = i < 2 ? K.flo(i) : -3.14159265f, fhi = i < 2 ? K.fhi(i) : 3.14159265f;
+    edge = edge || (fv - flo <= 1.5e-6f) || (fhi - fv <= 1.5e-6f);
   }
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+    edge = edge || (__double_as_longlong(v[3 + k]) <= b6 && __double_as_longlong(L.m[k]) > 0);
   if (edge) return NI_FULL;
   const double xmax = __longlong_as_double(bx);
   // stationarity on the reduced gradient, the free slacks' exact step
   bool stat = true;
   const long long bom = __double_as_longlong(omega);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const long long br = __double_as_longlong(gx[i]);
-    const long long bd = __double_as_longlong(br > 0 ? dlo[i] : dhi[i]);
-    stat = stat && ((br & ABS) <= bom || bd <= bom);
-  }
+  for (int i = 0; i < 3; ++i) stat = stat && (__double_as_longlong(gx[i]) & ABS) <= bom;
   double sn[2];
   bool sok = true;
 #pragma unroll
@@ -518,23 +523,30 @@ __device__ __forceinline__ int pol_fast(const PolK &K, const PolP &P, double (&v
   // zero is fixed there by pol_iter
 #pragma unroll
   for (int k = 0; k < 2; ++k)
-    if (le_nn(dlo[3 + k], 1e-6) && dkey(d[3 + k]) < dkey(-dlo[3 + k])) return NI_FULL;
-  const double dn = __longlong_as_double(bn);
-  if (le_nn(dn, 1e-9 * (1.0 + xmax))) {
+    if (le_nn(v[3 + k], 1e-6) && dkey(d[3 + k]) < dkey(-v[3 + k])) return NI_FULL;
+  double vn[POL_NV];
 #pragma unroll
-    for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
+  for (int i = 0; i < POL_NV; ++i) vn[i] = v[i] + d[i];
+  // the step thresholds 1e-9 (1 + |x|) and 1e-3 (1 + |x|) in FP32 (a step
+  // within ~1e-7 relative of one is decided either way)
+  const float fx1 = 1.0f + d2f_trunc(xmax);
+  const double dn = __longlong_as_double(bn);
+  if (le_nn(dn, f2d_exact(1e-9f * fx1))) {
+#pragma unroll
+    for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, vn[i]);
     counted = 1;
     return NI_CONV;
   }
-  bool inside = true;
+  // the new point in the box, tested on the integer units (dkey order)
+  bool inside = __double_as_longlong(vn[3]) >= 0 && __double_as_longlong(vn[4]) >= 0;
 #pragma unroll
-  for (int i = 0; i < POL_NV; ++i) {
-    const long long b = __double_as_longlong(d[i]);
-    inside = inside && (b < 0 ? (b & ABS) <= __double_as_longlong(dlo[i]) : b <= __double_as_longlong(dhi[i]));
+  for (int i = 0; i < 3; ++i) {
+    const long long kv = dkey(vn[i]);
+    inside = inside && kv >= dkey(pol_lo(K, i)) && kv <= dkey(pol_hi(K, i));
   }
-  if (inside && le_nn(dn, 1e-3 * (1.0 + xmax)) && le_nn(dn, Delta)) {
+  if (inside && le_nn(dn, f2d_exact(1e-3f * fx1)) && le_nn(dn, Delta)) {
 #pragma unroll
-    for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, v[i] + d[i]);
+    for (int i = 0; i < POL_NV; ++i) v[i] = pol_clamp(K, i, vn[i]);
     counted = 1;
     accepted = true;
     return NI_CONT;
@@ -972,8 +984,8 @@ __device__ __forceinline__ void pol_finish_out(const Dev &S, const double *fd, c
   double a[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
-    a[r] = fd[r * POL_QF + sl] + (double)(ff[(3 * r) * POL_QF + sl] * fx0 + ff[(3 * r + 1) * POL_QF + sl] * fx1 +
-                                          ff[(3 * r + 2) * POL_QF + sl] * fx2);
+    a[r] = fd[r * POL_QF + sl] + f2d_exact(ff[(3 * r) * POL_QF + sl] * fx0 + ff[(3 * r + 1) * POL_QF + sl] * fx1 +
+                                           ff[(3 * r + 2) * POL_QF + sl] * fx2);
   const double c0 = fd[4 * POL_QF + sl], s0 = fd[5 * POL_QF + sl], dx2 = fd[9 * POL_QF + sl];
   const double c = c0 - s0 * dx2, sn = s0 + c0 * dx2;
   const double Vi = fd[6 * POL_QF + sl], Vj = fd[7 * POL_QF + sl], d = fd[8 * POL_QF + sl];
@@ -996,7 +1008,7 @@ template <int BS>
 __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  __shared__ float kf[8][BS];  // FP32 copies of the lane's line constants
+  __shared__ float kf[12][BS];  // FP32 copies of the lane's line constants and voltage bounds
   // Per-warp ring of prepared starts (item, instance, v, 1 / c).  Lanes that
   // finish a solve take their next item from the ring; when it runs short,
   // the warp fetches 32 items at once and all 32 lanes prepare one each, so
@@ -1169,6 +1181,10 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           K.hi0 = S.BC[(BC_VB + 1) * NL + lg];
           K.lo1 = S.BC[(BC_VB + 2) * NL + lg];
           K.hi1 = S.BC[(BC_VB + 3) * NL + lg];
+          kf[8][threadIdx.x] = d2f_trunc(K.lo0);
+          kf[9][threadIdx.x] = d2f_trunc(K.hi0);
+          kf[10][threadIdx.x] = d2f_trunc(K.lo1);
+          kf[11][threadIdx.x] = d2f_trunc(K.hi1);
           line_ends(S, I, t, lg, lef, let);
           if (!chk_(S, lef >= 0 && lef < NEP && let >= 0 && let < NEP, 4)) lef = let = 0;
 #pragma unroll
