@@ -169,17 +169,23 @@ __device__ __forceinline__ double pol_clamp(const PolK &K, int i, double x) {
   return __double_as_longlong(x) > 0 ? x : 0.0;
 }
 
-// cos d and sin d for |d| <= pi: d = k/256 + r with |r| <= 1/512 (r exact),
-// cos(k/256) and sin(k/256) from the table, cos r and sin r from their
-// Taylor series to r^4 and r^3 (truncation below 2.4e-16 and 8e-20), then
-// the angle-sum formulas.  About 13 FP64 operations against 25 for the
-// library sincos; the table index is clamped on the integer units, so every
-// read is in bounds
+// cos d and sin d for |d| <= pi: d = k/256 + r with |r| <= 1/512 (+ 1e-6)
+// (r exact), cos(k/256) and sin(k/256) from the table, cos r and sin r from
+// their Taylor series to r^4 and r^3 (truncation below 2.5e-16 and 8e-20),
+// then the angle-sum formulas.  About 10 FP64 operations against 25 for
+// the library sincos.  k is the integer nearest to 256 d rounded from d's
+// truncated FP32 copy (the 1.5 * 2^23 shift on the FP32 pipe; its value
+// sits in the shifted sum's low mantissa bits), so no FP64 rounding or
+// conversion runs; it can miss the nearest integer only where 256 d lies
+// within 1e-4 of a half-integer, which |r| <= 1/512 + 1e-6 covers.  The
+// index is clamped on the integer units, so every read is in bounds (a NaN
+// angle gives NaN)
 __device__ __forceinline__ void pol_cossin(double d, double &c, double &s) {
-  const double kd = rint(d * (double)TRIG_N);
-  int k = (int)kd;
+  const float sh = __fadd_rn(__fmul_rn(d2f_trunc(d), (float)TRIG_N), 12582912.0f);
+  const float kf = __fsub_rn(sh, 12582912.0f);  // k itself (|k| <= 805 for |d| <= pi)
+  int k = (int)(__float_as_uint(sh) & 0x7fffffu) - 0x400000;
   k = k < -TRIG_K ? -TRIG_K : (k > TRIG_K ? TRIG_K : k);
-  const double r = fma(-kd, 1.0 / TRIG_N, d);
+  const double r = fma(-f2d_exact(kf), 1.0 / TRIG_N, d);
   const double r2 = r * r;
   const double sr = fma(r * r2, -1.0 / 6.0, r);
   const double cr = fma(r2, fma(r2, 1.0 / 24.0, -0.5), 1.0);
@@ -301,9 +307,10 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
       SEd = fma(pe[r], Ed[r], SEd);
     }
     const double Sq0 = fma(pe[0], K.q[0], pe[1] * K.q[1]), Sq1 = fma(pe[2], K.q[2], pe[3] * K.q[3]);
-    gx[0] = fma(Vi2x, Sq0, Vj * SE) + 2.0 * P.rva * ewi * Vi;
-    gx[1] = fma(Vj2x, Sq1, Vi * SE) + 2.0 * P.rva * ewj * Vj;
-    gx[2] = Pv * SEd + 0.5 * P.rva * et;
+    // (2 V_i Sq0 + 2 rho_va (V_i^2 - t_4) V_i as 2 V_i (Sq0 + rho_va (V_i^2 - t_4)))
+    gx[0] = fma(Vi2x, fma(P.rva, ewi, Sq0), Vj * SE);
+    gx[1] = fma(Vj2x, fma(P.rva, ewj, Sq1), Vi * SE);
+    gx[2] = fma(Pv, SEd, (0.5 * P.rva) * et);
   }
   // (UCAC_POL_FP64_NEWTON = 1 builds the all-FP64 Hessian and Newton system
   // on every lane, the same model: the A/B reference of the precision split)
