@@ -295,10 +295,10 @@ __device__ __forceinline__ void warp_reduce_q(const double (&q)[NQ], double *out
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
-  // round 1: lanes 0-15 keep SP and SD, lanes 16-31 SZ and OBJ
+  // first exchange: lanes 0-15 keep SP and SD, lanes 16-31 SZ and OBJ
   const double a = __dadd_rn(h16 ? q[Q_SZ] : q[Q_SP], __shfl_xor_sync(FULL, h16 ? q[Q_SP] : q[Q_SZ], 16));
   const double b = __dadd_rn(h16 ? q[Q_OBJ] : q[Q_SD], __shfl_xor_sync(FULL, h16 ? q[Q_SD] : q[Q_OBJ], 16));
-  // round 2: of each half, lanes with bit 3 clear keep a, the others b
+  // second exchange: of each half, lanes with bit 3 clear keep a, the others b
   double v = __dadd_rn(h8 ? b : a, __shfl_xor_sync(FULL, h8 ? a : b, 8));
 #pragma unroll
   for (int o = 4; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(FULL, v, o));

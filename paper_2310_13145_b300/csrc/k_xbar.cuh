@@ -55,14 +55,6 @@ __device__ __forceinline__ Fam fam_pq(const Inst &I) { return Fam{I.rpq, I.irpq,
 __device__ __forceinline__ Fam fam_va(const Inst &I) { return Fam{I.rva, I.irva, I.nbva}; }
 __device__ __forceinline__ Fam fam_uc(const Inst &I) { return Fam{I.ruc, I.iruc, I.nbuc}; }
 
-// a compile-time flag: the x-bar kernels take the pending outer update as a
-// template choice made once per warp, so the rows of a sweep without one
-// carry no (predicated-off) multiplier-clip instructions
-template <bool B>
-struct Flag {
-  static constexpr bool value = B;
-};
-
 // x-step target of a UC duplicate row from its x-bar value b: (b - z) - y/rho
 // with each operation rounded separately and a true division -- the UC
 // dynamic program's inputs depend on it bit for bit.
@@ -90,67 +82,9 @@ __device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a,
 // x-bar-step target of a row from its x value a and its w = z + y/rho
 __device__ __forceinline__ double row_mtarget(double a, double w) { return add_(a, w); }
 
-// max(q, |c|) for q >= 0 on the bit patterns (order-preserving for
-// non-negative doubles): integer work instead of an FP64 min/max
-__device__ __forceinline__ double max_abs_bits(double q, double c) {
-  const unsigned long long bc = (unsigned long long)__double_as_longlong(c) & 0x7fffffffffffffffULL;
-  const unsigned long long bq = (unsigned long long)__double_as_longlong(q);
-  return __longlong_as_double((long long)(bc > bq ? bc : bq));
-}
-
-// The row update from its loaded inputs a, y, lambda: the new z, y, w and
-// next target, and the row's residual terms into q.  SD: accumulate its
-// (b_new - b_old)^2 here (false when the caller adds it once for rows that
-// share b, as a bus's w and theta rows do).
-struct RowNew {
-  double z, y, w, t;
-};
-
-template <bool EXACT, bool SD = true>
-__device__ __forceinline__ RowNew row_step(double a, double y, double lam, double b_new, double b_old, const Fam &F,
-                                           double (&q)[NQ]) {
-  RowNew r;
-  const double c = sub_(a, b_new);
-  r.z = mul_(fma_(F.rho, c, add_(lam, y)), F.nbr);
-  const double cz = add_(c, r.z);
-  r.y = fma_(F.rho, cz, y);
-  r.w = row_w(r.z, r.y, F.irho);
-  r.t = EXACT ? row_target_exact(b_new, r.z, r.y, F.rho) : row_target_w(b_new, r.w);
-  q[Q_SP] = fma_(cz, cz, q[Q_SP]);
-  if (SD) {
-    const double db = sub_(b_new, b_old);
-    q[Q_SD] = fma_(db, db, q[Q_SD]);
-  }
-  q[Q_SZ] = fma_(r.z, r.z, q[Q_SZ]);
-  q[Q_INF] = max_abs_bits(q[Q_INF], c);
-  return r;
-}
-
-__device__ __forceinline__ void row_store(double *Y, double *Z, double *Tg, double *W, long long idx, const RowNew &r) {
-  Z[idx] = r.z;
-  Y[idx] = r.y;
-  W[idx] = r.w;
-  Tg[idx] = r.t;
-}
-
 // the outer update of one row, lambda <- clip(lambda + beta z) (Eq. step:outer)
 __device__ __forceinline__ double outer_lambda(double lam, double z, const RowCtx &R) {
   return clampd(fma_(R.beta_cur, z, lam), -R.lam_max, R.lam_max);
-}
-
-// load, update and store one row; PEND: an outer update is pending (R.pend,
-// warp-uniform) and is applied to the row's lambda first
-template <bool EXACT, bool PEND, bool SD = true>
-__device__ __forceinline__ void row_update(double *A, double *Y, double *Z, double *L, double *Tg, double *W,
-                                           long long idx, double b_new, double b_old, const Fam &F,
-                                           const RowCtx &R, double (&q)[NQ]) {
-  const double a = A[idx], y = Y[idx];
-  double lam = L[idx];
-  if (PEND) {
-    lam = outer_lambda(lam, Z[idx], R);
-    L[idx] = lam;
-  }
-  row_store(Y, Z, Tg, W, idx, row_step<EXACT, SD>(a, y, lam, b_new, b_old, F, q));
 }
 
 // ------------------------------------------------------------ bus (R8) ----
@@ -608,33 +542,62 @@ __global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
     S.G[F_UBSD * NGP + gp] = sdv;
     if (has_next) S.G[F_UBSU * NGP + gn] = su1;
     if (tau == 0) S.G[F_UBSU * NGP + gp] = su0;
-    // the rows, with and without the pending outer update (chosen per warp)
-    auto rows = [&](auto pend) {
-      constexpr bool PEND = decltype(pend)::value;
-#define RU_(E, r, idx, bn, bo, F)                                                                         \
-  row_update<E, PEND>(S.GA + (r)*NGP, S.GY + (r)*NGP, S.GZ + (r)*NGP, S.GL + (r)*NGP, S.GT + (r)*NGP, \
-                      S.GW + (r)*NGP, idx, bn, bo, F, R, q)
-      RU_(true, GR_ON, gp, on, on_old, Fuc);
-      RU_(true, GR_SD, gp, sdv, sd_old, Fuc);
-      RU_(false, GR_PL, gp, Pmin * on, Pmin * on_old, Fpq);
-      RU_(false, GR_PU, gp, Pmax * on, Pmax * on_old, Fpq);
-      RU_(false, GR_QL, gp, Qmin * on, Qmin * on_old, Fpq);
-      RU_(false, GR_QU, gp, Qmax * on, Qmax * on_old, Fpq);
-      RU_(false, GR_RD, gp, (-RD * on) - SD * sdv, (-RD * on_old) - SD * sd_old, Fpq);
-      if (has_next) {
-        RU_(true, GR_SU, gn, su1, su1_old, Fuc);
-        RU_(false, GR_RU, gn, RU * on + SU * su1, RU * on_old + SU * su1_old, Fpq);
+    // the rows: one loop body (double-word row algebra, as in the bus
+    // kernel; w and the next target in FP64 from the stored z, y, the UC
+    // duplicates' target by row_target_exact), the pending outer update a
+    // warp-uniform branch.  Row u: on, sd, pl, pu, ql, qu, rd at t; su, ru at
+    // t + 1 (with a next period); su, ru at t = 0 (thread t = 0 only)
+    const FamW Wpq = fam_w(Fpq), Wuc = fam_w(Fuc);
+    QAcc Q{dw_make(0.0f), dw_make(0.0f), dw_make(0.0f), 0.0f, 0.0f};
+#pragma unroll 1
+    for (int u = 0; u < 11; ++u) {
+      if ((u == 7 || u == 8) && !has_next) continue;
+      if (u >= 9 && tau != 0) break;
+      int r;
+      double bn, bo;
+      switch (u) {
+        case 0: r = GR_ON; bn = on; bo = on_old; break;
+        case 1: r = GR_SD; bn = sdv; bo = sd_old; break;
+        case 2: r = GR_PL; bn = Pmin * on; bo = Pmin * on_old; break;
+        case 3: r = GR_PU; bn = Pmax * on; bo = Pmax * on_old; break;
+        case 4: r = GR_QL; bn = Qmin * on; bo = Qmin * on_old; break;
+        case 5: r = GR_QU; bn = Qmax * on; bo = Qmax * on_old; break;
+        case 6: r = GR_RD; bn = (-RD * on) - SD * sdv; bo = (-RD * on_old) - SD * sd_old; break;
+        case 7: r = GR_SU; bn = su1; bo = su1_old; break;
+        case 8: r = GR_RU; bn = RU * on + SU * su1; bo = RU * on_old + SU * su1_old; break;
+        case 9: r = GR_SU; bn = su0; bo = su0_old; break;
+        default: r = GR_RU; bn = RU * u0 + SU * su0; bo = RU * u0 + SU * su0_old; break;
       }
-      if (tau == 0) {
-        RU_(true, GR_SU, gp, su0, su0_old, Fuc);
-        RU_(false, GR_RU, gp, RU * u0 + SU * su0, RU * u0 + SU * su0_old, Fpq);
+      const bool uc = r <= GR_SD || r == GR_SU;  // the duplicate rows (rho_uc, exact target)
+      const long long ri = (long long)r * NGP + ((u == 7 || u == 8) ? gn : gp);
+      double lam = S.GL[ri];
+      if (R.pend) {
+        lam = outer_lambda(lam, S.GZ[ri], R);
+        S.GL[ri] = lam;
       }
-#undef RU_
-    };
-    if (R.pend)
-      rows(Flag<true>{});
-    else
-      rows(Flag<false>{});
+      const FamW &F = uc ? Wuc : Wpq;
+      const dw b = W_(bn);
+      const dw c = dw_sub(W_(S.GA[ri]), b);
+      const dw y = W_(S.GY[ri]);
+      const dw z = dw_mul(dw_fma(F.rho, c, dw_add(W_(lam), y)), F.nbr);
+      const dw cz = dw_add(c, z);
+      const dw yn = dw_fma(F.rho, cz, y);
+      const dw db = dw_sub(b, W_(bo));
+      Q.sp = dw_fma(cz, cz, Q.sp);
+      Q.sd = dw_fma(db, db, Q.sd);
+      Q.sz = dw_fma(z, z, Q.sz);
+      qacc_inf(Q, c);
+      const double zd = dw_to_d(z), yd = dw_to_d(yn);
+      const double w = row_w(zd, yd, F.irho);
+      S.GZ[ri] = zd;
+      S.GY[ri] = yd;
+      S.GW[ri] = w;
+      S.GT[ri] = uc ? row_target_exact(bn, zd, yd, ruc) : row_target_w(bn, w);
+    }
+    q[Q_SP] = dw_to_d(Q.sp);
+    q[Q_SD] = dw_to_d(Q.sd);
+    q[Q_SZ] = dw_to_d(Q.sz);
+    q[Q_INF] = dw_to_d(dw{Q.ih, Q.il});
     const double p = S.G[F_P * NGP + gp];
     q[Q_OBJ] = S.c2p[gg] * p * p + S.c1p[gg] * p + S.c0[gg] * S.G[F_UON * NGP + gp] +
                S.csu[gg] * S.G[F_USU * NGP + gp] + S.csd[gg] * S.G[F_USD * NGP + gp];
