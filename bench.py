@@ -18,6 +18,7 @@ With N > 1 (torchrun) every rank runs its own replica of the workload
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -119,52 +120,101 @@ def whole_job_value(steps: int, world: int, max_ms: float) -> float:
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
-             "clocks_event_reasons.sw_power_cap"
+    """nvidia-smi clock and throttle-reason samples around a timed region.
+
+    Sampling starts before the warm-up and waits for its first sample
+    (nvidia-smi needs ~0.1-0.3 s, longer than a short timed region); one
+    sample every 50 ms, each stamped with nvidia-smi's own wall-clock
+    timestamp; mark(True) and
+    mark(False) stamp the region's start and end on the host, and stop()
+    keeps the samples taken within 0.1 s of the region (at least the last
+    one before it and the first one after it, waiting for that one)."""
+    FIELDS = "timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active," \
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown," \
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
 
     def __init__(self, index=0):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # the first sample, so that one precedes the timed region
+        deadline = time.time() + 3.0
+        while time.time() < deadline and not self._rows():
+            time.sleep(0.05)
+
+    def mark(self, begin):
+        now = datetime.datetime.now()
+        if begin:
+            self.t0 = now
+        else:
+            self.t1 = now
+
+    def _rows(self):
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f")
+                rows.append((ts, float(p[2]), float(p[3]), p[6], p[7], p[8], p[9]))
+            except ValueError:
+                continue
+        return rows
 
     def stop(self):
         if self.proc is None:
             return None
+        t1 = self.t1 or datetime.datetime.now()
+        deadline = time.time() + 2.0
+        while time.time() < deadline and not any(r[0] > t1 for r in self._rows()):
+            time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            p = [x.strip() for x in line.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                rows.append((float(p[1]), float(p[2]), p[5], p[6], p[7], p[8]))
-            except ValueError:
-                continue
+        rows = self._rows()
         os.unlink(self.path)
-        if not rows:
-            return None
-        reasons = set()
-        for r in rows:
-            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[2:]):
-                if val.lower() == "active":
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": sorted(reasons), "samples": len(rows)}
+        return clock_summary(rows, self.t0, t1)
+
+
+def clock_summary(rows, t0, t1):
+    """Median SM clock, maximum clock and throttle reasons of the samples
+    (timestamp, sm_mhz, sm_max_mhz, hw_slowdown, hw_thermal_slowdown,
+    sw_thermal_slowdown, sw_power_cap) taken within 0.1 s of [t0, t1], plus
+    the last sample before and the first after; None without samples."""
+    if not rows:
+        return None
+    t0 = t0 or rows[0][0]
+    pad = datetime.timedelta(seconds=0.1)
+    keep = [r for r in rows if t0 - pad <= r[0] <= t1 + pad]
+    before = [r for r in rows if r[0] < t0 - pad]
+    after = [r for r in rows if r[0] > t1 + pad]
+    if before:
+        keep.insert(0, before[-1])
+    if after:
+        keep.append(after[0])
+    reasons = set()
+    for r in keep:
+        for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[3:]):
+            if val.lower() == "active":
+                reasons.add(name)
+    return {"sm_mhz": statistics.median(r[1] for r in keep), "sm_max_mhz": max(r[2] for r in keep),
+            "reasons": sorted(reasons), "samples": len(keep),
+            "window_s": round((keep[-1][0] - keep[0][0]).total_seconds(), 3)}
 
 
 def measured_peaks():
@@ -346,19 +396,21 @@ def main():
         cache = os.path.join(os.path.expanduser("~"), ".cache", "ucac", "autotune.txt")
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         tuning = h.autotune(3, cache)
+    clk = ClockSampler(local)
+    clk.start()
     with torch.cuda.stream(stream):
         h.enqueue(a.warmup)
         stream.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        clk = ClockSampler(local)
-        clk.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        clk.mark(True)
         e0.record(stream)
         h.enqueue(a.steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.mark(False)
         clocks = clk.stop()
     ms = reduce_max(e0.elapsed_time(e1), world, device="cuda")
     value = whole_job_value(a.steps, world, ms)
