@@ -216,8 +216,10 @@ int ucac_check_inject(ucac_handle *h, int32_t site);
  * be NULL): p, q [T][n_gen] (generator x-side), w, theta [T][n_bus] (bus
  * copies: |V|^2 and the voltage angle), pf [T][n_branch][4] (p_ij, q_ij,
  * p_ji, q_ji from the line subproblems), u_on [T][n_gen] (0/1 from the UC
- * dynamic program).  Synchronises the handle's stream.  UCAC_E_ARG for a bad
- * handle or instance, UCAC_E_CUDA if a copy fails.
+ * dynamic program).  The copies are queued on the handle's stream behind
+ * its sweeps and the call returns once they are done; page-locked buffers
+ * let them run at the copy engines' rate.  UCAC_E_ARG for a bad handle or
+ * instance, UCAC_E_CUDA if a copy fails.
  */
 int ucac_solution(const ucac_handle *h, int32_t instance, double *p, double *q, double *w, double *theta,
                   double *pf, uint8_t *u_on);

@@ -944,19 +944,21 @@ int ucac_solution(const ucac_handle *hc, int32_t k, double *p, double *q, double
   const HInst &I = h->hi[k];
   const Dev &D = h->dev;
   const size_t ngp = (size_t)I.T * I.ng, nup = (size_t)I.T * I.nb, nbp = (size_t)I.T * I.nl;
-  CK(cudaStreamSynchronize(h->stream));
-  if (p) CK(cudaMemcpy(p, D.G + F_P * D.NGP + I.gpo, ngp * 8, cudaMemcpyDeviceToHost));
-  if (q) CK(cudaMemcpy(q, D.G + F_Q * D.NGP + I.gpo, ngp * 8, cudaMemcpyDeviceToHost));
-  if (w) CK(cudaMemcpy(w, D.U + FU_W * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost));
-  if (theta) CK(cudaMemcpy(theta, D.U + FU_TH * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost));
+  // every copy on the handle's stream behind the sweeps it has queued, one
+  // synchronisation at the end (copies into page-locked host memory then
+  // overlap and run at the copy engines' rate)
+  if (p) CK(cudaMemcpyAsync(p, D.G + F_P * D.NGP + I.gpo, ngp * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (q) CK(cudaMemcpyAsync(q, D.G + F_Q * D.NGP + I.gpo, ngp * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (w) CK(cudaMemcpyAsync(w, D.U + FU_W * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (theta) CK(cudaMemcpyAsync(theta, D.U + FU_TH * D.NUP + I.upo, nup * 8, cudaMemcpyDeviceToHost, h->stream));
   if (pf) {
     // gathered into the caller's [t][l][4] order on the device (the staging
     // rows hold at least 4 nbp doubles), then one copy
     k_solution_flows<256><<<(unsigned)((nbp + 255) / 256), 256, 0, h->stream>>>(h->dev, k, h->stage);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(pf, h->stage, nbp * 4 * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
   }
+  CK(cudaStreamSynchronize(h->stream));
   if (u_on) {
     std::vector<double> tmp(ngp);
     CK(cudaMemcpy(tmp.data(), D.G + F_UON * D.NGP + I.gpo, ngp * 8, cudaMemcpyDeviceToHost));

@@ -200,13 +200,29 @@ def ucac_residuals(h, instance: int = 0) -> dict:
     return {f: getattr(r, f) for f, _ in ucac_report._fields_}
 
 
-def ucac_solution(h, instance: int, T: int, ng: int, nb: int, nl: int) -> dict:
-    p = np.zeros((T, ng)); q = np.zeros((T, ng)); w = np.zeros((T, nb)); th = np.zeros((T, nb))
-    pf = np.zeros((T, nl, 4)); u = np.zeros((T, ng), np.uint8)
+def solution_arrays(T: int, ng: int, nb: int, nl: int, alloc=np.zeros) -> dict:
+    """Output arrays of ucac_solution for one instance (alloc(shape, dtype),
+    e.g. a page-locked allocator)."""
+    return {"p": alloc((T, ng), np.float64), "q": alloc((T, ng), np.float64), "w": alloc((T, nb), np.float64),
+            "theta": alloc((T, nb), np.float64), "pf": alloc((T, nl, 4), np.float64),
+            "u_on": alloc((T, ng), np.uint8)}
+
+
+def ucac_solution(h, instance: int, T: int, ng: int, nb: int, nl: int, out: dict | None = None) -> dict:
+    """The instance's solution; out: arrays from solution_arrays to fill
+    (C-contiguous, of those shapes and dtypes), else new ones."""
+    o = solution_arrays(T, ng, nb, nl) if out is None else out
+    for name, shape, dt in (("p", (T, ng), np.float64), ("q", (T, ng), np.float64), ("w", (T, nb), np.float64),
+                            ("theta", (T, nb), np.float64), ("pf", (T, nl, 4), np.float64),
+                            ("u_on", (T, ng), np.uint8)):
+        a = o[name]
+        if a.shape != shape or a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+            raise UcacError(f"solution array {name}: expected {shape} {np.dtype(dt)} C-contiguous")
+    p, q, w, th, pf, u = o["p"], o["q"], o["w"], o["theta"], o["pf"], o["u_on"]
     _check(lib().ucac_solution(h, int(instance), p.ctypes.data_as(_dp), q.ctypes.data_as(_dp), w.ctypes.data_as(_dp),
                                th.ctypes.data_as(_dp), pf.ctypes.data_as(_dp),
                                u.ctypes.data_as(C.POINTER(C.c_uint8))), h)
-    return {"p": p, "q": q, "w": w, "theta": th, "pf": pf, "u_on": u}
+    return o
 
 
 def ucac_line_counts(h, instance: int, T: int, nl: int) -> tuple:

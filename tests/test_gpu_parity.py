@@ -5,6 +5,7 @@ and the two results are compared field by field (continuous fields within a
 normwise relative 1e-9, UC decisions bit for bit).
 """
 import numpy as np
+import torch
 import pytest
 
 import oracle
@@ -300,6 +301,15 @@ def test_solution_readback(ucac_mod):
         assert sol["pf"].shape == flows.shape
         err = np.abs(sol["pf"] - flows).max()
         assert err <= 1e-9 * max(1.0, np.abs(flows).max()), (k, err)
+        # the same bits into caller arrays (page-locked ones, as the bench's
+        # end-to-end leg passes), and a wrong shape is refused
+        pin = lambda shape, dt: torch.empty(shape, dtype=torch.from_numpy(np.zeros(0, dt)).dtype).pin_memory().numpy()  # noqa: E731
+        out = ucac_mod.solution_arrays(g.T, g.n_gen, g.n_bus, g.n_branch, alloc=pin)
+        sol2 = ucac_mod.ucac_solution(h.h, k, g.T, g.n_gen, g.n_bus, g.n_branch, out=out)
+        assert sol2 is out and all(np.array_equal(sol[n], out[n]) for n in sol)
+    bad = ucac_mod.solution_arrays(grids[0].T, grids[0].n_gen + 1, grids[0].n_bus, grids[0].n_branch)
+    with pytest.raises(ucac_mod.UcacError):
+        ucac_mod.ucac_solution(h.h, 0, grids[0].T, grids[0].n_gen, grids[0].n_bus, grids[0].n_branch, out=bad)
     h.close()
 
 
