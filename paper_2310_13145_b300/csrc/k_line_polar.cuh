@@ -446,11 +446,15 @@ __device__ __forceinline__ T hq(const T (&H)[6], int i, int j) {
 }
 
 
-// a pending trial point: evaluated in full at the next trip, then accepted or
-// rejected by the ratio test against the model decrease pred
-struct PolTrial {
-  double v[POL_NV], ht[2], pred, scale, smax;
-};
+// A pending trial point: evaluated in full at the next trip, then accepted or
+// rejected by the ratio test against the model decrease pred.  The record
+// lives in shared memory, one column per lane (field f of a lane's record at
+// rec[32 f]): the point, the predicted h_k, pred, the step's scale and
+// largest x component, the model's linear and quadratic terms of the step
+// sg (pred = -(lin + quad/2)), h_k at the current point, and whether the
+// step left the box unprojected (then a rejection can shrink it in place).
+enum { TR_V = 0, TR_HT = 5, TR_PRED = 7, TR_SCALE = 8, TR_SMAX = 9, TR_LIN = 10, TR_QUAD = 11, TR_H0 = 12,
+       TR_FREE = 14, TR_N = 15 };
 enum { NI_TRIAL = 3, NI_FULL = 4 };
 
 // The common Newton iteration of a lane with no slack held at zero (FP32
@@ -567,7 +571,7 @@ __device__ __forceinline__ int pol_fast(const PolK &K, const PolP &P, double (&v
 template <typename T>
 __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v)[POL_NV], double &f,
                                         const double (&gx)[3], const PolLast &L, const T (&H)[6], double &Delta,
-                                        double omega, bool &accepted, int &counted, PolTrial &tr,
+                                        double omega, bool &accepted, int &counted, double *trp,
                                         bool &nearb) {
   accepted = false;
   counted = 0;
@@ -796,14 +800,14 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   counted = 1;
   // model decrease of a step sg: -(gr . sg + 1/2 sg^T H5 sg), where
   // sg^T H5 sg = sx^T H sx + sum_k c (grad g_k . sx + s_sigma_k)^2
-  auto model = [&](const double (&sg)[POL_NV]) -> double {
-    double lin = 0.0;
+  auto model = [&](const double (&sg)[POL_NV], double &lin, double &quad) -> double {
+    lin = 0.0;
 #pragma unroll
     for (int i = 0; i < POL_NV; ++i) lin += gr[i] * sg[i];
     const T s0 = (T)sg[0], s1 = (T)sg[1], s2 = (T)sg[2];
     const T sHs = s0 * (H[0] * s0 + H[1] * s1 + H[2] * s2) + s1 * (H[1] * s0 + H[3] * s1 + H[4] * s2) +
                   s2 * (H[2] * s0 + H[4] * s1 + H[5] * s2);
-    double quad = (double)sHs;
+    quad = (double)sHs;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const double e = dg[k][0] * sg[0] + dg[k][1] * sg[1] + dg[k][2] * sg[2] + sg[3 + k];
@@ -835,14 +839,18 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   }
   const double scale = le_nn(dn, Delta) ? 1.0 : Delta / dn;
   double vt[POL_NV], sg[POL_NV], smax = 0.0;
+  bool unproj = true;  // no component projected onto its bound
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) {
-    vt[i] = pol_clamp(K, i, v[i] + scale * d[i]);
+    const double u = v[i] + scale * d[i];
+    vt[i] = pol_clamp(K, i, u);
+    unproj = unproj && __double_as_longlong(vt[i]) == __double_as_longlong(u);
     sg[i] = vt[i] - v[i];
     if (i < 3) smax = fmax(smax, fabs(sg[i]));
   }
   full_grad();
-  const double pred = model(sg);
+  double mlin, mquad;
+  const double pred = model(sg, mlin, mquad);
   // predicted h_k of the trial step; free slacks absorb the remainder of
   // g_k exactly, a slack held at zero gets the correction
   // dx = -sum_k alpha_k grad g_k (Gram system of the held gradients) that
@@ -858,14 +866,19 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   if (nheld == 0) {
     // the trial point becomes the next trip's evaluation point: every lane
     // of the warp then runs one full evaluation per trip, and the ratio test
-    // follows it (a rejection re-evaluates the current point)
+    // follows it (see the trial record)
 #pragma unroll
-    for (int i = 0; i < POL_NV; ++i) tr.v[i] = vt[i];
-    tr.ht[0] = ht[0];
-    tr.ht[1] = ht[1];
-    tr.pred = pred;
-    tr.scale = scale;
-    tr.smax = smax;
+    for (int i = 0; i < POL_NV; ++i) trp[32 * (TR_V + i)] = vt[i];
+    trp[32 * TR_HT] = ht[0];
+    trp[32 * (TR_HT + 1)] = ht[1];
+    trp[32 * TR_PRED] = pred;
+    trp[32 * TR_SCALE] = scale;
+    trp[32 * TR_SMAX] = smax;
+    trp[32 * TR_LIN] = mlin;
+    trp[32 * TR_QUAD] = mquad;
+    trp[32 * TR_H0] = L.h[0];
+    trp[32 * (TR_H0 + 1)] = L.h[1];
+    trp[32 * TR_FREE] = unproj ? 1.0 : 0.0;
     return NI_TRIAL;
   }
   double at[4], ct, stn;
@@ -1078,7 +1091,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   // final point (at the next trip's single call site, with the rest of the
   // warp) and then finished from that evaluation: 1 converged, 2 stopped
   int fin_pend = 0;
-  PolTrial tr;
+  __shared__ double trs[BS / 32][TR_N][32];  // the lanes' trial records
+  double *trp = &trs[wib][0][lane];
   double f = 0.0, Delta = 1.0, hprev = INFINITY, omega = 0.0, cmax = 0.0;
   double v[POL_NV], gx[3], Hd[6];
   float Hf[6];
@@ -1250,27 +1264,54 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
       if (need_full) {
         // one call site for every lane: the point is the trial point or the
         // current point (two call sites would split the warp between copies)
-        if (!trial) {
+        double tv[POL_NV], tht[2];
 #pragma unroll
-          for (int i = 0; i < POL_NV; ++i) tr.v[i] = v[i];
-          tr.ht[0] = tr.ht[1] = 0.0;
-        }
-        pol_full(K, P, tr.v, gx, Hf, Hd, L, tr.ht, trial ? 3 : 0);
+        for (int i = 0; i < POL_NV; ++i) tv[i] = trial ? trp[32 * (TR_V + i)] : v[i];
+        tht[0] = trial ? trp[32 * TR_HT] : 0.0;
+        tht[1] = trial ? trp[32 * (TR_HT + 1)] : 0.0;
+        pol_full(K, P, tv, gx, Hf, Hd, L, tht, trial ? 3 : 0);
         if (trial) {
           trial = false;
           const double fe = pol_f(P, L);
           const double ared = f - fe;
-          if (tr.pred > 0.0 && ared >= 1e-4 * tr.pred) {
+          const double pred = trp[32 * TR_PRED], smax = trp[32 * TR_SMAX];
+          if (pred > 0.0 && ared >= 1e-4 * pred) {
 #pragma unroll
-            for (int i = 0; i < POL_NV; ++i) v[i] = tr.v[i];
+            for (int i = 0; i < POL_NV; ++i) v[i] = tv[i];
             f = fe;
-            if (ared >= 0.75 * tr.pred && tr.scale < 1.0) Delta = 2.0 * Delta;
+            if (ared >= 0.75 * pred && trp[32 * TR_SCALE] < 1.0) Delta = 2.0 * Delta;
           } else {
-            // rejected: the evaluation describes the trial point, so the
-            // current point is evaluated again at the next trip
-            Delta = 0.25 * tr.smax;
+            // rejected: the radius becomes a quarter of the step
+            Delta = 0.25 * smax;
             step_now = false;
-            if (Delta <= 1e-15 * (1.0 + fmax(fmax(fabs(v[0]), fabs(v[1])), fabs(v[2])))) out = NI_STOP;
+            if (Delta <= 1e-15 * (1.0 + fmax(fmax(fabs(v[0]), fabs(v[1])), fabs(v[2])))) {
+              out = NI_STOP;
+            } else if (trp[32 * TR_FREE] != 0.0) {
+              // The current point's Newton direction does not change with
+              // the radius, so its next step is this one scaled by a
+              // quarter; with no component projected onto a bound that is
+              // the point v + (t - v)/4, still in the box, with the model's
+              // terms scaled by 1/4 and 1/16 and h_k predicted on the same
+              // line.  It becomes the next trial at once, instead of
+              // evaluating the current point again to find the same step.
+              const double lin = 0.25 * trp[32 * TR_LIN], quad = 0.0625 * trp[32 * TR_QUAD];
+#pragma unroll
+              for (int i = 0; i < POL_NV; ++i) {
+                const double t = trp[32 * (TR_V + i)];
+                trp[32 * (TR_V + i)] = fma(0.25, t - v[i], v[i]);
+              }
+#pragma unroll
+              for (int k = 0; k < 2; ++k) {
+                const double h0 = trp[32 * (TR_H0 + k)];
+                trp[32 * (TR_HT + k)] = fma(0.25, trp[32 * (TR_HT + k)] - h0, h0);
+              }
+              trp[32 * TR_PRED] = -(lin + 0.5 * quad);
+              trp[32 * TR_LIN] = lin;
+              trp[32 * TR_QUAD] = quad;
+              trp[32 * TR_SCALE] = 0.25 * trp[32 * TR_SCALE];
+              trp[32 * TR_SMAX] = Delta;
+              trial = true;
+            }
           }
         }
       }
@@ -1285,11 +1326,11 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
         int counted;
         bool nearb;
         if (L.lim) {
-          out = pol_iter<double>(K, P, v, f, gx, L, Hd, Delta, omega, accepted, counted, tr, nearb);
+          out = pol_iter<double>(K, P, v, f, gx, L, Hd, Delta, omega, accepted, counted, trp, nearb);
         } else {
           out = pol_fast(K, P, v, gx, L, Hf, Delta, omega, accepted, counted);
           nearb = false;
-          if (out == NI_FULL) out = pol_iter<float>(K, P, v, f, gx, L, Hf, Delta, omega, accepted, counted, tr, nearb);
+          if (out == NI_FULL) out = pol_iter<float>(K, P, v, f, gx, L, Hf, Delta, omega, accepted, counted, trp, nearb);
         }
         hard = hard || nearb || L.lim;
         newton += counted;
