@@ -1069,12 +1069,26 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   const double eta = S.prm.eta;
   const int K_N = S.prm.K_N, K_AL = S.prm.K_AL;
   bool active = true;
-  long long bp = -1, lef = 0, let = 0;  // item, slots of its from / to end
+  long long bp = -1;  // item
+  // per-lane values used only where a solve starts or ends, kept in shared
+  // memory (one column per lane) to spare registers: the slots of the
+  // item's from / to end, the multiplier loop's previous |h| and penalty
+  // cap, and the statistics accumulated for the current instance
+  __shared__ long long lsl[BS / 32][2][32];
+  __shared__ double lal[BS / 32][2][32];
+  __shared__ unsigned long long lst[BS / 32][4][32];
+  long long &lef = lsl[wib][0][lane], &let = lsl[wib][1][lane];
+  double &hprev = lal[wib][0][lane], &cmax = lal[wib][1][lane];
+  unsigned long long &acc_nw = lst[wib][0][lane], &acc_al = lst[wib][1][lane], &acc_cap = lst[wib][2][lane],
+                     &acc_w = lst[wib][3][lane];
+  lef = let = 0;
+  hprev = INFINITY;
+  cmax = 0.0;
   int k = 0, itn = 0, al = 0, newton = 0;
   // per-lane statistics, flushed to the instance's counters when the lane
   // moves to another instance or retires (consecutive items mostly share one)
   int acc_k = -1;
-  unsigned long long acc_nw = 0, acc_al = 0, acc_cap = 0, acc_w = 0;
+  acc_nw = acc_al = acc_cap = acc_w = 0;
   auto flush = [&]() {
     if (acc_k >= 0) {
       unsigned long long *st = (unsigned long long *)(S.bstat + (long long)acc_k * 3);
@@ -1093,7 +1107,7 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
   int fin_pend = 0;
   __shared__ double trs[BS / 32][TR_N][32];  // the lanes' trial records
   double *trp = &trs[wib][0][lane];
-  double f = 0.0, Delta = 1.0, hprev = INFINITY, omega = 0.0, cmax = 0.0;
+  double f = 0.0, Delta = 1.0, omega = 0.0;
   double v[POL_NV], gx[3], Hd[6];
   float Hf[6];
   PolLast L;
