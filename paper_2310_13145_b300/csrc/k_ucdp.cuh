@@ -107,23 +107,36 @@ __device__ __forceinline__ double uc_dp_tab(int T, int TU, int TD, int u0, int K
 
 // DP for one generator on one thread.  tau_* point at period 0 of the
 // generator's column (element stride `st` between periods); L/C/D are
-// scratch columns with the same stride.
+// scratch columns with element stride `stt` (st when not given).
 template <typename WriteU>
 __device__ __forceinline__ double uc_dp(int T, int TU, int TD, int u0, int K0, double c0, double csu, double csd,
                                         double hr, const double *tau_on, const double *tau_su,
                                         const double *tau_sd, long long st, double *L, double *C,
-                                        unsigned char *D, WriteU uon) {
+                                        unsigned char *D, WriteU uon, long long stt = -1) {
+  if (stt < 0) stt = st;
   double lin[4];
   uc_lin4(c0, csu, csd, lin);
-  for (int t = 0; t < T; ++t) uc_stage4(T, t, st, tau_on[t * st], tau_su[t * st], tau_sd[t * st], lin, hr, L);
-  return uc_dp_tab(T, TU, TD, u0, K0, st, L, C, D, uon);
+  for (int t = 0; t < T; ++t) uc_stage4(T, t, stt, tau_on[t * st], tau_su[t * st], tau_sd[t * st], lin, hr, L);
+  return uc_dp_tab(T, TU, TD, u0, K0, stt, L, C, D, uon);
 }
 
 // In-sweep x^UC step: reads the duplicate-row targets tau = ubar - z - y/rho
 // (written by the x-bar^UC kernel of the previous sweep), writes u_on/u_su/
 // u_sd and the x-side values of the three duplicate rows.
+//
+// The tables are the thread's own: with sm_T > 0 (every instance has
+// T <= sm_T, and the launch gave BS * ucdp_smem_per_thread(sm_T) bytes of
+// dynamic shared memory) they sit in a shared-memory column per thread
+// (stride BS), so that the backward chain, which reads each step what the
+// step before wrote, waits on shared memory instead of an L2 round trip;
+// otherwise in the global scratch.  The arithmetic is the same either way.
+__host__ __device__ constexpr size_t ucdp_smem_per_thread(int T) {
+  return (size_t)(6 * T + 2) * sizeof(double) + (size_t)2 * T;
+}
+
 template <int BS>
-__global__ void __launch_bounds__(BS) k_ucdp(Dev S) {
+__global__ void __launch_bounds__(BS) k_ucdp(Dev S, int sm_T) {
+  extern __shared__ double ucdp_sm[];
   const int gr = warp_granule<BS>(S.g_gen.n);
   if (gr < 0) return;
   const int k = S.g_gen.inst[gr];
@@ -137,9 +150,12 @@ __global__ void __launch_bounds__(BS) k_ucdp(Dev S) {
   const double hr = __dmul_rn(0.5, I.ruc);
   const int TU = max(S.TU[gg], 1), TD = max(S.TD[gg], 1), u0 = S.u0[gg];
   const int K0 = min(max(S.K0[gg], 0), T);
-  double *L = S.dpL + 4LL * I.gpo + g;
-  double *C = S.dpC + 2LL * (I.gpo + I.go) + g;
-  unsigned char *D = S.dpD + 2LL * I.gpo + g;
+  const bool sm = sm_T > 0 && chk_(S, T <= sm_T, 60);
+  double *L = sm ? ucdp_sm + threadIdx.x : S.dpL + 4LL * I.gpo + g;
+  double *C = sm ? ucdp_sm + (size_t)BS * 4 * sm_T + threadIdx.x : S.dpC + 2LL * (I.gpo + I.go) + g;
+  unsigned char *D = sm ? (unsigned char *)(ucdp_sm + (size_t)BS * (6 * sm_T + 2)) + threadIdx.x
+                        : S.dpD + 2LL * I.gpo + g;
+  const long long st = sm ? BS : ng;
   if (S.prm.uc_relax) {
     // box relaxation of Eq. set:UC (first phase of the UC warm start): each
     // row minimises c u + rho/2 (u - tau)^2 over [0, 1]
@@ -159,7 +175,7 @@ __global__ void __launch_bounds__(BS) k_ucdp(Dev S) {
   double *uon_a = S.G + (long long)F_UON * NGP + base;
   uc_dp(T, TU, TD, u0, K0, S.c0[gg], S.csu[gg], S.csd[gg], hr, S.GT + GR_ON * NGP + base,
         S.GT + GR_SU * NGP + base, S.GT + GR_SD * NGP + base, (long long)ng, L, C, D,
-        [&](int t, int u) { uon_a[(long long)t * ng] = (double)u; });
+        [&](int t, int u) { uon_a[(long long)t * ng] = (double)u; }, st);
   int prev = u0;
   for (int t = 0; t < T; ++t) {
     const long long i = base + (long long)t * ng;

@@ -205,7 +205,48 @@ inline int blocks_for(int granules, int bs) { return std::max(1, (granules + bs 
     default: KERNEL<128><<<blocks_for(NGRAN, 128), 128, 0, STREAM>>>(ARG); break;             \
   }
 
-void launch_ucdp(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.ucdp, k_ucdp, h->ngr_gen, s, h->dev); }
+// the in-sweep DP with its tables in shared memory when a block's columns
+// fit (ucdp_smem_for), else in the global scratch
+constexpr size_t UCDP_SMEM_MAX = 160 * 1024;
+size_t ucdp_smem_for(const ucac_handle *h, int bs) {
+  int tmax = 0;
+  for (const HInst &I : h->hi) tmax = std::max(tmax, I.T);
+  const size_t b = (size_t)bs * ucdp_smem_per_thread(tmax);
+  return b <= UCDP_SMEM_MAX ? b : 0;
+}
+int ucdp_sm_T(const ucac_handle *h) {
+  int tmax = 0;
+  for (const HInst &I : h->hi) tmax = std::max(tmax, I.T);
+  return tmax;
+}
+// raises each block size's dynamic shared-memory limit to what the handle's
+// horizon needs (before any launch or capture)
+cudaError_t ucdp_smem_setup(ucac_handle *h) {
+  cudaError_t e = cudaSuccess;
+  const int bss[4] = {32, 64, 128, 256};
+  for (int bs : bss) {
+    const size_t b = ucdp_smem_for(h, bs);
+    if (!b || e != cudaSuccess) continue;
+    switch (bs) {
+      case 32: e = cudaFuncSetAttribute(k_ucdp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); break;
+      case 64: e = cudaFuncSetAttribute(k_ucdp<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); break;
+      case 128: e = cudaFuncSetAttribute(k_ucdp<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); break;
+      default: e = cudaFuncSetAttribute(k_ucdp<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); break;
+    }
+  }
+  return e;
+}
+void launch_ucdp(ucac_handle *h, cudaStream_t s) {
+  const int bs = h->tune.ucdp;
+  const size_t b = ucdp_smem_for(h, bs);
+  const int smT = b ? ucdp_sm_T(h) : 0;
+  switch (bs) {
+    case 32: k_ucdp<32><<<blocks_for(h->ngr_gen, 32), 32, b, s>>>(h->dev, smT); break;
+    case 64: k_ucdp<64><<<blocks_for(h->ngr_gen, 64), 64, b, s>>>(h->dev, smT); break;
+    case 256: k_ucdp<256><<<blocks_for(h->ngr_gen, 256), 256, b, s>>>(h->dev, smT); break;
+    default: k_ucdp<128><<<blocks_for(h->ngr_gen, 128), 128, b, s>>>(h->dev, smT); break;
+  }
+}
 void launch_gen(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.gen, k_gen, h->ngr_gp, s, h->dev); }
 void launch_bus(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.bus, k_bus, h->ngr_up, s, h->dev); }
 void launch_ucbar(ucac_handle *h, cudaStream_t s) { UCAC_DISPATCH_BS(h->tune.ucbar, k_ucbar, h->ngr_gp, s, h->dev); }
@@ -799,6 +840,7 @@ int ucac_create_batch(const ucac_grid *const *grids, const int32_t *horizons, co
     return fail(nullptr, UCAC_E_CUDA, m);
   }
   h->grid_branch = line_grid(h, h->tune.line);
+  chain(ucdp_smem_setup(h));
   {
     // the cold start, then the x-step targets from it
     long long max_nup = 0;
