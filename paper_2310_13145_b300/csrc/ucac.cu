@@ -219,21 +219,17 @@ int ucdp_sm_T(const ucac_handle *h) {
   for (const HInst &I : h->hi) tmax = std::max(tmax, I.T);
   return tmax;
 }
-// raises each block size's dynamic shared-memory limit to what the handle's
-// horizon needs (before any launch or capture)
-cudaError_t ucdp_smem_setup(ucac_handle *h) {
-  cudaError_t e = cudaSuccess;
-  const int bss[4] = {32, 64, 128, 256};
-  for (int bs : bss) {
-    const size_t b = ucdp_smem_for(h, bs);
-    if (!b || e != cudaSuccess) continue;
-    switch (bs) {
-      case 32: e = cudaFuncSetAttribute(k_ucdp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); break;
-      case 64: e = cudaFuncSetAttribute(k_ucdp<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); break;
-      case 128: e = cudaFuncSetAttribute(k_ucdp<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); break;
-      default: e = cudaFuncSetAttribute(k_ucdp<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b); break;
-    }
-  }
+// raises every block size's dynamic shared-memory limit to UCDP_SMEM_MAX,
+// the most any launch asks for (before any launch or capture).  The limit is
+// a property of the function, shared by all handles: a limit fitted to one
+// handle's horizon could fall below what another handle's captured graph
+// launches with, so it is never set lower than that maximum.
+cudaError_t ucdp_smem_setup(ucac_handle *) {
+  const int b = (int)UCDP_SMEM_MAX;
+  cudaError_t e = cudaFuncSetAttribute(k_ucdp<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ucdp<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ucdp<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ucdp<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   return e;
 }
 void launch_ucdp(ucac_handle *h, cudaStream_t s) {

@@ -479,3 +479,25 @@ def test_line_counts_sum_to_the_record(ucac_mod, line_form):
             hist = ucac_mod.count_histogram(nw)
             assert sum(hist) == g.T * g.n_branch
     h.close()
+
+
+def test_handles_with_different_horizons(ucac_mod):
+    # the sweep's UC dynamic program keeps its tables in shared memory sized
+    # by the handle's horizon; a later handle with a shorter horizon must not
+    # break the sweeps the first one has captured (the kernel's shared-memory
+    # limit is shared by all handles), and the two interleave bit for bit
+    long_g = synth.make_grid(20, 30, 6, 96, seed=11)
+    short_g = synth.make_grid(9, 12, 3, 6, seed=12)
+    ref = ucac_mod.Handle([long_g])
+    ref.enqueue(6)
+    want = ref.export(0)
+    ref.close()
+    a = ucac_mod.Handle([long_g])
+    a.enqueue(3)
+    b = ucac_mod.Handle([short_g])
+    b.enqueue(4)
+    a.enqueue(3)
+    assert np.array_equal(a.export(0), want)
+    assert a.residuals(0)["status"] >= 0 and b.residuals(0)["status"] >= 0
+    a.close()
+    b.close()
