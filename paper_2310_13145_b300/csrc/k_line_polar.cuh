@@ -447,14 +447,11 @@ __device__ __forceinline__ T hq(const T (&H)[6], int i, int j) {
 
 
 // A pending trial point: evaluated in full at the next trip, then accepted or
-// rejected by the ratio test against the model decrease pred.  The record
-// lives in shared memory, one column per lane (field f of a lane's record at
-// rec[32 f]): the point, the predicted h_k, pred, the step's scale and
-// largest x component, the model's linear and quadratic terms of the step
-// sg (pred = -(lin + quad/2)), h_k at the current point, and whether the
-// step left the box unprojected (then a rejection can shrink it in place).
-enum { TR_V = 0, TR_HT = 5, TR_PRED = 7, TR_SCALE = 8, TR_SMAX = 9, TR_LIN = 10, TR_QUAD = 11, TR_H0 = 12,
-       TR_FREE = 14, TR_N = 15 };
+// rejected by the ratio test against the model decrease pred.  The record is
+// read only on the trial path, so it lives in shared memory, one column per
+// lane (field f of a lane's record at rec[32 f]): the point, the predicted
+// h_k, pred, the step's scale and its largest x component.
+enum { TR_V = 0, TR_HT = 5, TR_PRED = 7, TR_SCALE = 8, TR_SMAX = 9, TR_N = 10 };
 enum { NI_TRIAL = 3, NI_FULL = 4 };
 
 // The common Newton iteration of a lane with no slack held at zero (FP32
@@ -800,14 +797,14 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   counted = 1;
   // model decrease of a step sg: -(gr . sg + 1/2 sg^T H5 sg), where
   // sg^T H5 sg = sx^T H sx + sum_k c (grad g_k . sx + s_sigma_k)^2
-  auto model = [&](const double (&sg)[POL_NV], double &lin, double &quad) -> double {
-    lin = 0.0;
+  auto model = [&](const double (&sg)[POL_NV]) -> double {
+    double lin = 0.0;
 #pragma unroll
     for (int i = 0; i < POL_NV; ++i) lin += gr[i] * sg[i];
     const T s0 = (T)sg[0], s1 = (T)sg[1], s2 = (T)sg[2];
     const T sHs = s0 * (H[0] * s0 + H[1] * s1 + H[2] * s2) + s1 * (H[1] * s0 + H[3] * s1 + H[4] * s2) +
                   s2 * (H[2] * s0 + H[4] * s1 + H[5] * s2);
-    quad = (double)sHs;
+    double quad = (double)sHs;
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const double e = dg[k][0] * sg[0] + dg[k][1] * sg[1] + dg[k][2] * sg[2] + sg[3 + k];
@@ -839,18 +836,14 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   }
   const double scale = le_nn(dn, Delta) ? 1.0 : Delta / dn;
   double vt[POL_NV], sg[POL_NV], smax = 0.0;
-  bool unproj = true;  // no component projected onto its bound
 #pragma unroll
   for (int i = 0; i < POL_NV; ++i) {
-    const double u = v[i] + scale * d[i];
-    vt[i] = pol_clamp(K, i, u);
-    unproj = unproj && __double_as_longlong(vt[i]) == __double_as_longlong(u);
+    vt[i] = pol_clamp(K, i, v[i] + scale * d[i]);
     sg[i] = vt[i] - v[i];
     if (i < 3) smax = fmax(smax, fabs(sg[i]));
   }
   full_grad();
-  double mlin, mquad;
-  const double pred = model(sg, mlin, mquad);
+  const double pred = model(sg);
   // predicted h_k of the trial step; free slacks absorb the remainder of
   // g_k exactly, a slack held at zero gets the correction
   // dx = -sum_k alpha_k grad g_k (Gram system of the held gradients) that
@@ -866,7 +859,7 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
   if (nheld == 0) {
     // the trial point becomes the next trip's evaluation point: every lane
     // of the warp then runs one full evaluation per trip, and the ratio test
-    // follows it (see the trial record)
+    // follows it (a rejection re-evaluates the current point)
 #pragma unroll
     for (int i = 0; i < POL_NV; ++i) trp[32 * (TR_V + i)] = vt[i];
     trp[32 * TR_HT] = ht[0];
@@ -874,11 +867,6 @@ __device__ __forceinline__ int pol_iter(const PolK &K, const PolP &P, double (&v
     trp[32 * TR_PRED] = pred;
     trp[32 * TR_SCALE] = scale;
     trp[32 * TR_SMAX] = smax;
-    trp[32 * TR_LIN] = mlin;
-    trp[32 * TR_QUAD] = mquad;
-    trp[32 * TR_H0] = L.h[0];
-    trp[32 * (TR_H0 + 1)] = L.h[1];
-    trp[32 * TR_FREE] = unproj ? 1.0 : 0.0;
     return NI_TRIAL;
   }
   double at[4], ct, stn;
@@ -1295,37 +1283,11 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
             f = fe;
             if (ared >= 0.75 * pred && trp[32 * TR_SCALE] < 1.0) Delta = 2.0 * Delta;
           } else {
-            // rejected: the radius becomes a quarter of the step
+            // rejected: the evaluation describes the trial point, so the
+            // current point is evaluated again at the next trip
             Delta = 0.25 * smax;
             step_now = false;
-            if (Delta <= 1e-15 * (1.0 + fmax(fmax(fabs(v[0]), fabs(v[1])), fabs(v[2])))) {
-              out = NI_STOP;
-            } else if (trp[32 * TR_FREE] != 0.0) {
-              // The current point's Newton direction does not change with
-              // the radius, so its next step is this one scaled by a
-              // quarter; with no component projected onto a bound that is
-              // the point v + (t - v)/4, still in the box, with the model's
-              // terms scaled by 1/4 and 1/16 and h_k predicted on the same
-              // line.  It becomes the next trial at once, instead of
-              // evaluating the current point again to find the same step.
-              const double lin = 0.25 * trp[32 * TR_LIN], quad = 0.0625 * trp[32 * TR_QUAD];
-#pragma unroll
-              for (int i = 0; i < POL_NV; ++i) {
-                const double t = trp[32 * (TR_V + i)];
-                trp[32 * (TR_V + i)] = fma(0.25, t - v[i], v[i]);
-              }
-#pragma unroll
-              for (int k = 0; k < 2; ++k) {
-                const double h0 = trp[32 * (TR_H0 + k)];
-                trp[32 * (TR_HT + k)] = fma(0.25, trp[32 * (TR_HT + k)] - h0, h0);
-              }
-              trp[32 * TR_PRED] = -(lin + 0.5 * quad);
-              trp[32 * TR_LIN] = lin;
-              trp[32 * TR_QUAD] = quad;
-              trp[32 * TR_SCALE] = 0.25 * trp[32 * TR_SCALE];
-              trp[32 * TR_SMAX] = Delta;
-              trial = true;
-            }
+            if (Delta <= 1e-15 * (1.0 + fmax(fmax(fabs(v[0]), fabs(v[1])), fabs(v[2])))) out = NI_STOP;
           }
         }
       }
