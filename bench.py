@@ -53,10 +53,10 @@ FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one launch of the polar line kernel on the
 # 16 x 2000-bus workload, from the same ncu capture of sweep 31; None for a
 # form or workload not captured
-LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 377.9e6}
+LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 379.1e6}
 # FP64 pipe cycles active over the line kernel's active cycles, from the same
 # capture (sm__pipe_fp64_cycles_active, sweep 31)
-LINE_FP64_BUSY = {"polar": 0.611, "w": 0.876}
+LINE_FP64_BUSY = {"polar": 0.615, "w": 0.876}
 # Algorithmic bytes (FP64 reads + writes each kernel must make) per unit of
 # the streaming x-bar and generator kernels, from their data layout (a row
 # keeps w = z + y/rho beside its next x-step target):
@@ -450,7 +450,7 @@ def main():
                 "note": "FLOP are the FP64 instructions the kernel executes; the common Newton step takes the "
                         "line-limit gradients in FP32 (660.8 FLOP per solve before it, 469.2 after, with 22% less "
                         "time; 419.1 since the common step forms no FP64 bound distances), and the FP64 pipe is "
-                        "busy 61% of the active cycles beside the per-lane solves' dependency and memory waits: "
+                        "busy 62% of the active cycles beside the per-lane solves' dependency and memory waits: "
                         "removing FP64 work the solve does not need lowers this FLOP-based fraction while the "
                         "kernel gets faster" if a.line_form == "polar" else None,
                 "newton_per_sweep": newton, "al_per_sweep": al,
