@@ -198,27 +198,34 @@ DW_HD dw dw_fma(dw x, dw y, dw z) {
 
 // ---------------------------------------------------------- conversions ---
 // FP64 -> double-word on the integer units: h keeps the top 24 significant
-// bits of x (truncation), l the next 24 (truncation), so h + l = x to ~2^-47
-// relative, with l of x's sign and |l| < ulp(h).  A magnitude below 2^-126
-// becomes a signed zero, one at or above 2^128 (infinities, NaN) a NaN; a
-// low part below FP32's normal range is dropped, so the error bound is
-// 2^-47 |x| + 2^-126 (the relative bound holds for |x| >= 2^-78).
+// bits of x (truncation), l the next 24 (truncation), so h + l = x to 2^-47
+// relative, with l of x's sign (or zero) and |l| < ulp(h).  A magnitude
+// below 2^-126 becomes a signed zero, one at or above 2^128 (infinities, NaN)
+// a NaN; the low part is kept, as a subnormal float where it falls below
+// FP32's normal range, while |x| >= 2^-102 and dropped below that, so the
+// error bound is 2^-47 |x| + 2^-126 (the relative bound alone holds for
+// |x| >= 2^-102).
 DW_HD dw dw_from_d(double x) {
   const uint64_t b = dw_dbits(x);
   const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
   const uint32_t e = (bh >> 20) & 0x7ffu, sg = bh & 0x80000000u;
-  const uint32_t fh = sg | (((e - 896u) << 23) + (((bh & 0xfffffu) << 3) | (bl >> 29)));
+  // the 32 bits from bit 29 up hold e's low 9 bits above the 23 fraction
+  // bits h keeps; adding 2^30 = 2^32 - (896 << 23) modulo 2^32 rebiases the
+  // exponent, which is exact in those 9 bits (and leaves bit 31 clear) for
+  // 897 <= e <= 1150
+  const uint32_t hx = (uint32_t)(b >> 29) + 0x40000000u;
   const bool small = e <= 896u, big = e >= 1151u;
-  const float h = dw_bitsf(small ? sg : (big ? (sg | 0x7fc00000u) : fh));
-  // the 29 bits below h's, R = bl & (2^29 - 1), are worth R 2^(e - 1075):
-  // with n leading zeros in R its leading one sits at bit 31 - n, so the
-  // float's biased exponent is e - 917 - n and its fraction the 23 bits
-  // after that one
-  const uint32_t R = bl & 0x1fffffffu;
-  const int n = R != 0u ? dw_clz(R) : 31;
-  const int E = (int)e - 917 - n;
-  const uint32_t m = ((R << n) << 1) >> 9;
-  const float l = dw_bitsf((R == 0u || small || big || E <= 0) ? sg : (sg | ((uint32_t)E << 23) | m));
+  const float h = dw_bitsf(small ? sg : (big ? (sg | 0x7fc00000u) : (sg | hx)));
+  // l: the 24 bits below h's, R = bits 28..5 of bl, are worth R 2^(e - 1070).
+  // A float of x's sign with exponent field e - 920 and R's low 23 bits as
+  // fraction is worth 2^(e - 1047) + (R mod 2^23) 2^(e - 1070); where R's top
+  // bit is clear, subtracting the float 2^(e - 1047) of the same sign leaves
+  // R 2^(e - 1070) exactly (both share one exponent), and where it is set
+  // that 2^(e - 1047) is R's own top bit
+  const uint32_t eb = (sg | (hx & 0x7f800000u)) - (24u << 23);
+  const uint32_t fl = eb | ((bl >> 5) & 0x7fffffu);
+  const float l0 = dw_fsub(dw_bitsf(fl), dw_bitsf((bl & 0x10000000u) != 0u ? 0u : eb));
+  const float l = (uint32_t)(e - 921u) <= 229u ? l0 : dw_bitsf(sg);
   return dw{h, l};
 }
 // float -> FP64 exactly on the integer units (a subnormal float becomes a
@@ -233,7 +240,8 @@ DW_HD double dw_f2d(float x) {
   return dw_bitsd(r);
 }
 // double-word -> FP64: h + l is exact in FP64 (at most 49 significant bits
-// for a normalised pair), so one FP64 addition of the widened parts
+// for a normalised pair), so one FP64 addition of the widened parts (a
+// subnormal low part is dropped by dw_f2d: an error below 2^-126)
 DW_HD double dw_to_d(dw x) {
 #if defined(__CUDA_ARCH__)
   return __dadd_rn(dw_f2d(x.h), dw_f2d(x.l));
@@ -245,7 +253,8 @@ DW_HD double dw_to_d(dw x) {
 // The operations above applied to FP64 inputs (each converted by
 // dw_from_d), for the tests that compare the device arithmetic with the
 // host's bit for bit: out[0..3] receive the result's parts as doubles.
-//   0: x -> (h, l, dw_to_d, 0)   1: x + y   2: x - y   3: x + (float)y
+//   0: x -> (h, l, dw_to_d, the bit pattern of l as an integer)
+//   1: x + y   2: x - y   3: x + (float)y
 //   4: x * y   5: x * (float)y   6: x^2   7: x * y + z
 DW_HD void dw_probe_op(int op, double x, double y, double z, double *out) {
   const dw a = dw_from_d(x), b = dw_from_d(y), cc = dw_from_d(z);
@@ -254,7 +263,7 @@ DW_HD void dw_probe_op(int op, double x, double y, double z, double *out) {
   out[2] = 0.0;
   out[3] = 0.0;
   switch (op) {
-    case 0: r = a; out[2] = dw_to_d(a); break;
+    case 0: r = a; out[2] = dw_to_d(a); out[3] = (double)dw_fbits(a.l); break;
     case 1: r = dw_add(a, b); break;
     case 2: r = dw_sub(a, b); break;
     case 3: r = dw_add_f(a, fy); break;

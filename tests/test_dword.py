@@ -57,7 +57,8 @@ def test_from_d_split(host):
     x = np.concatenate([sample(20000, 1, -30, 30), [1.0, -1.0, 2.0 ** -126, 3.0, np.pi, 1.0 + 2.0 ** -30,
                                                     1.0 + 2.0 ** -52, np.nextafter(2.0, 0.0), 0.1]])
     o = run_ops(host, 0, x)
-    h, l, back = o[:, 0], o[:, 1], o[:, 2]
+    h, back = o[:, 0], o[:, 2]
+    l = o[:, 3].astype(np.uint32).view(np.float32).astype(np.float64)  # exact, subnormals included
     # h is x truncated to 24 significant bits: same sign, |h| <= |x| < |h| + ulp(h)
     ulp_h = np.abs(h) * 2.0 ** -23
     assert np.all(np.sign(h) == np.sign(x))
@@ -68,9 +69,23 @@ def test_from_d_split(host):
     # together ~48 bits: |x - (h + l)| < 2^-47 |x| (+ 2^-126 where the low
     # part would be subnormal), and h + l is exact in FP64
     assert np.all(np.abs(x - (h + l)) <= 2.0 ** -47 * np.abs(x) + 2.0 ** -126)
-    big = np.abs(x) >= 2.0 ** -78
+    big = np.abs(x) >= 2.0 ** -102
     assert np.all(np.abs(x - (h + l))[big] <= 2.0 ** -47 * np.abs(x[big]))
-    assert np.array_equal(back, h + l)
+    assert np.array_equal(back, h + np.where(np.abs(l) < 2.0 ** -126, 0.0, l))
+    # near the bottom of the range the low part becomes a subnormal float,
+    # still exact: the window of 24 bits below h's is kept down to 2^-102
+    t = np.ldexp(1.0 + np.random.default_rng(4).integers(1, 2 ** 52, 400) * 2.0 ** -52,
+                 np.repeat(np.arange(-110, -90), 20))
+    ot = run_ops(host, 0, t)
+    lo = ot[:, 3].astype(np.uint32).view(np.float32).astype(np.float64)  # l from its bit pattern
+    keep = np.abs(t) >= 2.0 ** -102
+    ex = np.floor(np.log2(np.abs(t))).astype(int)
+    r = t - ot[:, 0]                                               # exact: the bits below h
+    w = np.ldexp(np.trunc(np.ldexp(r, 47 - ex)), ex - 47)          # truncated to the 24-bit window
+    assert np.array_equal(lo[keep], w[keep])
+    assert np.any(np.abs(lo[keep]) < 2.0 ** -126) and np.all(lo[~keep] == 0)
+    # dw_f2d (and so dw_to_d) drops a subnormal low part: an error below 2^-126
+    assert np.all(ot[:, 1] == np.where(np.abs(lo) < 2.0 ** -126, 0.0, lo))
     # values with at most 48 significant bits round-trip exactly
     y = np.ldexp(np.random.default_rng(3).integers(2 ** 47, 2 ** 48, 1000).astype(np.float64), -40)
     oy = run_ops(host, 0, y)
