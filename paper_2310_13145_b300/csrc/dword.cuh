@@ -229,15 +229,16 @@ DW_HD dw dw_from_d(double x) {
   return dw{h, l};
 }
 // float -> FP64 exactly on the integer units (a subnormal float becomes a
-// signed zero; infinities and NaN keep their kind)
+// signed zero; infinities and NaN keep their kind).  With the sign cleared,
+// a >> 3 holds the exponent field in bits 27..20 above the top 20 fraction
+// bits, so one addition of 896 << 20 rebiases it (1792 << 20 takes the
+// field 255 of infinities and NaN to 2047)
 DW_HD double dw_f2d(float x) {
   const uint32_t u = dw_fbits(x);
-  const uint32_t e = (u >> 23) & 0xffu, sg = u & 0x80000000u;
-  const uint32_t ee = e == 255u ? 2047u : e + 896u;
-  const uint32_t hi = sg | (ee << 20) | ((u & 0x7fffffu) >> 3);
-  const uint32_t lo = u << 29;
-  const uint64_t r = e != 0u ? (((uint64_t)hi << 32) | lo) : ((uint64_t)sg << 32);
-  return dw_bitsd(r);
+  const uint32_t a = u & 0x7fffffffu, sg = u & 0x80000000u;
+  const uint32_t hi = sg | ((a >> 3) + (a >= 0x7f800000u ? (1792u << 20) : (896u << 20)));
+  const bool z = a < 0x00800000u;
+  return dw_bitsd(((uint64_t)(z ? sg : hi) << 32) | (z ? 0u : (u << 29)));
 }
 // double-word -> FP64: h + l is exact in FP64 (at most 49 significant bits
 // for a normalised pair), so one FP64 addition of the widened parts (a

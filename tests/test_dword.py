@@ -149,3 +149,16 @@ def test_ops_with_float(host, name, op):
         exact, scale = (a + b, abs(a) + abs(b)) if name == "add_f" else (a * b, abs(a * b))
         got = dwval(o[i, 0], o[i, 1])
         assert abs(got - exact) <= Fraction(8.0 * U2) * scale, (name, i)
+
+
+def test_f2d_widens_floats_exactly(host):
+    # every float exponent field 1..254 with random fractions and both signs:
+    # x is a float, so h = x, l = 0, and the integer widening dw_f2d gives x
+    rng = np.random.default_rng(31)
+    bits = (rng.integers(0, 2, 254 * 40, dtype=np.uint32) << 31) | \
+        (np.repeat(np.arange(1, 255, dtype=np.uint32), 40) << 23) | rng.integers(0, 2 ** 23, 254 * 40, dtype=np.uint32)
+    x = bits.view(np.float32).astype(np.float64)
+    o = run_ops(host, 0, x)
+    ok = np.abs(x) >= 2.0 ** -126
+    assert np.array_equal(o[ok, 0], x[ok]) and np.all(o[:, 1] == 0.0) and np.array_equal(o[:, 2], x)
+    assert np.array_equal(np.signbit(o[:, 0]), np.signbit(x))
