@@ -218,18 +218,22 @@ __device__ __forceinline__ long long abs_bits(double x) { return __double_as_lon
 // a NaN above it (infinities and NaNs included).  f2d_exact widens a normal
 // float exactly; a subnormal float becomes a signed zero.
 __device__ __forceinline__ float d2f_trunc(double x) {
+  // the 32 bits from bit 29 up hold the exponent's low 9 bits above the top
+  // 23 fraction bits; adding 2^30 = 2^32 - (896 << 23) modulo 2^32 rebiases
+  // the exponent, exactly for biased exponents 897..1150 (the range tests
+  // compare the magnitude's high word)
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
-  const unsigned e = (hi >> 20) & 0x7ffu, sg = hi & 0x80000000u;
-  const unsigned f = sg | (((e - 896u) << 23) + (((hi & 0xfffffu) << 3) | (lo >> 29)));
-  return __uint_as_float(e <= 896u ? sg : (e < 1151u ? f : (sg | 0x7fc00000u)));
+  const unsigned hi = (unsigned)(b >> 32), a = hi & 0x7fffffffu, sg = hi & 0x80000000u;
+  const unsigned f = sg | ((unsigned)(b >> 29) + 0x40000000u);
+  return __uint_as_float(a < 0x38100000u ? sg : (a < 0x47f00000u ? f : (sg | 0x7fc00000u)));
 }
 __device__ __forceinline__ double f2d_exact(float x) {
+  // a >> 3 holds the exponent field above the top 20 fraction bits: one
+  // addition of 896 << 20 rebiases it
   const unsigned u = __float_as_uint(x);
-  const unsigned e = (u >> 23) & 0xffu, sg = u & 0x80000000u;
-  const unsigned hi = sg | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
-  const unsigned lo = u << 29;
-  return __hiloint2double((int)(e != 0u ? hi : sg), (int)(e != 0u ? lo : 0u));
+  const unsigned a = u & 0x7fffffffu, sg = u & 0x80000000u;
+  const bool z = a < 0x00800000u;
+  return __hiloint2double((int)(z ? sg : (sg | ((a >> 3) + (896u << 20)))), (int)(z ? 0u : (u << 29)));
 }
 
 

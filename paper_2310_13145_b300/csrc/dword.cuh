@@ -208,13 +208,13 @@ DW_HD dw dw_fma(dw x, dw y, dw z) {
 DW_HD dw dw_from_d(double x) {
   const uint64_t b = dw_dbits(x);
   const uint32_t bh = (uint32_t)(b >> 32), bl = (uint32_t)b;
-  const uint32_t e = (bh >> 20) & 0x7ffu, sg = bh & 0x80000000u;
+  const uint32_t a = bh & 0x7fffffffu, sg = bh & 0x80000000u;  // (the range tests compare a: e = a >> 20)
   // the 32 bits from bit 29 up hold e's low 9 bits above the 23 fraction
   // bits h keeps; adding 2^30 = 2^32 - (896 << 23) modulo 2^32 rebiases the
   // exponent, which is exact in those 9 bits (and leaves bit 31 clear) for
   // 897 <= e <= 1150
   const uint32_t hx = (uint32_t)(b >> 29) + 0x40000000u;
-  const bool small = e <= 896u, big = e >= 1151u;
+  const bool small = a < 0x38100000u, big = a >= 0x47f00000u;  // e <= 896, e >= 1151
   const float h = dw_bitsf(small ? sg : (big ? (sg | 0x7fc00000u) : (sg | hx)));
   // l: the 24 bits below h's, R = bits 28..5 of bl, are worth R 2^(e - 1070).
   // A float of x's sign with exponent field e - 920 and R's low 23 bits as
@@ -225,7 +225,7 @@ DW_HD dw dw_from_d(double x) {
   const uint32_t eb = (sg | (hx & 0x7f800000u)) - (24u << 23);
   const uint32_t fl = eb | ((bl >> 5) & 0x7fffffu);
   const float l0 = dw_fsub(dw_bitsf(fl), dw_bitsf((bl & 0x10000000u) != 0u ? 0u : eb));
-  const float l = (uint32_t)(e - 921u) <= 229u ? l0 : dw_bitsf(sg);
+  const float l = a - 0x39900000u < 0x0e600000u ? l0 : dw_bitsf(sg);  // 921 <= e <= 1150
   return dw{h, l};
 }
 // float -> FP64 exactly on the integer units (a subnormal float becomes a
