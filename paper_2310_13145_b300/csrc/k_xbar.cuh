@@ -134,10 +134,13 @@ __device__ __forceinline__ void row_dw(double *Y, double *Z, double *Tg, double 
   const dw cz = dw_add(c, z);
   const dw yn = dw_fma(F.rho, cz, y);
   Q.sp = dw_fma(cz, cz, Q.sp);
-  // (b - b_old = 0 leaves Q.sd unchanged: rows whose square the caller adds
-  // once pass their own b as b_old)
-  const dw db = sd ? dw_sub(b, bold) : dw_make(0.0f);
-  Q.sd = dw_fma(db, db, Q.sd);
+  // (rows whose square the caller adds once, the w and theta rows of the
+  // line ends, pass sd = false: warp-uniform there, it skips the 26
+  // operations of a zero square, which would leave Q.sd unchanged)
+  if (sd) {
+    const dw db = dw_sub(b, bold);
+    Q.sd = dw_fma(db, db, Q.sd);
+  }
   Q.sz = dw_fma(z, z, Q.sz);
   qacc_inf(Q, c);
   const double zd = dw_to_d(z), yd = dw_to_d(yn);
