@@ -123,6 +123,8 @@ __device__ __forceinline__ void pol_angle_terms(T ga0, T ka0, T ga2, T ka2, T c,
 }
 
 struct PolP {
+  // row targets: t_0..t_5, then the angle rows' difference t_6 - t_7 and
+  // mean (t_6 + t_7) / 2 (each formed once per solve)
   double tg[8];
   double rpq, rva;
   float frpq, frva;  // FP32 copies for the Hessian
@@ -211,7 +213,7 @@ __device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, double (
     const double e = a[r] - P.tg[r];
     spe = fma(P.rpq * e, e, spe);
   }
-  const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
+  const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - P.tg[6];
   double f = 0.5 * spe + 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
@@ -270,7 +272,7 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
     L.da[r][1] = r < 2 ? fVi * fE[r] : 2.0f * K.fq(r) * fVj + fVi * fE[r];
     L.da[r][2] = fP * fEd[r];
   }
-  const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - (P.tg[6] - P.tg[7]);
+  const double ewi = Vi2 - P.tg[4], ewj = Vj2 - P.tg[5], et = d - P.tg[6];
   double mhk[2];
   bool lim = false;
 #pragma unroll
@@ -396,7 +398,7 @@ __device__ __forceinline__ double pol_f(const PolP &P, const PolLast &L) {
     spe = fma(P.rpq * e, e, spe);
   }
   const double ewi = L.v[0] * L.v[0] - P.tg[4], ewj = L.v[1] * L.v[1] - P.tg[5];
-  const double et = L.v[2] - (P.tg[6] - P.tg[7]);
+  const double et = L.v[2] - P.tg[6];
   double f = 0.5 * spe + 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
 #pragma unroll
   for (int k = 0; k < 2; ++k) f += L.h[k] * (P.mu[k] + 0.5 * P.c * L.h[k]);
@@ -955,11 +957,12 @@ __device__ __forceinline__ void pol_start(const Dev &S, long long it, double (&v
 // warp POL_QF records in dynamic shared memory, laid out for all warps of
 // the block as doubles [warp][12][QF], floats [warp][15][QF], ints
 // [warp][3][QF]; the record fields:
-//   doubles 0-3 flows a_r, 4 cos, 5 sin, 6 V_i, 7 V_j, 8 d, 9 step in d, 10-11 t_6, t_7
+//   doubles 0-3 flows a_r, 4 cos, 5 sin, 6 V_i, 7 V_j, 8 d, 9 step in d,
+//     10 the angle targets' mean (t_6 + t_7) / 2, 11 1 / c
 //   floats 0-11 grad a_r (FP32, r * 3 + i), 12-14 the step in x (FP32)
 //   ints 0 item, 1-2 slots of the from / to end
 constexpr int POL_QF = 64;
-constexpr int POL_FD = 13, POL_FF = 15, POL_FI = 3;
+constexpr int POL_FD = 12, POL_FF = 15, POL_FI = 3;
 __host__ __device__ constexpr size_t pol_dyn_smem(int bs) {
   return (size_t)(bs / 32) * POL_QF * (POL_FD * sizeof(double) + POL_FF * sizeof(float) + POL_FI * sizeof(int));
 }
@@ -997,13 +1000,13 @@ __device__ __forceinline__ void pol_finish_out(const Dev &S, const double *fd, c
   const double c0 = fd[4 * POL_QF + sl], s0 = fd[5 * POL_QF + sl], dx2 = fd[9 * POL_QF + sl];
   const double c = c0 - s0 * dx2, sn = s0 + c0 * dx2;
   const double Vi = fd[6 * POL_QF + sl], Vj = fd[7 * POL_QF + sl], d = fd[8 * POL_QF + sl];
-  const double Pv = Vi * Vj, tm = 0.5 * (fd[10 * POL_QF + sl] + fd[11 * POL_QF + sl]);
+  const double Pv = Vi * Vj, tm = fd[10 * POL_QF + sl];
   const double v6[6] = {Vi * Vi, Vj * Vj, Pv * c, Pv * sn, tm + 0.5 * d, tm - 0.5 * d};
 #pragma unroll
   for (int i = 0; i < 6; ++i) S.B[(FB_V0 + i) * NBP + bp] = v6[i];
   S.LV[bp] = Vi;
   S.LV[NBP + bp] = Vj;
-  S.LV[2 * NBP + bp] = fd[12 * POL_QF + sl];
+  S.LV[2 * NBP + bp] = fd[11 * POL_QF + sl];
 #pragma unroll
   for (int r = 0; r < 4; ++r) S.EA[erow_u(r) * NEP + (erow_end(r) ? let : lef)] = a[r];
   S.EA[2 * NEP + lef] = v6[0];
@@ -1212,6 +1215,11 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
           if (!chk_(S, lef >= 0 && lef < NEP && let >= 0 && let < NEP, 4)) lef = let = 0;
 #pragma unroll
           for (int r8 = 0; r8 < 8; ++r8) P.tg[r8] = S.ET[erow_u(r8) * NEP + (erow_end(r8) ? let : lef)];
+          {
+            const double t6 = P.tg[6], t7 = P.tg[7];
+            P.tg[6] = t6 - t7;
+            P.tg[7] = 0.5 * (t6 + t7);
+          }
           P.rpq = I.rpq;
           P.rva = I.rva;
           P.frpq = I.frpq;
@@ -1382,9 +1390,8 @@ __global__ void __launch_bounds__(BS) k_line_polar(Dev S) {
               frd[7 * POL_QF + sl] = v[1];
               frd[8 * POL_QF + sl] = v[2];
               frd[9 * POL_QF + sl] = dxs;
-              frd[10 * POL_QF + sl] = P.tg[6];
-              frd[11 * POL_QF + sl] = P.tg[7];
-              frd[12 * POL_QF + sl] = P.ic;
+              frd[10 * POL_QF + sl] = P.tg[7];
+              frd[11 * POL_QF + sl] = P.ic;
 #pragma unroll
               for (int r = 0; r < 4; ++r)
 #pragma unroll
