@@ -22,9 +22,10 @@
 #include "dword.cuh"
 
 // resident blocks of 128 threads per SM requested for the bus kernel (its
-// register cap: 5 gives 96 registers, the fastest of 5, 6 and 8 measured)
+// register cap: 6 gives 80 registers, the fastest of 4, 5 and 6 measured
+// with the current double-word conversions; 76 bytes of spills)
 #ifndef UCAC_BUS_MINB
-#define UCAC_BUS_MINB 5
+#define UCAC_BUS_MINB 6
 #endif
 
 namespace ucac {
