@@ -171,6 +171,16 @@ __device__ __forceinline__ double pol_clamp(const PolK &K, int i, double x) {
   return __double_as_longlong(x) > 0 ? x : 0.0;
 }
 
+// 2 x and x / 2 of a positive normal double (V_i, V_j: the voltage bounds
+// are validated positive; rho_va) by one integer addition on the exponent
+// field of its high word, off the FP64 pipe (exact)
+__device__ __forceinline__ double twice_pos(double x) {
+  return __hiloint2double(__double2hiint(x) + (1 << 20), __double2loint(x));
+}
+__device__ __forceinline__ double half_pos(double x) {
+  return __hiloint2double(__double2hiint(x) - (1 << 20), __double2loint(x));
+}
+
 // cos d and sin d for |d| <= pi: d = k/256 + r with |r| <= 1/512 (+ 1e-6)
 // (r exact), cos(k/256) and sin(k/256) from the table, cos r and sin r from
 // their Taylor series to r^4 and r^3 (truncation below 2.5e-16 and 8e-20),
@@ -254,7 +264,7 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
   const double Pv = Vi * Vj, Vi2 = Vi * Vi, Vj2 = Vj * Vj;
   // (the FP32 copies are truncated on the integer units: d2f_trunc)
   const float fVi = d2f_trunc(Vi), fVj = d2f_trunc(Vj), fP = fVi * fVj;
-  const double Vi2x = 2.0 * Vi, Vj2x = 2.0 * Vj;
+  const double Vi2x = twice_pos(Vi), Vj2x = twice_pos(Vj);
   double E[4], Ed[4], pe[4];
   float fE[4], fEd[4];
   // FP32 gradient of the flow (for the FP32 Hessian and the first-order
@@ -312,7 +322,7 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
     // (2 V_i Sq0 + 2 rho_va (V_i^2 - t_4) V_i as 2 V_i (Sq0 + rho_va (V_i^2 - t_4)))
     gx[0] = fma(Vi2x, fma(P.rva, ewi, Sq0), Vj * SE);
     gx[1] = fma(Vj2x, fma(P.rva, ewj, Sq1), Vi * SE);
-    gx[2] = fma(Pv, SEd, (0.5 * P.rva) * et);
+    gx[2] = fma(Pv, SEd, half_pos(P.rva) * et);
   }
   // (UCAC_POL_FP64_NEWTON = 1 builds the all-FP64 Hessian and Newton system
   // on every lane, the same model: the A/B reference of the precision split)
