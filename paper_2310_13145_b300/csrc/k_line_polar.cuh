@@ -227,7 +227,7 @@ __device__ __forceinline__ double pol_obj(const PolK &K, const PolP &P, double (
   double f = 0.5 * spe + 0.5 * P.rva * (ewi * ewi + ewj * ewj) + 0.25 * P.rva * et * et;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    const double g = a[2 * k] * a[2 * k] + a[2 * k + 1] * a[2 * k + 1] - K.rate2;
+    const double g = fma(a[2 * k], a[2 * k], fma(a[2 * k + 1], a[2 * k + 1], -K.rate2));
     if ((free_mask >> k) & 1) v[3 + k] = fmax(ht[k] - g, 0.0);
     const double h = g + v[3 + k];
     f += h * (P.mu[k] + 0.5 * P.c * h);
@@ -288,7 +288,8 @@ __device__ __forceinline__ void pol_full(const PolK &K, const PolP &P, double (&
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     const int r0 = 2 * k, r1 = 2 * k + 1;
-    const double g = L.a[r0] * L.a[r0] + L.a[r1] * L.a[r1] - K.rate2;
+    // (two FMAs: the square of the end's q-row flow enters with -rate^2)
+    const double g = fma(L.a[r0], L.a[r0], fma(L.a[r1], L.a[r1], -K.rate2));
     if ((free_mask >> k) & 1) {  // second-order correction of a trial point (see pol_obj)
       v[3 + k] = fmax(ht[k] - g, 0.0);
       L.v[3 + k] = v[3 + k];
