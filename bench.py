@@ -42,13 +42,13 @@ UNIT = "sweeps/s"
 # processes), counted by the hardware: (DADD + DMUL + 2 DFMA) thread
 # instructions of one launch (ncu smsp__sass_thread_inst_executed_op_d*_pred_on)
 # divided by the launch's line-period solves.  16 x 2000-bus scenarios:
-# 512.6 M FLOP over 1,228,800 solves at sweep 31 (417.2 per solve; 184 per
+# 501.6 M FLOP over 1,228,800 solves at sweep 31 (408.2 per solve; 180 per
 # counted Newton iteration); the work per solve hardly moves over a run
 # (472.0 per solve at sweep 701 against 469.2 at sweep 31 in an earlier
 # capture), while the Newton count does.  The W-form kernel: 10,340.8 M
 # FLOP at sweep 31 (8,415 per solve).  The captures and their commands are
 # summarised under profiles/.
-LINE_FLOP_PER_SOLVE = {"polar": 417.2, "w": 8415.3}
+LINE_FLOP_PER_SOLVE = {"polar": 408.2, "w": 8415.3}
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) of one launch of the polar line kernel on the
 # 16 x 2000-bus workload, from the same ncu capture of sweep 31; None for a
@@ -56,7 +56,7 @@ FP64_NOMINAL_TFLOPS = 1.25
 LINE_TRAFFIC = {("polar", "c5_2000bus_T24x16"): 377.8e6}
 # FP64 pipe cycles active over the line kernel's active cycles, from the same
 # capture (sm__pipe_fp64_cycles_active, sweep 31)
-LINE_FP64_BUSY = {"polar": 0.620, "w": 0.876}
+LINE_FP64_BUSY = {"polar": 0.602, "w": 0.876}
 # Algorithmic bytes (FP64 reads + writes each kernel must make) per unit of
 # the streaming x-bar and generator kernels, from their data layout (a row
 # keeps w = z + y/rho beside its next x-step target):
@@ -449,8 +449,9 @@ def main():
                 "fp64_pipe_busy": LINE_FP64_BUSY.get(a.line_form),
                 "note": "FLOP are the FP64 instructions the kernel executes; the common Newton step takes the "
                         "line-limit gradients in FP32 (660.8 FLOP per solve before it, 469.2 after, with 22% less "
-                        "time; 417.2 since the common step forms no FP64 bound distances), and the FP64 pipe is "
-                        "busy 62% of the active cycles beside the per-lane solves' dependency and memory waits: "
+                        "time; 408.2 since the common step forms no FP64 bound distances and the evaluation doubles on "
+                        "the integer units), and the FP64 pipe is "
+                        "busy 60% of the active cycles beside the per-lane solves' dependency and memory waits: "
                         "removing FP64 work the solve does not need lowers this FLOP-based fraction while the "
                         "kernel gets faster" if a.line_form == "polar" else None,
                 "newton_per_sweep": newton, "al_per_sweep": al,
