@@ -15,7 +15,8 @@
 // box-constrained minimiser of that cell's quadratic, so the candidate whose
 // point lies in its own cell (least violation, to absorb rounding) is the
 // answer.  The piece of the previous iterate is tried first (near convergence
-// it is the answer, so one piece is solved instead of nine).  Pure FP64
+// it is the answer, so one piece is solved instead of nine), then its
+// neighbours, up to the first whose candidate lies in its own cell.  Pure FP64
 // register arithmetic, one thread per gen-period.
 #pragma once
 #include "common.cuh"
@@ -123,10 +124,16 @@ __device__ __forceinline__ GenOut gen_solve(double c2p, double c1p, double rho, 
   const int i0 = regime_of(p_prev, t_pl, t_pu), j0 = regime_of(p_prev - ph_prev, t_rd, t_ru);
   double best = piece(i0, j0, p, ph);
   if (best > tol) {
+    // the other eight, the previous piece's neighbours first (offsets
+    // modulo 3: one regime over in d, then in p, then both); a piece whose
+    // candidate lies in its own cell within tol is the minimiser, as for the
+    // first one, so the search stops there (else the least violation wins)
 #pragma unroll 1
-    for (int q = 0; q < 9; ++q) {
-      const int i = q / 3, j = q - 3 * (q / 3);
-      if (i == i0 && j == j0) continue;
+    for (int q = 1; q < 9; ++q) {
+      const int oi = q < 3 ? 0 : (q < 5 ? q - 2 : (q - 5) / 2 + 1), oj = q < 3 ? q : (q < 5 ? 0 : (q - 5) % 2 + 1);
+      int i = i0 + oi, j = j0 + oj;
+      i = i >= 3 ? i - 3 : i;
+      j = j >= 3 ? j - 3 : j;
       double pc, phc;
       const double viol = piece(i, j, pc, phc);
       if (viol < best) {
@@ -134,6 +141,7 @@ __device__ __forceinline__ GenOut gen_solve(double c2p, double c1p, double rho, 
         p = pc;
         ph = phc;
       }
+      if (best <= tol) break;
     }
   }
   o.p = p;
