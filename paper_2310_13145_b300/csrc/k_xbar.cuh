@@ -22,8 +22,8 @@
 #include "dword.cuh"
 
 // resident blocks of 128 threads per SM requested for the bus kernel (its
-// register cap: 6 gives 80 registers, the fastest of 4, 5 and 6 measured
-// with the current double-word conversions; 76 bytes of spills)
+// register cap: 6 gives 80 registers, the fastest of 4 to 8 measured with
+// the current double-word conversions; 76 bytes of spills)
 #ifndef UCAC_BUS_MINB
 #define UCAC_BUS_MINB 6
 #endif
