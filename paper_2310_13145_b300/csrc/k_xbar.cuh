@@ -27,6 +27,13 @@
 #ifndef UCAC_BUS_MINB
 #define UCAC_BUS_MINB 6
 #endif
+// resident blocks of 256 threads per SM requested for the UC box-QP kernel
+// (its register cap: 3 gives 80 registers and 24 warps per SM, 168 bytes
+// of spills, the fastest of 2, 3 and 4 measured: 0.119 -> 0.113 ms against
+// the uncapped 124 registers)
+#ifndef UCAC_UCBAR_MINB
+#define UCAC_UCBAR_MINB 3
+#endif
 
 namespace ucac {
 
@@ -486,7 +493,7 @@ __device__ __forceinline__ void boxqp3(int n, const double (&H)[3][3], const dou
 }
 
 template <int BS>
-__global__ void __launch_bounds__(BS) k_ucbar(Dev S) {
+__global__ void __launch_bounds__(BS, (UCAC_UCBAR_MINB * 256) / BS) k_ucbar(Dev S) {
   const int gr = warp_granule<BS>(S.g_gp.n);
   if (gr < 0) return;
   const int k = S.g_gp.inst[gr];
